@@ -1,0 +1,208 @@
+"""CPU oracle for the spliced protein-to-genome DP (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never touches it.
+
+The arithmetic lives in ``oracle.c`` (plain C, int32, full matrices): Eq. 7 of
+Li 2022 ("DP for protein-to-genome alignment") in local mode with the final
+splice model of the "Splice models" section.  This module only marshals
+arguments through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+
+AA = "ARNDCQEGHILKMFPSTWYV*X"
+OP_NAMES = "MIDFGNUV"
+
+# BLOSUM62 (Henikoff & Henikoff 1992), rows/cols in the order of AA[:20].
+_BLOSUM62_ROWS = """
+ 4 -1 -2 -2  0 -1 -1  0 -2 -1 -1 -1 -1 -2 -1  1  0 -3 -2  0
+-1  5  0 -2 -3  1  0 -2  0 -3 -2  2 -1 -3 -2 -1 -1 -3 -2 -3
+-2  0  6  1 -3  0  0  0  1 -3 -3  0 -2 -3 -2  1  0 -4 -2 -3
+-2 -2  1  6 -3  0  2 -1 -1 -3 -4 -1 -3 -3 -1  0 -1 -4 -3 -3
+ 0 -3 -3 -3  9 -3 -4 -3 -3 -1 -1 -3 -1 -2 -3 -1 -1 -2 -2 -1
+-1  1  0  0 -3  5  2 -2  0 -3 -2  1  0 -3 -1  0 -1 -2 -1 -2
+-1  0  0  2 -4  2  5 -2  0 -3 -3  1 -2 -3 -1  0 -1 -3 -2 -2
+ 0 -2  0 -1 -3 -2 -2  6 -2 -4 -4 -2 -3 -3 -2  0 -2 -2 -3 -3
+-2  0  1 -1 -3  0  0 -2  8 -3 -3 -1 -2 -1 -2 -1 -2 -2  2 -3
+-1 -3 -3 -3 -1 -3 -3 -4 -3  4  2 -3  1  0 -3 -2 -1 -3 -1  3
+-1 -2 -3 -4 -1 -2 -3 -4 -3  2  4 -2  2  0 -3 -2 -1 -2 -1  1
+-1  2  0 -1 -3  1  1 -2 -1 -3 -2  5 -1 -3 -1  0 -1 -3 -2 -2
+-1 -1 -2 -3 -1  0 -2 -3 -2  1  2 -1  5  0 -2 -1 -1 -1 -1  1
+-2 -3 -3 -3 -2 -3 -3 -3 -1  0  0 -3  0  6 -4 -2 -2  1  3 -1
+-1 -2 -2 -1 -3 -1 -1 -2 -2 -3 -3 -1 -2 -4  7 -1 -1 -4 -3 -2
+ 1 -1  1  0 -1  0  0  0 -1 -2 -2  0 -1 -2 -1  4  1 -3 -2 -2
+ 0 -1  0 -1 -1 -1 -1 -2 -2 -1 -1 -1 -1 -2 -1  1  5 -2 -2  0
+-3 -3 -4 -4 -2 -2 -3 -2 -2 -3 -2 -3 -1  1 -4 -3 -2 11  2 -3
+-2 -2 -2 -3 -2 -1 -2 -3  2 -1 -1 -2 -1  3 -3 -2 -2  2  7 -1
+ 0 -3 -3 -3 -1 -2 -2 -3 -3  3  1 -2  1 -1 -2 -2  0 -3 -1  4
+"""
+
+
+def blosum62_22() -> np.ndarray:
+    """22x22 int matrix in AA order: BLOSUM62 for the 20 amino acids,
+    -4 against a protein '*' (BLOSUM62's stop column), -1 against X."""
+    m = np.full((22, 22), -1, dtype=np.int32)
+    rows = [list(map(int, r.split())) for r in _BLOSUM62_ROWS.strip().splitlines()]
+    m[:20, :20] = np.array(rows, dtype=np.int32)
+    m[:20, 20] = -4
+    m[20, :20] = -4
+    m[20, 20] = 1
+    return m
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("e", ctypes.c_int32), ("f", ctypes.c_int32),
+                ("r", ctypes.c_int32), ("stop", ctypes.c_int32),
+                ("mat", (ctypes.c_int32 * 22) * 22)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("prot_st", ctypes.c_int32), ("prot_en", ctypes.c_int32),
+                ("nt_st", ctypes.c_int32), ("nt_en", ctypes.c_int32),
+                ("n_cigar", ctypes.c_int32)]
+
+
+# Default penalties (the paper prints none; see the design notes).
+DEFAULTS = dict(q=11, e=1, f=23, r=29, stop=23)
+
+
+def make_params(q=None, e=None, f=None, r=None, stop=None, mat=None) -> Params:
+    p = Params()
+    d = dict(DEFAULTS)
+    for k, v in (("q", q), ("e", e), ("f", f), ("r", r), ("stop", stop)):
+        if v is not None:
+            d[k] = v
+    p.q, p.e, p.f, p.r, p.stop = d["q"], d["e"], d["f"], d["r"], d["stop"]
+    m = blosum62_22() if mat is None else np.asarray(mat, dtype=np.int32)
+    for a in range(22):
+        for b in range(22):
+            p.mat[a][b] = int(m[a, b])
+    return p
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (plain gcc, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build_oracle()
+            L = ctypes.CDLL(_SO)
+            L.orc_align.argtypes = [ctypes.POINTER(Params), ctypes.c_char_p, ctypes.c_int32,
+                                    ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_uint32),
+                                    ctypes.c_int32]
+            L.orc_align.restype = ctypes.c_int
+            L.orc_rescore.argtypes = [ctypes.POINTER(Params), ctypes.c_char_p, ctypes.c_int32,
+                                      ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+            L.orc_rescore.restype = ctypes.c_int32
+            L.orc_translate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_translate.restype = ctypes.c_int
+            L.orc_donor.argtypes = [ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.c_int]
+            L.orc_donor.restype = ctypes.c_int
+            L.orc_acceptor.argtypes = [ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.c_int]
+            L.orc_acceptor.restype = ctypes.c_int
+            L.orc_aa_code.argtypes = [ctypes.c_int]
+            L.orc_aa_code.restype = ctypes.c_int
+            L.orc_nt_code.argtypes = [ctypes.c_int]
+            L.orc_nt_code.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+NEG_INF = -(2 ** 31) // 4
+
+
+def align(prot: str, nt: str, strand: int = 1, params: Params | None = None):
+    """Run the oracle on one pair.  Returns a dict with score, status,
+    coordinates (0-based half-open; nt on the input's forward strand) and the
+    CIGAR as a list of (op letter, length)."""
+    L = lib()
+    p = params if params is not None else make_params()
+    pb = prot.encode() if isinstance(prot, str) else bytes(prot)
+    tb = nt.encode() if isinstance(nt, str) else bytes(nt)
+    cap = len(pb) + len(tb) + 2
+    cig = (ctypes.c_uint32 * cap)()
+    res = Result()
+    rc = L.orc_align(ctypes.byref(p), pb, len(pb), tb, len(tb), int(strand), ctypes.byref(res), cig, cap)
+    if rc != 0:
+        raise ValueError("oracle rejected the input")
+    ops = [(OP_NAMES[cig[k] & 0xF], cig[k] >> 4) for k in range(res.n_cigar)]
+    raw = [cig[k] for k in range(res.n_cigar)]
+    return dict(score=res.score, status=res.status, prot_st=res.prot_st, prot_en=res.prot_en,
+                nt_st=res.nt_st, nt_en=res.nt_en, cigar=ops, cigar_raw=raw)
+
+
+def rescore(prot: str, nt: str, strand: int, prot_st: int, nt_st_aligned: int, cigar_raw,
+            params: Params | None = None):
+    """Op-sum score of a CIGAR from a start cell (aligned orientation).
+    Returns (score, prot_en, nt_en_aligned); score is NEG_INF if invalid."""
+    L = lib()
+    p = params if params is not None else make_params()
+    pb = prot.encode() if isinstance(prot, str) else bytes(prot)
+    tb = nt.encode() if isinstance(nt, str) else bytes(nt)
+    arr = (ctypes.c_uint32 * max(1, len(cigar_raw)))(*cigar_raw)
+    pe = ctypes.c_int32()
+    te = ctypes.c_int32()
+    s = L.orc_rescore(ctypes.byref(p), pb, len(pb), tb, len(tb), int(strand), int(prot_st),
+                      int(nt_st_aligned), arr, len(cigar_raw), ctypes.byref(pe), ctypes.byref(te))
+    return s, pe.value, te.value
+
+
+def encode_cigar(ops) -> list:
+    """[(letter, len), ...] -> packed op words (len << 4 | code)."""
+    return [(int(n) << 4) | OP_NAMES.index(c) for c, n in ops]
+
+
+def cigar_str(ops) -> str:
+    return "".join(f"{n}{c}" for c, n in ops)
+
+
+def translate_codon(b1: int, b2: int, b3: int) -> str:
+    return AA[lib().orc_translate(b1, b2, b3)]
+
+
+def donor(nt: str, x: int) -> int:
+    """d(x) of the final splice model; x is 1-based as in the paper."""
+    codes = [0] + ["ACGT".index(c) for c in nt.upper()]
+    arr = (ctypes.c_int8 * len(codes))(*codes)
+    return lib().orc_donor(arr, len(nt), x)
+
+
+def acceptor(nt: str, x: int) -> int:
+    codes = [0] + ["ACGT".index(c) for c in nt.upper()]
+    arr = (ctypes.c_int8 * len(codes))(*codes)
+    return lib().orc_acceptor(arr, len(nt), x)
+
+
+def revcomp(s: str) -> str:
+    return s.upper().translate(str.maketrans("ACGT", "TGCA"))[::-1]

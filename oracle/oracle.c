@@ -1,0 +1,428 @@
+/*
+ * oracle.c -- plain CPU oracle for the spliced protein-to-genome DP.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * statement of what the GPU path must compute.  Only the tests, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or constant with the CUDA library: every table below
+ * (genetic code, splice signals, alphabet) is written out here on its own.
+ *
+ * What it computes (Li 2022, "Protein-to-genome alignment with miniprot"):
+ *   - Eq. 7 (Methods, "DP for protein-to-genome alignment"): states I, D,
+ *     A, B, C and H over genome position i (1..|T|) and residue j (1..|P|),
+ *     with the match term read as H[i-3][j-1] + s(i,j) (the printed
+ *     H[i-3][j] cannot advance j; the worked example and Eq. 5 both consume
+ *     one residue per codon).
+ *   - The final splice model d(i), a(i) (Methods, "Splice models").
+ *   - Local mode: H restarts at 0; the best cell is the largest H, ties to
+ *     the smallest i and then the smallest j.
+ *   - Ties inside every max go to the earliest term in the printed order of
+ *     Eq. 7 (open before extend; M, I, D, F1, F2, G1, G2, A, B, C for H);
+ *     the restart to 0 wins a tie at 0.
+ *   - Split codons of phase-1/2 introns are not scored (Methods, after
+ *     Eq. 7).
+ *
+ * Everything is int32 with full (|T|+1) x (|P|+1) matrices for all six
+ * states; the traceback re-evaluates the recurrence at each cell, so no
+ * direction codes are stored.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_NEG_INF (INT32_MIN / 4)
+
+/* Protein / translated amino-acid alphabet: BLOSUM order, then stop, then X. */
+static const char ORC_AA[] = "ARNDCQEGHILKMFPSTWYV*X";
+#define ORC_AA_STOP 20
+#define ORC_AA_X 21
+
+/* Standard genetic code (NCBI table 1) in the customary T, C, A, G order of
+ * first, second and third codon base. */
+static const char ORC_CODE_TCAG[] =
+    "FFLLSSSSYY**CC*WLLLLPPPPHHQQRRRRIIIMTTTTNNKKSSRRVVVVAAAADDEEGGGG";
+
+typedef struct {
+    int32_t q, e, f, r, stop;   /* gap open, gap extend, frameshift, intron, stop codon */
+    int32_t mat[22][22];        /* [translated aa][protein residue], ORC_AA order */
+} orc_params;
+
+typedef struct {
+    int32_t score;
+    int32_t status;             /* 0 ok, 1 cigar capacity, 2 degenerate intron, 3 bad input */
+    int32_t prot_st, prot_en;   /* 0-based half-open on the protein */
+    int32_t nt_st, nt_en;       /* 0-based half-open on the INPUT's forward strand */
+    int32_t n_cigar;
+} orc_result;
+
+/* CIGAR op codes: len << 4 | code. */
+enum { OP_M = 0, OP_I = 1, OP_D = 2, OP_F = 3, OP_G = 4, OP_N = 5, OP_U = 6, OP_V = 7 };
+
+/* ---------------------------------------------------------------- encoding */
+
+/* Nucleotide letter -> 0..3 (A, C, G, T); anything else -> -1. */
+int orc_nt_code(int ch)
+{
+    switch (ch) {
+    case 'A': case 'a': return 0;
+    case 'C': case 'c': return 1;
+    case 'G': case 'g': return 2;
+    case 'T': case 't': return 3;
+    default: return -1;
+    }
+}
+
+/* Amino-acid letter -> index in ORC_AA; letters outside the 20 map to X. */
+int orc_aa_code(int ch)
+{
+    int c = (ch >= 'a' && ch <= 'z') ? ch - 32 : ch;
+    for (int k = 0; k < 21; ++k)
+        if (ORC_AA[k] == c) return k;
+    return ORC_AA_X;
+}
+
+static int tcag_index(int base_acgt)
+{
+    /* A C G T -> position in the T C A G ordering */
+    static const int m[4] = {2, 1, 3, 0};
+    return m[base_acgt];
+}
+
+/* Translate the codon b1 b2 b3 (0..3 each, ACGT) to an ORC_AA index. */
+int orc_translate(int b1, int b2, int b3)
+{
+    char aa = ORC_CODE_TCAG[16 * tcag_index(b1) + 4 * tcag_index(b2) + tcag_index(b3)];
+    return orc_aa_code(aa == '*' ? '*' : aa);
+}
+
+/* ------------------------------------------------------- splice signals */
+
+/* Base at 1-based position x of T, or -1 outside 1..n. */
+static int base_at(const int8_t *T, int n, int x)
+{
+    return (x >= 1 && x <= n) ? T[x] : -1;
+}
+
+enum { A_ = 0, C_ = 1, G_ = 2, T_ = 3 };
+
+/* Donor score d(x) of the final splice model (Methods, "Splice models"):
+ * looks at T[x+1..x+3]; bases outside T match nothing. */
+int orc_donor(const int8_t *T, int n, int x)
+{
+    int b1 = base_at(T, n, x + 1), b2 = base_at(T, n, x + 2), b3 = base_at(T, n, x + 3);
+    if (b1 == G_ && b2 == T_ && (b3 == A_ || b3 == G_)) return 0;   /* GTA, GTG */
+    if (b1 == G_ && b2 == T_ && (b3 == C_ || b3 == T_)) return 8;   /* GTC, GTT */
+    if (b1 == G_ && b2 == C_) return 15;                            /* GC */
+    if (b1 == A_ && b2 == T_) return 21;                            /* AT */
+    return 30;
+}
+
+/* Acceptor score a(x) of the final splice model: looks at T[x-2..x]. */
+int orc_acceptor(const int8_t *T, int n, int x)
+{
+    int b1 = base_at(T, n, x - 2), b2 = base_at(T, n, x - 1), b3 = base_at(T, n, x);
+    if ((b1 == C_ || b1 == T_) && b2 == A_ && b3 == G_) return 0;   /* CAG, TAG */
+    if ((b1 == A_ || b1 == G_) && b2 == A_ && b3 == G_) return 8;   /* AAG, GAG */
+    if (b2 == A_ && b3 == C_) return 21;                            /* AC */
+    return 30;
+}
+
+/* ------------------------------------------------------------- the DP */
+
+typedef struct {
+    int n, m;                  /* |T|, |P| */
+    int8_t *T;                 /* T[1..n] base codes */
+    int8_t *P;                 /* P[1..m] residue codes */
+    int32_t *H, *I, *D, *A, *B, *C;
+    const orc_params *p;
+} dp_t;
+
+#define IDX(dp, i, j) ((size_t)(i) * (size_t)((dp)->m + 1) + (size_t)(j))
+
+static int32_t getH(const dp_t *dp, int i, int j)
+{
+    if (i < 0 || j < 0) return ORC_NEG_INF;
+    return dp->H[IDX(dp, i, j)];
+}
+static int32_t getS(const dp_t *dp, const int32_t *X, int i, int j)
+{
+    (void)dp;
+    if (i < 0 || j < 0) return ORC_NEG_INF;
+    return X[IDX(dp, i, j)];
+}
+
+static int32_t max2(int32_t a, int32_t b) { return a >= b ? a : b; }
+
+/* s(i,j): the codon ending at i against residue j (Eq. 6 / Eq. 7).  A stop
+ * codon scores -stop against any residue; i < 3 has no codon. */
+static int32_t subst(const dp_t *dp, int i, int j)
+{
+    if (i < 3) return ORC_NEG_INF;
+    int aa = orc_translate(dp->T[i - 2], dp->T[i - 1], dp->T[i]);
+    if (aa == ORC_AA_STOP) return -dp->p->stop;
+    return dp->p->mat[aa][dp->P[j]];
+}
+
+static int32_t dfun(const dp_t *dp, int x) { return orc_donor(dp->T, dp->n, x); }
+static int32_t afun(const dp_t *dp, int x) { return orc_acceptor(dp->T, dp->n, x); }
+
+/* The ten H terms of Eq. 7 at (i, j) in printed order:
+ * 0 M, 1 I, 2 D, 3 F1, 4 F2, 5 G1, 6 G2, 7 A, 8 B, 9 C. */
+static void h_terms(const dp_t *dp, int i, int j, int32_t t[10])
+{
+    const orc_params *p = dp->p;
+    t[0] = (i >= 3) ? getH(dp, i - 3, j - 1) + subst(dp, i, j) : ORC_NEG_INF;
+    t[1] = dp->I[IDX(dp, i, j)];
+    t[2] = dp->D[IDX(dp, i, j)];
+    t[3] = getH(dp, i - 1, j - 1) - p->f;
+    t[4] = getH(dp, i - 2, j - 1) - p->f;
+    t[5] = getH(dp, i - 1, j) - p->f;
+    t[6] = getH(dp, i - 2, j) - p->f;
+    t[7] = dp->A[IDX(dp, i, j)] - afun(dp, i);
+    t[8] = dp->B[IDX(dp, i, j)] - afun(dp, i - 2);
+    t[9] = dp->C[IDX(dp, i, j)] - afun(dp, i - 1);
+}
+
+/* Fill all six matrices by Eq. 7 (local mode). */
+static void fill(dp_t *dp)
+{
+    const orc_params *p = dp->p;
+    int n = dp->n, m = dp->m;
+    for (int j = 0; j <= m; ++j) {
+        dp->H[IDX(dp, 0, j)] = 0;
+        dp->I[IDX(dp, 0, j)] = dp->D[IDX(dp, 0, j)] = ORC_NEG_INF;
+        dp->A[IDX(dp, 0, j)] = dp->B[IDX(dp, 0, j)] = dp->C[IDX(dp, 0, j)] = ORC_NEG_INF;
+    }
+    for (int i = 1; i <= n; ++i) {
+        dp->H[IDX(dp, i, 0)] = 0;
+        dp->I[IDX(dp, i, 0)] = dp->D[IDX(dp, i, 0)] = ORC_NEG_INF;
+        dp->A[IDX(dp, i, 0)] = dp->B[IDX(dp, i, 0)] = dp->C[IDX(dp, i, 0)] = ORC_NEG_INF;
+        for (int j = 1; j <= m; ++j) {
+            size_t c = IDX(dp, i, j);
+            dp->I[c] = max2(getH(dp, i, j - 1) - p->q, getS(dp, dp->I, i, j - 1)) - p->e;
+            dp->D[c] = max2(getH(dp, i - 3, j) - p->q, getS(dp, dp->D, i - 3, j)) - p->e;
+            dp->A[c] = max2(getH(dp, i - 1, j) - p->r - dfun(dp, i - 1), getS(dp, dp->A, i - 1, j));
+            dp->B[c] = max2(getH(dp, i - 1, j - 1) - p->r - dfun(dp, i), getS(dp, dp->B, i - 1, j));
+            dp->C[c] = max2(getH(dp, i - 1, j - 1) - p->r - dfun(dp, i + 1), getS(dp, dp->C, i - 1, j));
+            int32_t t[10];
+            h_terms(dp, i, j, t);
+            int32_t h = t[0];
+            for (int k = 1; k < 10; ++k) h = max2(h, t[k]);
+            dp->H[c] = h > 0 ? h : 0;
+        }
+    }
+}
+
+/* Emit an op into a reversed op list, merging consecutive M. */
+typedef struct {
+    uint32_t *ops;
+    int n, cap, overflow;
+} oplist;
+
+static void push_op(oplist *L, int code, int len)
+{
+    if (code == OP_M && L->n > 0 && (L->ops[L->n - 1] & 0xf) == OP_M) {
+        L->ops[L->n - 1] += (uint32_t)len << 4;
+        return;
+    }
+    if (L->n >= L->cap) { L->overflow = 1; return; }
+    L->ops[L->n++] = ((uint32_t)len << 4) | (uint32_t)code;
+}
+
+/* Trace back from (bi, bj) to the restart cell, re-evaluating Eq. 7 at each
+ * step with the same tie order as the fill.  Returns the start cell. */
+static int traceback(const dp_t *dp, int bi, int bj, oplist *L, int *si, int *sj)
+{
+    const orc_params *p = dp->p;
+    int i = bi, j = bj, degenerate = 0;
+    for (;;) {
+        if (i <= 0 || j <= 0) break;                 /* row/column 0: H = 0 */
+        int32_t h = dp->H[IDX(dp, i, j)];
+        if (h == 0) break;                           /* restart wins ties at 0 */
+        int32_t t[10];
+        h_terms(dp, i, j, t);
+        int src = -1;
+        for (int k = 0; k < 10; ++k)
+            if (t[k] == h) { src = k; break; }
+        if (src < 0) return -1;                      /* cannot happen */
+        if (src == 0) { push_op(L, OP_M, 1); i -= 3; j -= 1; }
+        else if (src == 3) { push_op(L, OP_F, 1); i -= 1; j -= 1; }
+        else if (src == 4) { push_op(L, OP_F, 2); i -= 2; j -= 1; }
+        else if (src == 5) { push_op(L, OP_G, 1); i -= 1; }
+        else if (src == 6) { push_op(L, OP_G, 2); i -= 2; }
+        else if (src == 1) {                         /* I run: residues, no nt */
+            int k = 0;
+            for (;;) {
+                ++k;
+                int32_t open = getH(dp, i, j - 1) - p->q - p->e;
+                int32_t ext = getS(dp, dp->I, i, j - 1) - p->e;
+                j -= 1;
+                if (open >= ext) break;
+            }
+            push_op(L, OP_I, k);
+        } else if (src == 2) {                       /* D run: codons, no residue */
+            int k = 0;
+            for (;;) {
+                ++k;
+                int32_t open = getH(dp, i - 3, j) - p->q - p->e;
+                int32_t ext = getS(dp, dp->D, i - 3, j) - p->e;
+                i -= 3;
+                if (open >= ext) break;
+            }
+            push_op(L, OP_D, k);
+        } else if (src == 7) {                       /* phase-0 intron */
+            int iexit = i;
+            for (;;) {
+                int32_t open = getH(dp, i - 1, j) - p->r - dfun(dp, i - 1);
+                int32_t ext = getS(dp, dp->A, i - 1, j);
+                if (open >= ext) break;
+                i -= 1;
+            }
+            /* opened at i: intron T[i..iexit] */
+            push_op(L, OP_N, iexit - i + 1);
+            i -= 1;
+        } else {                                     /* phase-1 (B) or phase-2 (C) intron */
+            int iexit = i;
+            int32_t *X = (src == 8) ? dp->B : dp->C;
+            for (;;) {
+                int32_t open = getH(dp, i - 1, j - 1) - p->r - dfun(dp, src == 8 ? i : i + 1);
+                int32_t ext = getS(dp, X, i - 1, j);
+                if (open >= ext) break;
+                i -= 1;
+            }
+            int len = iexit - i - 2;                 /* intron length */
+            if (len < 1) degenerate = 1;
+            push_op(L, src == 8 ? OP_U : OP_V, len > 0 ? len : 0);
+            i -= 1; j -= 1;
+        }
+    }
+    *si = i < 0 ? 0 : i;
+    *sj = j < 0 ? 0 : j;
+    return degenerate;
+}
+
+/* Align protein `prot` (ASCII, plen) to genome `nt` (ASCII ACGT, tlen) on
+ * the given strand (+1, or -1 = reverse complement of nt).  Writes the CIGAR
+ * (forward op order) to cigar[0..cap).  Returns 0 on success. */
+int orc_align(const orc_params *p, const char *prot, int32_t plen, const char *nt, int32_t tlen,
+              int32_t strand, orc_result *res, uint32_t *cigar, int32_t cap)
+{
+    memset(res, 0, sizeof(*res));
+    dp_t dp;
+    memset(&dp, 0, sizeof(dp));
+    dp.n = tlen;
+    dp.m = plen;
+    dp.p = p;
+    dp.T = (int8_t *)malloc((size_t)tlen + 1);
+    dp.P = (int8_t *)malloc((size_t)plen + 1);
+    if (!dp.T || !dp.P) { free(dp.T); free(dp.P); res->status = 3; return -1; }
+    for (int i = 1; i <= tlen; ++i) {
+        int b = orc_nt_code(nt[strand < 0 ? tlen - i : i - 1]);
+        if (b < 0) { free(dp.T); free(dp.P); res->status = 3; return -1; }
+        dp.T[i] = (int8_t)(strand < 0 ? 3 - b : b);
+    }
+    for (int j = 1; j <= plen; ++j) dp.P[j] = (int8_t)orc_aa_code(prot[j - 1]);
+
+    size_t cells = (size_t)(tlen + 1) * (size_t)(plen + 1);
+    int32_t *buf = (int32_t *)malloc(cells * 6 * sizeof(int32_t));
+    if (!buf) { free(dp.T); free(dp.P); res->status = 3; return -1; }
+    dp.H = buf; dp.I = buf + cells; dp.D = buf + 2 * cells;
+    dp.A = buf + 3 * cells; dp.B = buf + 4 * cells; dp.C = buf + 5 * cells;
+    fill(&dp);
+
+    /* best cell: largest H, then smallest i, then smallest j */
+    int32_t best = 0;
+    int bi = 0, bj = 0;
+    for (int i = 1; i <= tlen; ++i)
+        for (int j = 1; j <= plen; ++j)
+            if (dp.H[IDX(&dp, i, j)] > best) { best = dp.H[IDX(&dp, i, j)]; bi = i; bj = j; }
+
+    res->score = best;
+    if (best > 0) {
+        uint32_t *rev = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
+        oplist L = {rev, 0, cap, 0};
+        int si = 0, sj = 0;
+        int deg = traceback(&dp, bi, bj, &L, &si, &sj);
+        for (int k = 0; k < L.n; ++k) cigar[k] = rev[L.n - 1 - k];
+        free(rev);
+        res->n_cigar = L.n;
+        res->prot_st = sj;
+        res->prot_en = bj;
+        if (strand < 0) { res->nt_st = tlen - bi; res->nt_en = tlen - si; }
+        else { res->nt_st = si; res->nt_en = bi; }
+        if (L.overflow) res->status = 1;
+        else if (deg) res->status = 2;
+    }
+    free(buf);
+    free(dp.T);
+    free(dp.P);
+    return 0;
+}
+
+/* Score only: the same fill, returning the best H (for large cases). */
+int32_t orc_score(const orc_params *p, const char *prot, int32_t plen, const char *nt, int32_t tlen,
+                  int32_t strand)
+{
+    orc_result r;
+    uint32_t dummy[1];
+    if (orc_align(p, prot, plen, nt, tlen, strand, &r, dummy, 0) != 0) return -1;
+    return r.score;
+}
+
+/* Op-sum rescoring of a CIGAR (no DP): walks the ops from the aligned start
+ * (prot_st, nt position in the aligned orientation) and adds each op's cost
+ * as defined by the transitions of Eq. 7.  Returns the score and writes the
+ * end coordinates; returns ORC_NEG_INF if the path leaves the sequences. */
+int32_t orc_rescore(const orc_params *p, const char *prot, int32_t plen, const char *nt, int32_t tlen,
+                    int32_t strand, int32_t prot_st, int32_t nt_st_aligned, const uint32_t *cigar,
+                    int32_t n_cigar, int32_t *prot_en, int32_t *nt_en_aligned)
+{
+    int8_t *T = (int8_t *)malloc((size_t)tlen + 1);
+    for (int i = 1; i <= tlen; ++i) {
+        int b = orc_nt_code(nt[strand < 0 ? tlen - i : i - 1]);
+        T[i] = (int8_t)(strand < 0 ? 3 - b : b);
+    }
+    int i = nt_st_aligned, j = prot_st;   /* consumed so far */
+    int64_t sc = 0;
+    int bad = 0;
+    for (int k = 0; k < n_cigar && !bad; ++k) {
+        int op = (int)(cigar[k] & 0xf);
+        int len = (int)(cigar[k] >> 4);
+        switch (op) {
+        case OP_M:
+            for (int c = 0; c < len; ++c) {
+                if (i + 3 > tlen || j + 1 > plen) { bad = 1; break; }
+                int aa = orc_translate(T[i + 1], T[i + 2], T[i + 3]);
+                int pc = orc_aa_code(prot[j]);
+                sc += (aa == ORC_AA_STOP) ? -p->stop : p->mat[aa][pc];
+                i += 3; j += 1;
+            }
+            break;
+        case OP_I: sc -= p->q + (int64_t)p->e * len; j += len; break;
+        case OP_D: sc -= p->q + (int64_t)p->e * len; i += 3 * len; break;
+        case OP_F: sc -= p->f; i += len; j += 1; break;
+        case OP_G: sc -= p->f; i += len; break;
+        case OP_N: sc -= p->r + orc_donor(T, tlen, i) + orc_acceptor(T, tlen, i + len); i += len; break;
+        case OP_U: sc -= p->r + orc_donor(T, tlen, i + 1) + orc_acceptor(T, tlen, i + len + 1);
+                   i += len + 3; j += 1; break;
+        case OP_V: sc -= p->r + orc_donor(T, tlen, i + 2) + orc_acceptor(T, tlen, i + len + 2);
+                   i += len + 3; j += 1; break;
+        default: bad = 1;
+        }
+        if (i > tlen || j > plen) bad = 1;
+    }
+    free(T);
+    *prot_en = j;
+    *nt_en_aligned = i;
+    return bad ? ORC_NEG_INF : (int32_t)sc;
+}
+
+/* Reverse complement of an ASCII ACGT string (helper for tests). */
+void orc_revcomp(const char *in, int32_t n, char *out)
+{
+    static const char comp[4] = {'T', 'G', 'C', 'A'};
+    for (int k = 0; k < n; ++k) {
+        int b = orc_nt_code(in[n - 1 - k]);
+        out[k] = b < 0 ? 'N' : comp[b];
+    }
+}

@@ -1,0 +1,375 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+Li 2022 (miniprot), Methods: Eq. 5 (AE86 affine gaps), Eq. 6 (frameshifts),
+Eq. 7 (protein-to-genome DP), the final splice model ("Splice models") and
+the worked alignment example ("Residue alignment with dynamic programming").
+"""
+import itertools
+import os
+import random
+
+import numpy as np
+import pytest
+
+import bruteforce as bf
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _diag_sum(orc, prot):
+    B = orc.blosum62_22()
+    return int(sum(B[orc.AA.index(a), orc.AA.index(a)] for a in prot))
+
+
+def _rand_prot(rng, n):
+    return "".join(rng.choice("ARNDCQEGHILKMFPSTWYV") for _ in range(n))
+
+
+# Genetic code (NCBI table 1) typed independently by the generator.
+_CODE_ACGT = "KNKNTTTTRSRSIIMIQHQHPPPPRRRRLLLLEDEDAAAAGGGGVVVV*Y*YSSSS*CWCLFLF"
+
+
+def _cds(rng, prot):
+    syn = {}
+    for k, aa in enumerate(_CODE_ACGT):
+        syn.setdefault(aa, []).append("ACGT"[k // 16] + "ACGT"[(k // 4) % 4] + "ACGT"[k % 4])
+    return "".join(rng.choice(syn[a]) for a in prot)
+
+
+# ------------------------------------------------------------------ tables
+
+def test_genetic_code_matches_independent_table(orc):
+    for b1, b2, b3 in itertools.product(range(4), repeat=3):
+        assert orc.translate_codon(b1, b2, b3) == _CODE_ACGT[16 * b1 + 4 * b2 + b3]
+    # textbook spot checks
+    assert orc.translate_codon(0, 3, 2) == "M"                     # ATG
+    for s in ("TAA", "TAG", "TGA"):
+        assert orc.translate_codon(*("ACGT".index(c) for c in s)) == "*"
+    assert orc.translate_codon(3, 2, 2) == "W"                     # TGG
+
+
+def test_blosum62_properties(orc):
+    B = orc.blosum62_22()[:20, :20]
+    assert (B == B.T).all()
+    for k in range(20):
+        assert B[k, k] == B[k].max() and (B[k] < B[k, k]).sum() == 19
+    assert B.min() == -4 and B.max() == 11
+    assert int(np.trace(B)) == 4 + 5 + 6 + 6 + 9 + 5 + 5 + 6 + 8 + 4 + 4 + 5 + 5 + 6 + 7 + 4 + 5 + 11 + 7 + 4
+
+
+@pytest.mark.parametrize("motif,val", [("GTA", 0), ("GTG", 0), ("GTC", 8), ("GTT", 8),
+                                       ("GCA", 15), ("GCT", 15), ("ATA", 21), ("ATG", 21),
+                                       ("AGT", 30), ("CTA", 30), ("TTT", 30), ("GAA", 30)])
+def test_donor_rows(orc, motif, val):
+    # d(x) looks at T[x+1..x+3] (final model, "Splice models")
+    nt = "CC" + motif + "CC"
+    assert orc.donor(nt, 2) == val
+
+
+@pytest.mark.parametrize("motif,val", [("CAG", 0), ("TAG", 0), ("AAG", 8), ("GAG", 8),
+                                       ("CAC", 21), ("GAC", 21), ("TTG", 30), ("CAA", 30), ("AGG", 30)])
+def test_acceptor_rows(orc, motif, val):
+    # a(x) looks at T[x-2..x]
+    nt = "TT" + motif + "TT"
+    assert orc.acceptor(nt, 5) == val
+
+
+def test_splice_out_of_range(orc):
+    # bases outside T match nothing
+    assert orc.donor("AAGT", 2) == 30          # GT at the end: third base missing -> not GT[ACGT]
+    assert orc.donor("AAGC", 2) == 15          # two-base rows need only two bases
+    assert orc.donor("AAG", 2) == 30
+    assert orc.acceptor("AGTT", 2) == 30       # AG at the start: x-2 is outside T
+    assert orc.acceptor("ACTT", 2) == 21
+    assert orc.donor("GTA", 0) == 0 and orc.donor("GTA", -1) == 30
+    assert orc.acceptor("CAG", 3) == 0 and orc.acceptor("CAG", 4) == 30
+
+
+# ----------------------------------------------------------- brute force
+
+def _random_case(rng, n, m, valid=True):
+    prot = _rand_prot(rng, m)
+    if rng.random() < 0.5:
+        # plant a codon-level copy so that positive paths exist
+        nt = _cds(rng, prot)
+        extra = "".join(rng.choice("ACGT") for _ in range(max(0, n - len(nt))))
+        k = rng.randint(0, len(extra))
+        nt = (extra[:k] + nt + extra[k:])[:n]
+    else:
+        nt = "".join(rng.choice("ACGT") for _ in range(n))
+    if valid:
+        f = rng.randint(1, 6)
+        params = dict(q=rng.randint(0, 4), e=rng.randint(1, 3), f=f,
+                      stop=rng.randint(1, 6))
+        params["r"] = max(f, params["stop"], 4) + rng.randint(1, 4)
+    else:
+        params = dict(q=rng.randint(0, 5), e=rng.randint(0, 3), f=rng.randint(0, 12),
+                      r=rng.randint(0, 12), stop=rng.randint(0, 10))
+    return prot, nt, params
+
+
+def test_exhaustive_enumeration_equals_oracle(orc):
+    rng = random.Random(11)
+    for k in range(50):
+        n, m = (rng.randint(0, 6), rng.randint(0, 2)) if k < 40 else (rng.randint(4, 6), 3)
+        prot, nt, params = _random_case(rng, n, m, valid=rng.random() < 0.5)
+        paths = bf.all_paths(bf.Problem(prot, nt, **params))
+        want = bf.best_by_enumeration(paths)
+        got = orc.align(prot, nt, 1, orc.make_params(**params))["score"]
+        assert got == want, (prot, nt, params)
+
+
+def test_segment_recursion_equals_oracle(orc):
+    rng = random.Random(12)
+    for _ in range(150):
+        n, m = rng.randint(0, 20), rng.randint(0, 5)
+        prot, nt, params = _random_case(rng, n, m, valid=rng.random() < 0.5)
+        want = bf.segment_best(bf.Problem(prot, nt, **params))
+        got = orc.align(prot, nt, 1, orc.make_params(**params))["score"]
+        assert got == want, (prot, nt, params)
+
+
+def test_segment_recursion_default_params(orc):
+    rng = random.Random(13)
+    for _ in range(40):
+        m = rng.randint(1, 5)
+        prot = _rand_prot(rng, m)
+        cds = _cds(rng, prot)
+        nt = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 6))) + cds + \
+             "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 6)))
+        assert orc.align(prot, nt)["score"] == bf.segment_best(bf.Problem(prot, nt))
+
+
+def test_tie_rule_against_path_order(orc):
+    """The oracle's path is the optimum the stated tie rules select among all
+    enumerated optimal paths.  Small integer penalties make ties common."""
+    rng = random.Random(14)
+    mat = np.zeros((22, 22), dtype=np.int32)
+    B = orc.blosum62_22()
+    mat[:] = np.sign(B)           # values in {-1, 0, 1}: many equal-scoring paths
+    mat[np.arange(20), np.arange(20)] = 2
+    checked = 0
+    for _ in range(80):
+        n, m = rng.randint(3, 7), rng.randint(1, 2)
+        prot = _rand_prot(rng, m)
+        nt = "".join(rng.choice("ACGT") for _ in range(n))
+        if rng.random() < 0.6:
+            k = rng.randint(0, n - 3)
+            nt = (nt[:k] + _cds(rng, prot) + nt[k:])[:n]
+        params = dict(q=rng.randint(0, 2), e=1, f=rng.randint(1, 2), stop=1, r=3)
+        pb = bf.Problem(prot, nt, mat=mat, **params)
+        paths = bf.all_paths(pb)
+        choice = bf.tie_rule_choice(paths)
+        res = orc.align(prot, nt, 1, orc.make_params(mat=mat, **params))
+        if choice is None:
+            assert res["score"] == 0 and res["cigar"] == []
+            continue
+        si, sj, ops, ei, ej, sc = choice
+        assert res["score"] == sc
+        assert (res["prot_st"], res["prot_en"], res["nt_st"], res["nt_en"]) == (sj, ej, si, ei), (prot, nt, params)
+        assert res["cigar"] == bf.to_cigar(ops), (prot, nt, params, ops)
+        checked += 1
+    assert checked > 40
+
+
+# --------------------------------------------------- textbook special case
+
+def _gotoh_local(a, b, S, q, e):
+    """Textbook local alignment with affine gaps (Gotoh 1982; Eq. 5 form)."""
+    NEG = -10 ** 9
+    n, m = len(a), len(b)
+    H = [[0] * (m + 1) for _ in range(n + 1)]
+    E = [[NEG] * (m + 1) for _ in range(n + 1)]
+    F = [[NEG] * (m + 1) for _ in range(n + 1)]
+    best = 0
+    for i in range(1, n + 1):
+        for j in range(1, m + 1):
+            E[i][j] = max(H[i][j - 1] - q, E[i][j - 1]) - e
+            F[i][j] = max(H[i - 1][j] - q, F[i - 1][j]) - e
+            H[i][j] = max(0, H[i - 1][j - 1] + S(a[i - 1], b[j - 1]), E[i][j], F[i][j])
+            best = max(best, H[i][j])
+    return best
+
+
+def test_reduces_to_three_frame_gotoh(orc):
+    """With f = r = 10^6 no frameshift or intron can win; the DP is then the
+    AE86 local alignment (Eq. 5) of each translated frame against P."""
+    rng = random.Random(21)
+    B = orc.blosum62_22()
+    for _ in range(40):
+        m = rng.randint(1, 25)
+        prot = _rand_prot(rng, m)
+        nt = _cds(rng, _rand_prot(rng, rng.randint(0, 4))) + _cds(rng, prot)
+        nt = list(nt)
+        for _ in range(rng.randint(0, 6)):                     # point mutations
+            nt[rng.randrange(len(nt))] = rng.choice("ACGT")
+        for _ in range(rng.randint(0, 2)):                     # indels of 1 nt
+            k = rng.randrange(len(nt))
+            if rng.random() < 0.5:
+                nt.insert(k, rng.choice("ACGT"))
+            else:
+                del nt[k]
+        nt = "".join(nt)
+        q, e, stop = rng.randint(1, 12), rng.randint(1, 3), rng.randint(1, 30)
+
+        def S(x, y):
+            return -stop if x == "*" else int(B[orc.AA.index(x), orc.AA.index(y)])
+
+        want = 0
+        for o in range(3):
+            frame = [_CODE_ACGT[16 * "ACGT".index(nt[k]) + 4 * "ACGT".index(nt[k + 1]) + "ACGT".index(nt[k + 2])]
+                     for k in range(o, len(nt) - 2, 3)]
+            want = max(want, _gotoh_local(frame, prot, S, q, e))
+        got = orc.align(prot, nt, 1, orc.make_params(q=q, e=e, f=10 ** 6, r=10 ** 6, stop=stop))["score"]
+        assert got == want
+
+
+# ----------------------------------------------------------- invariants
+
+def test_exact_cds_scores_diagonal_sum(orc):
+    rng = random.Random(31)
+    for _ in range(30):
+        prot = _rand_prot(rng, rng.randint(1, 200))
+        r = orc.align(prot, _cds(rng, prot))
+        assert r["score"] == _diag_sum(orc, prot)
+        assert r["cigar"] == [("M", len(prot))]
+        assert (r["prot_st"], r["prot_en"], r["nt_st"], r["nt_en"]) == (0, len(prot), 0, 3 * len(prot))
+
+
+def test_minus_strand_matches_plus(orc):
+    for k, p in enumerate(synth.config2(seed=100 + 0, n=6)):
+        if len(p.prot) * len(p.nt) > 3_000_000:
+            continue
+        a = orc.align(p.prot, p.nt, p.strand)
+        b = orc.align(p.prot, orc.revcomp(p.nt), -p.strand)
+        assert a["score"] == b["score"]
+        assert (a["prot_st"], a["prot_en"]) == (b["prot_st"], b["prot_en"])
+        assert (a["nt_st"], a["nt_en"]) == (len(p.nt) - b["nt_en"], len(p.nt) - b["nt_st"])
+        assert a["cigar"] == b["cigar"]
+
+
+def test_cigar_rescoring_equals_score(orc):
+    pairs = [synth.config1()] + [p for p in synth.config2(seed=101, n=12) if p.cells < 2_500_000]
+    for p in pairs:
+        r = orc.align(p.prot, p.nt, p.strand)
+        n = len(p.nt)
+        st_aligned = r["nt_st"] if p.strand > 0 else n - r["nt_en"]
+        en_aligned = r["nt_en"] if p.strand > 0 else n - r["nt_st"]
+        sc, pe, te = orc.rescore(p.prot, p.nt, p.strand, r["prot_st"], st_aligned, r["cigar_raw"])
+        assert (sc, pe, te) == (r["score"], r["prot_en"], en_aligned)
+        assert r["status"] == 0
+
+
+# ------------------------------------------------------------ hand cases
+
+def test_hand_ungapped_with_flanks(orc):
+    rng = random.Random(41)
+    prot = _rand_prot(rng, 40)
+    nt = "TTTTTTTTTT" + _cds(rng, prot) + "TTTTTTTTTT"   # TTT codons are F, poly-T flanks
+    r = orc.align(prot, nt)
+    assert r["score"] >= _diag_sum(orc, prot)
+
+
+def test_hand_frameshift_insertion_and_deletion(orc):
+    """Eq. 6: one inserted base ('+', G1) costs f; a codon missing one base
+    ('$', F2) costs f and leaves its residue unscored."""
+    rng = random.Random(42)
+    p1, p2 = _rand_prot(rng, 30), _rand_prot(rng, 30)
+    c1, c2 = _cds(rng, p1), _cds(rng, p2)
+    big = dict(r=10 ** 6)
+    r = orc.align(p1 + p2, c1 + "A" + c2, 1, orc.make_params(**big))
+    assert r["score"] == _diag_sum(orc, p1 + p2) - 23
+    assert r["cigar"] == [("M", 30), ("G", 1), ("M", 30)]
+    # a Met codon (ATG) that lost its last base, between two Trp (TGG): the
+    # frame shifts back only through the '$' operation
+    q1, q2 = p1[:-1] + "W", "W" + p2[1:]
+    c1, c2 = _cds(rng, q1), _cds(rng, q2)
+    r = orc.align(q1 + "M" + q2, c1 + "AT" + c2, 1, orc.make_params(**big))
+    assert r["score"] == _diag_sum(orc, q1 + q2) - 23
+    assert r["cigar"] == [("M", 30), ("F", 2), ("M", 30)]
+
+
+def _intron_case(rng, phase, L=90):
+    prot = _rand_prot(rng, 40)
+    cds = _cds(rng, prot)
+    cut = 3 * 20 + phase
+    body = "".join(rng.choice("CT") for _ in range(L - 6))      # pyrimidine filler: no stop-free codon runs of note
+    intron = "GTA" + body + "CAG"                               # d = 0, a = 0
+    return prot, cds[:cut] + intron + cds[cut:], intron
+
+
+@pytest.mark.parametrize("phase,op", [(0, "N"), (1, "U"), (2, "V")])
+def test_hand_single_intron(orc, phase, op):
+    """One GTA...CAG intron (d = a = 0) costs r; a split codon (phase 1/2)
+    leaves its residue unscored (Methods, after Eq. 7)."""
+    rng = random.Random(43 + phase)
+    prot, nt, intron = _intron_case(rng, phase)
+    r = orc.align(prot, nt)
+    want = _diag_sum(orc, prot) - 29
+    if phase:
+        want -= _diag_sum(orc, prot[20])
+    assert r["score"] == want
+    if phase == 0:
+        assert r["cigar"] == [("M", 20), ("N", len(intron)), ("M", 20)]
+    else:
+        assert r["cigar"] == [("M", 20), (op, len(intron)), ("M", 19)]
+
+
+# ---------------------------------------------------------------- ties
+
+def test_best_cell_tie_smallest_i(orc):
+    r = orc.align("W", "TGGCCCTGG")
+    assert (r["score"], r["nt_st"], r["nt_en"]) == (11, 0, 3)
+
+
+def test_best_cell_tie_smallest_j(orc):
+    r = orc.align("WW", "TGG")
+    assert (r["score"], r["prot_st"], r["prot_en"]) == (11, 0, 1)
+
+
+def test_restart_wins_tie_at_zero(orc):
+    # ACT (Thr) vs A scores 0: the path restarts after it.
+    r = orc.align("AW", "ACTTGG")
+    assert r["score"] == 11
+    assert (r["prot_st"], r["nt_st"], r["cigar"]) == (1, 3, [("M", 1)])
+
+
+def test_empty_and_degenerate_inputs(orc):
+    assert orc.align("", "ACGT")["score"] == 0
+    assert orc.align("MW", "")["score"] == 0
+    assert orc.align("W", "TG")["score"] == 0          # no full codon
+    r = orc.align("P", "AAAAAA")                       # only negative cells
+    assert r["score"] == 0 and r["cigar"] == [] and r["prot_en"] == 0
+
+
+# ------------------------------------------------------ paper's example
+
+def _read_golden(name):
+    d = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split("=", 1)
+            d[k.strip()] = v.strip()
+    return d
+
+
+def test_paper_worked_example(orc):
+    """The worked alignment of the Methods section decodes to a valid path
+    whose op-sum equals the hand total; the DP's optimum is at least that
+    (it is not optimal: AAG/E scores +1 where the example uses '$$')."""
+    g = _read_golden("paper_example.txt")
+    prot, nt = g["prot"], g["genome"]
+    ops = [(t[-1], int(t[:-1])) for t in g["cigar"].split()]
+    cheap = {k: int(v) for k, v in (kv.split("=") for kv in g["cheap"].split())}
+    for params, want in ((orc.make_params(**cheap), int(g["cheap_score"])),
+                         (orc.make_params(), int(g["default_score"]))):
+        sc, pe, te = orc.rescore(prot, nt, 1, 0, 0, orc.encode_cigar(ops), params)
+        assert (sc, pe, te) == (want, len(prot), len(nt))
+        r = orc.align(prot, nt, 1, params)
+        assert r["score"] >= max(want, 0)
+        sc2, pe2, te2 = orc.rescore(prot, nt, 1, r["prot_st"], r["nt_st"], r["cigar_raw"], params)
+        assert (sc2, pe2, te2) == (r["score"], r["prot_en"], r["nt_en"])
