@@ -1,0 +1,208 @@
+/*
+ * mp_dp.h -- C ABI of the GB300 spliced protein-to-genome DP library.
+ *
+ * The library aligns batches of (protein, genomic region) pairs with the
+ * dynamic program of Li 2022 ("Protein-to-genome alignment with miniprot"),
+ * Eq. 7 (Methods, "DP for protein-to-genome alignment"): affine gaps (I, D),
+ * frameshifts (the four f terms) and phase-0/1/2 introns (A, B, C) scored
+ * together, with the final splice model d(i), a(i) of the "Splice models"
+ * section.  The problem statement it serves is the paper's: take a protein
+ * and a nucleotide sequence and return the spliced alignment between them
+ * (Introduction).
+ *
+ * Conventions used by every call:
+ *   - Alignment is local: H restarts at 0 and the best cell is the largest
+ *     H, ties to the smallest genome position and then the smallest residue.
+ *   - Ties inside each max of Eq. 7 go to the earliest printed term (open
+ *     before extend; M, I, D, F1, F2, G1, G2, A, B, C for H); a restart at 0
+ *     wins a tie at 0.
+ *   - Coordinates are 0-based half-open.  nt_st/nt_en are on the forward
+ *     strand of the sequence the caller passed, whatever the pair's strand.
+ *   - A CIGAR op is (len << 4) | code with the MP_OP_* codes below; ops run
+ *     in protein order (on the reverse complement for strand -1).
+ *   - Return codes: MP_OK (0) or a negative MP_E* value.  No C++ exception
+ *     crosses this boundary.  Per-pair failures are reported in
+ *     mp_result.status, not in the return code.
+ *   - All host pointers passed in are borrowed for the duration of the
+ *     call; the library copies what it needs.
+ *   - Calls on one context are not thread-safe, except mp_dp_submit and
+ *     mp_dp_poll, which may be called from any thread.
+ */
+#ifndef MP_DP_H
+#define MP_DP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- return codes */
+#define MP_OK 0
+#define MP_EINVAL (-1)    /* bad argument or parameter set */
+#define MP_ENOMEM (-2)    /* host or device allocation failed */
+#define MP_EBUDGET (-3)   /* the request cannot fit the traceback budget */
+#define MP_ETIMEOUT (-4)  /* mp_dp_poll: result not ready within the timeout */
+#define MP_ECUDA (-5)     /* a CUDA call failed; the context should be destroyed */
+#define MP_EPENDING (-6)  /* mp_dp_poll with timeout 0: not ready yet */
+#define MP_EAGAIN (-7)    /* mp_dp_submit: request ring full, retry later */
+#define MP_ETICKET (-8)   /* unknown or already-consumed ticket */
+#define MP_ESTATE (-9)    /* call not valid in the context's current state */
+
+/* -------------------------------------------------- per-pair status bits */
+#define MP_ST_OK 0x0
+#define MP_ST_RERUN 0x1     /* info: int16 scores saturated; recomputed exactly in int32 */
+#define MP_ST_BADSEQ 0x10   /* error: a character outside ACGT in the genome */
+#define MP_ST_BUDGET 0x20   /* error: this pair's traceback alone exceeds the budget */
+#define MP_ST_TRACE 0x40    /* error: internal traceback inconsistency (never expected) */
+#define MP_ST_ERRMASK 0xF0
+
+/* ---------------------------------------------------------- CIGAR ops */
+#define MP_OP_M 0  /* codons matched to residues; len = codons */
+#define MP_OP_I 1  /* residues against no genome (gap in T); len = residues */
+#define MP_OP_D 2  /* codons against no residue (gap in P); len = codons */
+#define MP_OP_F 3  /* frameshift '$': len = 1 or 2 nt for one residue (unscored) */
+#define MP_OP_G 4  /* frameshift '+': len = 1 or 2 inserted nt, no residue */
+#define MP_OP_N 5  /* phase-0 intron; len = intron nt */
+#define MP_OP_U 6  /* phase-1 intron; len = intron nt.  The op also spans the
+                      split codon's 1 nt before and 2 nt after the intron and
+                      one residue, which is not scored */
+#define MP_OP_V 7  /* phase-2 intron; as U with 2 nt before and 1 nt after */
+
+/* ------------------------------------------------------------- params */
+#define MP_SPLICE_FINAL 0   /* the final splice model of the "Splice models" section */
+#define MP_MODE_LOCAL 0     /* local alignment (the only mode of this version) */
+
+#define MP_PAIR_SCORE_ONLY 0x1u  /* mp_pair.flags: score and end cell only, no CIGAR */
+
+/* Scoring parameters.  The paper prints no default values for q, e, f, r or
+ * the stop penalty; mp_dp_default_params fills q=11, e=1, f=23, r=29,
+ * stop=23 and BLOSUM62.  mat is indexed [translated amino acid][protein
+ * residue] in the order ARNDCQEGHILKMFPSTWYV, then '*' (20) and X (21);
+ * row 20 is unused (a stop codon scores -stop against every residue) and
+ * protein letters outside the 20 amino acids and '*' map to X.
+ * mp_dp_init rejects sets under which an intron of length <= 0 could beat
+ * a frameshift or a match: it requires r > f, r > stop and r > -min(mat),
+ * all penalties >= 0 and e >= 1. */
+typedef struct {
+    int32_t q, e, f, r, stop;  /* gap open, gap extend, frameshift, intron, stop codon */
+    int8_t mat[22][22];
+    int32_t splice_model;      /* MP_SPLICE_FINAL */
+    int32_t mode;              /* MP_MODE_LOCAL */
+    uint64_t tb_budget_bytes;  /* device bytes for traceback codes (default 40 GiB, capped
+                                  by free device memory at init) */
+    int32_t force_int32;       /* 1: skip the packed int16 pass and run every pair in int32 */
+    int32_t max_pairs_per_launch; /* 0: no limit; 1: one pair per kernel launch (plain form) */
+    int32_t reserved[6];
+} mp_dp_params;
+
+/* One alignment request.  prot: ASCII amino acids; nt: ASCII A/C/G/T
+ * (either case).  strand -1 aligns the protein to the reverse complement of
+ * nt. */
+typedef struct {
+    const char *prot;
+    uint32_t prot_len;
+    const char *nt;
+    uint32_t nt_len;
+    int8_t strand;
+    uint32_t flags;            /* MP_PAIR_* */
+} mp_pair;
+
+/* One result.  cigar points into library-owned memory: for
+ * mp_dp_align_batch and mp_dp_batch_download it stays valid until the next
+ * such call on the context, or mp_dp_destroy; for mp_dp_poll, until the
+ * same ticket is polled a second time (which releases it) or mp_dp_destroy. */
+typedef struct {
+    int32_t score;
+    int32_t status;            /* MP_ST_* bits */
+    int32_t prot_st, prot_en;  /* 0-based half-open on the protein */
+    int32_t nt_st, nt_en;      /* 0-based half-open on the input's forward strand */
+    uint32_t n_cigar;
+    const uint32_t *cigar;
+} mp_result;
+
+typedef struct mp_dp_ctx mp_dp_ctx;
+typedef struct mp_dp_batch mp_dp_batch;
+
+/* Fill *p with the default parameter set described above. */
+void mp_dp_default_params(mp_dp_params *p);
+
+/* Create a context on CUDA device `device` with parameters *p (NULL:
+ * defaults).  Validates p as described above (MP_EINVAL).  Allocates the
+ * traceback arena lazily, at the first batch.  On success *ctx owns a CUDA
+ * stream and device buffers until mp_dp_destroy. */
+int mp_dp_init(mp_dp_ctx **ctx, const mp_dp_params *p, int device);
+
+/* Align n pairs end to end: host -> device copy, the DP, traceback, and
+ * device -> host copy of results.  out[k] corresponds to pairs[k].  Blocks
+ * until done.  Returns MP_EINVAL for a NULL or zero-length sequence pointer
+ * with nonzero length, or strand not +-1; per-pair sequence errors go to
+ * out[k].status. */
+int mp_dp_align_batch(mp_dp_ctx *ctx, const mp_pair *pairs, size_t n, mp_result *out);
+
+/* Staged form of mp_dp_align_batch, for callers that keep a batch resident
+ * on the device and run it repeatedly.  upload copies the inputs to the
+ * device and plans the waves; run enqueues the whole device pipeline
+ * (pack, DP, int32 re-run, traceback, CIGAR compaction) on the context's
+ * stream without blocking; sync waits for it; download copies results back
+ * (blocking).  A batch handle is owned by the caller until
+ * mp_dp_batch_free. */
+int mp_dp_batch_upload(mp_dp_ctx *ctx, const mp_pair *pairs, size_t n, mp_dp_batch **batch);
+int mp_dp_batch_run(mp_dp_ctx *ctx, mp_dp_batch *batch);
+int mp_dp_batch_sync(mp_dp_ctx *ctx);
+int mp_dp_batch_download(mp_dp_ctx *ctx, mp_dp_batch *batch, mp_result *out);
+void mp_dp_batch_free(mp_dp_ctx *ctx, mp_dp_batch *batch);
+
+/* Serving: submit one pair; never blocks.  *ticket identifies the result.
+ * MP_EAGAIN if the request ring is full.  The first submit starts the
+ * serving thread, which admits requests while the traceback bytes in
+ * flight stay within the budget and launches mixed-size batches as
+ * requests arrive (continuous batching). */
+int mp_dp_submit(mp_dp_ctx *ctx, const mp_pair *pair, uint64_t *ticket);
+
+/* Wait up to timeout_us (0: do not wait; negative: forever) for ticket's
+ * result.  MP_OK fills *out; its CIGAR stays valid until the ticket is
+ * polled again, which releases the result and returns MP_ETICKET, or
+ * mp_dp_destroy.  MP_EPENDING (timeout 0) or MP_ETIMEOUT when not ready;
+ * MP_ETICKET for an unknown or released ticket. */
+int mp_dp_poll(mp_dp_ctx *ctx, uint64_t ticket, mp_result *out, int64_t timeout_us);
+
+/* Wait up to timeout_us (as in mp_dp_poll) for any finished request that
+ * has not been handed out yet, in completion order.  On MP_OK, *ticket names
+ * it and *out holds its result with the same lifetime as mp_dp_poll's. */
+int mp_dp_wait_any(mp_dp_ctx *ctx, uint64_t *ticket, mp_result *out, int64_t timeout_us);
+
+/* Drain the serving thread, free every device and host buffer. */
+void mp_dp_destroy(mp_dp_ctx *ctx);
+
+/* Static string for a return code. */
+const char *mp_dp_strerror(int code);
+
+/* Counters of the last mp_dp_batch_run / mp_dp_align_batch on the context.
+ * Kernel times come from CUDA events recorded on the context's stream
+ * around each kernel when timing is enabled with mp_dp_set_timing. */
+typedef struct {
+    double cells;              /* sum over pairs of |P| * |T| */
+    double dp_ms;              /* packed int16 DP kernel(s) */
+    double rerun_ms;           /* int32 re-run kernel(s) */
+    double tb_ms;              /* traceback + compaction kernels */
+    double pack_ms;            /* input packing kernel */
+    double total_ms;           /* whole device pipeline */
+    int32_t n_waves;
+    int32_t n_rerun;           /* pairs re-run in int32 */
+    int32_t n_launches;        /* kernels launched by the last run */
+    int32_t n_dp_launches;     /* DP kernel launches (int16 + int32) */
+    uint64_t code_bytes;       /* traceback bytes written (algorithmic) */
+} mp_dp_stats;
+
+int mp_dp_set_timing(mp_dp_ctx *ctx, int enable);
+int mp_dp_get_stats(mp_dp_ctx *ctx, mp_dp_stats *s);
+
+/* Number of streaming multiprocessors of the context's device. */
+int mp_dp_num_sms(mp_dp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MP_DP_H */

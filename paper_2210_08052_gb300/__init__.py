@@ -1,0 +1,304 @@
+"""Python binding of the GB300 spliced protein-to-genome DP library.
+
+A thin ctypes layer over ``libmpdp.so`` (``include/mp_dp.h``): every call
+marshals arguments and forwards to the C ABI of the same name.  All of the
+alignment work runs in the library's CUDA kernels; there is no CPU path, and
+importing a function fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SO_PATH = _build.SO
+
+MP_OK, MP_EINVAL, MP_ENOMEM, MP_EBUDGET, MP_ETIMEOUT = 0, -1, -2, -3, -4
+MP_ECUDA, MP_EPENDING, MP_EAGAIN, MP_ETICKET, MP_ESTATE = -5, -6, -7, -8, -9
+MP_ST_RERUN, MP_ST_BADSEQ, MP_ST_BUDGET, MP_ST_TRACE, MP_ST_ERRMASK = 0x1, 0x10, 0x20, 0x40, 0xF0
+MP_PAIR_SCORE_ONLY = 0x1
+OP_NAMES = "MIDFGNUV"
+
+EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_batch_upload",
+            "mp_dp_batch_run", "mp_dp_batch_sync", "mp_dp_batch_download", "mp_dp_batch_free",
+            "mp_dp_submit", "mp_dp_poll", "mp_dp_wait_any", "mp_dp_destroy", "mp_dp_strerror",
+            "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms"]
+
+
+class mp_dp_params(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("e", ctypes.c_int32), ("f", ctypes.c_int32),
+                ("r", ctypes.c_int32), ("stop", ctypes.c_int32),
+                ("mat", (ctypes.c_int8 * 22) * 22),
+                ("splice_model", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("tb_budget_bytes", ctypes.c_uint64), ("force_int32", ctypes.c_int32),
+                ("max_pairs_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class mp_pair(ctypes.Structure):
+    _fields_ = [("prot", ctypes.c_char_p), ("prot_len", ctypes.c_uint32),
+                ("nt", ctypes.c_char_p), ("nt_len", ctypes.c_uint32),
+                ("strand", ctypes.c_int8), ("flags", ctypes.c_uint32)]
+
+
+class mp_result(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("prot_st", ctypes.c_int32), ("prot_en", ctypes.c_int32),
+                ("nt_st", ctypes.c_int32), ("nt_en", ctypes.c_int32),
+                ("n_cigar", ctypes.c_uint32), ("cigar", ctypes.POINTER(ctypes.c_uint32))]
+
+
+class mp_dp_stats(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_double), ("dp_ms", ctypes.c_double), ("rerun_ms", ctypes.c_double),
+                ("tb_ms", ctypes.c_double), ("pack_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("n_waves", ctypes.c_int32), ("n_rerun", ctypes.c_int32), ("n_launches", ctypes.c_int32),
+                ("n_dp_launches", ctypes.c_int32), ("code_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmpdp.so.  Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO_PATH):
+            raise RuntimeError(f"CUDA library not built ({SO_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(SO_PATH)
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        sig = {
+            "mp_dp_default_params": (None, [P(mp_dp_params)]),
+            "mp_dp_init": (ctypes.c_int, [P(vp), P(mp_dp_params), ctypes.c_int]),
+            "mp_dp_align_batch": (ctypes.c_int, [vp, P(mp_pair), ctypes.c_size_t, P(mp_result)]),
+            "mp_dp_batch_upload": (ctypes.c_int, [vp, P(mp_pair), ctypes.c_size_t, P(vp)]),
+            "mp_dp_batch_run": (ctypes.c_int, [vp, vp]),
+            "mp_dp_batch_sync": (ctypes.c_int, [vp]),
+            "mp_dp_batch_download": (ctypes.c_int, [vp, vp, P(mp_result)]),
+            "mp_dp_batch_free": (None, [vp, vp]),
+            "mp_dp_submit": (ctypes.c_int, [vp, P(mp_pair), P(ctypes.c_uint64)]),
+            "mp_dp_poll": (ctypes.c_int, [vp, ctypes.c_uint64, P(mp_result), ctypes.c_int64]),
+            "mp_dp_wait_any": (ctypes.c_int, [vp, P(ctypes.c_uint64), P(mp_result), ctypes.c_int64]),
+            "mp_dp_destroy": (None, [vp]),
+            "mp_dp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "mp_dp_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+            "mp_dp_get_stats": (ctypes.c_int, [vp, P(mp_dp_stats)]),
+            "mp_dp_num_sms": (ctypes.c_int, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class MPError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = lib().mp_dp_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})" if where else f"{msg} ({code})")
+
+
+def _check(rc, where):
+    if rc != MP_OK:
+        raise MPError(rc, where)
+
+
+# ------------------------------------------------------------------ params
+def mp_dp_default_params(**overrides) -> mp_dp_params:
+    p = mp_dp_params()
+    lib().mp_dp_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "mat":
+            m = np.asarray(v, dtype=np.int64)
+            for a in range(22):
+                for b in range(22):
+                    p.mat[a][b] = int(m[a, b])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def params_matrix(p: mp_dp_params) -> np.ndarray:
+    return np.array([[p.mat[a][b] for b in range(22)] for a in range(22)], dtype=np.int32)
+
+
+# ------------------------------------------------------------------- pairs
+class _PairArray:
+    """ctypes array of mp_pair; keeps the encoded sequences alive."""
+
+    def __init__(self, pairs):
+        self.keep = []
+        n = len(pairs)
+        self.arr = (mp_pair * max(n, 1))()
+        for k, p in enumerate(pairs):
+            prot, nt, strand, flags = _unpack_pair(p)
+            self.keep.append(prot)
+            self.keep.append(nt)
+            self.arr[k].prot = prot
+            self.arr[k].prot_len = len(prot)
+            self.arr[k].nt = nt
+            self.arr[k].nt_len = len(nt)
+            self.arr[k].strand = strand
+            self.arr[k].flags = flags
+        self.n = n
+
+
+def _unpack_pair(p):
+    if isinstance(p, (tuple, list)):
+        prot, nt = p[0], p[1]
+        strand = p[2] if len(p) > 2 else 1
+        flags = p[3] if len(p) > 3 else 0
+    else:
+        prot, nt, strand = p.prot, p.nt, getattr(p, "strand", 1)
+        flags = MP_PAIR_SCORE_ONLY if getattr(p, "score_only", False) else 0
+    prot = prot.encode() if isinstance(prot, str) else bytes(prot)
+    nt = nt.encode() if isinstance(nt, str) else bytes(nt)
+    return prot, nt, int(strand), int(flags)
+
+
+def result_dict(r: mp_result) -> dict:
+    cig = [(OP_NAMES[r.cigar[k] & 0xF], r.cigar[k] >> 4) for k in range(r.n_cigar)] if r.n_cigar else []
+    raw = [r.cigar[k] for k in range(r.n_cigar)] if r.n_cigar else []
+    return dict(score=r.score, status=r.status, prot_st=r.prot_st, prot_en=r.prot_en,
+                nt_st=r.nt_st, nt_en=r.nt_en, cigar=cig, cigar_raw=raw)
+
+
+# ------------------------------------------------------------- C-ABI mirror
+def mp_dp_init(params: mp_dp_params | None = None, device: int = 0) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(lib().mp_dp_init(ctypes.byref(ctx), ctypes.byref(params) if params is not None else None, device),
+           "mp_dp_init")
+    return ctx
+
+
+def mp_dp_destroy(ctx) -> None:
+    lib().mp_dp_destroy(ctx)
+
+
+def mp_dp_align_batch(ctx, pairs, raw: bool = False):
+    """Align a list of pairs end to end.  Returns a list of result dicts, or
+    with raw=True a dict of numpy arrays (scores, status, coordinates, CIGAR
+    offsets and one flat op array)."""
+    pa = _PairArray(pairs)
+    res = (mp_result * max(pa.n, 1))()
+    _check(lib().mp_dp_align_batch(ctx, pa.arr, pa.n, res), "mp_dp_align_batch")
+    return _results(res, pa.n, raw)
+
+
+def _results(res, n, raw):
+    if not raw:
+        return [result_dict(res[k]) for k in range(n)]
+    buf = np.frombuffer(res, dtype=np.dtype([("score", "<i4"), ("status", "<i4"), ("prot_st", "<i4"),
+                                             ("prot_en", "<i4"), ("nt_st", "<i4"), ("nt_en", "<i4"),
+                                             ("n_cigar", "<u4"), ("pad", "<u4"), ("cigar", "<u8")]),
+                        count=n)
+    return buf.copy()
+
+
+def mp_dp_batch_upload(ctx, pairs):
+    pa = _PairArray(pairs)
+    b = ctypes.c_void_p()
+    _check(lib().mp_dp_batch_upload(ctx, pa.arr, pa.n, ctypes.byref(b)), "mp_dp_batch_upload")
+    return b, pa.n
+
+
+def mp_dp_batch_run(ctx, batch) -> None:
+    _check(lib().mp_dp_batch_run(ctx, batch[0]), "mp_dp_batch_run")
+
+
+def mp_dp_batch_sync(ctx) -> None:
+    _check(lib().mp_dp_batch_sync(ctx), "mp_dp_batch_sync")
+
+
+def mp_dp_batch_download(ctx, batch, raw: bool = False):
+    n = batch[1]
+    res = (mp_result * max(n, 1))()
+    _check(lib().mp_dp_batch_download(ctx, batch[0], res), "mp_dp_batch_download")
+    return _results(res, n, raw)
+
+
+def mp_dp_batch_free(ctx, batch) -> None:
+    lib().mp_dp_batch_free(ctx, batch[0])
+
+
+def mp_dp_submit(ctx, pair) -> int:
+    pa = _PairArray([pair])
+    t = ctypes.c_uint64()
+    rc = lib().mp_dp_submit(ctx, pa.arr, ctypes.byref(t))
+    if rc == MP_EAGAIN:
+        return -1
+    _check(rc, "mp_dp_submit")
+    return t.value
+
+
+def mp_dp_poll(ctx, ticket: int, timeout_us: int = -1):
+    """Result dict, or None while pending (MP_EPENDING / MP_ETIMEOUT)."""
+    r = mp_result()
+    rc = lib().mp_dp_poll(ctx, ticket, ctypes.byref(r), timeout_us)
+    if rc in (MP_EPENDING, MP_ETIMEOUT):
+        return None
+    _check(rc, "mp_dp_poll")
+    return result_dict(r)
+
+
+def mp_dp_wait_any(ctx, timeout_us: int = -1):
+    """(ticket, result dict) of the next finished request, or None."""
+    r = mp_result()
+    t = ctypes.c_uint64()
+    rc = lib().mp_dp_wait_any(ctx, ctypes.byref(t), ctypes.byref(r), timeout_us)
+    if rc in (MP_EPENDING, MP_ETIMEOUT):
+        return None
+    _check(rc, "mp_dp_wait_any")
+    return t.value, result_dict(r)
+
+
+def mp_dp_set_timing(ctx, enable: bool = True) -> None:
+    _check(lib().mp_dp_set_timing(ctx, 1 if enable else 0), "mp_dp_set_timing")
+
+
+def mp_dp_get_stats(ctx) -> dict:
+    s = mp_dp_stats()
+    _check(lib().mp_dp_get_stats(ctx, ctypes.byref(s)), "mp_dp_get_stats")
+    return {k: getattr(s, k) for k, _ in mp_dp_stats._fields_}
+
+
+def mp_dp_num_sms(ctx) -> int:
+    return lib().mp_dp_num_sms(ctx)
+
+
+def mp_dp_strerror(code: int) -> str:
+    return lib().mp_dp_strerror(code).decode()
+
+
+class Context:
+    """Owning wrapper: ``with Context() as ctx: ctx.align(pairs)``."""
+
+    def __init__(self, params: mp_dp_params | None = None, device: int = 0, **overrides):
+        if params is None and overrides:
+            params = mp_dp_default_params(**overrides)
+        self.params = params
+        self.ctx = mp_dp_init(params, device)
+
+    def align(self, pairs, raw=False):
+        return mp_dp_align_batch(self.ctx, pairs, raw)
+
+    def close(self):
+        if self.ctx:
+            mp_dp_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,663 @@
+// Spliced protein-to-genome DP, Li 2022 Eq. 7 (Methods, "DP for
+// protein-to-genome alignment"), local mode, with the final splice model
+// (Methods, "Splice models").  Hand-written for sm_103a.
+//
+// Layout of the computation
+// -------------------------
+// One warp owns one (protein, region) pair.  The protein is cut into strips
+// of 64 residues; lane l holds residues 2l ("lo") and 2l+1 ("hi") of the
+// strip.  The warp sweeps anti-diagonals: at step t the lo cell of lane l is
+// genome position ii = t - 2l and the hi cell is ii - 1, so every cell
+// depends only on cells of earlier steps:
+//   - the residue to the left (j-1) comes from lane l-1's hi cell of the
+//     previous step (one __shfl_up_sync of a packed [H, I] word), or, for
+//     the hi cell, from the lane's own lo cell of the previous step;
+//   - genome-direction terms (i-1, i-2, i-3) come from the lane's own
+//     register history.
+// Strip s+1 reads the last residue of strip s from a per-pair boundary
+// buffer ([H, I] per genome position).
+//
+// Arithmetic
+// ----------
+// The int16 path keeps each state as two biased 16-bit lanes in one 32-bit
+// register (value v stored as v + 32768).  Maxima use max.u16x2; additions
+// of packed penalties are plain 32-bit adds, exact because no half crosses
+// 0 or 65536.  A pair whose best score reaches 32000 is re-run in the int32
+// instantiation of the same kernel.
+//
+// Traceback codes
+// ---------------
+// Each cell stores 16 bits: STOP (H == 0), one "term >= H" bit per H term of
+// Eq. 7 in printed order, and one "open >= extend" bit per gap and intron
+// state.  The traceback takes the first set term bit, which realises the
+// earliest-term-wins tie rule.  Bits are produced as sign bits of packed
+// differences and gathered with sign-replicating byte permutes.
+#include "mp_internal.cuh"
+
+namespace mpdp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- helpers
+template <uint32_t S>
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "n"(S));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+// ------------------------------------------------------ genetic code table
+constexpr char kAAOrder[] = "ARNDCQEGHILKMFPSTWYV*";
+// NCBI table 1 with codons enumerated as A, C, G, T in each position.
+constexpr char kCodeACGT[] = "KNKNTTTTRSRSIIMIQHQHPPPPRRRRLLLLEDEDAAAAGGGGVVVV*Y*YSSSS*CWCLFLF";
+
+constexpr int aa_index(char c)
+{
+    for (int k = 0; k < 21; ++k)
+        if (kAAOrder[k] == c) return k;
+    return 21;
+}
+
+struct CodeTable {
+    int8_t v[64];
+};
+
+constexpr CodeTable make_code_table()
+{
+    CodeTable t{};
+    for (int k = 0; k < 64; ++k) t.v[k] = static_cast<int8_t>(aa_index(kCodeACGT[k]));
+    return t;
+}
+
+__constant__ CodeTable c_code = make_code_table();
+
+// --------------------------------------------------------- splice signals
+// Final splice model.  Bases: 0 A, 1 C, 2 G, 3 T; v* false = outside T,
+// which matches no motif.
+__device__ __forceinline__ int donor_score(int b1, int b2, int b3, bool v1, bool v2, bool v3)
+{
+    // d(x) from T[x+1..x+3]: GT[AG] 0, GT[CT] 8, GC 15, AT 21, else 30
+    if (v1 && v2) {
+        if (b1 == 2 && b2 == 3) {
+            if (v3) return (b3 == 0 || b3 == 2) ? 0 : 8;
+            return 30;
+        }
+        if (b1 == 2 && b2 == 1) return 15;
+        if (b1 == 0 && b2 == 3) return 21;
+    }
+    return 30;
+}
+
+__device__ __forceinline__ int acceptor_score(int b1, int b2, int b3, bool v1, bool v2, bool v3)
+{
+    // a(x) from T[x-2..x]: [CT]AG 0, [AG]AG 8, AC (last two) 21, else 30
+    if (v2 && v3 && b2 == 0) {
+        if (b3 == 2) {
+            if (!v1) return 30;
+            return (b1 == 1 || b1 == 3) ? 0 : 8;
+        }
+        if (b3 == 1) return 21;
+    }
+    return 30;
+}
+
+// Per-genome-position record for the lo cell at 0-based position ii
+// (1-based i = ii + 1):
+//   x = [r + d(i+1), r + d(i)]   (16-bit halves, lo first)
+//   y = [a(i), a(i-1)]
+//   z = byte offset of the profile row of the codon ending at i
+__device__ __forceinline__ uint4 make_record(const uint32_t *g, int n, int ii, int r)
+{
+    const int s = ii - 3;                  // window T0[ii-3 .. ii+4]
+    const int w = s >> 4;                  // floor division (s may be negative)
+    const int sh = (s & 15) * 2;
+    const uint64_t pair64 = (static_cast<uint64_t>(g[w + 1]) << 32) | g[w];
+    const uint32_t win = static_cast<uint32_t>(pair64 >> sh);
+    int b[8];
+    bool v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        b[k] = (win >> (2 * k)) & 3;
+        v[k] = static_cast<unsigned>(s + k) < static_cast<unsigned>(n);
+    }
+    const int aa = (v[1] && v[3]) ? c_code.v[b[1] * 16 + b[2] * 4 + b[3]] : 21;
+    const int dC = donor_score(b[5], b[6], b[7], v[5], v[6], v[7]);     // d(i+1)
+    const int dB = donor_score(b[4], b[5], b[6], v[4], v[5], v[6]);     // d(i)
+    const int aA = acceptor_score(b[1], b[2], b[3], v[1], v[2], v[3]);  // a(i)
+    const int aC = acceptor_score(b[0], b[1], b[2], v[0], v[1], v[2]);  // a(i-1)
+    uint4 rec;
+    rec.x = static_cast<uint32_t>(r + dC) | (static_cast<uint32_t>(r + dB) << 16);
+    rec.y = static_cast<uint32_t>(aA) | (static_cast<uint32_t>(aC) << 16);
+    rec.z = static_cast<uint32_t>(aa) * 128u;
+    rec.w = 0;
+    return rec;
+}
+
+__device__ __forceinline__ int subst_score(const ScoreParams &sp, int aa, int pc)
+{
+    if (aa == 21) return -512;             // no complete codon (i < 3)
+    if (aa == 20) return -sp.stop;         // stop codon against any residue
+    return sp.mat[aa][pc];
+}
+
+// --------------------------------------------------------------- smem
+template <typename BndT>
+struct WarpSmem {
+    uint4 ring[kRing + kRingPad];
+    uint32_t prof[kProfRows * 32];
+    BndT bin[kChunk];
+    BndT bout[kChunk];
+};
+
+// ================================================================ int16 ops
+struct Ops16 {
+    using Bnd = uint32_t;                  // [H, I] biased 16-bit
+    static constexpr uint32_t Z = 0x80008000u;      // biased 0 in both halves
+    static constexpr uint32_t NEGV = 0x40004000u;   // biased -16384
+    static constexpr uint32_t K = 0x80008000u;
+    static constexpr uint32_t SBIAS = 0x02000200u;  // profile entries hold s + 512
+    static constexpr Bnd kBnd0 = 0x40008000u;       // column 0: H = 0, I = -inf
+
+    struct Consts {
+        uint32_t QE, E, F, KF;             // packed q+e, e, f and K - f
+    };
+    struct State {
+        uint32_t H1, H2, H3, L0, L1, L2, L3, IL, D1, D2, D3, A1, B1, C1;
+        uint32_t VD1, VD2, VA1, VA2, X1;
+        uint32_t TC, bklo, bkhi;
+    };
+
+    static __device__ __forceinline__ Consts consts(const ScoreParams &sp)
+    {
+        Consts c;
+        const uint32_t qe = sp.q + sp.e;
+        c.QE = qe | (qe << 16);
+        c.E = static_cast<uint32_t>(sp.e) | (static_cast<uint32_t>(sp.e) << 16);
+        c.F = static_cast<uint32_t>(sp.f) | (static_cast<uint32_t>(sp.f) << 16);
+        c.KF = K - c.F;
+        return c;
+    }
+
+    static __device__ __forceinline__ uint32_t prof_entry(int slo, int shi)
+    {
+        return static_cast<uint32_t>(slo + 512) | (static_cast<uint32_t>(shi + 512) << 16);
+    }
+
+    // State before step 0: every cell not yet reached is outside the matrix
+    // (-inf) except the row-0 cell at ii = -1, where H = 0.  w0 is the
+    // boundary entry at ii = 0 (used by lane 0).
+    static __device__ __forceinline__ void init(State &s, int lane, Bnd w0, uint4 recm1, uint4 recm2,
+                                                uint32_t xm1)
+    {
+        s.H1 = Z; s.H2 = NEGV; s.H3 = NEGV;
+        s.L1 = Z; s.L2 = NEGV; s.L3 = NEGV;
+        s.L0 = (lane == 0) ? ((w0 & 0xffffu) | 0x80000000u) : NEGV;
+        s.IL = (lane == 0) ? ((w0 >> 16) | 0x40000000u) : NEGV;
+        s.D1 = s.D2 = s.D3 = NEGV;
+        s.A1 = s.B1 = s.C1 = NEGV;
+        s.VD1 = recm1.x; s.VD2 = recm2.x;
+        s.VA1 = recm1.y; s.VA2 = recm2.y;
+        s.X1 = xm1;
+        s.TC = 0xffffu; s.bklo = 0; s.bkhi = 0;
+    }
+
+    // One anti-diagonal step.  Returns the packed 2x16-bit code word.
+    template <bool MASKED>
+    static __device__ __forceinline__ uint32_t step(State &s, const Consts &c, const uint4 rec,
+                                                    const uint32_t *prof_lane, Bnd bin, Bnd *bout,
+                                                    int lane, int ii, int n)
+    {
+        const uint32_t VD0 = rec.x, VA0 = rec.y;
+        const uint32_t X0 = *reinterpret_cast<const uint32_t *>(
+            reinterpret_cast<const char *>(prof_lane) + rec.z);
+        const uint32_t S = prmt<0x7610>(X0, s.X1);        // lo: s(i, 2l); hi: s(i-1, 2l+1)
+        const uint32_t M = s.L3 + S - SBIAS;
+        const uint32_t Iopen = s.L0 - c.QE, Iext = s.IL - c.E;
+        uint32_t I0 = vmax(Iopen, Iext);
+        const uint32_t Dopen = s.H3 - c.QE, Dext = s.D3 - c.E;
+        uint32_t D0 = vmax(Dopen, Dext);
+        const uint32_t Aopen = s.H1 - s.VD2;              // H[i-1][j] - r - d(i-1)
+        uint32_t A0 = vmax(Aopen, s.A1);
+        const uint32_t Bopen = s.L1 - s.VD1;              // H[i-1][j-1] - r - d(i)
+        uint32_t B0 = vmax(Bopen, s.B1);
+        const uint32_t Copen = s.L1 - VD0;                // H[i-1][j-1] - r - d(i+1)
+        uint32_t C0 = vmax(Copen, s.C1);
+        const uint32_t Fm = vmax(s.L1, s.L2) - c.F;
+        const uint32_t Gm = vmax(s.H1, s.H2) - c.F;
+        const uint32_t Ap = A0 - VA0;                     // A - a(i)
+        const uint32_t Bp = B0 - s.VA2;                   // B - a(i-2)
+        const uint32_t Cp = C0 - s.VA1;                   // C - a(i-1)
+        uint32_t H0 = vmax(vmax(vmax(M, I0), vmax(D0, Fm)), vmax(vmax(Gm, Ap), vmax(vmax(Bp, Cp), Z)));
+
+        uint32_t vmask = 0xffffffffu;
+        if (MASKED) {
+            // cells before row 1 are outside the matrix; ii = -1 is row 0
+            const uint32_t kill = (ii < 0 ? 0x0000ffffu : 0u) | (ii < 1 ? 0xffff0000u : 0u);
+            const uint32_t row0 = (ii == -1 ? 0x0000ffffu : 0u) | (ii == 0 ? 0xffff0000u : 0u);
+            const uint32_t hforce = (row0 & Z) | (~row0 & NEGV);
+            H0 = (H0 & ~kill) | (hforce & kill);
+            I0 = (I0 & ~kill) | (NEGV & kill);
+            D0 = (D0 & ~kill) | (NEGV & kill);
+            A0 = (A0 & ~kill) | (NEGV & kill);
+            B0 = (B0 & ~kill) | (NEGV & kill);
+            C0 = (C0 & ~kill) | (NEGV & kill);
+            vmask = ((ii >= 0 && ii < n) ? 0x0000ffffu : 0u) | ((ii >= 1 && ii <= n) ? 0xffff0000u : 0u);
+        }
+
+        // "a >= b" per half lands in bits 15 and 31 of a - b + K
+        const uint32_t g0 = Z - H0 + K;
+        const uint32_t g1 = M - H0 + K;
+        const uint32_t g2 = I0 - H0 + K;
+        const uint32_t g3 = D0 - H0 + K;
+        const uint32_t g4 = s.L1 - H0 + c.KF;
+        const uint32_t g5 = s.L2 - H0 + c.KF;
+        const uint32_t g6 = s.H1 - H0 + c.KF;
+        const uint32_t g7 = s.H2 - H0 + c.KF;
+        const uint32_t g8 = Ap - H0 + K;
+        const uint32_t g9 = Bp - H0 + K;
+        const uint32_t g10 = Cp - H0 + K;
+        const uint32_t g11 = Iopen - Iext + K;
+        const uint32_t g12 = Dopen - Dext + K;
+        const uint32_t g13 = Aopen - s.A1 + K;
+        const uint32_t g14 = Bopen - s.B1 + K;
+        const uint32_t g15 = Copen - s.C1 + K;
+        // bytes: [flag k lo, flag k hi, flag k+8 lo, flag k+8 hi], sign-replicated
+        uint32_t acc = prmt<0xFDB9>(g0, g8) & 0x01010101u;
+        acc |= prmt<0xFDB9>(g1, g9) & 0x02020202u;
+        acc |= prmt<0xFDB9>(g2, g10) & 0x04040404u;
+        acc |= prmt<0xFDB9>(g3, g11) & 0x08080808u;
+        acc |= prmt<0xFDB9>(g4, g12) & 0x10101010u;
+        acc |= prmt<0xFDB9>(g5, g13) & 0x20202020u;
+        acc |= prmt<0xFDB9>(g6, g14) & 0x40404040u;
+        acc |= prmt<0xFDB9>(g7, g15) & 0x80808080u;
+        const uint32_t code = prmt<0x3120>(acc, 0u);     // [lo code16, hi code16]
+
+        // hand [H, I] of the hi cell to the next lane; lane 0 takes the strip boundary
+        const uint32_t W = prmt<0x7632>(H0, I0);
+        uint32_t R = __shfl_up_sync(kFull, W, 1);
+        if (lane == 0) R = bin;
+        if (lane == 31) *bout = W;
+        s.L3 = s.L2; s.L2 = s.L1; s.L1 = s.L0;
+        s.L0 = prmt<0x5410>(R, H0);
+        s.IL = prmt<0x5432>(R, I0);
+        s.H3 = s.H2; s.H2 = s.H1; s.H1 = H0;
+        s.D3 = s.D2; s.D2 = s.D1; s.D1 = D0;
+        s.A1 = A0; s.B1 = B0; s.C1 = C0;
+        s.VD2 = s.VD1; s.VD1 = VD0;
+        s.VA2 = s.VA1; s.VA1 = VA0;
+        s.X1 = X0;
+
+        // best cell: key = H << 16 | (0xffff - step within chunk); the
+        // largest key is the largest H at its first step
+        const uint32_t Hm = H0 & vmask;
+        s.bklo = max(s.bklo, prmt<0x5410>(s.TC, Hm));
+        s.bkhi = max(s.bkhi, prmt<0x7610>(s.TC, Hm));
+        s.TC -= 1;
+        return code;
+    }
+
+    // Extract (score, step) of one half's best key; score < 0 if none.
+    static __device__ __forceinline__ void take_best(const State &s, int half, int t0, int &score, int &t)
+    {
+        const uint32_t k = half ? s.bkhi : s.bklo;
+        score = static_cast<int>(k >> 16) - 32768;
+        t = t0 + static_cast<int>(0xffffu - (k & 0xffffu));
+    }
+    static __device__ __forceinline__ void reset_best(State &s)
+    {
+        s.TC = 0xffffu; s.bklo = 0; s.bkhi = 0;
+    }
+};
+
+// ================================================================ int32 ops
+struct V2 {
+    int32_t lo, hi;
+};
+
+__device__ __forceinline__ V2 mx(V2 a, V2 b) { return V2{max(a.lo, b.lo), max(a.hi, b.hi)}; }
+__device__ __forceinline__ V2 sub(V2 a, V2 b) { return V2{a.lo - b.lo, a.hi - b.hi}; }
+__device__ __forceinline__ V2 subc(V2 a, int32_t b) { return V2{a.lo - b, a.hi - b}; }
+__device__ __forceinline__ V2 add(V2 a, V2 b) { return V2{a.lo + b.lo, a.hi + b.hi}; }
+__device__ __forceinline__ V2 unpack16(uint32_t w)
+{
+    return V2{static_cast<int32_t>(w & 0xffffu), static_cast<int32_t>(w >> 16)};
+}
+
+struct Ops32 {
+    struct Bnd {
+        int32_t h, i;
+    };
+    static constexpr int32_t NEG = -(1 << 28);
+    static constexpr Bnd kBnd0 = {0, NEG};
+
+    struct Consts {
+        int32_t qe, e, f;
+    };
+    struct State {
+        V2 H1, H2, H3, L0, L1, L2, L3, IL, D1, D2, D3, A1, B1, C1;
+        V2 VD1, VD2, VA1, VA2;
+        uint32_t X1;
+        int32_t bslo, bshi, btlo, bthi, t;
+    };
+
+    static __device__ __forceinline__ Consts consts(const ScoreParams &sp)
+    {
+        return Consts{sp.q + sp.e, sp.e, sp.f};
+    }
+
+    static __device__ __forceinline__ uint32_t prof_entry(int slo, int shi)
+    {
+        return (static_cast<uint32_t>(slo) & 0xffffu) | (static_cast<uint32_t>(shi) << 16);
+    }
+
+    static __device__ __forceinline__ void init(State &s, int lane, Bnd w0, uint4 recm1, uint4 recm2,
+                                                uint32_t xm1)
+    {
+        const V2 ng{NEG, NEG};
+        s.H1 = V2{0, 0}; s.H2 = ng; s.H3 = ng;
+        s.L1 = V2{0, 0}; s.L2 = ng; s.L3 = ng;
+        s.L0 = (lane == 0) ? V2{w0.h, 0} : ng;
+        s.IL = (lane == 0) ? V2{w0.i, NEG} : ng;
+        s.D1 = s.D2 = s.D3 = ng;
+        s.A1 = s.B1 = s.C1 = ng;
+        s.VD1 = unpack16(recm1.x); s.VD2 = unpack16(recm2.x);
+        s.VA1 = unpack16(recm1.y); s.VA2 = unpack16(recm2.y);
+        s.X1 = xm1;
+        s.bslo = s.bshi = 0; s.btlo = s.bthi = 0; s.t = 0;
+    }
+
+    template <bool MASKED>
+    static __device__ __forceinline__ uint32_t step(State &s, const Consts &c, const uint4 rec,
+                                                    const uint32_t *prof_lane, Bnd bin, Bnd *bout,
+                                                    int lane, int ii, int n)
+    {
+        const V2 VD0 = unpack16(rec.x), VA0 = unpack16(rec.y);
+        const uint32_t X0 = *reinterpret_cast<const uint32_t *>(
+            reinterpret_cast<const char *>(prof_lane) + rec.z);
+        const V2 S{static_cast<int32_t>(X0 << 16) >> 16, static_cast<int32_t>(s.X1) >> 16};
+        const V2 M = add(s.L3, S);
+        const V2 Iopen = subc(s.L0, c.qe), Iext = subc(s.IL, c.e);
+        V2 I0 = mx(Iopen, Iext);
+        const V2 Dopen = subc(s.H3, c.qe), Dext = subc(s.D3, c.e);
+        V2 D0 = mx(Dopen, Dext);
+        const V2 Aopen = sub(s.H1, s.VD2);
+        V2 A0 = mx(Aopen, s.A1);
+        const V2 Bopen = sub(s.L1, s.VD1);
+        V2 B0 = mx(Bopen, s.B1);
+        const V2 Copen = sub(s.L1, VD0);
+        V2 C0 = mx(Copen, s.C1);
+        const V2 Fm = subc(mx(s.L1, s.L2), c.f);
+        const V2 Gm = subc(mx(s.H1, s.H2), c.f);
+        const V2 Ap = sub(A0, VA0), Bp = sub(B0, s.VA2), Cp = sub(C0, s.VA1);
+        V2 H0 = mx(mx(mx(M, I0), mx(D0, Fm)), mx(mx(Gm, Ap), mx(mx(Bp, Cp), V2{0, 0})));
+
+        bool vlo = true, vhi = true;
+        if (MASKED) {
+            if (ii < 0) { H0.lo = (ii == -1) ? 0 : NEG; I0.lo = D0.lo = A0.lo = B0.lo = C0.lo = NEG; }
+            if (ii < 1) { H0.hi = (ii == 0) ? 0 : NEG; I0.hi = D0.hi = A0.hi = B0.hi = C0.hi = NEG; }
+            vlo = ii >= 0 && ii < n;
+            vhi = ii >= 1 && ii <= n;
+        }
+
+        // sign of a - b is set iff a < b: the flag is its complement
+        const V2 d[16] = {sub(V2{0, 0}, H0), sub(M, H0), sub(I0, H0), sub(D0, H0),
+                          subc(sub(s.L1, H0), c.f), subc(sub(s.L2, H0), c.f),
+                          subc(sub(s.H1, H0), c.f), subc(sub(s.H2, H0), c.f),
+                          sub(Ap, H0), sub(Bp, H0), sub(Cp, H0),
+                          sub(Iopen, Iext), sub(Dopen, Dext), sub(Aopen, s.A1),
+                          sub(Bopen, s.B1), sub(Copen, s.C1)};
+        uint32_t acc = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            acc |= ~prmt<0xFFBB>(static_cast<uint32_t>(d[k].lo), static_cast<uint32_t>(d[k].hi)) &
+                   (0x00010001u << k);
+        const uint32_t code = acc;
+
+        const int32_t Wh = H0.hi, Wi = I0.hi;
+        int32_t Rh = __shfl_up_sync(kFull, Wh, 1);
+        int32_t Ri = __shfl_up_sync(kFull, Wi, 1);
+        if (lane == 0) { Rh = bin.h; Ri = bin.i; }
+        if (lane == 31) *bout = Bnd{Wh, Wi};
+        s.L3 = s.L2; s.L2 = s.L1; s.L1 = s.L0;
+        s.L0 = V2{Rh, H0.lo};
+        s.IL = V2{Ri, I0.lo};
+        s.H3 = s.H2; s.H2 = s.H1; s.H1 = H0;
+        s.D3 = s.D2; s.D2 = s.D1; s.D1 = D0;
+        s.A1 = A0; s.B1 = B0; s.C1 = C0;
+        s.VD2 = s.VD1; s.VD1 = VD0;
+        s.VA2 = s.VA1; s.VA1 = VA0;
+        s.X1 = X0;
+
+        if (vlo && H0.lo > s.bslo) { s.bslo = H0.lo; s.btlo = s.t; }
+        if (vhi && H0.hi > s.bshi) { s.bshi = H0.hi; s.bthi = s.t; }
+        s.t += 1;
+        return code;
+    }
+
+    static __device__ __forceinline__ void take_best(const State &s, int half, int t0, int &score, int &t)
+    {
+        (void)t0;
+        score = half ? s.bshi : s.bslo;
+        t = half ? s.bthi : s.btlo;
+        if (score <= 0) score = -1;
+    }
+    static __device__ __forceinline__ void reset_best(State &s) { (void)s; }
+};
+
+// ============================================================ strip driver
+struct Best {
+    int score, ii, jj;
+};
+
+__device__ __forceinline__ bool better(int s, int i, int j, const Best &b)
+{
+    return s > b.score || (s == b.score && (i < b.ii || (i == b.ii && j < b.jj)));
+}
+
+template <typename Ops, bool MASKED, bool STORE>
+__device__ __forceinline__ void run_chunk(typename Ops::State &st, const typename Ops::Consts &c,
+                                          WarpSmem<typename Ops::Bnd> &sm, int lane, int t0, int n,
+                                          uint8_t *code_strip)
+{
+#pragma unroll 1
+    for (int b = 0; b < kChunk / kBody; ++b) {
+        const int tb = t0 + b * kBody;
+        const uint4 *recp = &sm.ring[(tb - 2 * lane) & (kRing - 1)];
+        uint32_t cw[kBody];
+#pragma unroll
+        for (int k = 0; k < kBody; ++k) {
+            cw[k] = Ops::template step<MASKED>(st, c, recp[k], sm.prof + lane, sm.bin[b * kBody + k],
+                                               &sm.bout[b * kBody + k], lane, tb + k - 2 * lane, n);
+            if (STORE && (k & 3) == 3) {
+                uint4 v = make_uint4(cw[k - 3], cw[k - 2], cw[k - 1], cw[k]);
+                *reinterpret_cast<uint4 *>(code_strip + static_cast<size_t>(tb + k - 3) * kStepBytes +
+                                           lane * 16) = v;
+            }
+        }
+    }
+}
+
+template <typename Ops>
+__device__ void align_pair(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint32_t p, int lane)
+{
+    using Bnd = typename Ops::Bnd;
+    const PairDesc pd = a.pairs[p];
+    const int n = static_cast<int>(pd.nt_len);
+    const int m = static_cast<int>(pd.prot_len);
+    const bool store = !(pd.flags & PF_SCORE_ONLY);
+    const uint32_t *g = a.nt2 + pd.nt_word_off;
+    const uint8_t *P = a.prot + pd.prot_off;
+    Bnd *bnd = reinterpret_cast<Bnd *>(a.bnd) + pd.bnd_off + kBndPad;   // bnd[ii], ii >= -64
+    const typename Ops::Consts c = Ops::consts(a.sp);
+    const int nsteps = n + kStripW - 1;
+    const int nchunks = (nsteps + kChunk - 1) / kChunk;
+    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes;
+    const int nstrips = (m + kStripW - 1) / kStripW;
+
+    // column 0 of the matrix: H = 0, I = -inf at every genome position
+    for (int k = lane; k < nchunks * kChunk + 2 * kBndPad; k += 32) bnd[k - kBndPad] = Ops::kBnd0;
+    __syncwarp();
+
+    Best best{0, 0x7fffffff, 0x7fffffff};
+    for (int s = 0; s < nstrips; ++s) {
+        // profile: prof[aa][lane] = [s(aa, P[2l]), s(aa, P[2l+1])]
+        const int jlo = s * kStripW + 2 * lane, jhi = jlo + 1;
+        const int plo = jlo < m ? P[jlo] : 21, phi = jhi < m ? P[jhi] : 21;
+#pragma unroll 2
+        for (int aa = 0; aa < kProfRows; ++aa)
+            sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), subst_score(a.sp, aa, phi));
+        // records for ii in [-96, 95]
+        for (int ii = -kChunk + lane; ii < kChunk; ii += 32) {
+            const uint4 rec = make_record(g, n, ii, a.sp.r);
+            const int slot = ii & (kRing - 1);
+            sm.ring[slot] = rec;
+            if (slot < kRingPad) sm.ring[slot + kRing] = rec;
+        }
+        __syncwarp();
+        typename Ops::State st;
+        {
+            const int ii0 = -2 * lane;
+            const uint4 rm1 = sm.ring[(ii0 - 1) & (kRing - 1)];
+            const uint4 rm2 = sm.ring[(ii0 - 2) & (kRing - 1)];
+            const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
+            Ops::init(st, lane, bnd[0], rm1, rm2, xm1);
+        }
+        uint8_t *code_strip = a.codes + pd.code_off + static_cast<size_t>(s) * strip_bytes;
+
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int t0 = ch * kChunk;
+            if (ch > 0) {
+                for (int ii = t0 + lane; ii < t0 + kChunk; ii += 32) {
+                    const uint4 rec = make_record(g, n, ii, a.sp.r);
+                    const int slot = ii & (kRing - 1);
+                    sm.ring[slot] = rec;
+                    if (slot < kRingPad) sm.ring[slot + kRing] = rec;
+                }
+            }
+            for (int k = lane; k < kChunk; k += 32) sm.bin[k] = bnd[t0 + 1 + k];
+            __syncwarp();
+            const bool masked = (t0 < kStripW) || (t0 + kChunk > n);
+            if (masked) {
+                if (store) run_chunk<Ops, true, true>(st, c, sm, lane, t0, n, code_strip);
+                else run_chunk<Ops, true, false>(st, c, sm, lane, t0, n, code_strip);
+            } else {
+                if (store) run_chunk<Ops, false, true>(st, c, sm, lane, t0, n, code_strip);
+                else run_chunk<Ops, false, false>(st, c, sm, lane, t0, n, code_strip);
+            }
+            __syncwarp();
+            for (int k = lane; k < kChunk; k += 32) bnd[t0 + k - (kStripW - 1)] = sm.bout[k];
+            // fold this chunk's best cells into the running best
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int sc, t;
+                Ops::take_best(st, h, t0, sc, t);
+                const int jj = s * kStripW + 2 * lane + h;
+                const int ii = t - 2 * lane - h;
+                if (sc > 0 && jj < m && better(sc, ii, jj, best)) best = Best{sc, ii, jj};
+            }
+            Ops::reset_best(st);
+            __syncwarp();
+        }
+    }
+    // warp reduction of (score desc, ii asc, jj asc)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        Best o;
+        o.score = __shfl_xor_sync(kFull, best.score, off);
+        o.ii = __shfl_xor_sync(kFull, best.ii, off);
+        o.jj = __shfl_xor_sync(kFull, best.jj, off);
+        if (better(o.score, o.ii, o.jj, best)) best = o;
+    }
+    if (lane == 0) {
+        PairOut &o = a.out[p];
+        o.score = best.score;
+        o.best_ii = best.score > 0 ? best.ii : -1;
+        o.best_jj = best.score > 0 ? best.jj : -1;
+        if (sizeof(Bnd) == 4 && best.score >= kOverflowT) {
+            o.status |= MP_ST_RERUN;
+            const uint32_t slot = atomicAdd(a.rerun_count, 1u);
+            a.rerun_list[slot] = p;
+        }
+    }
+    __syncwarp();
+}
+
+template <typename Ops>
+__global__ void __launch_bounds__(kWarpsPerCta * 32) dp_kernel(const DPArgs a, int rerun_only)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using SM = WarpSmem<typename Ops::Bnd>;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    SM &sm = reinterpret_cast<SM *>(smem_raw)[warp];
+    const uint32_t *list = rerun_only ? a.rerun_list : a.work;
+    const uint32_t count = rerun_only ? *a.rerun_count : a.n_work;
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(a.head, 1u);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= count) break;
+        const uint32_t p = list[idx];
+        if (a.pairs[p].flags & (PF_SKIP | PF_BADSEQ)) continue;
+        align_pair<Ops>(a, sm, p, lane);
+    }
+}
+
+}  // namespace
+
+size_t dp16_smem_bytes() { return sizeof(WarpSmem<Ops16::Bnd>) * kWarpsPerCta; }
+size_t dp32_smem_bytes() { return sizeof(WarpSmem<Ops32::Bnd>) * kWarpsPerCta; }
+
+static int blocks_per_sm(const void *fn, size_t smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kWarpsPerCta * 32, smem) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+int dp16_blocks_per_sm()
+{
+    static int nb = -1;
+    if (nb < 0) {
+        cudaFuncSetAttribute(dp_kernel<Ops16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(dp16_smem_bytes()));
+        nb = blocks_per_sm(reinterpret_cast<const void *>(dp_kernel<Ops16>), dp16_smem_bytes());
+    }
+    return nb;
+}
+
+int dp32_blocks_per_sm()
+{
+    static int nb = -1;
+    if (nb < 0) {
+        cudaFuncSetAttribute(dp_kernel<Ops32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(dp32_smem_bytes()));
+        nb = blocks_per_sm(reinterpret_cast<const void *>(dp_kernel<Ops32>), dp32_smem_bytes());
+    }
+    return nb;
+}
+
+cudaError_t launch_dp16(const DPArgs &a, int grid, cudaStream_t st)
+{
+    dp16_blocks_per_sm();
+    dp_kernel<Ops16><<<grid, kWarpsPerCta * 32, dp16_smem_bytes(), st>>>(a, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t st)
+{
+    dp32_blocks_per_sm();
+    dp_kernel<Ops32><<<grid, kWarpsPerCta * 32, dp32_smem_bytes(), st>>>(a, rerun_only ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace mpdp

@@ -1,0 +1,108 @@
+// Internal device-side definitions shared by the kernels and the runtime.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mp_dp.h"
+
+namespace mpdp {
+
+// ---- geometry -----------------------------------------------------------
+constexpr int kStripW = 64;     // residues per strip: two per lane
+constexpr int kChunk = 96;      // DP steps per chunk (record / boundary staging)
+constexpr int kBody = 12;       // steps per unrolled body (multiple of 3 and 4)
+constexpr int kRing = 256;      // per-nt record ring entries
+constexpr int kRingPad = 12;    // mirrored entries so a body never wraps
+constexpr int kProfRows = 22;   // translated amino acid 0..19, stop 20, no codon 21
+constexpr int kBndPad = 64;     // boundary entries before genome position 0
+constexpr int kWarpsPerCta = 8; // persistent DP kernel
+constexpr int kNtPadWords = 8;  // zero words around each packed genome
+
+// bytes of traceback codes per strip step: 64 cells * 2 B
+constexpr int kStepBytes = kStripW * 2;
+
+// int16 path: scores at or above this re-run in int32 (intermediates stay
+// below 32767 while every H is below it; see the design notes)
+constexpr int kOverflowT = 32000;
+
+// ---- code word bits (one 16-bit code per cell) -----------------------------
+// bit 0        H == 0 (restart; wins ties)
+// bits 1..10   term k >= H for M, I, D, F1, F2, G1, G2, A, B, C
+// bits 11..15  open >= extend for I, D, A, B, C
+enum : uint32_t {
+    CB_STOP = 1u << 0, CB_M = 1u << 1, CB_I = 1u << 2, CB_D = 1u << 3,
+    CB_F1 = 1u << 4, CB_F2 = 1u << 5, CB_G1 = 1u << 6, CB_G2 = 1u << 7,
+    CB_A = 1u << 8, CB_B = 1u << 9, CB_C = 1u << 10,
+    CB_IO = 1u << 11, CB_DO = 1u << 12, CB_AO = 1u << 13, CB_BO = 1u << 14, CB_CO = 1u << 15,
+};
+
+// ---- per-pair device descriptors -------------------------------------------
+struct PairDesc {
+    uint64_t code_off;      // byte offset of strip 0 in the wave's code arena
+    uint64_t bnd_off;       // entry offset of this pair's boundary buffer
+    uint32_t prot_off;      // offset into the residue-code array
+    uint32_t nt_word_off;   // word offset of genome base 0 in the packed array
+    uint32_t prot_len;
+    uint32_t nt_len;
+    uint32_t asc_prot_off;  // offsets into the uploaded ASCII
+    uint64_t asc_nt_off;
+    uint32_t cig_cap;       // capacity of this pair's reversed-op slot
+    uint64_t cig_off;       // offset of that slot
+    uint32_t flags;         // PF_*
+    int32_t strand;
+};
+
+enum : uint32_t { PF_SCORE_ONLY = 1u, PF_BADSEQ = 2u, PF_SKIP = 4u, PF_BUDGET = 8u };
+
+struct PairOut {
+    int32_t score;
+    int32_t status;         // MP_ST_* bits
+    int32_t best_ii, best_jj;  // 0-based cell of the best H (aligned orientation)
+    int32_t st_ii, st_jj;      // first cell after the restart (aligned orientation)
+    uint32_t n_ops;         // reversed ops written by the traceback
+    uint32_t cig_out;       // offset in the compacted CIGAR array
+};
+
+struct ScoreParams {
+    int32_t q, e, f, r, stop;
+    int8_t mat[22][22];
+};
+
+struct DPArgs {
+    const PairDesc *pairs;
+    const uint32_t *work;   // pair indices, processing order
+    uint32_t n_work;
+    uint32_t *head;         // work-queue counter
+    const uint8_t *prot;    // residue codes
+    const uint32_t *nt2;    // packed genome (base k at bits 2(k%16) of word k/16)
+    uint8_t *codes;         // traceback code arena
+    void *bnd;              // boundary arena
+    PairOut *out;
+    uint32_t *rerun_list;   // pairs whose int16 run saturated
+    uint32_t *rerun_count;
+    ScoreParams sp;
+};
+
+struct TBArgs {
+    const PairDesc *pairs;
+    const uint32_t *work;
+    uint32_t n_work;
+    const uint8_t *codes;
+    PairOut *out;
+    uint32_t *ops;          // reversed-op slots
+};
+
+// kernel launchers (defined in the .cu files)
+cudaError_t launch_pack(const PairDesc *pairs, uint32_t n, const char *ascii, uint8_t *prot,
+                        uint32_t *nt2, PairOut *out, cudaStream_t st);
+cudaError_t launch_dp16(const DPArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t st);
+cudaError_t launch_tb(const TBArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_compact(const PairDesc *pairs, PairOut *out, uint32_t n, const uint32_t *ops,
+                           uint32_t *cig, uint32_t *total, cudaStream_t st);
+int dp16_blocks_per_sm();
+int dp32_blocks_per_sm();
+size_t dp16_smem_bytes();
+size_t dp32_smem_bytes();
+
+}  // namespace mpdp

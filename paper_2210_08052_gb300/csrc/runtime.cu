@@ -1,0 +1,889 @@
+// Host runtime of the spliced-DP library: contexts, batch planning into
+// traceback-budgeted waves, the device pipeline (captured once per batch as
+// a CUDA graph and replayed), result download, and the serving loop.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "mp_internal.cuh"
+
+using namespace mpdp;
+
+namespace {
+
+// ------------------------------------------------------------ defaults
+// BLOSUM62 (Henikoff & Henikoff 1992) in ARNDCQEGHILKMFPSTWYV order.
+const int8_t kBlosum62[20][20] = {
+    {4, -1, -2, -2, 0, -1, -1, 0, -2, -1, -1, -1, -1, -2, -1, 1, 0, -3, -2, 0},
+    {-1, 5, 0, -2, -3, 1, 0, -2, 0, -3, -2, 2, -1, -3, -2, -1, -1, -3, -2, -3},
+    {-2, 0, 6, 1, -3, 0, 0, 0, 1, -3, -3, 0, -2, -3, -2, 1, 0, -4, -2, -3},
+    {-2, -2, 1, 6, -3, 0, 2, -1, -1, -3, -4, -1, -3, -3, -1, 0, -1, -4, -3, -3},
+    {0, -3, -3, -3, 9, -3, -4, -3, -3, -1, -1, -3, -1, -2, -3, -1, -1, -2, -2, -1},
+    {-1, 1, 0, 0, -3, 5, 2, -2, 0, -3, -2, 1, 0, -3, -1, 0, -1, -2, -1, -2},
+    {-1, 0, 0, 2, -4, 2, 5, -2, 0, -3, -3, 1, -2, -3, -1, 0, -1, -3, -2, -2},
+    {0, -2, 0, -1, -3, -2, -2, 6, -2, -4, -4, -2, -3, -3, -2, 0, -2, -2, -3, -3},
+    {-2, 0, 1, -1, -3, 0, 0, -2, 8, -3, -3, -1, -2, -1, -2, -1, -2, -2, 2, -3},
+    {-1, -3, -3, -3, -1, -3, -3, -4, -3, 4, 2, -3, 1, 0, -3, -2, -1, -3, -1, 3},
+    {-1, -2, -3, -4, -1, -2, -3, -4, -3, 2, 4, -2, 2, 0, -3, -2, -1, -2, -1, 1},
+    {-1, 2, 0, -1, -3, 1, 1, -2, -1, -3, -2, 5, -1, -3, -1, 0, -1, -3, -2, -2},
+    {-1, -1, -2, -3, -1, 0, -2, -3, -2, 1, 2, -1, 5, 0, -2, -1, -1, -1, -1, 1},
+    {-2, -3, -3, -3, -2, -3, -3, -3, -1, 0, 0, -3, 0, 6, -4, -2, -2, 1, 3, -1},
+    {-1, -2, -2, -1, -3, -1, -1, -2, -2, -3, -3, -1, -2, -4, 7, -1, -1, -4, -3, -2},
+    {1, -1, 1, 0, -1, 0, 0, 0, -1, -2, -2, 0, -1, -2, -1, 4, 1, -3, -2, -2},
+    {0, -1, 0, -1, -1, -1, -1, -2, -2, -1, -1, -1, -1, -2, -1, 1, 5, -2, -2, 0},
+    {-3, -3, -4, -4, -2, -2, -3, -2, -2, -3, -2, -3, -1, 1, -4, -3, -2, 11, 2, -3},
+    {-2, -2, -2, -3, -2, -1, -2, -3, 2, -1, -1, -2, -1, 3, -3, -2, -2, 2, 7, -1},
+    {0, -3, -3, -3, -1, -2, -2, -3, -3, 3, 1, -2, 1, -1, -2, -2, 0, -3, -1, 4},
+};
+
+constexpr uint64_t kDefaultBudget = 40ull << 30;
+
+inline uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// Traceback bytes of one pair: strips x padded steps x 128 B.
+inline uint64_t code_bytes(uint32_t m, uint32_t n)
+{
+    const uint64_t nchunks = div_up(static_cast<uint64_t>(n) + kStripW - 1, kChunk);
+    return div_up(m, kStripW) * nchunks * kChunk * kStepBytes;
+}
+
+inline uint64_t bnd_entries(uint32_t n)
+{
+    const uint64_t nchunks = div_up(static_cast<uint64_t>(n) + kStripW - 1, kChunk);
+    return nchunks * kChunk + 2 * kBndPad + 32;
+}
+
+#define CK(x)                                                                         \
+    do {                                                                              \
+        cudaError_t e_ = (x);                                                         \
+        if (e_ != cudaSuccess) {                                                      \
+            if (getenv("MP_DP_DEBUG"))                                                \
+                fprintf(stderr, "mp_dp: %s failed: %s\n", #x, cudaGetErrorString(e_)); \
+            return MP_ECUDA;                                                          \
+        }                                                                             \
+    } while (0)
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;   // elements
+    cudaError_t reserve(size_t n)
+    {
+        if (n <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) cap = n;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+template <typename T>
+struct HostBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    cudaError_t reserve(size_t n)
+    {
+        if (n <= cap) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMallocHost(&p, std::max<size_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) cap = n;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct Wave {
+    uint32_t begin, end;    // range of the work order
+    uint64_t code_bytes;
+};
+
+enum { EV_START = 0, EV_PACK, EV_DP, EV_RERUN, EV_TB, EV_END, EV_PER_WAVE = 3 };
+
+}  // namespace
+
+struct mp_dp_batch {
+    size_t n = 0;
+    std::vector<PairDesc> desc;
+    std::vector<uint32_t> order;
+    std::vector<Wave> waves;
+    std::vector<uint32_t> nt_len;
+    std::vector<int8_t> strand;
+    uint64_t ascii_bytes = 0, prot_total = 0, nt_words = 0, bnd_total = 0, ops_total = 0;
+    double cells = 0;
+    uint64_t code_bytes_total = 0;
+    // device
+    DevBuf<char> ascii;
+    DevBuf<PairDesc> d_desc;
+    DevBuf<uint8_t> prot;
+    DevBuf<uint32_t> nt2;
+    DevBuf<PairOut> out;
+    DevBuf<uint32_t> ops, cig, work, counters, rerun_list;
+    DevBuf<uint64_t> bnd;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_timed = false;
+    int runs = 0;
+    std::vector<cudaEvent_t> events;
+    // host results
+    std::vector<PairOut> h_out;
+    std::vector<uint32_t> h_cig;
+    int n_launches = 0, n_dp_launches = 0;
+};
+
+struct Request {
+    uint64_t ticket;
+    std::string prot, nt;
+    int8_t strand;
+    uint32_t flags;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Done {
+    mp_result r;
+    std::vector<uint32_t> cigar;
+    bool delivered = false;
+};
+
+struct Slot;
+
+struct mp_dp_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    mp_dp_params params{};
+    ScoreParams sp{};
+    uint64_t budget = 0;
+    DevBuf<uint8_t> codes;      // traceback arena (shared by the waves of a batch)
+    HostBuf<char> staging;
+    bool timing = false;
+    mp_dp_stats stats{};
+    mp_dp_batch *last = nullptr;   // batch used by mp_dp_align_batch
+    std::vector<uint32_t> host_cig;
+
+    // serving
+    std::mutex mu;
+    std::condition_variable cv_req, cv_done;
+    std::deque<Request> queue;
+    std::unordered_map<uint64_t, Done> done;
+    std::unordered_set<uint64_t> inflight;
+    std::deque<uint64_t> completed;       // completion order, for mp_dp_wait_any
+    std::atomic<uint64_t> next_ticket{1};
+    std::thread server;
+    bool server_running = false, stopping = false;
+    size_t ring_cap = 1 << 20;
+    int n_slots = 3;                      // micro-batches in flight on the device
+    uint64_t slot_budget = 0;
+    uint64_t served_batches = 0, served_pairs = 0;
+};
+
+// ====================================================================== API
+extern "C" {
+
+void mp_dp_default_params(mp_dp_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->q = 11; p->e = 1; p->f = 23; p->r = 29; p->stop = 23;
+    for (int a = 0; a < 22; ++a)
+        for (int b = 0; b < 22; ++b) p->mat[a][b] = -1;        // X against anything
+    for (int a = 0; a < 20; ++a) {
+        for (int b = 0; b < 20; ++b) p->mat[a][b] = kBlosum62[a][b];
+        p->mat[a][20] = -4;                                    // BLOSUM62 stop column
+        p->mat[20][a] = -4;
+    }
+    p->mat[20][20] = 1;
+    p->splice_model = MP_SPLICE_FINAL;
+    p->mode = MP_MODE_LOCAL;
+    p->tb_budget_bytes = kDefaultBudget;
+}
+
+const char *mp_dp_strerror(int code)
+{
+    switch (code) {
+    case MP_OK: return "ok";
+    case MP_EINVAL: return "invalid argument";
+    case MP_ENOMEM: return "out of memory";
+    case MP_EBUDGET: return "request exceeds the traceback budget";
+    case MP_ETIMEOUT: return "timed out";
+    case MP_ECUDA: return "CUDA error";
+    case MP_EPENDING: return "result pending";
+    case MP_EAGAIN: return "request ring full";
+    case MP_ETICKET: return "unknown ticket";
+    case MP_ESTATE: return "invalid state";
+    default: return "unknown error";
+    }
+}
+
+static int validate_params(const mp_dp_params *p)
+{
+    if (p->q < 0 || p->e < 1 || p->f < 0 || p->r < 0 || p->stop < 0) return MP_EINVAL;
+    if (p->q + p->e > 1000 || p->f > 1000 || p->r > 1000 || p->stop > 512) return MP_EINVAL;
+    int mn = 0;
+    for (int a = 0; a < 20; ++a)
+        for (int b = 0; b < 22; ++b) mn = std::min<int>(mn, p->mat[a][b]);
+    // an intron of length <= 0 must lose to a frameshift or a match from the same cell
+    if (!(p->r > p->f && p->r > p->stop && p->r > -mn)) return MP_EINVAL;
+    if (p->splice_model != MP_SPLICE_FINAL || p->mode != MP_MODE_LOCAL) return MP_EINVAL;
+    if (p->max_pairs_per_launch < 0) return MP_EINVAL;
+    return MP_OK;
+}
+
+int mp_dp_init(mp_dp_ctx **out, const mp_dp_params *p, int device)
+{
+    if (!out) return MP_EINVAL;
+    *out = nullptr;
+    mp_dp_params prm;
+    if (p) prm = *p;
+    else mp_dp_default_params(&prm);
+    if (validate_params(&prm) != MP_OK) return MP_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MP_ECUDA;
+    mp_dp_ctx *c = new (std::nothrow) mp_dp_ctx();
+    if (!c) return MP_ENOMEM;
+    c->device = device;
+    c->params = prm;
+    if (cudaSetDevice(device) != cudaSuccess) { delete c; return MP_ECUDA; }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return MP_ECUDA; }
+    c->num_sms = prop.multiProcessorCount;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return MP_ECUDA; }
+    c->sp.q = prm.q; c->sp.e = prm.e; c->sp.f = prm.f; c->sp.r = prm.r; c->sp.stop = prm.stop;
+    memcpy(c->sp.mat, prm.mat, sizeof(c->sp.mat));
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    uint64_t budget = prm.tb_budget_bytes ? prm.tb_budget_bytes : kDefaultBudget;
+    budget = std::min<uint64_t>(budget, static_cast<uint64_t>(free_b * 0.6));
+    c->budget = budget;
+    *out = c;
+    return MP_OK;
+}
+
+int mp_dp_num_sms(mp_dp_ctx *c) { return c ? c->num_sms : 0; }
+
+int mp_dp_set_timing(mp_dp_ctx *c, int enable)
+{
+    if (!c) return MP_EINVAL;
+    c->timing = enable != 0;
+    return MP_OK;
+}
+
+int mp_dp_get_stats(mp_dp_ctx *c, mp_dp_stats *s)
+{
+    if (!c || !s) return MP_EINVAL;
+    *s = c->stats;
+    return MP_OK;
+}
+
+static void free_batch_device(mp_dp_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    b->events.clear();
+    b->ascii.release(); b->d_desc.release(); b->prot.release(); b->nt2.release(); b->out.release();
+    b->ops.release(); b->cig.release(); b->work.release(); b->counters.release(); b->rerun_list.release();
+    b->bnd.release();
+}
+
+void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
+{
+    if (!b) return;
+    if (c) cudaSetDevice(c->device);
+    free_batch_device(b);
+    delete b;
+}
+
+int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch **out)
+{
+    if (!c || !out || (n && !pairs)) return MP_EINVAL;
+    *out = nullptr;
+    for (size_t k = 0; k < n; ++k) {
+        const mp_pair &q = pairs[k];
+        if ((q.prot_len && !q.prot) || (q.nt_len && !q.nt)) return MP_EINVAL;
+        if (q.strand != 1 && q.strand != -1) return MP_EINVAL;
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) return MP_ECUDA;
+    mp_dp_batch *b = new (std::nothrow) mp_dp_batch();
+    if (!b) return MP_ENOMEM;
+    b->n = n;
+    b->desc.resize(n);
+    b->nt_len.resize(n);
+    b->strand.resize(n);
+    // ---- layout
+    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0;
+    for (size_t k = 0; k < n; ++k) {
+        const mp_pair &q = pairs[k];
+        PairDesc &d = b->desc[k];
+        memset(&d, 0, sizeof(d));
+        d.prot_len = q.prot_len;
+        d.nt_len = q.nt_len;
+        d.strand = q.strand;
+        d.asc_prot_off = static_cast<uint32_t>(asc);
+        asc += q.prot_len;
+        d.asc_nt_off = asc;
+        asc += q.nt_len;
+        asc = div_up(asc, 16) * 16;
+        d.prot_off = static_cast<uint32_t>(pro);
+        pro += q.prot_len;
+        d.nt_word_off = static_cast<uint32_t>(ntw + kNtPadWords);
+        ntw += div_up(q.nt_len, 16) + 2 * kNtPadWords;
+        d.bnd_off = bnd;
+        bnd += bnd_entries(q.nt_len);
+        d.cig_off = ops;
+        d.cig_cap = q.prot_len + q.nt_len + 2;
+        ops += d.cig_cap;
+        if (q.flags & MP_PAIR_SCORE_ONLY) d.flags |= PF_SCORE_ONLY;
+        if (q.prot_len == 0 || q.nt_len == 0) d.flags |= PF_SKIP;
+        b->nt_len[k] = q.nt_len;
+        b->strand[k] = q.strand;
+        b->cells += static_cast<double>(q.prot_len) * q.nt_len;
+    }
+    if (asc > 0xffffffffull || pro > 0xffffffffull || ntw > 0xffffffffull) { delete b; return MP_EINVAL; }
+    b->ascii_bytes = asc; b->prot_total = pro; b->nt_words = ntw; b->bnd_total = bnd; b->ops_total = ops;
+
+    // ---- work order: largest first (longest-processing-time first)
+    b->order.resize(n);
+    for (size_t k = 0; k < n; ++k) b->order[k] = static_cast<uint32_t>(k);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
+        const uint64_t cx = static_cast<uint64_t>(b->desc[x].prot_len) * b->desc[x].nt_len;
+        const uint64_t cy = static_cast<uint64_t>(b->desc[y].prot_len) * b->desc[y].nt_len;
+        return cx > cy;
+    });
+    // ---- waves under the traceback budget
+    const uint64_t cap = c->budget;
+    uint64_t cur = 0, maxw = 0;
+    uint32_t wbeg = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        PairDesc &d = b->desc[b->order[k]];
+        if (d.flags & (PF_SKIP | PF_SCORE_ONLY)) continue;
+        const uint64_t cb = code_bytes(d.prot_len, d.nt_len);
+        if (cb > cap) {
+            d.flags |= PF_BUDGET | PF_SCORE_ONLY;
+            continue;
+        }
+        if (cur + cb > cap) {
+            b->waves.push_back(Wave{wbeg, k, cur});
+            maxw = std::max(maxw, cur);
+            wbeg = k;
+            cur = 0;
+        }
+        d.code_off = cur;
+        cur += div_up(cb, 256) * 256;
+        b->code_bytes_total += cb;
+    }
+    b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), cur});
+    maxw = std::max(maxw, cur);
+
+    // ---- device buffers
+    cudaError_t e = cudaSuccess;
+    if ((e = b->ascii.reserve(asc + 16)) != cudaSuccess || (e = b->d_desc.reserve(n)) != cudaSuccess ||
+        (e = b->prot.reserve(pro + 16)) != cudaSuccess || (e = b->nt2.reserve(ntw + 16)) != cudaSuccess ||
+        (e = b->out.reserve(n)) != cudaSuccess || (e = b->ops.reserve(ops + 1)) != cudaSuccess ||
+        (e = b->cig.reserve(ops + 1)) != cudaSuccess || (e = b->work.reserve(n + 1)) != cudaSuccess ||
+        (e = b->counters.reserve(4 * b->waves.size() + 4)) != cudaSuccess ||
+        (e = b->rerun_list.reserve(n + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
+        (e = c->codes.reserve(std::max<uint64_t>(maxw, 256))) != cudaSuccess) {
+        free_batch_device(b);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
+    }
+    // ---- host -> device
+    if (c->staging.reserve(asc + 16) != cudaSuccess) { free_batch_device(b); delete b; return MP_ENOMEM; }
+    for (size_t k = 0; k < n; ++k) {
+        const mp_pair &q = pairs[k];
+        if (q.prot_len) memcpy(c->staging.p + b->desc[k].asc_prot_off, q.prot, q.prot_len);
+        if (q.nt_len) memcpy(c->staging.p + b->desc[k].asc_nt_off, q.nt, q.nt_len);
+    }
+    cudaStream_t st = c->stream;
+    if (cudaMemcpyAsync(b->ascii.p, c->staging.p, asc, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        free_batch_device(b);
+        delete b;
+        return MP_ECUDA;
+    }
+    *out = b;
+    return MP_OK;
+}
+
+// Enqueue the device pipeline of a batch on stream st.
+static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool timed)
+{
+    const uint32_t n = static_cast<uint32_t>(b->n);
+    int launches = 0, dp_launches = 0;
+    auto rec = [&](int idx) -> cudaError_t {
+        return timed ? cudaEventRecord(b->events[idx], st) : cudaSuccess;
+    };
+    CK(rec(0));
+    CK(cudaMemsetAsync(b->counters.p, 0, sizeof(uint32_t) * (4 * b->waves.size() + 4), st));
+    CK(launch_pack(b->d_desc.p, n, b->ascii.p, b->prot.p, b->nt2.p, b->out.p, st));
+    ++launches;
+    CK(rec(1));
+    const int g16 = c->num_sms * dp16_blocks_per_sm();
+    const int g32 = c->num_sms * dp32_blocks_per_sm();
+    const int per_launch = c->params.max_pairs_per_launch;
+    for (size_t w = 0; w < b->waves.size(); ++w) {
+        const Wave &wv = b->waves[w];
+        DPArgs a{};
+        a.pairs = b->d_desc.p;
+        a.prot = b->prot.p;
+        a.nt2 = b->nt2.p;
+        a.codes = c->codes.p;
+        a.bnd = b->bnd.p;
+        a.out = b->out.p;
+        a.rerun_list = b->rerun_list.p + wv.begin;
+        a.rerun_count = b->counters.p + 4 * w + 2;
+        a.sp = c->sp;
+        const uint32_t cnt = wv.end - wv.begin;
+        if (per_launch > 0) {
+            // plain form: one kernel launch per group of pairs
+            for (uint32_t k = 0; k < cnt; k += per_launch) {
+                DPArgs a1 = a;
+                a1.work = b->work.p + wv.begin + k;
+                a1.n_work = std::min<uint32_t>(per_launch, cnt - k);
+                a1.head = b->counters.p + 4 * b->waves.size() + (k & 1);
+                CK(cudaMemsetAsync(a1.head, 0, sizeof(uint32_t), st));
+                if (c->params.force_int32) CK(launch_dp32(a1, 1, false, st));
+                else CK(launch_dp16(a1, 1, st));
+                ++launches;
+                ++dp_launches;
+            }
+        } else {
+            a.work = b->work.p + wv.begin;
+            a.n_work = cnt;
+            a.head = b->counters.p + 4 * w;
+            const int grid16 = std::max(1, std::min<int>(g16, static_cast<int>((cnt + kWarpsPerCta - 1) / kWarpsPerCta)));
+            const int grid32 = std::max(1, std::min<int>(g32, static_cast<int>((cnt + kWarpsPerCta - 1) / kWarpsPerCta)));
+            if (c->params.force_int32) CK(launch_dp32(a, grid32, false, st));
+            else CK(launch_dp16(a, grid16, st));
+            ++launches;
+            ++dp_launches;
+        }
+        CK(rec(2 + EV_PER_WAVE * w));
+        if (!c->params.force_int32) {
+            a.head = b->counters.p + 4 * w + 1;
+            a.work = nullptr;
+            a.n_work = 0;
+            const int grid32 = std::max(1, std::min<int>(g32, 2 * c->num_sms));
+            CK(launch_dp32(a, grid32, true, st));
+            ++launches;
+            ++dp_launches;
+        }
+        CK(rec(3 + EV_PER_WAVE * w));
+        TBArgs t{};
+        t.pairs = b->d_desc.p;
+        t.work = b->work.p + wv.begin;
+        t.n_work = cnt;
+        t.codes = c->codes.p;
+        t.out = b->out.p;
+        t.ops = b->ops.p;
+        const int tgrid = std::max(1, std::min<int>(c->num_sms * 8, static_cast<int>((cnt + 7) / 8)));
+        CK(launch_tb(t, tgrid, st));
+        ++launches;
+        CK(rec(4 + EV_PER_WAVE * w));
+    }
+    CK(launch_compact(b->d_desc.p, b->out.p, n, b->ops.p, b->cig.p, b->counters.p + 4 * b->waves.size() + 2, st));
+    launches += 2;
+    CK(rec(static_cast<int>(2 + EV_PER_WAVE * b->waves.size())));
+    b->n_launches = launches;
+    b->n_dp_launches = dp_launches;
+    return MP_OK;
+}
+
+int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
+{
+    if (!c || !b) return MP_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MP_ECUDA;
+    cudaStream_t st = c->stream;
+    const bool timed = c->timing;
+    const size_t nev = 3 + EV_PER_WAVE * b->waves.size();
+    if (timed && b->events.size() < nev) {
+        for (size_t k = b->events.size(); k < nev; ++k) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            b->events.push_back(e);
+        }
+    }
+    // a batch run once is launched directly; from its second run on, the
+    // pipeline is captured once as a CUDA graph and replayed
+    const bool use_graph = c->params.max_pairs_per_launch == 0 && ++b->runs >= 2;
+    if (use_graph && b->graph && b->graph_timed != timed) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (use_graph && !b->graph) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_pipeline(c, b, st, timed);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc != MP_OK) {
+            if (e == cudaSuccess) cudaGraphDestroy(g);
+            return rc;
+        }
+        CK(e);
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        b->graph_timed = timed;
+    }
+    if (use_graph) CK(cudaGraphLaunch(b->graph, st));
+    else {
+        int rc = enqueue_pipeline(c, b, st, timed);
+        if (rc != MP_OK) return rc;
+    }
+    c->last = b;
+    return MP_OK;
+}
+
+static int collect_stats(mp_dp_ctx *c, mp_dp_batch *b)
+{
+    mp_dp_stats &s = c->stats;
+    memset(&s, 0, sizeof(s));
+    s.cells = b->cells;
+    s.n_waves = static_cast<int32_t>(b->waves.size());
+    s.n_launches = b->n_launches;
+    s.n_dp_launches = b->n_dp_launches;
+    s.code_bytes = b->code_bytes_total;
+    if (c->timing && !b->events.empty()) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, b->events[0], b->events[1]));
+        s.pack_ms = ms;
+        cudaEvent_t prev = b->events[1];
+        for (size_t w = 0; w < b->waves.size(); ++w) {
+            const size_t base = 2 + EV_PER_WAVE * w;
+            CK(cudaEventElapsedTime(&ms, prev, b->events[base])); s.dp_ms += ms;
+            CK(cudaEventElapsedTime(&ms, b->events[base], b->events[base + 1])); s.rerun_ms += ms;
+            CK(cudaEventElapsedTime(&ms, b->events[base + 1], b->events[base + 2])); s.tb_ms += ms;
+            prev = b->events[base + 2];
+        }
+        CK(cudaEventElapsedTime(&ms, prev, b->events[2 + EV_PER_WAVE * b->waves.size()]));
+        s.tb_ms += ms;
+        CK(cudaEventElapsedTime(&ms, b->events[0], b->events[2 + EV_PER_WAVE * b->waves.size()]));
+        s.total_ms = ms;
+    }
+    return MP_OK;
+}
+
+int mp_dp_batch_sync(mp_dp_ctx *c)
+{
+    if (!c) return MP_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MP_ECUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->last) return collect_stats(c, c->last);
+    return MP_OK;
+}
+
+int mp_dp_batch_download(mp_dp_ctx *c, mp_dp_batch *b, mp_result *out)
+{
+    if (!c || !b || (b->n && !out)) return MP_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MP_ECUDA;
+    cudaStream_t st = c->stream;
+    const size_t n = b->n;
+    b->h_out.resize(n);
+    uint32_t total = 0;
+    CK(cudaMemcpyAsync(b->h_out.data(), b->out.p, n * sizeof(PairOut), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&total, b->counters.p + 4 * b->waves.size() + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->host_cig.resize(std::max<size_t>(total, 1));
+    if (total) {
+        CK(cudaMemcpyAsync(c->host_cig.data(), b->cig.p, total * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    int32_t nrerun = 0;
+    for (size_t k = 0; k < n; ++k) {
+        const PairOut &o = b->h_out[k];
+        const PairDesc &d = b->desc[k];
+        mp_result &r = out[k];
+        memset(&r, 0, sizeof(r));
+        r.status = o.status;
+        if (o.status & MP_ST_RERUN) ++nrerun;
+        if ((o.status & MP_ST_ERRMASK) & ~MP_ST_BUDGET) continue;
+        r.score = o.score > 0 ? o.score : 0;
+        const int32_t tn = static_cast<int32_t>(d.nt_len);
+        if (r.score <= 0) continue;
+        const bool score_only = (d.flags & (PF_SCORE_ONLY | PF_BUDGET)) != 0;
+        const int32_t en_al = o.best_ii + 1;
+        r.prot_en = o.best_jj + 1;
+        if (score_only) {
+            r.prot_st = -1;
+            if (d.strand > 0) { r.nt_st = -1; r.nt_en = en_al; }
+            else { r.nt_st = tn - en_al; r.nt_en = -1; }
+            continue;
+        }
+        r.prot_st = o.st_jj;
+        if (d.strand > 0) { r.nt_st = o.st_ii; r.nt_en = en_al; }
+        else { r.nt_st = tn - en_al; r.nt_en = tn - o.st_ii; }
+        r.n_cigar = o.n_ops;
+        r.cigar = o.n_ops ? c->host_cig.data() + o.cig_out : nullptr;
+    }
+    c->stats.n_rerun = nrerun;
+    return MP_OK;
+}
+
+int mp_dp_align_batch(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *out)
+{
+    if (!c || (n && (!pairs || !out))) return MP_EINVAL;
+    mp_dp_batch *b = nullptr;
+    int rc = mp_dp_batch_upload(c, pairs, n, &b);
+    if (rc != MP_OK) return rc;
+    rc = mp_dp_batch_run(c, b);
+    if (rc == MP_OK) rc = mp_dp_batch_sync(c);
+    if (rc == MP_OK) rc = mp_dp_batch_download(c, b, out);
+    c->last = nullptr;
+    mp_dp_batch_free(c, b);
+    return rc;
+}
+
+}  // extern "C"
+
+// ================================================================ serving
+// A serving thread turns submitted requests into micro-batches.  Each of
+// n_slots slots owns a private context (stream, arenas) with an equal share
+// of the traceback budget; a request is admitted into the next free slot
+// while the slot's traceback bytes stay within its share, and the slot's
+// pipeline is enqueued at once, so batches formed while others are still on
+// the device run concurrently with them (continuous batching).
+struct Slot {
+    mp_dp_ctx *ctx = nullptr;
+    mp_dp_batch *batch = nullptr;
+    std::vector<uint64_t> tickets;
+    std::vector<mp_result> res;
+    bool busy = false;
+};
+
+static void finish_slot(mp_dp_ctx *c, Slot &s, bool ok)
+{
+    if (ok && mp_dp_batch_download(s.ctx, s.batch, s.res.data()) != MP_OK) ok = false;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (size_t k = 0; k < s.tickets.size(); ++k) {
+            Done d;
+            if (ok) {
+                d.r = s.res[k];
+                d.cigar.assign(s.res[k].cigar, s.res[k].cigar + s.res[k].n_cigar);
+            } else {
+                memset(&d.r, 0, sizeof(d.r));
+                d.r.status = MP_ST_TRACE;
+            }
+            d.r.cigar = nullptr;
+            c->inflight.erase(s.tickets[k]);
+            c->done.emplace(s.tickets[k], std::move(d));
+            c->completed.push_back(s.tickets[k]);
+        }
+        c->served_batches += 1;
+        c->served_pairs += s.tickets.size();
+    }
+    c->cv_done.notify_all();
+    mp_dp_batch_free(s.ctx, s.batch);
+    s.batch = nullptr;
+    s.busy = false;
+    s.tickets.clear();
+}
+
+static void serve_loop(mp_dp_ctx *c)
+{
+    cudaSetDevice(c->device);
+    std::vector<Slot> slots(c->n_slots);
+    bool init_ok = true;
+    for (auto &s : slots) {
+        mp_dp_params p = c->params;
+        p.tb_budget_bytes = c->slot_budget;
+        p.max_pairs_per_launch = 0;
+        if (mp_dp_init(&s.ctx, &p, c->device) != MP_OK) init_ok = false;
+    }
+    std::vector<Request> take;
+    for (;;) {
+        bool progressed = false;
+        // retire finished slots
+        for (auto &s : slots) {
+            if (s.busy && cudaStreamQuery(s.ctx->stream) != cudaErrorNotReady) {
+                finish_slot(c, s, cudaStreamQuery(s.ctx->stream) == cudaSuccess);
+                progressed = true;
+            }
+        }
+        // admit queued requests into free slots
+        for (auto &s : slots) {
+            if (s.busy || !init_ok) continue;
+            take.clear();
+            {
+                std::lock_guard<std::mutex> lk(c->mu);
+                uint64_t bytes = 0;
+                while (!c->queue.empty()) {
+                    const Request &r = c->queue.front();
+                    const uint64_t cb = (r.flags & MP_PAIR_SCORE_ONLY) ? 0 : code_bytes(r.prot.size(), r.nt.size());
+                    if (!take.empty() && bytes + cb > c->slot_budget) break;
+                    bytes += cb;
+                    take.push_back(std::move(c->queue.front()));
+                    c->queue.pop_front();
+                }
+            }
+            if (take.empty()) break;
+            std::vector<mp_pair> pairs(take.size());
+            for (size_t k = 0; k < take.size(); ++k) {
+                pairs[k].prot = take[k].prot.data();
+                pairs[k].prot_len = static_cast<uint32_t>(take[k].prot.size());
+                pairs[k].nt = take[k].nt.data();
+                pairs[k].nt_len = static_cast<uint32_t>(take[k].nt.size());
+                pairs[k].strand = take[k].strand;
+                pairs[k].flags = take[k].flags;
+            }
+            s.tickets.clear();
+            for (auto &r : take) s.tickets.push_back(r.ticket);
+            s.res.assign(take.size(), mp_result{});
+            bool ok = mp_dp_batch_upload(s.ctx, pairs.data(), pairs.size(), &s.batch) == MP_OK;
+            if (ok) ok = mp_dp_batch_run(s.ctx, s.batch) == MP_OK;
+            s.busy = true;
+            if (!ok) finish_slot(c, s, false);
+            progressed = true;
+        }
+        if (!progressed) {
+            std::unique_lock<std::mutex> lk(c->mu);
+            bool any_busy = false;
+            for (auto &s : slots) any_busy |= s.busy;
+            if (c->stopping && !any_busy && c->queue.empty()) break;
+            if (any_busy) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+            } else {
+                c->cv_req.wait_for(lk, std::chrono::milliseconds(5),
+                                   [&] { return !c->queue.empty() || c->stopping; });
+            }
+        }
+    }
+    for (auto &s : slots) {
+        if (s.batch) mp_dp_batch_free(s.ctx, s.batch);
+        if (s.ctx) mp_dp_destroy(s.ctx);
+    }
+}
+
+extern "C" int mp_dp_submit(mp_dp_ctx *c, const mp_pair *q, uint64_t *ticket)
+{
+    if (!c || !q || !ticket) return MP_EINVAL;
+    if ((q->prot_len && !q->prot) || (q->nt_len && !q->nt) || (q->strand != 1 && q->strand != -1))
+        return MP_EINVAL;
+    std::unique_lock<std::mutex> lk(c->mu);
+    if (c->slot_budget == 0) c->slot_budget = c->budget / static_cast<uint64_t>(c->n_slots);
+    if (!(q->flags & MP_PAIR_SCORE_ONLY) && code_bytes(q->prot_len, q->nt_len) > c->slot_budget)
+        return MP_EBUDGET;
+    if (c->stopping) return MP_ESTATE;
+    if (c->queue.size() >= c->ring_cap) return MP_EAGAIN;
+    Request r;
+    r.ticket = c->next_ticket++;
+    r.prot.assign(q->prot, q->prot_len);
+    r.nt.assign(q->nt, q->nt_len);
+    r.strand = q->strand;
+    r.flags = q->flags;
+    r.t_submit = std::chrono::steady_clock::now();
+    *ticket = r.ticket;
+    c->inflight.insert(r.ticket);
+    c->queue.push_back(std::move(r));
+    if (!c->server_running) {
+        c->server_running = true;
+        c->server = std::thread(serve_loop, c);
+    }
+    lk.unlock();
+    c->cv_req.notify_one();
+    return MP_OK;
+}
+
+// Hand out a finished result; the caller holds c->mu.
+static int deliver(mp_dp_ctx *c, uint64_t ticket, mp_result *out)
+{
+    auto it = c->done.find(ticket);
+    if (it == c->done.end()) return MP_ETICKET;
+    Done &d = it->second;
+    if (d.delivered) {
+        c->done.erase(it);
+        return MP_ETICKET;
+    }
+    d.delivered = true;
+    *out = d.r;
+    out->cigar = d.cigar.empty() ? nullptr : d.cigar.data();
+    return MP_OK;
+}
+
+extern "C" int mp_dp_poll(mp_dp_ctx *c, uint64_t ticket, mp_result *out, int64_t timeout_us)
+{
+    if (!c || !out) return MP_EINVAL;
+    std::unique_lock<std::mutex> lk(c->mu);
+    if (c->done.count(ticket)) return deliver(c, ticket, out);
+    if (!c->inflight.count(ticket)) return MP_ETICKET;
+    if (timeout_us == 0) return MP_EPENDING;
+    auto ready = [&] { return c->done.count(ticket) > 0 || c->stopping; };
+    if (timeout_us < 0) c->cv_done.wait(lk, ready);
+    else c->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+    if (!c->done.count(ticket)) return MP_ETIMEOUT;
+    return deliver(c, ticket, out);
+}
+
+extern "C" int mp_dp_wait_any(mp_dp_ctx *c, uint64_t *ticket, mp_result *out, int64_t timeout_us)
+{
+    if (!c || !ticket || !out) return MP_EINVAL;
+    std::unique_lock<std::mutex> lk(c->mu);
+    auto pick = [&]() -> bool {
+        while (!c->completed.empty()) {
+            const uint64_t t = c->completed.front();
+            c->completed.pop_front();
+            auto it = c->done.find(t);
+            if (it != c->done.end() && !it->second.delivered) {
+                *ticket = t;
+                return true;
+            }
+        }
+        return false;
+    };
+    if (pick()) return deliver(c, *ticket, out);
+    if (timeout_us == 0) return MP_EPENDING;
+    auto ready = [&] { return !c->completed.empty() || c->stopping; };
+    if (timeout_us < 0) c->cv_done.wait(lk, ready);
+    else c->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+    if (pick()) return deliver(c, *ticket, out);
+    return MP_ETIMEOUT;
+}
+
+extern "C" void mp_dp_destroy(mp_dp_ctx *c)
+{
+    if (!c) return;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->stopping = true;
+    }
+    c->cv_req.notify_all();
+    c->cv_done.notify_all();
+    if (c->server.joinable()) c->server.join();
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->codes.release();
+    c->staging.release();
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}

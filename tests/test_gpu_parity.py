@@ -1,0 +1,305 @@
+"""GPU vs oracle parity through the C ABI.
+
+The bar is bit-exact equality of score, coordinates (0-based half-open) and
+CIGAR with the oracle (plain C, int32, full matrices) on seeded inputs: tiny
+exhaustive-size pairs, sizes spanning several 64-residue strips and 96-step
+chunks with ragged tails, the 1,111-nt single pair, the 4,096-pair batch at
+full size (sampled pairs against the oracle; every pair's CIGAR rescored),
+both strands, int16 saturation with the int32 re-run, and edge cases.
+"""
+import ctypes
+import random
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("score", "prot_st", "prot_en", "nt_st", "nt_en", "cigar")
+
+
+@pytest.fixture(scope="module")
+def mp():
+    from paper_2210_08052_gb300 import build
+    build.build()
+    import paper_2210_08052_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mp):
+    c = mp.mp_dp_init(None, 0)
+    yield c
+    mp.mp_dp_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def ctx32(mp):
+    c = mp.mp_dp_init(mp.mp_dp_default_params(force_int32=1), 0)
+    yield c
+    mp.mp_dp_destroy(c)
+
+
+def _orc_params(orc, p):
+    return orc.make_params(q=p.q, e=p.e, f=p.f, r=p.r, stop=p.stop,
+                           mat=np.array([[p.mat[a][b] for b in range(22)] for a in range(22)]))
+
+
+def _compare(orc, pairs, got, params=None, limit=5):
+    bad = []
+    for k, (p, g) in enumerate(zip(pairs, got)):
+        w = orc.align(p.prot, p.nt, p.strand, params)
+        diff = [key for key in KEYS if g[key] != w[key]]
+        if diff or g["status"] & 0xF0:
+            bad.append((k, diff, {key: g[key] for key in diff}, {key: w[key] for key in diff},
+                        g["status"], len(p.prot), len(p.nt)))
+            if len(bad) >= limit:
+                break
+    assert not bad, bad
+
+
+def _rand_prot(rng, n):
+    return "".join(rng.choice("ARNDCQEGHILKMFPSTWYV") for _ in range(n))
+
+
+def test_config1_parity(mp, ctx, ctx32, orc):
+    p = synth.config1()
+    for c in (ctx, ctx32):
+        got = mp.mp_dp_align_batch(c, [p])
+        _compare(orc, [p], got)
+
+
+def test_tiny_pairs(mp, ctx, orc):
+    rng = random.Random(5)
+    srng = np.random.default_rng(5)
+    pairs = []
+    for _ in range(1000):
+        m, n = rng.randint(1, 8), rng.randint(1, 40)
+        prot = _rand_prot(rng, m)
+        if rng.random() < 0.6:
+            nt = synth.reverse_translate(srng, prot)
+            pad = synth.random_dna(srng, max(0, n - len(nt)))
+            k = rng.randint(0, len(pad))
+            nt = pad[:k] + nt + pad[k:]
+        else:
+            nt = synth.random_dna(srng, n)
+        pairs.append(synth.Pair(prot, nt, rng.choice((1, -1))))
+    got = mp.mp_dp_align_batch(ctx, pairs)
+    _compare(orc, pairs, got)
+
+
+@pytest.mark.parametrize("pset", [dict(q=2, e=1, f=3, r=6, stop=2), dict(q=0, e=1, f=1, r=5, stop=4),
+                                  dict(q=5, e=2, f=9, r=12, stop=11)])
+def test_tiny_pairs_other_params(mp, orc, pset):
+    """Cheap penalties make frameshifts, introns and ties frequent."""
+    params = mp.mp_dp_default_params(**pset)
+    c = mp.mp_dp_init(params, 0)
+    try:
+        rng = random.Random(hash(tuple(pset.values())) & 0xffff)
+        srng = np.random.default_rng(rng.randint(0, 1 << 30))
+        pairs = []
+        for _ in range(400):
+            prot = _rand_prot(rng, rng.randint(1, 12))
+            nt = synth.random_dna(srng, rng.randint(1, 60))
+            if rng.random() < 0.5:
+                region, _ = synth.gen.plant_gene(srng, prot, 0.2, rng.randint(0, 2),
+                                                 [rng.randint(8, 30)] if rng.random() < 0.6 else [], 5, 5)
+                nt = region
+            pairs.append(synth.Pair(prot, nt, 1))
+        got = mp.mp_dp_align_batch(c, pairs)
+        _compare(orc, pairs, got, _orc_params(orc, params))
+    finally:
+        mp.mp_dp_destroy(c)
+
+
+def _gene_pairs(seed, count, mmax, intron_max):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(rng.integers(1, mmax + 1))
+        prot = synth.random_protein(rng, m)
+        k = int(rng.integers(0, 4))
+        lens = [int(rng.integers(30, intron_max)) for _ in range(k)]
+        region, _ = synth.gen.plant_gene(rng, prot, float(rng.uniform(0.05, 0.4)), int(rng.integers(0, 3)),
+                                         lens, int(rng.integers(0, 300)), int(rng.integers(0, 300)), 0.45)
+        strand = 1
+        if rng.random() < 0.5:
+            region = synth.revcomp(region)
+            strand = -1
+        out.append(synth.Pair(prot, region, strand))
+    return out
+
+
+def test_sizes_across_strips_and_chunks(mp, ctx, ctx32, orc):
+    """1..300 residues (up to 5 strips, ragged last strip) against regions of
+    up to a few kb (many 96-step chunks, ragged last chunk)."""
+    pairs = _gene_pairs(11, 160, 300, 900)
+    got = mp.mp_dp_align_batch(ctx, pairs)
+    _compare(orc, pairs, got)
+    got32 = mp.mp_dp_align_batch(ctx32, pairs)
+    assert [{k: g[k] for k in KEYS} for g in got32] == [{k: g[k] for k in KEYS} for g in got]
+
+
+def test_boundary_lengths(mp, ctx, orc):
+    """Protein lengths at strip edges and regions at chunk edges."""
+    rng = np.random.default_rng(3)
+    pairs = []
+    for m in (1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129):
+        for n in (1, 2, 3, 4, 33, 63, 64, 65, 95, 96, 97, 159, 160, 161, 191, 192, 193, 300):
+            prot = synth.random_protein(rng, m)
+            cds = synth.reverse_translate(rng, prot)
+            nt = (cds + synth.random_dna(rng, n))[:n] if rng.random() < 0.5 else synth.random_dna(rng, n)
+            pairs.append(synth.Pair(prot, nt, 1 if rng.random() < 0.5 else -1))
+    got = mp.mp_dp_align_batch(ctx, pairs)
+    _compare(orc, pairs, got)
+
+
+def test_full_batch_sampled_and_rescored(mp, ctx, orc):
+    """The 4,096-pair workload in one batch, as the benchmark runs it: a
+    stratified sample (including the largest pairs) against the oracle, and
+    every pair's CIGAR rescored by op-sum to the reported score."""
+    pairs = synth.config2()
+    got = mp.mp_dp_align_batch(ctx, pairs)
+    cells = np.array([p.cells for p in pairs])
+    order = np.argsort(cells)
+    pick = set(order[-3:].tolist()) | set(order[:: len(order) // 40].tolist())
+    sample = sorted(pick)
+    _compare(orc, [pairs[k] for k in sample], [got[k] for k in sample])
+    bad = []
+    for p, g in zip(pairs, got):
+        assert g["status"] & 0xF0 == 0
+        if g["score"] == 0:
+            continue
+        n = len(p.nt)
+        st = g["nt_st"] if p.strand > 0 else n - g["nt_en"]
+        en = g["nt_en"] if p.strand > 0 else n - g["nt_st"]
+        sc, pe, te = orc.rescore(p.prot, p.nt, p.strand, g["prot_st"], st, g["cigar_raw"])
+        if (sc, pe, te) != (g["score"], g["prot_en"], en):
+            bad.append((sc, g["score"], pe, g["prot_en"], te, en))
+    assert not bad, bad[:5]
+
+
+def test_strands_agree(mp, ctx):
+    pairs = _gene_pairs(21, 60, 200, 600)
+    flipped = [synth.Pair(p.prot, synth.revcomp(p.nt), -p.strand) for p in pairs]
+    a = mp.mp_dp_align_batch(ctx, pairs)
+    b = mp.mp_dp_align_batch(ctx, flipped)
+    for p, x, y in zip(pairs, a, b):
+        n = len(p.nt)
+        assert x["score"] == y["score"] and x["cigar"] == y["cigar"]
+        assert (x["prot_st"], x["prot_en"]) == (y["prot_st"], y["prot_en"])
+        assert (x["nt_st"], x["nt_en"]) == (n - y["nt_en"], n - y["nt_st"])
+
+
+def test_int16_saturation_reruns_exactly(mp, ctx, orc):
+    """Scores past the int16 range (W-rich proteins, W:W = 11) are re-run in
+    int32 on the GPU and still match the oracle exactly."""
+    rng = np.random.default_rng(9)
+    pairs = []
+    for m in (3200, 3400):
+        prot = "".join("W" if rng.random() < 0.9 else "C" for _ in range(m))
+        cds = synth.reverse_translate(rng, prot)
+        nt = synth.random_dna(rng, 100) + cds[: 3 * 1400] + "GTAAGT" + synth.random_dna(rng, 200) + "CAG" + \
+            cds[3 * 1400:] + synth.random_dna(rng, 80)
+        pairs.append(synth.Pair(prot, nt, 1))
+    pairs.append(_gene_pairs(5, 1, 100, 200)[0])
+    got = mp.mp_dp_align_batch(ctx, pairs)
+    assert got[0]["status"] & 1 and got[1]["status"] & 1 and not got[2]["status"] & 1
+    assert got[0]["score"] > 32767
+    _compare(orc, pairs, got)
+
+
+def test_edge_cases(mp, ctx, orc):
+    pairs = [synth.Pair("", "ACGTACGT", 1), synth.Pair("MW", "", 1), synth.Pair("W", "TG", 1),
+             synth.Pair("W", "TGG", 1), synth.Pair("W", "tgg", -1), synth.Pair("WW", "TGG", 1),
+             synth.Pair("mkvw", "atgaaagtttgg", 1), synth.Pair("M*XBZUW", "ATGTAAGGGGGGGGGGTGG", 1),
+             synth.Pair("P", "AAAAAA", 1)]
+    got = mp.mp_dp_align_batch(ctx, pairs)
+    _compare(orc, pairs, got)
+    bad = mp.mp_dp_align_batch(ctx, [synth.Pair("MW", "ATGNTGG", 1), synth.Pair("W", "TGG", 1)])
+    assert bad[0]["status"] & mp.MP_ST_BADSEQ and bad[0]["score"] == 0
+    assert bad[1]["status"] == 0 and bad[1]["score"] == 11
+
+
+def test_score_only_pairs(mp, ctx, orc):
+    pairs = _gene_pairs(31, 30, 150, 400)
+    so = [synth.Pair(p.prot, p.nt, p.strand, True) for p in pairs]
+    full = mp.mp_dp_align_batch(ctx, pairs)
+    got = mp.mp_dp_align_batch(ctx, so)
+    for p, g, f in zip(pairs, got, full):
+        assert g["score"] == f["score"] and g["cigar"] == [] and g["prot_en"] == f["prot_en"]
+        if f["score"] > 0:
+            assert (g["nt_en"] if p.strand > 0 else g["nt_st"]) == (f["nt_en"] if p.strand > 0 else f["nt_st"])
+
+
+def test_plain_per_pair_launches(mp, orc):
+    pairs = _gene_pairs(41, 12, 200, 500)
+    c = mp.mp_dp_init(mp.mp_dp_default_params(max_pairs_per_launch=1), 0)
+    try:
+        got = mp.mp_dp_align_batch(c, pairs)
+        _compare(orc, pairs, got)
+    finally:
+        mp.mp_dp_destroy(c)
+
+
+def test_repeated_runs_and_graph_replay(mp, ctx):
+    pairs = _gene_pairs(51, 50, 250, 700)
+    b = mp.mp_dp_batch_upload(ctx, pairs)
+    try:
+        outs = []
+        for _ in range(4):               # run 1 direct, runs 2+ replay the captured graph
+            mp.mp_dp_batch_run(ctx, b)
+            mp.mp_dp_batch_sync(ctx)
+            outs.append([{k: g[k] for k in KEYS} for g in mp.mp_dp_batch_download(ctx, b)])
+        assert all(o == outs[0] for o in outs)
+        assert outs[0] == [{k: g[k] for k in KEYS} for g in mp.mp_dp_align_batch(ctx, pairs)]
+    finally:
+        mp.mp_dp_batch_free(ctx, b)
+
+
+def test_small_budget_waves(mp, ctx, orc):
+    pairs = _gene_pairs(61, 40, 300, 800)
+    c = mp.mp_dp_init(mp.mp_dp_default_params(tb_budget_bytes=2 << 20), 0)
+    try:
+        got = mp.mp_dp_align_batch(c, pairs)
+        ref = mp.mp_dp_align_batch(ctx, pairs)
+        for g, r, p in zip(got, ref, pairs):
+            if g["status"] & mp.MP_ST_BUDGET:
+                assert g["score"] == r["score"] and g["prot_en"] == r["prot_en"]
+            else:
+                assert {k: g[k] for k in KEYS} == {k: r[k] for k in KEYS}
+        assert any(g["status"] & mp.MP_ST_BUDGET for g in got)
+        assert sum(1 for g in got if not g["status"] & mp.MP_ST_BUDGET) > 10
+        st = mp.mp_dp_get_stats(c)
+        assert st["n_waves"] > 1
+    finally:
+        mp.mp_dp_destroy(c)
+
+
+def test_serving_alone_and_in_mix(mp, ctx):
+    """Each request's result is the same served alone, in a burst with
+    others in flight, and from the batch call."""
+    pairs = _gene_pairs(71, 80, 250, 700)
+    ref = mp.mp_dp_align_batch(ctx, pairs)
+    c = mp.mp_dp_init(None, 0)
+    try:
+        alone = []
+        for p in pairs[:10]:
+            t = mp.mp_dp_submit(c, p)
+            alone.append(mp.mp_dp_poll(c, t, -1))
+        tickets = [mp.mp_dp_submit(c, p) for p in pairs]
+        mix = {}
+        while len(mix) < len(tickets):
+            r = mp.mp_dp_wait_any(c, 5_000_000)
+            assert r is not None
+            mix[r[0]] = r[1]
+        for k in range(10):
+            assert {x: alone[k][x] for x in KEYS} == {x: ref[k][x] for x in KEYS}
+        for t, r in zip(tickets, ref):
+            assert {x: mix[t][x] for x in KEYS} == {x: r[x] for x in KEYS}
+        assert mp.lib().mp_dp_poll(c, tickets[0], ctypes.byref(mp.mp_result()), 0) == mp.MP_ETICKET
+    finally:
+        mp.mp_dp_destroy(c)
