@@ -1,0 +1,388 @@
+"""Benchmark of the spliced protein-to-genome DP on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Step = one pass of the whole device pipeline (pack, packed-int16 DP with
+int32 re-run, traceback, CIGAR compaction) over the 4,096-pair workload
+(protein log-normal median 350 aa; Poisson(3) introns; 1 kb flanks; half on
+the reverse strand), inputs resident in HBM.  Prints one JSON line.
+Under torchrun each rank aligns its own 4,096-pair batch (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Spliced-DP GCUPS + pairs/s, batched vs plain, 1 GB300; serving p50/p99 ms"
+WORKLOAD = ("4096 (protein, region) pairs: protein log-normal median 350 aa (50-2000); "
+            "Poisson(3) GT-AG introns, log-normal median 800 nt; 10-40% substitutions; 0-3 frameshifts; "
+            "1 kb flanks at 40% GC; half reverse strand; seed 2 (+1000 per rank)")
+# algorithmic integer ops per cell: 27 max/add of Eq. 7 + 16 comparisons deciding the traceback code
+OPS_PER_CELL = 43
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """Sample nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_baseline(pairs, seconds: float = 15.0):
+    """The oracle, as it stands, on the host cores: one pair per thread,
+    pairs drawn in a fixed shuffled order until the time budget is spent."""
+    import random
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    oracle.build_oracle()
+    cores = os.cpu_count() or 1
+    idx = list(range(len(pairs)))
+    random.Random(0).shuffle(idx)
+    idx = [k for k in idx if pairs[k].cells <= 20_000_000]
+    done_cells = 0
+    n_done = 0
+    t0 = time.perf_counter()
+    deadline = t0 + seconds
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        it = iter(idx)
+        futs = set()
+
+        def submit():
+            k = next(it, None)
+            if k is None or time.perf_counter() > deadline:
+                return False
+            p = pairs[k]
+            futs.add((ex.submit(oracle.align, p.prot, p.nt, p.strand), p.cells))
+            return True
+
+        for _ in range(cores):
+            if not submit():
+                break
+        while futs:
+            f, c = next(iter(futs))
+            f.result()
+            futs.discard((f, c))
+            done_cells += c
+            n_done += 1
+            submit()
+    dt = time.perf_counter() - t0
+    return {"value": done_cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n_done} pairs of the workload ({done_cells / 1e9:.2f} G cells, pairs <= 20 M cells) "
+                      f"in {dt:.1f} s, one pair per thread"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle on the host cores, each step a bounded sample."""
+    import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pairs = synth.config2()
+    per_step = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(pairs, per_step / 4)
+    vals = []
+    t0 = time.perf_counter()
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(pairs, per_step)
+        vals.append(cb["value"])
+    dt = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000 / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": value,
+                             "unit": "GCUPS"},
+            "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def serve_once(mp, pairs, rate: float, seconds: float, device: int):
+    """Open-loop Poisson arrivals; latency = submit -> result available."""
+    import random
+
+    ctx = mp.mp_dp_init(None, device)
+    rng = random.Random(4)
+    lat = []
+    t_sub = {}
+    stop = threading.Event()
+    lock = threading.Lock()
+
+    def consumer():
+        while not stop.is_set() or len(lat) < len(t_sub):
+            r = mp.mp_dp_wait_any(ctx, 200_000)
+            if r is None:
+                if stop.is_set() and len(lat) >= len(t_sub):
+                    break
+                continue
+            now = time.perf_counter()
+            with lock:
+                lat.append(now - t_sub[r[0]])
+
+    th = threading.Thread(target=consumer, daemon=True)
+    # warm the serving thread
+    t = mp.mp_dp_submit(ctx, pairs[0])
+    mp.mp_dp_poll(ctx, t, -1)
+    th.start()
+    t0 = time.perf_counter()
+    nxt = t0
+    k = 0
+    while True:
+        nxt += rng.expovariate(rate)
+        if nxt - t0 > seconds:
+            break
+        while time.perf_counter() < nxt:
+            pass
+        p = pairs[k % len(pairs)]
+        k += 1
+        with lock:
+            tk = mp.mp_dp_submit(ctx, p)
+            t_sub[tk] = time.perf_counter()
+    stop.set()
+    th.join(timeout=120)
+    wall = time.perf_counter() - t0
+    mp.mp_dp_destroy(ctx)
+    lat.sort()
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] * 1000 if lat else None
+    return {"rate_per_s": rate, "seconds": seconds, "submitted": k, "completed": len(lat),
+            "pairs_per_s": len(lat) / wall, "p50_ms": q(0.50), "p99_ms": q(0.99)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/serving/cpu legs")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rates", default="10000")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import numpy as np
+
+    import synth
+    import paper_2210_08052_gb300 as mp
+    from paper_2210_08052_gb300 import build as mpbuild
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        mpbuild.build()
+    if dist:
+        dist.barrier()
+    mpbuild.build()
+
+    pairs = synth.config2(seed=2 + 1000 * rank)
+    cells = float(sum(p.cells for p in pairs))
+    ctx = mp.mp_dp_init(None, local)
+    mp.mp_dp_set_timing(ctx, True)
+    batch = mp.mp_dp_batch_upload(ctx, pairs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        mp.mp_dp_batch_run(ctx, batch)
+        mp.mp_dp_batch_sync(ctx)
+    dp_ms, rr_ms, tb_ms, tot_ms = [], [], [], []
+    barrier()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            mp.mp_dp_batch_run(ctx, batch)
+            mp.mp_dp_batch_sync(ctx)
+            st = mp.mp_dp_get_stats(ctx)
+            dp_ms.append(st["dp_ms"]); rr_ms.append(st["rerun_ms"]); tb_ms.append(st["tb_ms"])
+            tot_ms.append(st["total_ms"])
+        barrier()
+        elapsed = time.perf_counter() - t0
+    stats = mp.mp_dp_get_stats(ctx)
+    res = mp.mp_dp_batch_download(ctx, batch, raw=True)
+    n_rerun = int(((res["status"] & 1) != 0).sum())
+    mp.mp_dp_batch_free(ctx, batch)
+    t_max = elapsed
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max * 1000 / args.steps
+    gcups = cells * world / (t_max / args.steps) / 1e9
+    pairs_per_s = len(pairs) * world / (t_max / args.steps)
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_steps = max(2, min(args.steps, 3))
+    mp.mp_dp_set_timing(ctx, False)
+    mp.mp_dp_align_batch(ctx, pairs, raw=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        out = mp.mp_dp_align_batch(ctx, pairs, raw=True)
+    barrier()
+    e2e_t = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    ascii_bytes = sum(len(p.prot) + len(p.nt) for p in pairs)
+    h2d = ascii_bytes + len(pairs) * (72 + 4)          # sequences + pair descriptors + work order
+    d2h = len(pairs) * 32 + 4 + int(out["n_cigar"].sum()) * 4
+    e2e = {"value": cells * world / (e2e_t / e2e_steps) / 1e9, "unit": "GCUPS",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "pairs_per_s": len(pairs) * world / (e2e_t / e2e_steps)}
+    mp.mp_dp_destroy(ctx)
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+        return
+
+    peaks = _peaks()
+    clocks = clk.summary()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    f_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = nsm * 128 * 2 * f_mhz * 1e6 / 1e12          # int16 lane-ops/s (Tops)
+    dp_avg_ms = statistics.mean(dp_ms) if dp_ms else None
+    achieved = cells * OPS_PER_CELL / (dp_avg_ms / 1000) / 1e12 if dp_avg_ms else None
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "dp16_traffic.json")) as fh:
+            tj = json.load(fh)
+            traffic = tj.get("bytes_per_launch_full_workload")
+    except (OSError, ValueError):
+        pass
+    line = {
+        "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs": len(pairs), "cells": cells,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "256 MB buffer written between timed steps; each step also writes "
+                         f"{stats['code_bytes'] / 1e9:.1f} GB of traceback codes"},
+        "pairs_per_s": pairs_per_s,
+        "kernel_ms": {"dp_int16": dp_avg_ms, "rerun_int32": statistics.mean(rr_ms),
+                      "traceback_compact": statistics.mean(tb_ms), "pipeline": statistics.mean(tot_ms)},
+        "n_rerun": n_rerun,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s (int16 lane-ops)",
+                     "frac": (achieved / peak_ops) if achieved else None, "traffic": traffic,
+                     "ops_per_cell": OPS_PER_CELL,
+                     "peak_basis": f"{nsm} SMs x 128 lanes x 2 int16 halves x {f_mhz:.0f} MHz (median SM clock "
+                                   "under load)",
+                     "hbm_write_gbs": stats["code_bytes"] / (dp_avg_ms / 1000) / 1e9 if dp_avg_ms else None,
+                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "clocks": clocks,
+        "gpu_launches": stats["n_launches"] * args.steps,
+        "e2e": e2e,
+    }
+    if not args.no_extras:
+        # plain form: one pair per kernel launch, on a sample
+        ctxp = mp.mp_dp_init(mp.mp_dp_default_params(max_pairs_per_launch=1), local)
+        rng = np.random.default_rng(0)
+        sample = [pairs[k] for k in rng.choice(len(pairs), 48, replace=False)]
+        mp.mp_dp_align_batch(ctxp, sample[:2], raw=True)
+        bp = mp.mp_dp_batch_upload(ctxp, sample)
+        mp.mp_dp_batch_run(ctxp, bp)
+        mp.mp_dp_batch_sync(ctxp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mp.mp_dp_batch_run(ctxp, bp)
+        mp.mp_dp_batch_sync(ctxp)
+        tp = time.perf_counter() - t0
+        mp.mp_dp_batch_free(ctxp, bp)
+        mp.mp_dp_destroy(ctxp)
+        pc = sum(p.cells for p in sample)
+        line["plain"] = {"value": pc / tp / 1e9, "unit": "GCUPS", "pairs_per_s": len(sample) / tp,
+                         "sample": f"{len(sample)} random pairs of the workload, one kernel launch per pair",
+                         "batched_over_plain": gcups / (pc / tp / 1e9)}
+        # serving
+        try:
+            sp = synth.serving_pairs()
+            line["serving"] = [serve_once(mp, sp, float(r), args.serve_seconds, local)
+                               for r in args.serve_rates.split(",")]
+        except Exception as exc:  # noqa: BLE001
+            line["serving"] = {"error": str(exc)}
+        line["cpu_baseline"] = cpu_baseline(pairs)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+
+
+if __name__ == "__main__":
+    main()

@@ -289,7 +289,9 @@ def test_serving_alone_and_in_mix(mp, ctx):
         alone = []
         for p in pairs[:10]:
             t = mp.mp_dp_submit(c, p)
-            alone.append(mp.mp_dp_poll(c, t, -1))
+            r = mp.mp_dp_poll(c, t, 30_000_000)
+            assert r is not None
+            alone.append(r)
         tickets = [mp.mp_dp_submit(c, p) for p in pairs]
         mix = {}
         while len(mix) < len(tickets):
