@@ -110,6 +110,8 @@ def plant_gene(rng, prot: str, subst_rate: float, n_fs: int, intron_lens, flank5
     cds = list("".join(codons))
     fs = []
     for _ in range(n_fs):
+        if len(cds) < 4:
+            break
         L = int(fs_len) if fs_len is not None else int(rng.integers(1, 3))
         pos = int(rng.integers(1, len(cds)))
         if fs_insert_only or rng.random() < 0.5:
@@ -121,7 +123,8 @@ def plant_gene(rng, prot: str, subst_rate: float, n_fs: int, intron_lens, flank5
             fs.append(("del", pos, L))
     cds = "".join(cds)
     # intron positions uniform over the CDS (so phases 0, 1 and 2 all occur)
-    k = len(intron_lens)
+    k = min(len(intron_lens), max(0, len(cds) - 1))
+    intron_lens = list(intron_lens)[:k]
     cuts = sorted(rng.choice(np.arange(1, len(cds)), size=k, replace=False).tolist()) if k else []
     pieces, prev = [], 0
     for c, L in zip(cuts, intron_lens):
