@@ -260,21 +260,31 @@ def test_repeated_runs_and_graph_replay(mp, ctx):
         mp.mp_dp_batch_free(ctx, b)
 
 
+def _code_bytes(m, n):
+    """Traceback bytes of one pair: 64-residue strips x 96-step chunks x 128 B."""
+    return -(-m // 64) * -(-(n + 63) // 96) * 96 * 128
+
+
 def test_small_budget_waves(mp, ctx, orc):
+    """A budget smaller than the batch splits it into waves; a pair larger
+    than the whole budget is scored without traceback (MP_ST_BUDGET)."""
     pairs = _gene_pairs(61, 40, 300, 800)
-    c = mp.mp_dp_init(mp.mp_dp_default_params(tb_budget_bytes=2 << 20), 0)
+    need = sorted(_code_bytes(len(p.prot), len(p.nt)) for p in pairs)
+    budget = need[-3] + 4096                      # the two largest pairs do not fit
+    c = mp.mp_dp_init(mp.mp_dp_default_params(tb_budget_bytes=budget), 0)
     try:
         got = mp.mp_dp_align_batch(c, pairs)
         ref = mp.mp_dp_align_batch(ctx, pairs)
         for g, r, p in zip(got, ref, pairs):
-            if g["status"] & mp.MP_ST_BUDGET:
+            if _code_bytes(len(p.prot), len(p.nt)) > budget:
+                assert g["status"] & mp.MP_ST_BUDGET
                 assert g["score"] == r["score"] and g["prot_en"] == r["prot_en"]
             else:
+                assert not g["status"] & mp.MP_ST_BUDGET
                 assert {k: g[k] for k in KEYS} == {k: r[k] for k in KEYS}
-        assert any(g["status"] & mp.MP_ST_BUDGET for g in got)
-        assert sum(1 for g in got if not g["status"] & mp.MP_ST_BUDGET) > 10
-        st = mp.mp_dp_get_stats(c)
-        assert st["n_waves"] > 1
+        assert sum(1 for g in got if g["status"] & mp.MP_ST_BUDGET) == 2
+        assert mp.mp_dp_get_stats(c)["n_waves"] > 1
+        _compare(orc, pairs[:8], ref[:8])
     finally:
         mp.mp_dp_destroy(c)
 
