@@ -441,7 +441,8 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
     const uint32_t n = static_cast<uint32_t>(b->n);
     int launches = 0, dp_launches = 0;
     auto rec = [&](int idx) -> cudaError_t {
-        return timed ? cudaEventRecord(b->events[idx], st) : cudaSuccess;
+        // External: inside a stream capture the record becomes an event-record node
+        return timed ? cudaEventRecordWithFlags(b->events[idx], st, cudaEventRecordExternal) : cudaSuccess;
     };
     CK(rec(0));
     CK(cudaMemsetAsync(b->counters.p, 0, sizeof(uint32_t) * (4 * b->waves.size() + 4), st));
