@@ -436,13 +436,15 @@ int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch
 }
 
 // Enqueue the device pipeline of a batch on stream st.
-static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool timed)
+static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool timed, bool capturing)
 {
     const uint32_t n = static_cast<uint32_t>(b->n);
     int launches = 0, dp_launches = 0;
     auto rec = [&](int idx) -> cudaError_t {
-        // External: inside a stream capture the record becomes an event-record node
-        return timed ? cudaEventRecordWithFlags(b->events[idx], st, cudaEventRecordExternal) : cudaSuccess;
+        // inside a stream capture only an External record becomes an event-record node
+        if (!timed) return cudaSuccess;
+        return capturing ? cudaEventRecordWithFlags(b->events[idx], st, cudaEventRecordExternal)
+                         : cudaEventRecord(b->events[idx], st);
     };
     CK(rec(0));
     CK(cudaMemsetAsync(b->counters.p, 0, sizeof(uint32_t) * (4 * b->waves.size() + 4), st));
@@ -544,7 +546,7 @@ int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
     if (use_graph && !b->graph) {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_pipeline(c, b, st, timed);
+        int rc = enqueue_pipeline(c, b, st, timed, true);
         cudaError_t e = cudaStreamEndCapture(st, &g);
         if (rc != MP_OK) {
             if (e == cudaSuccess) cudaGraphDestroy(g);
@@ -558,7 +560,7 @@ int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
     }
     if (use_graph) CK(cudaGraphLaunch(b->graph, st));
     else {
-        int rc = enqueue_pipeline(c, b, st, timed);
+        int rc = enqueue_pipeline(c, b, st, timed, false);
         if (rc != MP_OK) return rc;
     }
     c->last = b;
