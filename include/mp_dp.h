@@ -56,6 +56,7 @@ extern "C" {
 #define MP_ST_BADSEQ 0x10   /* error: a character outside ACGT in the genome */
 #define MP_ST_BUDGET 0x20   /* error: this pair's traceback alone exceeds the budget */
 #define MP_ST_TRACE 0x40    /* error: internal traceback inconsistency (never expected) */
+#define MP_ST_TIMEOUT 0x80  /* error: a bounded wait between cooperating warps expired */
 #define MP_ST_ERRMASK 0xF0
 
 /* ---------------------------------------------------------- CIGAR ops */

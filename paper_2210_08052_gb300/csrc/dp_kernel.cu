@@ -486,13 +486,50 @@ __device__ __forceinline__ void run_chunk(typename Ops::State &st, const typenam
     }
 }
 
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_l2(const T *p);
+template <>
+__device__ __forceinline__ uint32_t ld_l2<uint32_t>(const uint32_t *p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ Ops32::Bnd ld_l2<Ops32::Bnd>(const Ops32::Bnd *p)
+{
+    const int2 v = __ldcg(reinterpret_cast<const int2 *>(p));
+    return Ops32::Bnd{v.x, v.y};
+}
+
+// (score, ii, jj) -> key whose unsigned maximum is the best cell under the
+// tie rule: largest score, then smallest ii, then smallest jj
+__device__ __forceinline__ unsigned long long best_key(int score, int ii, int jj)
+{
+    return (static_cast<unsigned long long>(score) << 40) |
+           (static_cast<unsigned long long>(0xfffffu - static_cast<uint32_t>(ii)) << 20) |
+           static_cast<unsigned long long>(0xfffffu - static_cast<uint32_t>(jj));
+}
+
+// One 64-residue strip s of pair p.  Strip s reads the boundary row (H and
+// I of residue 64s-1 at every genome position) that strip s-1 publishes
+// chunk by chunk, and publishes its own last residue for strip s+1.
 template <typename Ops>
-__device__ void align_pair(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint32_t p, int lane)
+__device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint32_t p, int s, int lane,
+                          bool rerun)
 {
     using Bnd = typename Ops::Bnd;
     const PairDesc pd = a.pairs[p];
     const int n = static_cast<int>(pd.nt_len);
     const int m = static_cast<int>(pd.prot_len);
+    const int nstrips = static_cast<int>(pd.n_strips);
     const bool store = !(pd.flags & PF_SCORE_ONLY);
     const uint32_t *g = a.nt2 + pd.nt_word_off;
     const uint8_t *P = a.prot + pd.prot_off;
@@ -501,72 +538,98 @@ __device__ void align_pair(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uin
     const int nsteps = n + kStripW - 1;
     const int nchunks = (nsteps + kChunk - 1) / kChunk;
     const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes;
-    const int nstrips = (m + kStripW - 1) / kStripW;
+    const uint32_t *prev = a.progress + pd.strip_base + s - 1;   // valid for s > 0
+    uint32_t *mine = a.progress + pd.strip_base + s;
+    bool timed_out = false;
 
-    // column 0 of the matrix: H = 0, I = -inf at every genome position
-    for (int k = lane; k < nchunks * kChunk + 2 * kBndPad; k += 32) bnd[k - kBndPad] = Ops::kBnd0;
-    __syncwarp();
+    // wait until strip s-1 has published `need` chunks (bounded)
+    auto wait_for = [&](uint32_t need) {
+        if (s == 0 || timed_out) return;
+        uint32_t ok = 1;
+        if (lane == 0) {
+            uint32_t it = 0;
+            while (ld_acquire(prev) < need) {
+                __nanosleep(256);
+                if (++it > kSpinLimit) { ok = 0; break; }
+            }
+        }
+        ok = __shfl_sync(kFull, ok, 0);
+        if (!ok) timed_out = true;
+        __syncwarp();
+    };
 
-    Best best{0, 0x7fffffff, 0x7fffffff};
-    for (int s = 0; s < nstrips; ++s) {
-        // profile: prof[aa][lane] = [s(aa, P[2l]), s(aa, P[2l+1])]
-        const int jlo = s * kStripW + 2 * lane, jhi = jlo + 1;
-        const int plo = jlo < m ? P[jlo] : 21, phi = jhi < m ? P[jhi] : 21;
+    // profile: prof[aa][lane] = [s(aa, P[2l]), s(aa, P[2l+1])]
+    const int jlo = s * kStripW + 2 * lane, jhi = jlo + 1;
+    const int plo = jlo < m ? P[jlo] : 21, phi = jhi < m ? P[jhi] : 21;
 #pragma unroll 2
-        for (int aa = 0; aa < kProfRows; ++aa)
-            sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), subst_score(a.sp, aa, phi));
-        // records for ii in [-96, 95]
-        for (int ii = -kChunk + lane; ii < kChunk; ii += 32) {
-            const uint4 rec = make_record(g, n, ii, a.sp.r);
-            const int slot = ii & (kRing - 1);
-            sm.ring[slot] = rec;
-            if (slot < kRingPad) sm.ring[slot + kRing] = rec;
+    for (int aa = 0; aa < kProfRows; ++aa)
+        sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), subst_score(a.sp, aa, phi));
+    // records for ii in [-96, 95]
+    for (int ii = -kChunk + lane; ii < kChunk; ii += 32) {
+        const uint4 rec = make_record(g, n, ii, a.sp.r);
+        const int slot = ii & (kRing - 1);
+        sm.ring[slot] = rec;
+        if (slot < kRingPad) sm.ring[slot + kRing] = rec;
+    }
+    wait_for(nchunks < 2 ? nchunks : 2);
+    __syncwarp();
+    typename Ops::State st;
+    {
+        const int ii0 = -2 * lane;
+        const uint4 rm1 = sm.ring[(ii0 - 1) & (kRing - 1)];
+        const uint4 rm2 = sm.ring[(ii0 - 2) & (kRing - 1)];
+        const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
+        const Bnd w0 = s == 0 ? Ops::kBnd0 : ld_l2(bnd);
+        Ops::init(st, lane, w0, rm1, rm2, xm1);
+    }
+    uint8_t *code_strip = a.codes + pd.code_off + static_cast<size_t>(s) * strip_bytes;
+    Best best{0, 0x7fffffff, 0x7fffffff};
+
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int t0 = ch * kChunk;
+        if (ch > 0) {
+            for (int ii = t0 + lane; ii < t0 + kChunk; ii += 32) {
+                const uint4 rec = make_record(g, n, ii, a.sp.r);
+                const int slot = ii & (kRing - 1);
+                sm.ring[slot] = rec;
+                if (slot < kRingPad) sm.ring[slot + kRing] = rec;
+            }
+            // the boundary entries of this chunk are flushed by strip s-1's chunks ch and ch+1
+            wait_for(ch + 2 < nchunks ? ch + 2 : nchunks);
+        }
+        if (s == 0) {
+            for (int k = lane; k < kChunk; k += 32) sm.bin[k] = Ops::kBnd0;   // column 0: H = 0, I = -inf
+        } else {
+            for (int k = lane; k < kChunk; k += 32) sm.bin[k] = ld_l2(bnd + t0 + 1 + k);
         }
         __syncwarp();
-        typename Ops::State st;
-        {
-            const int ii0 = -2 * lane;
-            const uint4 rm1 = sm.ring[(ii0 - 1) & (kRing - 1)];
-            const uint4 rm2 = sm.ring[(ii0 - 2) & (kRing - 1)];
-            const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
-            Ops::init(st, lane, bnd[0], rm1, rm2, xm1);
+        const bool masked = (t0 < kStripW) || (t0 + kChunk > n);
+        if (masked) {
+            if (store) run_chunk<Ops, true, true>(st, c, sm, lane, t0, n, code_strip);
+            else run_chunk<Ops, true, false>(st, c, sm, lane, t0, n, code_strip);
+        } else {
+            if (store) run_chunk<Ops, false, true>(st, c, sm, lane, t0, n, code_strip);
+            else run_chunk<Ops, false, false>(st, c, sm, lane, t0, n, code_strip);
         }
-        uint8_t *code_strip = a.codes + pd.code_off + static_cast<size_t>(s) * strip_bytes;
-
-        for (int ch = 0; ch < nchunks; ++ch) {
-            const int t0 = ch * kChunk;
-            if (ch > 0) {
-                for (int ii = t0 + lane; ii < t0 + kChunk; ii += 32) {
-                    const uint4 rec = make_record(g, n, ii, a.sp.r);
-                    const int slot = ii & (kRing - 1);
-                    sm.ring[slot] = rec;
-                    if (slot < kRingPad) sm.ring[slot + kRing] = rec;
-                }
-            }
-            for (int k = lane; k < kChunk; k += 32) sm.bin[k] = bnd[t0 + 1 + k];
-            __syncwarp();
-            const bool masked = (t0 < kStripW) || (t0 + kChunk > n);
-            if (masked) {
-                if (store) run_chunk<Ops, true, true>(st, c, sm, lane, t0, n, code_strip);
-                else run_chunk<Ops, true, false>(st, c, sm, lane, t0, n, code_strip);
-            } else {
-                if (store) run_chunk<Ops, false, true>(st, c, sm, lane, t0, n, code_strip);
-                else run_chunk<Ops, false, false>(st, c, sm, lane, t0, n, code_strip);
-            }
-            __syncwarp();
+        __syncwarp();
+        if (s + 1 < nstrips) {
+            // publish residue 64s+63 for strip s+1
             for (int k = lane; k < kChunk; k += 32) bnd[t0 + k - (kStripW - 1)] = sm.bout[k];
-            // fold this chunk's best cells into the running best
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int sc, t;
-                Ops::take_best(st, h, t0, sc, t);
-                const int jj = s * kStripW + 2 * lane + h;
-                const int ii = t - 2 * lane - h;
-                if (sc > 0 && jj < m && better(sc, ii, jj, best)) best = Best{sc, ii, jj};
-            }
-            Ops::reset_best(st);
+            __threadfence();
             __syncwarp();
+            if (lane == 0) st_release(mine, static_cast<uint32_t>(ch + 1));
         }
+        // fold this chunk's best cells into the strip's best
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int sc, t;
+            Ops::take_best(st, h, t0, sc, t);
+            const int jj = s * kStripW + 2 * lane + h;
+            const int ii = t - 2 * lane - h;
+            if (sc > 0 && jj < m && better(sc, ii, jj, best)) best = Best{sc, ii, jj};
+        }
+        Ops::reset_best(st);
+        __syncwarp();
     }
     // warp reduction of (score desc, ii asc, jj asc)
 #pragma unroll
@@ -578,14 +641,28 @@ __device__ void align_pair(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uin
         if (better(o.score, o.ii, o.jj, best)) best = o;
     }
     if (lane == 0) {
-        PairOut &o = a.out[p];
-        o.score = best.score;
-        o.best_ii = best.score > 0 ? best.ii : -1;
-        o.best_jj = best.score > 0 ? best.jj : -1;
-        if (sizeof(Bnd) == 4 && best.score >= kOverflowT) {
-            o.status |= MP_ST_RERUN;
-            const uint32_t slot = atomicAdd(a.rerun_count, 1u);
-            a.rerun_list[slot] = p;
+        if (best.score > 0) atomicMax(a.best_key + p, best_key(best.score, best.ii, best.jj));
+        if (timed_out) atomicOr(&a.out[p].status, MP_ST_TIMEOUT);
+        __threadfence();
+        const uint32_t done = atomicAdd(a.strips_done + p, 1u);
+        if (done == static_cast<uint32_t>(nstrips - 1)) {
+            // last strip of the pair: publish the pair's best cell
+            __threadfence();
+            const unsigned long long key = atomicAdd(a.best_key + p, 0ull);
+            PairOut &o = a.out[p];
+            const int score = static_cast<int>(key >> 40);
+            o.score = score;
+            o.best_ii = score > 0 ? static_cast<int>(0xfffffu - ((key >> 20) & 0xfffffu)) : -1;
+            o.best_jj = score > 0 ? static_cast<int>(0xfffffu - (key & 0xfffffu)) : -1;
+            if (!rerun && sizeof(Bnd) == 4 && score >= kOverflowT && !(o.status & MP_ST_TIMEOUT)) {
+                // int16 saturated: queue every strip of this pair for the int32 kernel
+                o.status |= MP_ST_RERUN;
+                a.best_key[p] = 0;
+                a.strips_done[p] = 0;
+                for (int k = 0; k < nstrips; ++k) a.progress[pd.strip_base + k] = 0;
+                const uint32_t slot = atomicAdd(a.rerun_count, static_cast<uint32_t>(nstrips));
+                for (int k = 0; k < nstrips; ++k) a.rerun_items[slot + k] = make_uint2(p, k);
+            }
         }
     }
     __syncwarp();
@@ -598,16 +675,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) dp_kernel(const DPArgs a, i
     using SM = WarpSmem<typename Ops::Bnd>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     SM &sm = reinterpret_cast<SM *>(smem_raw)[warp];
-    const uint32_t *list = rerun_only ? a.rerun_list : a.work;
-    const uint32_t count = rerun_only ? *a.rerun_count : a.n_work;
+    const uint2 *list = rerun_only ? a.rerun_items : a.items;
+    const uint32_t count = rerun_only ? *a.rerun_count : a.n_items;
     for (;;) {
         uint32_t idx = 0;
         if (lane == 0) idx = atomicAdd(a.head, 1u);
         idx = __shfl_sync(kFull, idx, 0);
         if (idx >= count) break;
-        const uint32_t p = list[idx];
-        if (a.pairs[p].flags & (PF_SKIP | PF_BADSEQ)) continue;
-        align_pair<Ops>(a, sm, p, lane);
+        const uint2 it = list[idx];
+        run_strip<Ops>(a, sm, it.x, static_cast<int>(it.y), lane, rerun_only != 0);
     }
 }
 

@@ -16,7 +16,7 @@ constexpr int kRingPad = 12;    // mirrored entries so a body never wraps
 constexpr int kProfRows = 22;   // translated amino acid 0..19, stop 20, no codon 21
 constexpr int kBndPad = 64;     // boundary entries before genome position 0
 constexpr int kWarpsPerCta = 8; // persistent DP kernel
-constexpr int kNtPadWords = 8;  // zero words around each packed genome
+constexpr int kNtPadWords = 16; // zero words around each packed genome
 
 // bytes of traceback codes per strip step: 64 cells * 2 B
 constexpr int kStepBytes = kStripW * 2;
@@ -50,6 +50,8 @@ struct PairDesc {
     uint64_t cig_off;       // offset of that slot
     uint32_t flags;         // PF_*
     int32_t strand;
+    uint32_t strip_base;    // index of strip 0 in the per-strip progress array
+    uint32_t n_strips;
 };
 
 enum : uint32_t { PF_SCORE_ONLY = 1u, PF_BADSEQ = 2u, PF_SKIP = 4u, PF_BUDGET = 8u };
@@ -68,20 +70,29 @@ struct ScoreParams {
     int8_t mat[22][22];
 };
 
+// A work item is one 64-residue strip of one pair: x = pair, y = strip.
+// Strips of a pair are queued in order; the warp running strip s consumes
+// the boundary row strip s-1 publishes chunk by chunk.
 struct DPArgs {
     const PairDesc *pairs;
-    const uint32_t *work;   // pair indices, processing order
-    uint32_t n_work;
+    const uint2 *items;     // processing order
+    uint32_t n_items;
     uint32_t *head;         // work-queue counter
     const uint8_t *prot;    // residue codes
     const uint32_t *nt2;    // packed genome (base k at bits 2(k%16) of word k/16)
     uint8_t *codes;         // traceback code arena
     void *bnd;              // boundary arena
     PairOut *out;
-    uint32_t *rerun_list;   // pairs whose int16 run saturated
+    uint32_t *progress;     // per strip: chunks whose boundary row is published
+    unsigned long long *best_key;   // per pair: max of (score, -ii, -jj)
+    uint32_t *strips_done;  // per pair
+    uint2 *rerun_items;     // strips of pairs whose int16 run saturated
     uint32_t *rerun_count;
     ScoreParams sp;
 };
+
+// bounded wait of a consumer strip for its producer (iterations of ~0.25 us)
+constexpr uint32_t kSpinLimit = 40u * 1000u * 1000u;
 
 struct TBArgs {
     const PairDesc *pairs;

@@ -120,7 +120,8 @@ struct HostBuf {
 };
 
 struct Wave {
-    uint32_t begin, end;    // range of the work order
+    uint32_t begin, end;    // range of the pair order
+    uint32_t ibegin, iend;  // range of the strip-item order
     uint64_t code_bytes;
 };
 
@@ -144,8 +145,14 @@ struct mp_dp_batch {
     DevBuf<uint8_t> prot;
     DevBuf<uint32_t> nt2;
     DevBuf<PairOut> out;
-    DevBuf<uint32_t> ops, cig, work, counters, rerun_list;
+    DevBuf<uint32_t> ops, cig, work;
+    DevBuf<uint2> items, rerun_items;
     DevBuf<uint64_t> bnd;
+    // per-run state, zeroed by one memset: counters | strips_done | progress | best_key
+    DevBuf<unsigned long long> state;
+    size_t state_bytes = 0, off_done = 0, off_progress = 0, off_key = 0;
+    std::vector<uint2> h_items;
+    std::vector<uint32_t> item_off;     // first item of each pair in the order (by order index)
     cudaGraphExec_t graph = nullptr;
     bool graph_timed = false;
     int runs = 0;
@@ -307,8 +314,8 @@ static void free_batch_device(mp_dp_batch *b)
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     b->events.clear();
     b->ascii.release(); b->d_desc.release(); b->prot.release(); b->nt2.release(); b->out.release();
-    b->ops.release(); b->cig.release(); b->work.release(); b->counters.release(); b->rerun_list.release();
-    b->bnd.release();
+    b->ops.release(); b->cig.release(); b->work.release(); b->items.release(); b->rerun_items.release();
+    b->bnd.release(); b->state.release();
 }
 
 void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
@@ -319,28 +326,32 @@ void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
     delete b;
 }
 
-int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch **out)
+// (Re)fill batch b with n pairs: plan strips, waves and offsets on the host,
+// grow the device buffers when needed, and copy the inputs to the device.
+static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_t n)
 {
-    if (!c || !out || (n && !pairs)) return MP_EINVAL;
-    *out = nullptr;
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
         if ((q.prot_len && !q.prot) || (q.nt_len && !q.nt)) return MP_EINVAL;
         if (q.strand != 1 && q.strand != -1) return MP_EINVAL;
+        if (q.prot_len >= (1u << 20) || q.nt_len >= (1u << 20) - 1024) return MP_EINVAL;
     }
     if (cudaSetDevice(c->device) != cudaSuccess) return MP_ECUDA;
-    mp_dp_batch *b = new (std::nothrow) mp_dp_batch();
-    if (!b) return MP_ENOMEM;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->runs = 0;
     b->n = n;
-    b->desc.resize(n);
+    b->desc.assign(n, PairDesc{});
     b->nt_len.resize(n);
     b->strand.resize(n);
+    b->waves.clear();
+    b->cells = 0;
+    b->code_bytes_total = 0;
     // ---- layout
-    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0;
+    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0;
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
         PairDesc &d = b->desc[k];
-        memset(&d, 0, sizeof(d));
         d.prot_len = q.prot_len;
         d.nt_len = q.nt_len;
         d.strand = q.strand;
@@ -358,16 +369,20 @@ int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch
         d.cig_off = ops;
         d.cig_cap = q.prot_len + q.nt_len + 2;
         ops += d.cig_cap;
+        d.n_strips = static_cast<uint32_t>(div_up(q.prot_len, kStripW));
+        d.strip_base = static_cast<uint32_t>(strips);
+        strips += d.n_strips;
         if (q.flags & MP_PAIR_SCORE_ONLY) d.flags |= PF_SCORE_ONLY;
         if (q.prot_len == 0 || q.nt_len == 0) d.flags |= PF_SKIP;
         b->nt_len[k] = q.nt_len;
         b->strand[k] = q.strand;
         b->cells += static_cast<double>(q.prot_len) * q.nt_len;
     }
-    if (asc > 0xffffffffull || pro > 0xffffffffull || ntw > 0xffffffffull) { delete b; return MP_EINVAL; }
+    if (asc > 0xffffffffull || pro > 0xffffffffull || ntw > 0xffffffffull || strips > 0xffffffffull)
+        return MP_EINVAL;
     b->ascii_bytes = asc; b->prot_total = pro; b->nt_words = ntw; b->bnd_total = bnd; b->ops_total = ops;
 
-    // ---- work order: largest first (longest-processing-time first)
+    // ---- pair order: largest first (longest-processing-time first)
     b->order.resize(n);
     for (size_t k = 0; k < n; ++k) b->order[k] = static_cast<uint32_t>(k);
     std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
@@ -375,61 +390,85 @@ int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch
         const uint64_t cy = static_cast<uint64_t>(b->desc[y].prot_len) * b->desc[y].nt_len;
         return cx > cy;
     });
-    // ---- waves under the traceback budget
+    // ---- waves under the traceback budget; strip items in pair order
     const uint64_t cap = c->budget;
     uint64_t cur = 0, maxw = 0;
-    uint32_t wbeg = 0;
+    uint32_t wbeg = 0, ibeg = 0;
+    b->h_items.clear();
+    b->h_items.reserve(strips);
+    b->item_off.assign(n + 1, 0);
     for (uint32_t k = 0; k < n; ++k) {
-        PairDesc &d = b->desc[b->order[k]];
-        if (d.flags & (PF_SKIP | PF_SCORE_ONLY)) continue;
-        const uint64_t cb = code_bytes(d.prot_len, d.nt_len);
-        if (cb > cap) {
-            d.flags |= PF_BUDGET | PF_SCORE_ONLY;
-            continue;
+        const uint32_t p = b->order[k];
+        PairDesc &d = b->desc[p];
+        b->item_off[k] = static_cast<uint32_t>(b->h_items.size());
+        if (d.flags & PF_SKIP) continue;
+        uint64_t cb = 0;
+        if (!(d.flags & PF_SCORE_ONLY)) {
+            cb = code_bytes(d.prot_len, d.nt_len);
+            if (cb > cap) {
+                d.flags |= PF_BUDGET | PF_SCORE_ONLY;
+                cb = 0;
+            }
         }
-        if (cur + cb > cap) {
-            b->waves.push_back(Wave{wbeg, k, cur});
+        if (cb && cur + cb > cap) {
+            b->waves.push_back(Wave{wbeg, k, ibeg, static_cast<uint32_t>(b->h_items.size()), cur});
             maxw = std::max(maxw, cur);
             wbeg = k;
+            ibeg = static_cast<uint32_t>(b->h_items.size());
             cur = 0;
         }
         d.code_off = cur;
         cur += div_up(cb, 256) * 256;
         b->code_bytes_total += cb;
+        for (uint32_t s = 0; s < d.n_strips; ++s) b->h_items.push_back(make_uint2(p, s));
     }
-    b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), cur});
+    b->item_off[n] = static_cast<uint32_t>(b->h_items.size());
+    b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), ibeg, static_cast<uint32_t>(b->h_items.size()), cur});
     maxw = std::max(maxw, cur);
+    // per-run state block
+    const size_t ncnt = 4 * b->waves.size() + 4;
+    b->off_done = div_up(ncnt * 4, 8) * 8;
+    b->off_progress = b->off_done + div_up(n * 4, 8) * 8;
+    b->off_key = b->off_progress + div_up(strips * 4, 8) * 8;
+    b->state_bytes = b->off_key + n * 8 + 8;
 
-    // ---- device buffers
+    // ---- device buffers (grown, never shrunk)
     cudaError_t e = cudaSuccess;
-    if ((e = b->ascii.reserve(asc + 16)) != cudaSuccess || (e = b->d_desc.reserve(n)) != cudaSuccess ||
-        (e = b->prot.reserve(pro + 16)) != cudaSuccess || (e = b->nt2.reserve(ntw + 16)) != cudaSuccess ||
-        (e = b->out.reserve(n)) != cudaSuccess || (e = b->ops.reserve(ops + 1)) != cudaSuccess ||
+    if ((e = b->ascii.reserve(asc + 16)) != cudaSuccess || (e = b->d_desc.reserve(n + 1)) != cudaSuccess ||
+        (e = b->prot.reserve(pro + 16)) != cudaSuccess || (e = b->nt2.reserve(ntw + 32)) != cudaSuccess ||
+        (e = b->out.reserve(n + 1)) != cudaSuccess || (e = b->ops.reserve(ops + 1)) != cudaSuccess ||
         (e = b->cig.reserve(ops + 1)) != cudaSuccess || (e = b->work.reserve(n + 1)) != cudaSuccess ||
-        (e = b->counters.reserve(4 * b->waves.size() + 4)) != cudaSuccess ||
-        (e = b->rerun_list.reserve(n + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
+        (e = b->items.reserve(strips + 1)) != cudaSuccess || (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess ||
+        (e = b->state.reserve(b->state_bytes / 8 + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
         (e = c->codes.reserve(std::max<uint64_t>(maxw, 256))) != cudaSuccess) {
-        free_batch_device(b);
-        delete b;
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
     // ---- host -> device
-    if (c->staging.reserve(asc + 16) != cudaSuccess) { free_batch_device(b); delete b; return MP_ENOMEM; }
+    if (c->staging.reserve(asc + 16) != cudaSuccess) return MP_ENOMEM;
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
         if (q.prot_len) memcpy(c->staging.p + b->desc[k].asc_prot_off, q.prot, q.prot_len);
         if (q.nt_len) memcpy(c->staging.p + b->desc[k].asc_nt_off, q.nt, q.nt_len);
     }
     cudaStream_t st = c->stream;
-    if (cudaMemcpyAsync(b->ascii.p, c->staging.p, asc, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        free_batch_device(b);
-        delete b;
-        return MP_ECUDA;
+    CK(cudaMemcpyAsync(b->ascii.p, c->staging.p, asc, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->items.p, b->h_items.data(), b->h_items.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return MP_OK;
+}
+
+int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch **out)
+{
+    if (!c || !out || (n && !pairs)) return MP_EINVAL;
+    *out = nullptr;
+    mp_dp_batch *b = new (std::nothrow) mp_dp_batch();
+    if (!b) return MP_ENOMEM;
+    const int rc = upload_impl(c, b, pairs, n);
+    if (rc != MP_OK) {
+        mp_dp_batch_free(c, b);
+        return rc;
     }
     *out = b;
     return MP_OK;
@@ -446,15 +485,18 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         return capturing ? cudaEventRecordWithFlags(b->events[idx], st, cudaEventRecordExternal)
                          : cudaEventRecord(b->events[idx], st);
     };
+    char *state = reinterpret_cast<char *>(b->state.p);
+    uint32_t *counters = reinterpret_cast<uint32_t *>(state);
+    const size_t W = b->waves.size();
     CK(rec(0));
-    CK(cudaMemsetAsync(b->counters.p, 0, sizeof(uint32_t) * (4 * b->waves.size() + 4), st));
+    CK(cudaMemsetAsync(state, 0, b->state_bytes, st));
     CK(launch_pack(b->d_desc.p, n, b->ascii.p, b->prot.p, b->nt2.p, b->out.p, st));
     ++launches;
     CK(rec(1));
     const int g16 = c->num_sms * dp16_blocks_per_sm();
     const int g32 = c->num_sms * dp32_blocks_per_sm();
     const int per_launch = c->params.max_pairs_per_launch;
-    for (size_t w = 0; w < b->waves.size(); ++w) {
+    for (size_t w = 0; w < W; ++w) {
         const Wave &wv = b->waves[w];
         DPArgs a{};
         a.pairs = b->d_desc.p;
@@ -463,29 +505,36 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         a.codes = c->codes.p;
         a.bnd = b->bnd.p;
         a.out = b->out.p;
-        a.rerun_list = b->rerun_list.p + wv.begin;
-        a.rerun_count = b->counters.p + 4 * w + 2;
+        a.progress = reinterpret_cast<uint32_t *>(state + b->off_progress);
+        a.best_key = reinterpret_cast<unsigned long long *>(state + b->off_key);
+        a.strips_done = reinterpret_cast<uint32_t *>(state + b->off_done);
+        a.rerun_items = b->rerun_items.p + wv.ibegin;
+        a.rerun_count = counters + 4 * w + 2;
         a.sp = c->sp;
-        const uint32_t cnt = wv.end - wv.begin;
+        const uint32_t nitems = wv.iend - wv.ibegin;
         if (per_launch > 0) {
             // plain form: one kernel launch per group of pairs
-            for (uint32_t k = 0; k < cnt; k += per_launch) {
+            for (uint32_t k = wv.begin; k < wv.end; k += per_launch) {
+                const uint32_t k2 = std::min<uint32_t>(wv.end, k + per_launch);
                 DPArgs a1 = a;
-                a1.work = b->work.p + wv.begin + k;
-                a1.n_work = std::min<uint32_t>(per_launch, cnt - k);
-                a1.head = b->counters.p + 4 * b->waves.size() + (k & 1);
+                a1.items = b->items.p + b->item_off[k];
+                a1.n_items = b->item_off[k2] - b->item_off[k];
+                if (!a1.n_items) continue;
+                a1.head = counters + 4 * W + (k & 1);
                 CK(cudaMemsetAsync(a1.head, 0, sizeof(uint32_t), st));
-                if (c->params.force_int32) CK(launch_dp32(a1, 1, false, st));
-                else CK(launch_dp16(a1, 1, st));
+                const int grid = std::max(1, std::min<int>(c->num_sms, static_cast<int>((a1.n_items + kWarpsPerCta - 1) / kWarpsPerCta)));
+                if (c->params.force_int32) CK(launch_dp32(a1, grid, false, st));
+                else CK(launch_dp16(a1, grid, st));
                 ++launches;
                 ++dp_launches;
             }
         } else {
-            a.work = b->work.p + wv.begin;
-            a.n_work = cnt;
-            a.head = b->counters.p + 4 * w;
-            const int grid16 = std::max(1, std::min<int>(g16, static_cast<int>((cnt + kWarpsPerCta - 1) / kWarpsPerCta)));
-            const int grid32 = std::max(1, std::min<int>(g32, static_cast<int>((cnt + kWarpsPerCta - 1) / kWarpsPerCta)));
+            a.items = b->items.p + wv.ibegin;
+            a.n_items = nitems;
+            a.head = counters + 4 * w;
+            const int want = static_cast<int>((nitems + kWarpsPerCta - 1) / kWarpsPerCta);
+            const int grid16 = std::max(1, std::min<int>(g16, want));
+            const int grid32 = std::max(1, std::min<int>(g32, want));
             if (c->params.force_int32) CK(launch_dp32(a, grid32, false, st));
             else CK(launch_dp16(a, grid16, st));
             ++launches;
@@ -493,11 +542,10 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         }
         CK(rec(2 + EV_PER_WAVE * w));
         if (!c->params.force_int32) {
-            a.head = b->counters.p + 4 * w + 1;
-            a.work = nullptr;
-            a.n_work = 0;
-            const int grid32 = std::max(1, std::min<int>(g32, 2 * c->num_sms));
-            CK(launch_dp32(a, grid32, true, st));
+            a.head = counters + 4 * w + 1;
+            a.items = nullptr;
+            a.n_items = 0;
+            CK(launch_dp32(a, g32, true, st));
             ++launches;
             ++dp_launches;
         }
@@ -505,18 +553,18 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         TBArgs t{};
         t.pairs = b->d_desc.p;
         t.work = b->work.p + wv.begin;
-        t.n_work = cnt;
+        t.n_work = wv.end - wv.begin;
         t.codes = c->codes.p;
         t.out = b->out.p;
         t.ops = b->ops.p;
-        const int tgrid = std::max(1, std::min<int>(c->num_sms * 8, static_cast<int>((cnt + 7) / 8)));
+        const int tgrid = std::max(1, std::min<int>(c->num_sms * 8, static_cast<int>((t.n_work + 7) / 8)));
         CK(launch_tb(t, tgrid, st));
         ++launches;
         CK(rec(4 + EV_PER_WAVE * w));
     }
-    CK(launch_compact(b->d_desc.p, b->out.p, n, b->ops.p, b->cig.p, b->counters.p + 4 * b->waves.size() + 2, st));
+    CK(launch_compact(b->d_desc.p, b->out.p, n, b->ops.p, b->cig.p, counters + 4 * W + 2, st));
     launches += 2;
-    CK(rec(static_cast<int>(2 + EV_PER_WAVE * b->waves.size())));
+    CK(rec(static_cast<int>(2 + EV_PER_WAVE * W)));
     b->n_launches = launches;
     b->n_dp_launches = dp_launches;
     return MP_OK;
@@ -614,7 +662,8 @@ int mp_dp_batch_download(mp_dp_ctx *c, mp_dp_batch *b, mp_result *out)
     b->h_out.resize(n);
     uint32_t total = 0;
     CK(cudaMemcpyAsync(b->h_out.data(), b->out.p, n * sizeof(PairOut), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&total, b->counters.p + 4 * b->waves.size() + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&total, reinterpret_cast<uint32_t *>(b->state.p) + 4 * b->waves.size() + 2, sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c->host_cig.resize(std::max<size_t>(total, 1));
     if (total) {
@@ -706,8 +755,6 @@ static void finish_slot(mp_dp_ctx *c, Slot &s, bool ok)
         c->served_pairs += s.tickets.size();
     }
     c->cv_done.notify_all();
-    mp_dp_batch_free(s.ctx, s.batch);
-    s.batch = nullptr;
     s.busy = false;
     s.tickets.clear();
 }
@@ -762,7 +809,9 @@ static void serve_loop(mp_dp_ctx *c)
             s.tickets.clear();
             for (auto &r : take) s.tickets.push_back(r.ticket);
             s.res.assign(take.size(), mp_result{});
-            bool ok = mp_dp_batch_upload(s.ctx, pairs.data(), pairs.size(), &s.batch) == MP_OK;
+            // the slot's batch keeps its device buffers from one micro-batch to the next
+            if (!s.batch) s.batch = new (std::nothrow) mp_dp_batch();
+            bool ok = s.batch && upload_impl(s.ctx, s.batch, pairs.data(), pairs.size()) == MP_OK;
             if (ok) ok = mp_dp_batch_run(s.ctx, s.batch) == MP_OK;
             s.busy = true;
             if (!ok) finish_slot(c, s, false);
