@@ -166,6 +166,7 @@ struct Ops16 {
     static constexpr uint32_t K = 0x80008000u;
     static constexpr uint32_t SBIAS = 0x02000200u;  // profile entries hold s + 512
     static constexpr Bnd kBnd0 = 0x40008000u;       // column 0: H = 0, I = -inf
+    static constexpr int kMinBlocks = 3;             // shared memory allows 3 CTAs per SM
 
     struct Consts {
         uint32_t QE, E, F, KF;             // packed q+e, e, f and K - f
@@ -338,6 +339,7 @@ struct Ops32 {
     };
     static constexpr int32_t NEG = -(1 << 28);
     static constexpr Bnd kBnd0 = {0, NEG};
+    static constexpr int kMinBlocks = 2;
 
     struct Consts {
         int32_t qe, e, f;
@@ -669,7 +671,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
 }
 
 template <typename Ops>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) dp_kernel(const DPArgs a, int rerun_only)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, Ops::kMinBlocks) dp_kernel(const DPArgs a, int rerun_only)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SM = WarpSmem<typename Ops::Bnd>;
