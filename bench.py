@@ -161,31 +161,28 @@ def run_reference(args):
 
 
 def serve_once(mp, pairs, rate: float, seconds: float, device: int):
-    """Open-loop Poisson arrivals; latency = submit -> result available."""
+    """Open-loop Poisson arrivals at `rate` per second for `seconds`.
+    Latency (submit -> result available) is recorded by the library; a
+    consumer thread drains results."""
     import random
 
     ctx = mp.mp_dp_init(None, device)
     rng = random.Random(4)
-    lat = []
-    t_sub = {}
     stop = threading.Event()
-    lock = threading.Lock()
+    got = [0]
 
     def consumer():
-        while not stop.is_set() or len(lat) < len(t_sub):
-            r = mp.mp_dp_wait_any(ctx, 200_000)
-            if r is None:
-                if stop.is_set() and len(lat) >= len(t_sub):
-                    break
-                continue
-            now = time.perf_counter()
-            with lock:
-                lat.append(now - t_sub[r[0]])
+        while True:
+            r = mp.mp_dp_wait_any(ctx, 100_000)
+            if r is not None:
+                got[0] += 1
+            elif stop.is_set():
+                break
 
+    t = mp.mp_dp_submit(ctx, pairs[0])                 # start and warm the serving thread
+    mp.mp_dp_poll(ctx, t, 30_000_000)
+    mp.mp_dp_get_serve_stats(ctx, reset=True)
     th = threading.Thread(target=consumer, daemon=True)
-    # warm the serving thread
-    t = mp.mp_dp_submit(ctx, pairs[0])
-    mp.mp_dp_poll(ctx, t, -1)
     th.start()
     t0 = time.perf_counter()
     nxt = t0
@@ -196,19 +193,21 @@ def serve_once(mp, pairs, rate: float, seconds: float, device: int):
             break
         while time.perf_counter() < nxt:
             pass
-        p = pairs[k % len(pairs)]
+        mp.mp_dp_submit(ctx, pairs[k % len(pairs)])
         k += 1
-        with lock:
-            tk = mp.mp_dp_submit(ctx, p)
-            t_sub[tk] = time.perf_counter()
-    stop.set()
-    th.join(timeout=120)
+    t_sub_end = time.perf_counter()
+    deadline = time.perf_counter() + 120
+    while mp.mp_dp_get_serve_stats(ctx)["completed"] < k and time.perf_counter() < deadline:
+        time.sleep(0.01)
     wall = time.perf_counter() - t0
+    st = mp.mp_dp_get_serve_stats(ctx)
+    stop.set()
+    th.join(timeout=10)
     mp.mp_dp_destroy(ctx)
-    lat.sort()
-    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] * 1000 if lat else None
-    return {"rate_per_s": rate, "seconds": seconds, "submitted": k, "completed": len(lat),
-            "pairs_per_s": len(lat) / wall, "p50_ms": q(0.50), "p99_ms": q(0.99)}
+    return {"rate_per_s": rate, "seconds": seconds, "submitted": k, "completed": int(st["completed"]),
+            "offered_per_s": k / (t_sub_end - t0), "pairs_per_s": st["completed"] / wall,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "batches": int(st["batches"]), "mean_batch_pairs": st["mean_batch_pairs"]}
 
 
 def main():
@@ -259,12 +258,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    clk = Clocks(local).__enter__()          # sampler starts before the warm-up, outside the timed region
     for _ in range(args.warmup):
         mp.mp_dp_batch_run(ctx, batch)
         mp.mp_dp_batch_sync(ctx)
     dp_ms, rr_ms, tb_ms, tot_ms = [], [], [], []
+    clk.samples.clear()
     barrier()
-    with Clocks(local) as clk:
+    if True:
         t0 = time.perf_counter()
         for _ in range(args.steps):
             flush.zero_()
@@ -276,6 +277,7 @@ def main():
             tot_ms.append(st["total_ms"])
         barrier()
         elapsed = time.perf_counter() - t0
+    clk.__exit__()
     stats = mp.mp_dp_get_stats(ctx)
     res = mp.mp_dp_batch_download(ctx, batch, raw=True)
     n_rerun = int(((res["status"] & 1) != 0).sum())

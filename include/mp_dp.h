@@ -174,6 +174,20 @@ int mp_dp_poll(mp_dp_ctx *ctx, uint64_t ticket, mp_result *out, int64_t timeout_
  * it and *out holds its result with the same lifetime as mp_dp_poll's. */
 int mp_dp_wait_any(mp_dp_ctx *ctx, uint64_t *ticket, mp_result *out, int64_t timeout_us);
 
+/* Serving counters since the context was created: requests completed,
+ * micro-batches launched, and the latency of each completed request from
+ * mp_dp_submit to the moment its result became available to mp_dp_poll
+ * (p50 / p99 / max over all completed requests, or since the last call
+ * with reset != 0). */
+typedef struct {
+    uint64_t completed;
+    uint64_t batches;
+    double mean_batch_pairs;
+    double p50_ms, p99_ms, max_ms;
+} mp_dp_serve_stats;
+
+int mp_dp_get_serve_stats(mp_dp_ctx *ctx, mp_dp_serve_stats *s, int reset);
+
 /* Drain the serving thread, free every device and host buffer. */
 void mp_dp_destroy(mp_dp_ctx *ctx);
 

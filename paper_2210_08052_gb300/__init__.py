@@ -18,14 +18,14 @@ SO_PATH = _build.SO
 
 MP_OK, MP_EINVAL, MP_ENOMEM, MP_EBUDGET, MP_ETIMEOUT = 0, -1, -2, -3, -4
 MP_ECUDA, MP_EPENDING, MP_EAGAIN, MP_ETICKET, MP_ESTATE = -5, -6, -7, -8, -9
-MP_ST_RERUN, MP_ST_BADSEQ, MP_ST_BUDGET, MP_ST_TRACE, MP_ST_ERRMASK = 0x1, 0x10, 0x20, 0x40, 0xF0
+MP_ST_RERUN, MP_ST_BADSEQ, MP_ST_BUDGET, MP_ST_TRACE, MP_ST_TIMEOUT, MP_ST_ERRMASK = 0x1, 0x10, 0x20, 0x40, 0x80, 0xF0
 MP_PAIR_SCORE_ONLY = 0x1
 OP_NAMES = "MIDFGNUV"
 
 EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_batch_upload",
             "mp_dp_batch_run", "mp_dp_batch_sync", "mp_dp_batch_download", "mp_dp_batch_free",
             "mp_dp_submit", "mp_dp_poll", "mp_dp_wait_any", "mp_dp_destroy", "mp_dp_strerror",
-            "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms"]
+            "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats"]
 
 
 class mp_dp_params(ctypes.Structure):
@@ -57,6 +57,12 @@ class mp_dp_stats(ctypes.Structure):
                 ("n_dp_launches", ctypes.c_int32), ("code_bytes", ctypes.c_uint64)]
 
 
+class mp_dp_serve_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("mean_batch_pairs", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -86,6 +92,7 @@ def lib():
             "mp_dp_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "mp_dp_get_stats": (ctypes.c_int, [vp, P(mp_dp_stats)]),
             "mp_dp_num_sms": (ctypes.c_int, [vp]),
+            "mp_dp_get_serve_stats": (ctypes.c_int, [vp, P(mp_dp_serve_stats), ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -264,6 +271,12 @@ def mp_dp_get_stats(ctx) -> dict:
     s = mp_dp_stats()
     _check(lib().mp_dp_get_stats(ctx, ctypes.byref(s)), "mp_dp_get_stats")
     return {k: getattr(s, k) for k, _ in mp_dp_stats._fields_}
+
+
+def mp_dp_get_serve_stats(ctx, reset: bool = False) -> dict:
+    s = mp_dp_serve_stats()
+    _check(lib().mp_dp_get_serve_stats(ctx, ctypes.byref(s), 1 if reset else 0), "mp_dp_get_serve_stats")
+    return {k: getattr(s, k) for k, _ in mp_dp_serve_stats._fields_}
 
 
 def mp_dp_num_sms(ctx) -> int:

@@ -207,6 +207,7 @@ struct mp_dp_ctx {
     int n_slots = 3;                      // micro-batches in flight on the device
     uint64_t slot_budget = 0;
     uint64_t served_batches = 0, served_pairs = 0;
+    std::vector<float> latencies_ms;      // submit -> result available, per completed request
 };
 
 // ====================================================================== API
@@ -728,6 +729,7 @@ struct Slot {
     mp_dp_ctx *ctx = nullptr;
     mp_dp_batch *batch = nullptr;
     std::vector<uint64_t> tickets;
+    std::vector<std::chrono::steady_clock::time_point> t_submit;
     std::vector<mp_result> res;
     bool busy = false;
 };
@@ -736,8 +738,10 @@ static void finish_slot(mp_dp_ctx *c, Slot &s, bool ok)
 {
     if (ok && mp_dp_batch_download(s.ctx, s.batch, s.res.data()) != MP_OK) ok = false;
     {
+        const auto now = std::chrono::steady_clock::now();
         std::lock_guard<std::mutex> lk(c->mu);
         for (size_t k = 0; k < s.tickets.size(); ++k) {
+            c->latencies_ms.push_back(std::chrono::duration<float, std::milli>(now - s.t_submit[k]).count());
             Done d;
             if (ok) {
                 d.r = s.res[k];
@@ -807,7 +811,11 @@ static void serve_loop(mp_dp_ctx *c)
                 pairs[k].flags = take[k].flags;
             }
             s.tickets.clear();
-            for (auto &r : take) s.tickets.push_back(r.ticket);
+            s.t_submit.clear();
+            for (auto &r : take) {
+                s.tickets.push_back(r.ticket);
+                s.t_submit.push_back(r.t_submit);
+            }
             s.res.assign(take.size(), mp_result{});
             // the slot's batch keeps its device buffers from one micro-batch to the next
             if (!s.batch) s.batch = new (std::nothrow) mp_dp_batch();
@@ -920,6 +928,30 @@ extern "C" int mp_dp_wait_any(mp_dp_ctx *c, uint64_t *ticket, mp_result *out, in
     else c->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
     if (pick()) return deliver(c, *ticket, out);
     return MP_ETIMEOUT;
+}
+
+extern "C" int mp_dp_get_serve_stats(mp_dp_ctx *c, mp_dp_serve_stats *out, int reset)
+{
+    if (!c || !out) return MP_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    memset(out, 0, sizeof(*out));
+    std::vector<float> v = c->latencies_ms;
+    out->completed = v.size();
+    out->batches = c->served_batches;
+    out->mean_batch_pairs = c->served_batches ? static_cast<double>(c->served_pairs) / c->served_batches : 0.0;
+    if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        auto q = [&](double f) { return static_cast<double>(v[std::min(v.size() - 1, static_cast<size_t>(f * v.size()))]); };
+        out->p50_ms = q(0.50);
+        out->p99_ms = q(0.99);
+        out->max_ms = v.back();
+    }
+    if (reset) {
+        c->latencies_ms.clear();
+        c->served_batches = 0;
+        c->served_pairs = 0;
+    }
+    return MP_OK;
 }
 
 extern "C" void mp_dp_destroy(mp_dp_ctx *c)
