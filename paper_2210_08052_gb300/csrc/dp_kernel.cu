@@ -617,7 +617,8 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
         if (s + 1 < nstrips) {
             // publish residue 64s+63 for strip s+1
             for (int k = lane; k < kChunk; k += 32) bnd[t0 + k - (kStripW - 1)] = sm.bout[k];
-            __threadfence();
+            // __syncwarp orders every lane's stores before lane 0's release
+            // (release is cumulative), so one release store publishes the chunk
             __syncwarp();
             if (lane == 0) st_release(mine, static_cast<uint32_t>(ch + 1));
         }
