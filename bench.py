@@ -252,6 +252,8 @@ def main():
     mp.mp_dp_set_timing(ctx, True)
     batch = mp.mp_dp_batch_upload(ctx, pairs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush.zero_()                            # first touch of the flush buffer stays outside the timed region
+    torch.cuda.synchronize()
 
     def barrier():
         if dist:

@@ -29,7 +29,8 @@
 // ---------------
 // Each cell stores 16 bits: STOP (H == 0), one "term >= H" bit per H term of
 // Eq. 7 in printed order, and one "open >= extend" bit per gap and intron
-// state.  The traceback takes the first set term bit, which realises the
+// state.  The 32-bit word of a lane and step holds its two cells with bytes
+// [lo bits 0-7, hi bits 0-7, lo bits 8-15, hi bits 8-15].  The traceback takes the first set term bit, which realises the
 // earliest-term-wins tie rule.  Bits are produced as sign bits of packed
 // differences and gathered with sign-replicating byte permutes.
 #include "mp_internal.cuh"
@@ -220,7 +221,7 @@ struct Ops16 {
         const uint32_t VD0 = rec.x, VA0 = rec.y;
         const uint32_t X0 = *reinterpret_cast<const uint32_t *>(
             reinterpret_cast<const char *>(prof_lane) + rec.z);
-        const uint32_t S = prmt<0x7610>(X0, s.X1);        // lo: s(i, 2l); hi: s(i-1, 2l+1)
+        const uint32_t S = (X0 & 0x0000ffffu) | (s.X1 & 0xffff0000u);   // lo: s(i, 2l); hi: s(i-1, 2l+1)
         const uint32_t M = s.L3 + S - SBIAS;
         const uint32_t Iopen = s.L0 - c.QE, Iext = s.IL - c.E;
         uint32_t I0 = vmax(Iopen, Iext);
@@ -280,7 +281,7 @@ struct Ops16 {
         acc |= prmt<0xFDB9>(g5, g13) & 0x20202020u;
         acc |= prmt<0xFDB9>(g6, g14) & 0x40404040u;
         acc |= prmt<0xFDB9>(g7, g15) & 0x80808080u;
-        const uint32_t code = prmt<0x3120>(acc, 0u);     // [lo code16, hi code16]
+        const uint32_t code = acc;   // bytes: lo flags 0-7, hi flags 0-7, lo flags 8-15, hi flags 8-15
 
         // hand [H, I] of the hi cell to the next lane; lane 0 takes the strip boundary
         const uint32_t W = prmt<0x7632>(H0, I0);
@@ -300,8 +301,8 @@ struct Ops16 {
         // best cell: key = H << 16 | (0xffff - step within chunk); the
         // largest key is the largest H at its first step
         const uint32_t Hm = H0 & vmask;
-        s.bklo = max(s.bklo, prmt<0x5410>(s.TC, Hm));
-        s.bkhi = max(s.bkhi, prmt<0x7610>(s.TC, Hm));
+        s.bklo = max(s.bklo, Hm * 65536u + s.TC);                 // [TC, H.lo]
+        s.bkhi = max(s.bkhi, (Hm & 0xffff0000u) | s.TC);         // [TC, H.hi]
         s.TC -= 1;
         return code;
     }
@@ -417,11 +418,13 @@ struct Ops32 {
                           sub(Ap, H0), sub(Bp, H0), sub(Cp, H0),
                           sub(Iopen, Iext), sub(Dopen, Dext), sub(Aopen, s.A1),
                           sub(Bopen, s.B1), sub(Copen, s.C1)};
+        // same byte layout as the int16 path: lo flags 0-7, hi flags 0-7,
+        // lo flags 8-15, hi flags 8-15
         uint32_t acc = 0;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            acc |= ~prmt<0xFFBB>(static_cast<uint32_t>(d[k].lo), static_cast<uint32_t>(d[k].hi)) &
-                   (0x00010001u << k);
+            acc |= ~prmt<0xFBFB>(static_cast<uint32_t>(d[k].lo), static_cast<uint32_t>(d[k].hi)) &
+                   (k < 8 ? (0x00000101u << k) : (0x01010000u << (k - 8)));
         const uint32_t code = acc;
 
         const int32_t Wh = H0.hi, Wi = I0.hi;

@@ -102,7 +102,9 @@ struct CodeView {
         const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(
             base + static_cast<size_t>(s) * strip_bytes + static_cast<size_t>(t >> 2) * 512 +
             (r >> 1) * 16 + (t & 3) * 4));
-        return (r & 1) ? (w >> 16) : (w & 0xffffu);
+        // bytes of w: [lo bits 0-7, hi bits 0-7, lo bits 8-15, hi bits 8-15]
+        const uint32_t v = w >> (8 * (r & 1));
+        return (v & 0xffu) | ((v >> 8) & 0xff00u);
     }
 };
 
