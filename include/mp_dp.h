@@ -49,6 +49,7 @@ extern "C" {
 #define MP_EAGAIN (-7)    /* mp_dp_submit: request ring full, retry later */
 #define MP_ETICKET (-8)   /* unknown or already-consumed ticket */
 #define MP_ESTATE (-9)    /* call not valid in the context's current state */
+#define MP_ETOOLARGE (-10) /* mp_dp_score_pair_noalloc: input beyond its fixed scratch limits */
 
 /* -------------------------------------------------- per-pair status bits */
 #define MP_ST_OK 0x0
@@ -190,6 +191,40 @@ int mp_dp_get_serve_stats(mp_dp_ctx *ctx, mp_dp_serve_stats *s, int reset);
 
 /* Drain the serving thread, free every device and host buffer. */
 void mp_dp_destroy(mp_dp_ctx *ctx);
+
+/* Allocation-free scoring of one pair (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory: code running inside a
+ * CUDA stream capture, where cudaMalloc is forbidden or breaks the capture,
+ * and services that fix their device memory at start-up and must not
+ * allocate, free or synchronize the device afterwards.  The call runs the
+ * same DP as mp_dp_align_batch (packed int16, exact int32 re-run on
+ * saturation), score only, for one pair, and allocates nothing: its scratch
+ * is a fixed array of about 290 KB inside this library, held by every GPU
+ * that loads the library until the process exits.
+ *
+ *   params  scoring parameters (NULL: defaults), validated as by mp_dp_init
+ *   d_prot  device pointer to prot_len ASCII residues, prot_len <= 4096
+ *   d_nt    device pointer to nt_len ASCII nucleotides, nt_len <= 32768
+ *   strand  +1, or -1 to align to the reverse complement of d_nt
+ *   d_out   device pointer to 4 int32, written as {score, status (MP_ST_*),
+ *           protein end, genome end}: the end cell of the best alignment as
+ *           0-based exclusive ends; for strand -1 the genome value is the
+ *           forward-strand start of the alignment (as nt_st of mp_result)
+ *   stream  CUDA stream (cudaStream_t) to launch on; NULL = default stream
+ *
+ * Returns MP_ETOOLARGE beyond the size limits, MP_EINVAL for bad arguments
+ * or parameters, MP_ECUDA if a CUDA call fails; otherwise MP_OK once the
+ * work is enqueued (the result is ready when the stream reaches it).
+ * The first call on a device looks up the scratch address and sets a kernel
+ * attribute (once per device, with that device current); make that first
+ * call before any stream capture.  Every call shares the one scratch array,
+ * which keeps the last call's contents (the kernel clears what must start
+ * at zero); calls that overlap on the GPU (other streams, or other host
+ * threads) race on it and must be serialized by the caller. */
+int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *d_prot, uint32_t prot_len,
+                             const char *d_nt, uint32_t nt_len, int8_t strand, int32_t *d_out,
+                             void *stream);
 
 /* Static string for a return code. */
 const char *mp_dp_strerror(int code);

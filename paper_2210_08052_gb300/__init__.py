@@ -17,7 +17,7 @@ from . import build as _build
 SO_PATH = _build.SO
 
 MP_OK, MP_EINVAL, MP_ENOMEM, MP_EBUDGET, MP_ETIMEOUT = 0, -1, -2, -3, -4
-MP_ECUDA, MP_EPENDING, MP_EAGAIN, MP_ETICKET, MP_ESTATE = -5, -6, -7, -8, -9
+MP_ECUDA, MP_EPENDING, MP_EAGAIN, MP_ETICKET, MP_ESTATE, MP_ETOOLARGE = -5, -6, -7, -8, -9, -10
 MP_ST_RERUN, MP_ST_BADSEQ, MP_ST_BUDGET, MP_ST_TRACE, MP_ST_TIMEOUT, MP_ST_ERRMASK = 0x1, 0x10, 0x20, 0x40, 0x80, 0xF0
 MP_PAIR_SCORE_ONLY = 0x1
 OP_NAMES = "MIDFGNUV"
@@ -25,7 +25,8 @@ OP_NAMES = "MIDFGNUV"
 EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_batch_upload",
             "mp_dp_batch_run", "mp_dp_batch_sync", "mp_dp_batch_download", "mp_dp_batch_free",
             "mp_dp_submit", "mp_dp_poll", "mp_dp_wait_any", "mp_dp_destroy", "mp_dp_strerror",
-            "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats"]
+            "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats",
+            "mp_dp_score_pair_noalloc"]
 
 
 class mp_dp_params(ctypes.Structure):
@@ -93,6 +94,8 @@ def lib():
             "mp_dp_get_stats": (ctypes.c_int, [vp, P(mp_dp_stats)]),
             "mp_dp_num_sms": (ctypes.c_int, [vp]),
             "mp_dp_get_serve_stats": (ctypes.c_int, [vp, P(mp_dp_serve_stats), ctypes.c_int]),
+            "mp_dp_score_pair_noalloc": (ctypes.c_int, [P(mp_dp_params), vp, ctypes.c_uint32, vp, ctypes.c_uint32,
+                                                        ctypes.c_int8, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -281,6 +284,15 @@ def mp_dp_get_serve_stats(ctx, reset: bool = False) -> dict:
 
 def mp_dp_num_sms(ctx) -> int:
     return lib().mp_dp_num_sms(ctx)
+
+
+def mp_dp_score_pair_noalloc(params, d_prot: int, prot_len: int, d_nt: int, nt_len: int, strand: int,
+                             d_out: int, stream: int = 0) -> int:
+    """Allocation-free scoring of one pair from device pointers (see the C
+    header).  Returns the C return code; d_out receives 4 int32."""
+    return lib().mp_dp_score_pair_noalloc(ctypes.byref(params) if params is not None else None,
+                                          ctypes.c_void_p(d_prot), prot_len, ctypes.c_void_p(d_nt), nt_len,
+                                          strand, ctypes.c_void_p(d_out), ctypes.c_void_p(stream))
 
 
 def mp_dp_strerror(code: int) -> str:

@@ -33,6 +33,8 @@
 // [lo bits 0-7, hi bits 0-7, lo bits 8-15, hi bits 8-15].  The traceback takes the first set term bit, which realises the
 // earliest-term-wins tie rule.  Bits are produced as sign bits of packed
 // differences and gathered with sign-replicating byte permutes.
+#include <mutex>
+
 #include "mp_internal.cuh"
 
 namespace mpdp {
@@ -743,3 +745,208 @@ cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t
 }
 
 }  // namespace mpdp
+
+// ===========================================================================
+// Allocation-free scoring of one pair.
+//
+// Some callers cannot call cudaMalloc: code that runs inside a CUDA stream
+// capture (an allocation there is either forbidden or breaks the capture),
+// and services that fix their device memory at start-up and may not
+// allocate or free afterwards (cudaMalloc/cudaFree also synchronize the
+// device, which such a service cannot afford in its serving path).  For
+// them mp_dp_score_pair_noalloc runs the same packed-int16 DP (with the
+// same int32 re-run on saturation) on one pair, score only, using a fixed
+// scratch array that lives in this library's module for the life of the
+// process.  Every GPU that loads the library holds this array until exit.
+// ===========================================================================
+namespace mpdp {
+namespace {
+
+constexpr int kNAMaxProt = 4096;                     // residues
+constexpr int kNAMaxNt = 32768;                      // nucleotides
+constexpr int kNAMaxStrips = kNAMaxProt / kStripW;   // 64
+constexpr int kNANtWords = kNAMaxNt / 16 + 2 * kNtPadWords;
+constexpr int kNABndEntries =
+    ((kNAMaxNt + kStripW - 1 + kChunk - 1) / kChunk) * kChunk + 2 * kBndPad + 32;
+
+struct NoAllocScratch {
+    PairDesc desc;
+    PairOut out;
+    unsigned long long best_key;
+    uint32_t strips_done, rerun_count, head16, head32;
+    uint32_t progress[kNAMaxStrips];
+    uint2 rerun_items[kNAMaxStrips];
+    uint32_t nt2[kNANtWords];
+    uint8_t prot[kNAMaxProt];
+    Ops32::Bnd bnd[kNABndEntries];                   // int32 entries; the int16 pass uses the first half
+};
+
+// The scratch itself (about 290 KB).  Host code must not pass this name to a
+// kernel: on the host it is only a stand-in for the symbol.  Its device
+// address is looked up with cudaGetSymbolAddress at set-up.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+__device__ __forceinline__ uint8_t na_aa_code(unsigned char c)
+{
+    // ARNDCQEGHILKMFPSTWYV -> 0..19, '*' -> 20, anything else -> X (21)
+    const char *order = "arndcqeghilkmfpstwyv";
+    const unsigned char l = c | 0x20;
+    for (int k = 0; k < 20; ++k)
+        if (order[k] == l) return static_cast<uint8_t>(k);
+    return c == '*' ? 20 : 21;
+}
+
+__device__ __forceinline__ int na_nt_code(unsigned char c)
+{
+    switch (c | 0x20) {
+    case 'a': return 0;
+    case 'c': return 1;
+    case 'g': return 2;
+    case 't': return 3;
+    default: return -1;
+    }
+}
+
+// One CTA of kWarpsPerCta warps: pack the pair into the scratch, run its
+// strips on cooperating warps (int16, then int32 if it saturated), write
+// {score, status, protein end, genome end on the forward strand} to out4.
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 1)
+dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_ascii, int n, int strand,
+                  int32_t *out4, NoAllocScratch *S)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int bad;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nstrips = (m + kStripW - 1) / kStripW;
+    if (threadIdx.x == 0) {
+        PairDesc d{};
+        d.prot_len = static_cast<uint32_t>(m);
+        d.nt_len = static_cast<uint32_t>(n);
+        d.nt_word_off = kNtPadWords;
+        d.flags = PF_SCORE_ONLY;
+        d.strand = strand;
+        d.n_strips = static_cast<uint32_t>(nstrips);
+        S->desc = d;
+        PairOut o{};
+        o.best_ii = o.best_jj = -1;
+        S->out = o;
+        S->best_key = 0;
+        S->strips_done = S->rerun_count = S->head16 = S->head32 = 0;
+        bad = 0;
+    }
+    // every call starts from zeroed progress counters
+    for (int k = threadIdx.x; k < kNAMaxStrips; k += blockDim.x) S->progress[k] = 0;
+    for (int k = threadIdx.x; k < m; k += blockDim.x)
+        S->prot[k] = na_aa_code(static_cast<unsigned char>(prot_ascii[k]));
+    const int nwords = (n + 15) / 16;
+    for (int w = static_cast<int>(threadIdx.x) - kNtPadWords; w < nwords + kNtPadWords; w += blockDim.x) {
+        uint32_t word = 0;
+        for (int k = 0; k < 16 && w >= 0 && w < nwords; ++k) {
+            const int pos = w * 16 + k;
+            if (pos >= n) break;
+            int b = na_nt_code(static_cast<unsigned char>(strand >= 0 ? nt_ascii[pos] : nt_ascii[n - 1 - pos]));
+            if (b < 0) { bad = 1; b = 0; }
+            if (strand < 0) b = 3 - b;
+            word |= static_cast<uint32_t>(b) << (2 * k);
+        }
+        S->nt2[kNtPadWords + w] = word;
+    }
+    __syncthreads();
+    if (!bad && m > 0 && n > 0) {
+        DPArgs a{};
+        a.pairs = &S->desc;
+        a.prot = S->prot;
+        a.nt2 = S->nt2;
+        a.codes = nullptr;                       // score only: no traceback codes
+        a.bnd = S->bnd;
+        a.out = &S->out;
+        a.progress = S->progress;
+        a.best_key = &S->best_key;
+        a.strips_done = &S->strips_done;
+        a.rerun_items = S->rerun_items;
+        a.rerun_count = &S->rerun_count;
+        a.sp = sp;
+        {
+            auto &sm = reinterpret_cast<WarpSmem<Ops16::Bnd> *>(smem_raw)[warp];
+            for (;;) {
+                uint32_t s = 0;
+                if (lane == 0) s = atomicAdd(&S->head16, 1u);
+                s = __shfl_sync(kFull, s, 0);
+                if (s >= static_cast<uint32_t>(nstrips)) break;
+                run_strip<Ops16>(a, sm, 0, static_cast<int>(s), lane, false);
+            }
+        }
+        __syncthreads();
+        const uint32_t nre = *reinterpret_cast<volatile uint32_t *>(&S->rerun_count);
+        if (nre) {
+            auto &sm = reinterpret_cast<WarpSmem<Ops32::Bnd> *>(smem_raw)[warp];
+            for (;;) {
+                uint32_t s = 0;
+                if (lane == 0) s = atomicAdd(&S->head32, 1u);
+                s = __shfl_sync(kFull, s, 0);
+                if (s >= nre) break;
+                run_strip<Ops32>(a, sm, 0, static_cast<int>(S->rerun_items[s].y), lane, true);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const PairOut o = S->out;                // written by this block before the barrier
+        const int score = bad ? 0 : (o.score > 0 ? o.score : 0);
+        out4[0] = score;
+        out4[1] = bad ? MP_ST_BADSEQ : o.status;
+        out4[2] = score > 0 ? o.best_jj + 1 : 0;
+        out4[3] = score > 0 ? (strand >= 0 ? o.best_ii + 1 : n - (o.best_ii + 1)) : 0;
+    }
+}
+
+constexpr size_t kNASmem = sizeof(WarpSmem<Ops32::Bnd>) * kWarpsPerCta;   // covers the int16 layout too
+
+}  // namespace
+}  // namespace mpdp
+
+extern "C" int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *d_prot, uint32_t prot_len,
+                                        const char *d_nt, uint32_t nt_len, int8_t strand, int32_t *d_out,
+                                        void *stream)
+{
+    using namespace mpdp;
+    if (prot_len > static_cast<uint32_t>(kNAMaxProt) || nt_len > static_cast<uint32_t>(kNAMaxNt))
+        return MP_ETOOLARGE;
+    if (!d_out || (prot_len && !d_prot) || (nt_len && !d_nt) || (strand != 1 && strand != -1)) return MP_EINVAL;
+    mp_dp_params p;
+    if (params) p = *params;
+    else mp_dp_default_params(&p);
+    int mn = 0;
+    for (int x = 0; x < 20; ++x)
+        for (int y = 0; y < 22; ++y) mn = p.mat[x][y] < mn ? p.mat[x][y] : mn;
+    if (p.q < 0 || p.e < 1 || p.f < 0 || p.r < 0 || p.stop < 0 || p.q + p.e > 1000 || p.f > 1000 ||
+        p.r > 1000 || p.stop > 512 || !(p.r > p.f && p.r > p.stop && p.r > -mn))
+        return MP_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return MP_ECUDA;
+    // Set-up, once per device, with that device current: the device address
+    // of the scratch array and the kernel's shared-memory attribute.  The
+    // first call on a device does this, so make it before any stream capture.
+    constexpr int kMaxDev = 64;
+    static void *scratch_ptr[kMaxDev] = {};
+    static std::once_flag once[kMaxDev];
+    if (dev >= kMaxDev) return MP_ECUDA;
+    cudaError_t setup_err = cudaSuccess;
+    std::call_once(once[dev], [&] {
+        void *ptr = nullptr;
+        setup_err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (setup_err == cudaSuccess)
+            setup_err = cudaFuncSetAttribute(dp_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kNASmem));
+        if (setup_err == cudaSuccess) scratch_ptr[dev] = ptr;
+    });
+    if (setup_err != cudaSuccess || !scratch_ptr[dev]) return MP_ECUDA;
+    ScoreParams sp;
+    sp.q = p.q; sp.e = p.e; sp.f = p.f; sp.r = p.r; sp.stop = p.stop;
+    for (int x = 0; x < 22; ++x)
+        for (int y = 0; y < 22; ++y) sp.mat[x][y] = p.mat[x][y];
+    dp_noalloc_kernel<<<1, kWarpsPerCta * 32, kNASmem, static_cast<cudaStream_t>(stream)>>>(
+        sp, d_prot, static_cast<int>(prot_len), d_nt, static_cast<int>(nt_len), strand, d_out,
+        static_cast<NoAllocScratch *>(scratch_ptr[dev]));
+    return cudaGetLastError() == cudaSuccess ? MP_OK : MP_ECUDA;
+}

@@ -244,6 +244,7 @@ const char *mp_dp_strerror(int code)
     case MP_EAGAIN: return "request ring full";
     case MP_ETICKET: return "unknown ticket";
     case MP_ESTATE: return "invalid state";
+    case MP_ETOOLARGE: return "input exceeds the fixed scratch of the allocation-free entry point";
     default: return "unknown error";
     }
 }
