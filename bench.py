@@ -27,6 +27,9 @@ METRIC = "Spliced-DP GCUPS + pairs/s, batched vs plain, 1 GB300; serving p50/p99
 WORKLOAD = ("4096 (protein, region) pairs: protein log-normal median 350 aa (50-2000); "
             "Poisson(3) GT-AG introns, log-normal median 800 nt; 10-40% substitutions; 0-3 frameshifts; "
             "1 kb flanks at 40% GC; half reverse strand; seed 2 (+1000 per rank)")
+WORKLOAD_C3 = ("20000 (protein, region) pairs, uneven sizes: protein log-uniform 20-5000 aa; introns as the "
+               "4096-pair workload plus a 2% tail of 20-100 kb; regions <= 200 kb; 5% score-only decoys; "
+               "seed 3 (+1000 per rank)")
 # algorithmic integer ops per cell: 27 max/add of Eq. 7 + 16 comparisons deciding the traceback code
 OPS_PER_CELL = 43
 
@@ -221,6 +224,8 @@ def main():
     ap.add_argument("--serve-rates", default="10000")
     ap.add_argument("--pairs", type=int, default=4096, help="first N pairs of the workload (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: skip the end-to-end leg")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: the 4,096-pair batch (default); c3: the 20,000-pair uneven-size stress batch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -246,7 +251,12 @@ def main():
         dist.barrier()
     mpbuild.build()
 
-    pairs = synth.config2(seed=2 + 1000 * rank)[: args.pairs]
+    if args.workload == "c3":
+        pairs = synth.config3(seed=3 + 1000 * rank)[: args.pairs if args.pairs != 4096 else None]
+        workload = WORKLOAD_C3
+    else:
+        pairs = synth.config2(seed=2 + 1000 * rank)[: args.pairs]
+        workload = WORKLOAD
     cells = float(sum(p.cells for p in pairs))
     ctx = mp.mp_dp_init(None, local)
     mp.mp_dp_set_timing(ctx, True)
@@ -340,7 +350,7 @@ def main():
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pairs": len(pairs), "cells": cells,
+        "config": {"workload": workload, "pairs": len(pairs), "cells": cells, "waves": stats["n_waves"],
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps; each step also writes "
                          f"{stats['code_bytes'] / 1e9:.1f} GB of traceback codes"},

@@ -77,6 +77,7 @@ extern "C" {
 #define MP_MODE_LOCAL 0     /* local alignment (the only mode of this version) */
 
 #define MP_PAIR_SCORE_ONLY 0x1u  /* mp_pair.flags: score and end cell only, no CIGAR */
+#define MP_DEBUG_NO_PUBLISH 0x1  /* mp_dp_params.debug_flags (tests only) */
 
 /* Scoring parameters.  The paper prints no default values for q, e, f, r or
  * the stop penalty; mp_dp_default_params fills q=11, e=1, f=23, r=29,
@@ -96,7 +97,12 @@ typedef struct {
                                   by free device memory at init) */
     int32_t force_int32;       /* 1: skip the packed int16 pass and run every pair in int32 */
     int32_t max_pairs_per_launch; /* 0: no limit; 1: one pair per kernel launch (plain form) */
-    int32_t reserved[6];
+    int32_t wait_limit;        /* polls (~0.25 us each) before a warp waiting on the previous
+                                  strip of its pair gives up and marks the pair MP_ST_TIMEOUT;
+                                  0: default (4e7) */
+    int32_t debug_flags;       /* test hook: MP_DEBUG_NO_PUBLISH makes every strip withhold its
+                                  boundary row, so the waits of the next strip run out */
+    int32_t reserved[4];
 } mp_dp_params;
 
 /* One alignment request.  prot: ASCII amino acids; nt: ASCII A/C/G/T

@@ -20,6 +20,7 @@ MP_OK, MP_EINVAL, MP_ENOMEM, MP_EBUDGET, MP_ETIMEOUT = 0, -1, -2, -3, -4
 MP_ECUDA, MP_EPENDING, MP_EAGAIN, MP_ETICKET, MP_ESTATE, MP_ETOOLARGE = -5, -6, -7, -8, -9, -10
 MP_ST_RERUN, MP_ST_BADSEQ, MP_ST_BUDGET, MP_ST_TRACE, MP_ST_TIMEOUT, MP_ST_ERRMASK = 0x1, 0x10, 0x20, 0x40, 0x80, 0xF0
 MP_PAIR_SCORE_ONLY = 0x1
+MP_DEBUG_NO_PUBLISH = 0x1
 OP_NAMES = "MIDFGNUV"
 
 EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_batch_upload",
@@ -35,7 +36,8 @@ class mp_dp_params(ctypes.Structure):
                 ("mat", (ctypes.c_int8 * 22) * 22),
                 ("splice_model", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("tb_budget_bytes", ctypes.c_uint64), ("force_int32", ctypes.c_int32),
-                ("max_pairs_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("max_pairs_per_launch", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
+                ("debug_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class mp_pair(ctypes.Structure):

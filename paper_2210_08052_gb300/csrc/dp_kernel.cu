@@ -550,6 +550,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     bool timed_out = false;
 
     // wait until strip s-1 has published `need` chunks (bounded)
+    const uint32_t spin_limit = a.spin_limit ? a.spin_limit : kSpinLimit;
     auto wait_for = [&](uint32_t need) {
         if (s == 0 || timed_out) return;
         uint32_t ok = 1;
@@ -557,7 +558,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
             uint32_t it = 0;
             while (ld_acquire(prev) < need) {
                 __nanosleep(256);
-                if (++it > kSpinLimit) { ok = 0; break; }
+                if (++it > spin_limit) { ok = 0; break; }
             }
         }
         ok = __shfl_sync(kFull, ok, 0);
@@ -619,7 +620,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
             else run_chunk<Ops, false, false>(st, c, sm, lane, t0, n, code_strip);
         }
         __syncwarp();
-        if (s + 1 < nstrips) {
+        if (s + 1 < nstrips && !a.no_publish) {
             // publish residue 64s+63 for strip s+1
             for (int k = lane; k < kChunk; k += 32) bnd[t0 + k - (kStripW - 1)] = sm.bout[k];
             // __syncwarp orders every lane's stores before lane 0's release

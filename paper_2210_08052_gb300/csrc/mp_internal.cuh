@@ -89,6 +89,8 @@ struct DPArgs {
     uint2 *rerun_items;     // strips of pairs whose int16 run saturated
     uint32_t *rerun_count;
     ScoreParams sp;
+    uint32_t spin_limit;    // polls before a wait gives up (0: kSpinLimit)
+    uint32_t no_publish;    // test hook: withhold boundary rows
 };
 
 // bounded wait of a consumer strip for its producer (iterations of ~0.25 us)

@@ -259,7 +259,7 @@ static int validate_params(const mp_dp_params *p)
     // an intron of length <= 0 must lose to a frameshift or a match from the same cell
     if (!(p->r > p->f && p->r > p->stop && p->r > -mn)) return MP_EINVAL;
     if (p->splice_model != MP_SPLICE_FINAL || p->mode != MP_MODE_LOCAL) return MP_EINVAL;
-    if (p->max_pairs_per_launch < 0) return MP_EINVAL;
+    if (p->max_pairs_per_launch < 0 || p->wait_limit < 0) return MP_EINVAL;
     return MP_OK;
 }
 
@@ -513,6 +513,8 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         a.rerun_items = b->rerun_items.p + wv.ibegin;
         a.rerun_count = counters + 4 * w + 2;
         a.sp = c->sp;
+        a.spin_limit = c->params.wait_limit > 0 ? static_cast<uint32_t>(c->params.wait_limit) : 0u;
+        a.no_publish = (c->params.debug_flags & MP_DEBUG_NO_PUBLISH) ? 1u : 0u;
         const uint32_t nitems = wv.iend - wv.ibegin;
         if (per_launch > 0) {
             // plain form: one kernel launch per group of pairs

@@ -60,9 +60,13 @@ def pairs_cells(pairs) -> int:
     return int(sum(len(p.prot) * len(p.nt) for p in pairs))
 
 
+_AA20_BYTES = np.frombuffer(AA20.encode(), dtype=np.uint8)
+_BASE_BYTES = np.frombuffer(b"ACGT", dtype=np.uint8)
+
+
 def random_protein(rng: np.random.Generator, n: int) -> str:
     idx = rng.choice(20, size=n, p=_FREQ)
-    return "".join(AA20[k] for k in idx)
+    return _AA20_BYTES[idx].tobytes().decode()
 
 
 def random_dna(rng: np.random.Generator, n: int, gc: float = 0.5) -> str:
@@ -70,7 +74,7 @@ def random_dna(rng: np.random.Generator, n: int, gc: float = 0.5) -> str:
         return ""
     p = np.array([(1 - gc) / 2, gc / 2, gc / 2, (1 - gc) / 2])
     idx = rng.choice(4, size=n, p=p)
-    return "".join(_BASES[k] for k in idx)
+    return _BASE_BYTES[idx].tobytes().decode()
 
 
 def reverse_translate(rng: np.random.Generator, prot: str) -> str:

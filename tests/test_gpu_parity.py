@@ -315,3 +315,58 @@ def test_serving_alone_and_in_mix(mp, ctx):
         assert mp.lib().mp_dp_poll(c, tickets[0], ctypes.byref(mp.mp_result()), 0) == mp.MP_ETICKET
     finally:
         mp.mp_dp_destroy(c)
+
+
+def test_cooperating_wait_runs_out_without_fault(mp, ctx, orc):
+    """Failure detection without a GPU fault: with every boundary row
+    withheld, each warp waiting on the previous strip of its pair gives up
+    after a short poll limit; the kernel completes, multi-strip pairs are
+    reported MP_ST_TIMEOUT, single-strip pairs are unaffected, and the
+    context and device stay usable."""
+    pairs = _gene_pairs(81, 24, 300, 500)
+    c = mp.mp_dp_init(mp.mp_dp_default_params(wait_limit=2000, debug_flags=mp.MP_DEBUG_NO_PUBLISH), 0)
+    try:
+        got = mp.mp_dp_align_batch(c, pairs)
+        for p, g in zip(pairs, got):
+            if len(p.prot) > 64:
+                assert g["status"] & mp.MP_ST_TIMEOUT
+            else:
+                assert not g["status"] & 0xF0
+        again = mp.mp_dp_align_batch(ctx, pairs)
+        _compare(orc, pairs[:6], again[:6])
+        assert any(len(p.prot) > 64 for p in pairs) and any(len(p.prot) <= 64 for p in pairs)
+    finally:
+        mp.mp_dp_destroy(c)
+
+
+def test_uneven_stress_batch_sampled(mp, ctx, orc):
+    """The 20,000-pair uneven-size workload (up to 5,000 residues and 200 kb
+    regions, 5% score-only decoys) in one call, spread over traceback
+    waves: a stratified sample against the oracle, every CIGAR rescored."""
+    pairs = synth.config3()
+    got = mp.mp_dp_align_batch(ctx, pairs)
+    assert mp.mp_dp_get_stats(ctx)["n_waves"] > 1
+    cells = np.array([p.cells for p in pairs])
+    small = np.flatnonzero(cells < 12_000_000)
+    order = small[np.argsort(cells[small])]
+    sample = sorted(set(order[:: max(1, len(order) // 30)].tolist()) | set(order[-2:].tolist()))
+    for k in sample:
+        p, g = pairs[k], got[k]
+        w = orc.align(p.prot, p.nt, p.strand)
+        assert g["score"] == w["score"] and g["prot_en"] == w["prot_en"], k
+        if p.score_only:
+            assert g["cigar"] == [] and g["nt_en"] == w["nt_en"]
+        else:
+            assert {x: g[x] for x in KEYS} == {x: w[x] for x in KEYS}, k
+    bad = []
+    for p, g in zip(pairs, got):
+        assert g["status"] & 0xF0 == 0
+        if p.score_only or g["score"] == 0:
+            continue
+        n = len(p.nt)
+        st = g["nt_st"] if p.strand > 0 else n - g["nt_en"]
+        en = g["nt_en"] if p.strand > 0 else n - g["nt_st"]
+        sc, pe, te = orc.rescore(p.prot, p.nt, p.strand, g["prot_st"], st, g["cigar_raw"])
+        if (sc, pe, te) != (g["score"], g["prot_en"], en):
+            bad.append((sc, g["score"]))
+    assert not bad, bad[:5]
