@@ -34,6 +34,24 @@ WORKLOAD_C3 = ("20000 (protein, region) pairs, uneven sizes: protein log-uniform
 OPS_PER_CELL = 43
 
 
+def _profiled_traffic(cells: float):
+    """DRAM bytes per DP launch, from the committed ncu summary, scaled by
+    cells; None unless that summary was taken on the current kernel source."""
+    import hashlib
+    import re
+
+    try:
+        src = open(os.path.join(ROOT, "paper_2210_08052_gb300", "csrc", "dp_kernel.cu"), "rb").read()
+        text = open(os.path.join(ROOT, "profiles", "dp16_c2small_full.md")).read()
+    except OSError:
+        return None
+    h = re.search(r"sha256 \(first 16 hex\): ([0-9a-f]{16})", text)
+    b = re.search(r"traffic_bytes_per_cell: ([0-9.]+)", text)
+    if not h or not b or hashlib.sha256(src).hexdigest()[:16] != h.group(1):
+        return None
+    return float(b.group(1)) * cells
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -339,13 +357,7 @@ def main():
     peak_ops = nsm * 128 * 2 * f_mhz * 1e6 / 1e12          # int16 lane-ops/s (Tops)
     dp_avg_ms = statistics.mean(dp_ms) if dp_ms else None
     achieved = cells * OPS_PER_CELL / (dp_avg_ms / 1000) / 1e12 if dp_avg_ms else None
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "dp16_traffic.json")) as fh:
-            tj = json.load(fh)
-            traffic = tj.get("bytes_per_launch_full_workload")
-    except (OSError, ValueError):
-        pass
+    traffic = _profiled_traffic(cells)
     line = {
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -572,14 +572,17 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
 #pragma unroll 2
     for (int aa = 0; aa < kProfRows; ++aa)
         sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), subst_score(a.sp, aa, phi));
-    // records for ii in [-96, 95]
-    for (int ii = -kChunk + lane; ii < kChunk; ii += 32) {
+    // records for ii in [-max(kChunk, kStripW), kChunk)
+    for (int ii = -(kChunk > kStripW ? kChunk : kStripW) + lane; ii < kChunk; ii += 32) {
         const uint4 rec = make_record(g, n, ii, a.sp.r);
         const int slot = ii & (kRing - 1);
         sm.ring[slot] = rec;
         if (slot < kRingPad) sm.ring[slot + kRing] = rec;
     }
-    wait_for(nchunks < 2 ? nchunks : 2);
+    // chunk c reads boundary entries c*kChunk+1 .. (c+1)*kChunk, which strip s-1
+    // writes kStripW-1 steps later: up to its chunk c + 1 + (kStripW-1)/kChunk
+    constexpr int kLag = 2 + (kStripW - 1) / kChunk;
+    wait_for(nchunks < kLag ? nchunks : kLag);
     __syncwarp();
     typename Ops::State st;
     {
@@ -602,8 +605,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
                 sm.ring[slot] = rec;
                 if (slot < kRingPad) sm.ring[slot + kRing] = rec;
             }
-            // the boundary entries of this chunk are flushed by strip s-1's chunks ch and ch+1
-            wait_for(ch + 2 < nchunks ? ch + 2 : nchunks);
+            wait_for(ch + kLag < nchunks ? ch + kLag : nchunks);
         }
         if (s == 0) {
             for (int k = lane; k < kChunk; k += 32) sm.bin[k] = Ops::kBnd0;   // column 0: H = 0, I = -inf
