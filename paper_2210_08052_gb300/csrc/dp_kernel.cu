@@ -25,16 +25,17 @@
 // 0 or 65536.  A pair whose best score reaches 32000 is re-run in the int32
 // instantiation of the same kernel.
 //
-// Traceback codes
-// ---------------
-// Each cell stores 16 bits: STOP (H == 0), one "term >= H" bit per H term of
-// Eq. 7 in printed order, and one "open >= extend" bit per gap and intron
-// state.  The 32-bit word of a lane and step holds its two cells with bytes
-// [lo bits 0-7, hi bits 0-7, lo bits 8-15, hi bits 8-15].  The traceback takes the first set term bit, which realises the
-// earliest-term-wins tie rule.  Bits are produced as sign bits of packed
-// differences and gathered with sign-replicating byte permutes.
+// Traceback stream
+// ----------------
+// The kernel stores the H value of every cell (2 bytes in the int16 path,
+// 4 bytes in the int32 re-run): the 32-bit H register of a lane already
+// holds its two cells, so the stream costs one 16-byte store per lane every
+// 4 steps and no arithmetic.  The traceback kernel re-derives each decision
+// of Eq. 7 from these values (the gap and intron states in closed form),
+// with the same tie order.
 #include <mutex>
 
+#include "mp_device.cuh"
 #include "mp_internal.cuh"
 
 namespace mpdp {
@@ -56,61 +57,6 @@ __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b)
     uint32_t r;
     asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
     return r;
-}
-
-// ------------------------------------------------------ genetic code table
-constexpr char kAAOrder[] = "ARNDCQEGHILKMFPSTWYV*";
-// NCBI table 1 with codons enumerated as A, C, G, T in each position.
-constexpr char kCodeACGT[] = "KNKNTTTTRSRSIIMIQHQHPPPPRRRRLLLLEDEDAAAAGGGGVVVV*Y*YSSSS*CWCLFLF";
-
-constexpr int aa_index(char c)
-{
-    for (int k = 0; k < 21; ++k)
-        if (kAAOrder[k] == c) return k;
-    return 21;
-}
-
-struct CodeTable {
-    int8_t v[64];
-};
-
-constexpr CodeTable make_code_table()
-{
-    CodeTable t{};
-    for (int k = 0; k < 64; ++k) t.v[k] = static_cast<int8_t>(aa_index(kCodeACGT[k]));
-    return t;
-}
-
-__constant__ CodeTable c_code = make_code_table();
-
-// --------------------------------------------------------- splice signals
-// Final splice model.  Bases: 0 A, 1 C, 2 G, 3 T; v* false = outside T,
-// which matches no motif.
-__device__ __forceinline__ int donor_score(int b1, int b2, int b3, bool v1, bool v2, bool v3)
-{
-    // d(x) from T[x+1..x+3]: GT[AG] 0, GT[CT] 8, GC 15, AT 21, else 30
-    if (v1 && v2) {
-        if (b1 == 2 && b2 == 3) {
-            if (v3) return (b3 == 0 || b3 == 2) ? 0 : 8;
-            return 30;
-        }
-        if (b1 == 2 && b2 == 1) return 15;
-        if (b1 == 0 && b2 == 3) return 21;
-    }
-    return 30;
-}
-
-__device__ __forceinline__ int acceptor_score(int b1, int b2, int b3, bool v1, bool v2, bool v3)
-{
-    // a(x) from T[x-2..x]: [CT]AG 0, [AG]AG 8, AC (last two) 21, else 30
-    if (v2 && v3 && b2 == 0) {
-        if (b3 == 2) {
-            if (!v1) return 30;
-            return (b1 == 1 || b1 == 3) ? 0 : 8;
-        }
-        if (b3 == 1) return 21;
-    }
-    return 30;
 }
 
 // Per-genome-position record for the lo cell at 0-based position ii
@@ -143,13 +89,6 @@ __device__ __forceinline__ uint4 make_record(const uint32_t *g, int n, int ii, i
     rec.z = static_cast<uint32_t>(aa) * 128u;
     rec.w = 0;
     return rec;
-}
-
-__device__ __forceinline__ int subst_score(const ScoreParams &sp, int aa, int pc)
-{
-    if (aa == 21) return -512;             // no complete codon (i < 3)
-    if (aa == 20) return -sp.stop;         // stop codon against any residue
-    return sp.mat[aa][pc];
 }
 
 // --------------------------------------------------------------- smem
@@ -214,7 +153,9 @@ struct Ops16 {
         s.TC = 0xffffu; s.bklo = 0; s.bkhi = 0;
     }
 
-    // One anti-diagonal step.  Returns the packed 2x16-bit code word.
+    using Word = uint32_t;                  // traceback word of one lane and step: [H lo, H hi]
+
+    // One anti-diagonal step.  Returns the lane's two H values (biased).
     template <bool MASKED>
     static __device__ __forceinline__ uint32_t step(State &s, const Consts &c, const uint4 rec,
                                                     const uint32_t *prof_lane, Bnd bin, Bnd *bout,
@@ -257,34 +198,6 @@ struct Ops16 {
             vmask = ((ii >= 0 && ii < n) ? 0x0000ffffu : 0u) | ((ii >= 1 && ii <= n) ? 0xffff0000u : 0u);
         }
 
-        // "a >= b" per half lands in bits 15 and 31 of a - b + K
-        const uint32_t g0 = Z - H0 + K;
-        const uint32_t g1 = M - H0 + K;
-        const uint32_t g2 = I0 - H0 + K;
-        const uint32_t g3 = D0 - H0 + K;
-        const uint32_t g4 = s.L1 - H0 + c.KF;
-        const uint32_t g5 = s.L2 - H0 + c.KF;
-        const uint32_t g6 = s.H1 - H0 + c.KF;
-        const uint32_t g7 = s.H2 - H0 + c.KF;
-        const uint32_t g8 = Ap - H0 + K;
-        const uint32_t g9 = Bp - H0 + K;
-        const uint32_t g10 = Cp - H0 + K;
-        const uint32_t g11 = Iopen - Iext + K;
-        const uint32_t g12 = Dopen - Dext + K;
-        const uint32_t g13 = Aopen - s.A1 + K;
-        const uint32_t g14 = Bopen - s.B1 + K;
-        const uint32_t g15 = Copen - s.C1 + K;
-        // bytes: [flag k lo, flag k hi, flag k+8 lo, flag k+8 hi], sign-replicated
-        uint32_t acc = prmt<0xFDB9>(g0, g8) & 0x01010101u;
-        acc |= prmt<0xFDB9>(g1, g9) & 0x02020202u;
-        acc |= prmt<0xFDB9>(g2, g10) & 0x04040404u;
-        acc |= prmt<0xFDB9>(g3, g11) & 0x08080808u;
-        acc |= prmt<0xFDB9>(g4, g12) & 0x10101010u;
-        acc |= prmt<0xFDB9>(g5, g13) & 0x20202020u;
-        acc |= prmt<0xFDB9>(g6, g14) & 0x40404040u;
-        acc |= prmt<0xFDB9>(g7, g15) & 0x80808080u;
-        const uint32_t code = acc;   // bytes: lo flags 0-7, hi flags 0-7, lo flags 8-15, hi flags 8-15
-
         // hand [H, I] of the hi cell to the next lane; lane 0 takes the strip boundary
         const uint32_t W = prmt<0x7632>(H0, I0);
         uint32_t R = __shfl_up_sync(kFull, W, 1);
@@ -306,7 +219,14 @@ struct Ops16 {
         s.bklo = max(s.bklo, Hm * 65536u + s.TC);                 // [TC, H.lo]
         s.bkhi = max(s.bkhi, (Hm & 0xffff0000u) | s.TC);         // [TC, H.hi]
         s.TC -= 1;
-        return code;
+        return H0;
+    }
+
+    // four steps of one lane: one 16-byte store
+    static __device__ __forceinline__ void store4(uint8_t *strip, int t, int lane, const Word *w)
+    {
+        *reinterpret_cast<uint4 *>(strip + static_cast<size_t>(t) * kStepBytes + lane * 16) =
+            make_uint4(w[0], w[1], w[2], w[3]);
     }
 
     // Extract (score, step) of one half's best key; score < 0 if none.
@@ -380,10 +300,12 @@ struct Ops32 {
         s.bslo = s.bshi = 0; s.btlo = s.bthi = 0; s.t = 0;
     }
 
+    using Word = uint2;                     // [H lo, H hi] as int32
+
     template <bool MASKED>
-    static __device__ __forceinline__ uint32_t step(State &s, const Consts &c, const uint4 rec,
-                                                    const uint32_t *prof_lane, Bnd bin, Bnd *bout,
-                                                    int lane, int ii, int n)
+    static __device__ __forceinline__ uint2 step(State &s, const Consts &c, const uint4 rec,
+                                                 const uint32_t *prof_lane, Bnd bin, Bnd *bout,
+                                                 int lane, int ii, int n)
     {
         const V2 VD0 = unpack16(rec.x), VA0 = unpack16(rec.y);
         const uint32_t X0 = *reinterpret_cast<const uint32_t *>(
@@ -413,22 +335,6 @@ struct Ops32 {
             vhi = ii >= 1 && ii <= n;
         }
 
-        // sign of a - b is set iff a < b: the flag is its complement
-        const V2 d[16] = {sub(V2{0, 0}, H0), sub(M, H0), sub(I0, H0), sub(D0, H0),
-                          subc(sub(s.L1, H0), c.f), subc(sub(s.L2, H0), c.f),
-                          subc(sub(s.H1, H0), c.f), subc(sub(s.H2, H0), c.f),
-                          sub(Ap, H0), sub(Bp, H0), sub(Cp, H0),
-                          sub(Iopen, Iext), sub(Dopen, Dext), sub(Aopen, s.A1),
-                          sub(Bopen, s.B1), sub(Copen, s.C1)};
-        // same byte layout as the int16 path: lo flags 0-7, hi flags 0-7,
-        // lo flags 8-15, hi flags 8-15
-        uint32_t acc = 0;
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            acc |= ~prmt<0xFBFB>(static_cast<uint32_t>(d[k].lo), static_cast<uint32_t>(d[k].hi)) &
-                   (k < 8 ? (0x00000101u << k) : (0x01010000u << (k - 8)));
-        const uint32_t code = acc;
-
         const int32_t Wh = H0.hi, Wi = I0.hi;
         int32_t Rh = __shfl_up_sync(kFull, Wh, 1);
         int32_t Ri = __shfl_up_sync(kFull, Wi, 1);
@@ -447,7 +353,15 @@ struct Ops32 {
         if (vlo && H0.lo > s.bslo) { s.bslo = H0.lo; s.btlo = s.t; }
         if (vhi && H0.hi > s.bshi) { s.bshi = H0.hi; s.bthi = s.t; }
         s.t += 1;
-        return code;
+        return make_uint2(static_cast<uint32_t>(H0.lo), static_cast<uint32_t>(H0.hi));
+    }
+
+    // four steps of one lane: two 16-byte stores (4 bytes per cell)
+    static __device__ __forceinline__ void store4(uint8_t *strip, int t, int lane, const Word *w)
+    {
+        uint4 *d = reinterpret_cast<uint4 *>(strip + static_cast<size_t>(t) * (2 * kStepBytes) + lane * 32);
+        d[0] = make_uint4(w[0].x, w[0].y, w[1].x, w[1].y);
+        d[1] = make_uint4(w[2].x, w[2].y, w[3].x, w[3].y);
     }
 
     static __device__ __forceinline__ void take_best(const State &s, int half, int t0, int &score, int &t)
@@ -479,16 +393,12 @@ __device__ __forceinline__ void run_chunk(typename Ops::State &st, const typenam
     for (int b = 0; b < kChunk / kBody; ++b) {
         const int tb = t0 + b * kBody;
         const uint4 *recp = &sm.ring[(tb - 2 * lane) & (kRing - 1)];
-        uint32_t cw[kBody];
+        typename Ops::Word cw[kBody];
 #pragma unroll
         for (int k = 0; k < kBody; ++k) {
             cw[k] = Ops::template step<MASKED>(st, c, recp[k], sm.prof + lane, sm.bin[b * kBody + k],
                                                &sm.bout[b * kBody + k], lane, tb + k - 2 * lane, n);
-            if (STORE && (k & 3) == 3) {
-                uint4 v = make_uint4(cw[k - 3], cw[k - 2], cw[k - 1], cw[k]);
-                *reinterpret_cast<uint4 *>(code_strip + static_cast<size_t>(tb + k - 3) * kStepBytes +
-                                           lane * 16) = v;
-            }
+            if (STORE && (k & 3) == 3) Ops::store4(code_strip, tb + k - 3, lane, &cw[k - 3]);
         }
     }
 }
@@ -544,7 +454,8 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     const typename Ops::Consts c = Ops::consts(a.sp);
     const int nsteps = n + kStripW - 1;
     const int nchunks = (nsteps + kChunk - 1) / kChunk;
-    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes;
+    // 2 bytes per cell in the int16 path, 4 in the int32 path
+    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes * (sizeof(Bnd) / 4);
     const uint32_t *prev = a.progress + pd.strip_base + s - 1;   // valid for s > 0
     uint32_t *mine = a.progress + pd.strip_base + s;
     bool timed_out = false;
@@ -663,9 +574,14 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
             PairOut &o = a.out[p];
             const int score = static_cast<int>(key >> 40);
             o.score = score;
+            if (sizeof(Bnd) == 8) o.status |= kStInt32Stream;
             o.best_ii = score > 0 ? static_cast<int>(0xfffffu - ((key >> 20) & 0xfffffu)) : -1;
             o.best_jj = score > 0 ? static_cast<int>(0xfffffu - (key & 0xfffffu)) : -1;
-            if (!rerun && sizeof(Bnd) == 4 && score >= kOverflowT && !(o.status & MP_ST_TIMEOUT)) {
+            if (!rerun && sizeof(Bnd) == 4 && score >= kOverflowT && !(o.status & MP_ST_TIMEOUT) &&
+                !(pd.flags & PF_WIDE)) {
+                // cannot happen: the pair's score bound was below the int16 limit
+                o.status |= MP_ST_TRACE;
+            } else if (!rerun && sizeof(Bnd) == 4 && score >= kOverflowT && !(o.status & MP_ST_TIMEOUT)) {
                 // int16 saturated: queue every strip of this pair for the int32 kernel
                 o.status |= MP_ST_RERUN;
                 a.best_key[p] = 0;
@@ -826,7 +742,7 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
         d.prot_len = static_cast<uint32_t>(m);
         d.nt_len = static_cast<uint32_t>(n);
         d.nt_word_off = kNtPadWords;
-        d.flags = PF_SCORE_ONLY;
+        d.flags = PF_SCORE_ONLY | PF_WIDE;       // score only: no traceback stream in either mode
         d.strand = strand;
         d.n_strips = static_cast<uint32_t>(nstrips);
         S->desc = d;
@@ -897,7 +813,7 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
         const PairOut o = S->out;                // written by this block before the barrier
         const int score = bad ? 0 : (o.score > 0 ? o.score : 0);
         out4[0] = score;
-        out4[1] = bad ? MP_ST_BADSEQ : o.status;
+        out4[1] = bad ? MP_ST_BADSEQ : (o.status & 0xff);
         out4[2] = score > 0 ? o.best_jj + 1 : 0;
         out4[3] = score > 0 ? (strand >= 0 ? o.best_ii + 1 : n - (o.best_ii + 1)) : 0;
     }

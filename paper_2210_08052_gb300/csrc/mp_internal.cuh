@@ -18,23 +18,14 @@ constexpr int kBndPad = 64;     // boundary entries before genome position 0
 constexpr int kWarpsPerCta = 8; // persistent DP kernel
 constexpr int kNtPadWords = 16; // zero words around each packed genome
 
-// bytes of traceback codes per strip step: 64 cells * 2 B
+// bytes of the traceback stream per strip step in the int16 path: 64 cells * 2 B
+// (the int32 path stores 4 B per cell)
 constexpr int kStepBytes = kStripW * 2;
 
 // int16 path: scores at or above this re-run in int32 (intermediates stay
 // below 32767 while every H is below it; see the design notes)
 constexpr int kOverflowT = 32000;
 
-// ---- code word bits (one 16-bit code per cell) -----------------------------
-// bit 0        H == 0 (restart; wins ties)
-// bits 1..10   term k >= H for M, I, D, F1, F2, G1, G2, A, B, C
-// bits 11..15  open >= extend for I, D, A, B, C
-enum : uint32_t {
-    CB_STOP = 1u << 0, CB_M = 1u << 1, CB_I = 1u << 2, CB_D = 1u << 3,
-    CB_F1 = 1u << 4, CB_F2 = 1u << 5, CB_G1 = 1u << 6, CB_G2 = 1u << 7,
-    CB_A = 1u << 8, CB_B = 1u << 9, CB_C = 1u << 10,
-    CB_IO = 1u << 11, CB_DO = 1u << 12, CB_AO = 1u << 13, CB_BO = 1u << 14, CB_CO = 1u << 15,
-};
 
 // ---- per-pair device descriptors -------------------------------------------
 struct PairDesc {
@@ -54,7 +45,13 @@ struct PairDesc {
     uint32_t n_strips;
 };
 
-enum : uint32_t { PF_SCORE_ONLY = 1u, PF_BADSEQ = 2u, PF_SKIP = 4u, PF_BUDGET = 8u };
+// internal PairOut.status bit (never returned to callers): the pair's
+// traceback stream was written by the int32 kernel (4 bytes per cell)
+constexpr int32_t kStInt32Stream = 0x100;
+
+// PF_WIDE: the pair's score could exceed the int16 range, so its traceback
+// region is sized for the int32 re-run (4 bytes per cell)
+enum : uint32_t { PF_SCORE_ONLY = 1u, PF_BADSEQ = 2u, PF_SKIP = 4u, PF_BUDGET = 8u, PF_WIDE = 16u };
 
 struct PairOut {
     int32_t score;
@@ -100,9 +97,12 @@ struct TBArgs {
     const PairDesc *pairs;
     const uint32_t *work;
     uint32_t n_work;
-    const uint8_t *codes;
+    const uint8_t *codes;   // traceback stream (H of every cell)
+    const uint8_t *prot;    // residue codes
+    const uint32_t *nt2;    // packed genome
     PairOut *out;
     uint32_t *ops;          // reversed-op slots
+    ScoreParams sp;
 };
 
 // kernel launchers (defined in the .cu files)

@@ -52,11 +52,37 @@ constexpr uint64_t kDefaultBudget = 40ull << 30;
 
 inline uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
-// Traceback bytes of one pair: strips x padded steps x 128 B.
-inline uint64_t code_bytes(uint32_t m, uint32_t n)
+// Traceback bytes of one pair: strips x padded steps x 128 B (x 2 when the
+// pair may need the int32 re-run, whose stream holds 4 B per cell).
+inline uint64_t code_bytes(uint32_t m, uint32_t n, bool wide = false)
 {
     const uint64_t nchunks = div_up(static_cast<uint64_t>(n) + kStripW - 1, kChunk);
-    return div_up(m, kStripW) * nchunks * kChunk * kStepBytes;
+    return div_up(m, kStripW) * nchunks * kChunk * kStepBytes * (wide ? 2 : 1);
+}
+
+// Residue letter -> code (ARNDCQEGHILKMFPSTWYV 0..19, '*' 20, else X 21).
+inline int host_aa_code(unsigned char c)
+{
+    static const char order[] = "arndcqeghilkmfpstwyv";
+    const unsigned char l = c | 0x20;
+    for (int k = 0; k < 20; ++k)
+        if (order[k] == l) return k;
+    return c == '*' ? 20 : 21;
+}
+
+// Upper bound of any H of the pair: every residue scores at most its best
+// substitution and every other term of Eq. 7 is a penalty.
+inline int64_t score_bound(const ScoreParams &sp, const char *prot, uint32_t m)
+{
+    int best[22];
+    for (int pc = 0; pc < 22; ++pc) {
+        int b = -sp.stop;
+        for (int t = 0; t < 20; ++t) b = std::max<int>(b, sp.mat[t][pc]);
+        best[pc] = std::max(b, 0);
+    }
+    int64_t s = 0;
+    for (uint32_t k = 0; k < m; ++k) s += best[host_aa_code(static_cast<unsigned char>(prot[k]))];
+    return s;
 }
 
 inline uint64_t bnd_entries(uint32_t n)
@@ -376,6 +402,8 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         strips += d.n_strips;
         if (q.flags & MP_PAIR_SCORE_ONLY) d.flags |= PF_SCORE_ONLY;
         if (q.prot_len == 0 || q.nt_len == 0) d.flags |= PF_SKIP;
+        if (c->params.force_int32 || (q.prot_len && score_bound(c->sp, q.prot, q.prot_len) >= kOverflowT))
+            d.flags |= PF_WIDE;
         b->nt_len[k] = q.nt_len;
         b->strand[k] = q.strand;
         b->cells += static_cast<double>(q.prot_len) * q.nt_len;
@@ -406,7 +434,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         if (d.flags & PF_SKIP) continue;
         uint64_t cb = 0;
         if (!(d.flags & PF_SCORE_ONLY)) {
-            cb = code_bytes(d.prot_len, d.nt_len);
+            cb = code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
             if (cb > cap) {
                 d.flags |= PF_BUDGET | PF_SCORE_ONLY;
                 cb = 0;
@@ -559,8 +587,11 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         t.work = b->work.p + wv.begin;
         t.n_work = wv.end - wv.begin;
         t.codes = c->codes.p;
+        t.prot = b->prot.p;
+        t.nt2 = b->nt2.p;
         t.out = b->out.p;
         t.ops = b->ops.p;
+        t.sp = c->sp;
         const int tgrid = std::max(1, std::min<int>(c->num_sms * 8, static_cast<int>((t.n_work + 7) / 8)));
         CK(launch_tb(t, tgrid, st));
         ++launches;
@@ -680,7 +711,7 @@ int mp_dp_batch_download(mp_dp_ctx *c, mp_dp_batch *b, mp_result *out)
         const PairDesc &d = b->desc[k];
         mp_result &r = out[k];
         memset(&r, 0, sizeof(r));
-        r.status = o.status;
+        r.status = o.status & 0xff;
         if (o.status & MP_ST_RERUN) ++nrerun;
         if ((o.status & MP_ST_ERRMASK) & ~MP_ST_BUDGET) continue;
         r.score = o.score > 0 ? o.score : 0;
@@ -796,7 +827,10 @@ static void serve_loop(mp_dp_ctx *c)
                 uint64_t bytes = 0;
                 while (!c->queue.empty()) {
                     const Request &r = c->queue.front();
-                    const uint64_t cb = (r.flags & MP_PAIR_SCORE_ONLY) ? 0 : code_bytes(r.prot.size(), r.nt.size());
+                    const uint64_t cb = (r.flags & MP_PAIR_SCORE_ONLY)
+                                            ? 0
+                                            : code_bytes(r.prot.size(), r.nt.size(),
+                                                         score_bound(c->sp, r.prot.data(), r.prot.size()) >= kOverflowT);
                     if (!take.empty() && bytes + cb > c->slot_budget) break;
                     bytes += cb;
                     take.push_back(std::move(c->queue.front()));
@@ -855,7 +889,8 @@ extern "C" int mp_dp_submit(mp_dp_ctx *c, const mp_pair *q, uint64_t *ticket)
         return MP_EINVAL;
     std::unique_lock<std::mutex> lk(c->mu);
     if (c->slot_budget == 0) c->slot_budget = c->budget / static_cast<uint64_t>(c->n_slots);
-    if (!(q->flags & MP_PAIR_SCORE_ONLY) && code_bytes(q->prot_len, q->nt_len) > c->slot_budget)
+    if (!(q->flags & MP_PAIR_SCORE_ONLY) &&
+        code_bytes(q->prot_len, q->nt_len, score_bound(c->sp, q->prot, q->prot_len) >= kOverflowT) > c->slot_budget)
         return MP_EBUDGET;
     if (c->stopping) return MP_ESTATE;
     if (c->queue.size() >= c->ring_cap) return MP_EAGAIN;

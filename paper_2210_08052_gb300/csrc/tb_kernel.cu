@@ -1,11 +1,12 @@
 // Input packing, traceback and CIGAR compaction kernels.
 //
-// Traceback walks the direction codes written by the DP kernel from the best
-// cell back to the restart, following the paths of Li 2022 Eq. 7 (Methods,
-// "DP for protein-to-genome alignment"): M, I, D, the four frameshift terms
-// and the three intron states, with the intron coordinates of the phase-1/2
+// Traceback walks from the best cell back to the restart over the H values
+// the DP kernel stored, following the paths of Li 2022 Eq. 7 (Methods, "DP
+// for protein-to-genome alignment"): M, I, D, the four frameshift terms and
+// the three intron states, with the intron coordinates of the phase-1/2
 // states as the paper places them (after Eq. 7).  One warp per pair: codons
-// of an M run, gap runs and intron runs are scanned 32 cells at a time.
+// of an M run, gap rows and intron columns are scanned 32 cells at a time.
+#include "mp_device.cuh"
 #include "mp_internal.cuh"
 
 namespace mpdp {
@@ -90,21 +91,61 @@ __global__ void pack_kernel(const PairDesc *pairs, uint32_t n, const char *ascii
 }
 
 // ------------------------------------------------------------- traceback
-struct CodeView {
+constexpr int kNeg = -(1 << 28);
+
+// Read access to one pair: its traceback stream (H of every cell), genome
+// and protein.  Cells are 1-based (i, j) as in Eq. 7; row 0 and column 0
+// hold H = 0 and rows above 0 are outside the matrix.
+struct PairView {
     const uint8_t *base;
     size_t strip_bytes;
+    bool wide;               // int32 stream (4 B per cell)
+    const uint32_t *g;       // packed genome
+    const uint8_t *P;        // residue codes
+    int n, m;
+    const ScoreParams *sp;
+    const int8_t *mat;       // shared-memory copy of sp->mat
 
-    // 16-bit code of the 1-based cell (i, j)
-    __device__ __forceinline__ uint32_t at(int i, int j) const
+    __device__ __forceinline__ int H(int i, int j) const
     {
+        if (i < 0) return kNeg;
+        if (i == 0 || j == 0) return 0;
         const int ii = i - 1, jj = j - 1;
         const int s = jj >> 6, r = jj & 63, t = ii + r;
+        if (wide) {
+            return __ldg(reinterpret_cast<const int *>(base + static_cast<size_t>(s) * strip_bytes +
+                                                       static_cast<size_t>(t >> 2) * 1024 + (r >> 1) * 32 +
+                                                       (t & 3) * 8 + (r & 1) * 4));
+        }
         const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(
-            base + static_cast<size_t>(s) * strip_bytes + static_cast<size_t>(t >> 2) * 512 +
-            (r >> 1) * 16 + (t & 3) * 4));
-        // bytes of w: [lo bits 0-7, hi bits 0-7, lo bits 8-15, hi bits 8-15]
-        const uint32_t v = w >> (8 * (r & 1));
-        return (v & 0xffu) | ((v >> 8) & 0xff00u);
+            base + static_cast<size_t>(s) * strip_bytes + static_cast<size_t>(t >> 2) * 512 + (r >> 1) * 16 +
+            (t & 3) * 4));
+        return static_cast<int>((r & 1) ? (w >> 16) : (w & 0xffffu)) - 32768;
+    }
+    // base at 1-based position x (0..3), valid iff 1 <= x <= n
+    __device__ __forceinline__ int b(int x) const
+    {
+        return (__ldg(g + ((x - 1) >> 4)) >> (2 * ((x - 1) & 15))) & 3;
+    }
+    __device__ __forceinline__ bool in(int x) const { return x >= 1 && x <= n; }
+    // final splice model: d(x) looks at T[x+1..x+3], a(x) at T[x-2..x]
+    __device__ __forceinline__ int d(int x) const
+    {
+        const bool v1 = in(x + 1), v2 = in(x + 2), v3 = in(x + 3);
+        return donor_score(v1 ? b(x + 1) : 0, v2 ? b(x + 2) : 0, v3 ? b(x + 3) : 0, v1, v2, v3);
+    }
+    __device__ __forceinline__ int a(int x) const
+    {
+        const bool v1 = in(x - 2), v2 = in(x - 1), v3 = in(x);
+        return acceptor_score(v1 ? b(x - 2) : 0, v2 ? b(x - 1) : 0, v3 ? b(x) : 0, v1, v2, v3);
+    }
+    // s(i, j): codon T[i-2..i] against residue P[j]
+    __device__ __forceinline__ int s(int i, int j) const
+    {
+        if (i < 3 || i > n) return kNeg;
+        const int aa = c_code.v[b(i - 2) * 16 + b(i - 1) * 4 + b(i)];
+        if (aa == 20) return -sp->stop;
+        return mat[aa * 22 + P[j - 1]];
     }
 };
 
@@ -134,98 +175,100 @@ struct OpWriter {
     }
 };
 
-enum { ST_H = 0, ST_I, ST_D, ST_A, ST_B, ST_C };
+// First k in [1, kmax] (warp-parallel, 32 candidates per round) for which
+// pred(k) holds; 0 if none.
+template <typename Pred>
+__device__ __forceinline__ int first_hit(int kmax, int lane, Pred pred)
+{
+    for (int k0 = 1; k0 <= kmax; k0 += 32) {
+        const int k = k0 + lane;
+        const unsigned bal = __ballot_sync(kFull, k <= kmax && pred(k));
+        if (bal) return k0 + __ffs(bal) - 1;
+    }
+    return 0;
+}
 
-__device__ void trace_pair(const TBArgs &a, uint32_t p, int lane)
+// Walk back from the best cell to the restart.  At an H cell the source is
+// the first term of Eq. 7 (M, I, D, F1, F2, G1, G2, A, B, C) whose value
+// equals H, the restart when H = 0.  The gap and intron terms use the
+// closed forms of their recurrences,
+//   I[i][j] = max_k H[i][j-k] - q - e k,      D[i][j] = max_k H[i-3k][j] - q - e k,
+//   A[i][j] = max_{i'<=i} H[i'-1][j] - r - d(i'-1),
+//   B[i][j] = max_{i'<=i} H[i'-1][j-1] - r - d(i'),  C: the same with d(i'+1),
+// each bounded above by H[i][j]; the run length the tie rule picks (open
+// before extend) is the shortest one reaching H.
+__device__ void trace_pair(const TBArgs &a, const int8_t *mat_s, uint32_t p, int lane)
 {
     const PairDesc pd = a.pairs[p];
     PairOut &o = a.out[p];
     const int n = static_cast<int>(pd.nt_len);
     const int nchunks = (n + kStripW - 1 + kChunk - 1) / kChunk;
-    const CodeView cv{a.codes + pd.code_off, static_cast<size_t>(nchunks) * kChunk * kStepBytes};
+    const bool wide = (o.status & kStInt32Stream) != 0;
+    const PairView v{a.codes + pd.code_off,
+                     static_cast<size_t>(nchunks) * kChunk * kStepBytes * (wide ? 2 : 1),
+                     wide, a.nt2 + pd.nt_word_off, a.prot + pd.prot_off, n, static_cast<int>(pd.prot_len),
+                     &a.sp, mat_s};
+    const int q = a.sp.q, e = a.sp.e, f = a.sp.f, r = a.sp.r;
+    const int hmax = o.score;
     int i = o.best_ii + 1, j = o.best_jj + 1;
     OpWriter w{a.ops + pd.cig_off, pd.cig_cap, 0, 0, 0, false};
     bool error = false;
-    int state = ST_H, iexit = 0;
     for (;;) {
-        if (state == ST_H) {
-            if (i <= 0 || j <= 0) break;
-            // codes along the codon diagonal: cells (i - 3k, j - k)
-            const int ik = i - 3 * lane, jk = j - lane;
-            const bool in = ik >= 1 && jk >= 1;
-            const uint32_t c = in ? cv.at(ik, jk) : CB_STOP;
-            const bool is_m = in && !(c & CB_STOP) && (c & CB_M);
-            const unsigned nonm = __ballot_sync(kFull, !is_m);
-            const int cnt = nonm ? __ffs(nonm) - 1 : 32;
-            if (cnt > 0) {
-                if (lane == 0) w.push(MP_OP_M, cnt);
-                i -= 3 * cnt;
-                j -= cnt;
-            }
-            if (cnt == 32) continue;
-            const uint32_t cf = __shfl_sync(kFull, c, cnt);
-            if (i <= 0 || j <= 0 || (cf & CB_STOP)) break;
-            const uint32_t terms = cf & 0x7feu;
-            if (!terms) { error = true; break; }
-            const int src = __ffs(terms) - 1;   // 2 I, 3 D, 4 F1, 5 F2, 6 G1, 7 G2, 8 A, 9 B, 10 C
-            switch (src) {
-            case 2: state = ST_I; break;
-            case 3: state = ST_D; break;
-            case 4: if (lane == 0) w.push(MP_OP_F, 1); i -= 1; j -= 1; break;
-            case 5: if (lane == 0) w.push(MP_OP_F, 2); i -= 2; j -= 1; break;
-            case 6: if (lane == 0) w.push(MP_OP_G, 1); i -= 1; break;
-            case 7: if (lane == 0) w.push(MP_OP_G, 2); i -= 2; break;
-            case 8: state = ST_A; iexit = i; break;
-            case 9: state = ST_B; iexit = i; break;
-            case 10: state = ST_C; iexit = i; break;
-            default: error = true; break;
-            }
-            if (error) break;
-        } else {
-            // a run: find the first cell (walking back) whose open flag is set
-            uint32_t bit;
-            int di, dj;
-            switch (state) {
-            case ST_I: bit = CB_IO; di = 0; dj = 1; break;
-            case ST_D: bit = CB_DO; di = 3; dj = 0; break;
-            case ST_A: bit = CB_AO; di = 1; dj = 0; break;
-            case ST_B: bit = CB_BO; di = 1; dj = 0; break;
-            default: bit = CB_CO; di = 1; dj = 0; break;
-            }
-            int k0 = 0, found = -1;
-            for (;;) {
-                const int ik = i - di * (k0 + lane), jk = j - dj * (k0 + lane);
-                const bool in = ik >= 1 && jk >= 1;
-                const bool open = in && (cv.at(ik, jk) & bit);
-                const unsigned bal = __ballot_sync(kFull, open || !in);
-                if (bal) {
-                    const int f = __ffs(bal) - 1;
-                    const bool f_in = __shfl_sync(kFull, in ? 1 : 0, f);
-                    if (!f_in) error = true;
-                    found = k0 + f;
-                    break;
-                }
-                k0 += 32;
-            }
-            if (error) break;
-            const int io = i - di * found, jo = j - dj * found;   // cell where the run opened
-            switch (state) {
-            case ST_I: if (lane == 0) w.push(MP_OP_I, found + 1); j = jo - 1; break;
-            case ST_D: if (lane == 0) w.push(MP_OP_D, found + 1); i = io - 3; break;
-            case ST_A: if (lane == 0) w.push(MP_OP_N, iexit - io + 1); i = io - 1; break;
-            case ST_B:
-            case ST_C: {
-                const int L = iexit - io - 2;
-                if (L < 1) error = true;
-                if (lane == 0) w.push(state == ST_B ? MP_OP_U : MP_OP_V, L > 0 ? L : 0);
-                i = io - 1;
-                j = jo - 1;
-                break;
-            }
-            }
-            if (error) break;
-            state = ST_H;
+        if (i <= 0 || j <= 0) break;
+        // M runs: cells (i - 3k, j - k) along the codon diagonal
+        const int ik = i - 3 * lane, jk = j - lane;
+        const bool inside = ik >= 1 && jk >= 1;
+        const int hk = inside ? v.H(ik, jk) : 0;
+        int hn = __shfl_down_sync(kFull, hk, 1);
+        if (lane == 31) hn = (ik >= 3 && jk >= 1) ? v.H(ik - 3, jk - 1) : kNeg;
+        const bool is_m = inside && hk > 0 && ik >= 3 && hk == hn + v.s(ik, jk);
+        const unsigned nonm = __ballot_sync(kFull, !is_m);
+        const int cnt = nonm ? __ffs(nonm) - 1 : 32;
+        if (cnt > 0) {
+            if (lane == 0) w.push(MP_OP_M, cnt);
+            i -= 3 * cnt;
+            j -= cnt;
         }
+        if (cnt == 32) continue;
+        const int h = __shfl_sync(kFull, hk, cnt);
+        if (i <= 0 || j <= 0 || h <= 0) break;                 // restart wins a tie at 0
+        // I: residues against no genome
+        const int kgap = (hmax - q - h) / e;
+        int k = kgap >= 1 ? first_hit(j < kgap ? j : kgap, lane,
+                                      [&](int kk) { return v.H(i, j - kk) - q - e * kk == h; })
+                          : 0;
+        if (k) { if (lane == 0) w.push(MP_OP_I, k); j -= k; continue; }
+        // D: codons against no residue
+        k = kgap >= 1 ? first_hit(i / 3 < kgap ? i / 3 : kgap, lane,
+                                  [&](int kk) { return v.H(i - 3 * kk, j) - q - e * kk == h; })
+                      : 0;
+        if (k) { if (lane == 0) w.push(MP_OP_D, k); i -= 3 * k; continue; }
+        // frameshifts
+        if (v.H(i - 1, j - 1) - f == h) { if (lane == 0) w.push(MP_OP_F, 1); i -= 1; j -= 1; continue; }
+        if (v.H(i - 2, j - 1) - f == h) { if (lane == 0) w.push(MP_OP_F, 2); i -= 2; j -= 1; continue; }
+        if (v.H(i - 1, j) - f == h) { if (lane == 0) w.push(MP_OP_G, 1); i -= 1; continue; }
+        if (v.H(i - 2, j) - f == h) { if (lane == 0) w.push(MP_OP_G, 2); i -= 2; continue; }
+        // introns: the opening i' nearest to the exit i (k = i - i' + 1)
+        const int va = h + v.a(i);
+        k = first_hit(i, lane, [&](int kk) { const int ip = i - kk + 1; return v.H(ip - 1, j) - r - v.d(ip - 1) == va; });
+        if (k) {
+            if (lane == 0) w.push(MP_OP_N, k);              // intron T[i'..i], length i - i' + 1
+            i -= k;
+            continue;
+        }
+        const int vb = h + v.a(i - 2), vc = h + v.a(i - 1);
+        int op = MP_OP_U;
+        k = first_hit(i, lane, [&](int kk) { const int ip = i - kk + 1; return v.H(ip - 1, j - 1) - r - v.d(ip) == vb; });
+        if (!k) {
+            op = MP_OP_V;
+            k = first_hit(i, lane, [&](int kk) { const int ip = i - kk + 1; return v.H(ip - 1, j - 1) - r - v.d(ip + 1) == vc; });
+        }
+        if (!k) { error = true; break; }
+        const int L = k - 3;                                  // intron length i - i' - 2
+        if (L < 1) { error = true; break; }
+        if (lane == 0) w.push(op, L);
+        i -= k;
+        j -= 1;
     }
     if (lane == 0) {
         w.flush();
@@ -238,6 +281,9 @@ __device__ void trace_pair(const TBArgs &a, uint32_t p, int lane)
 
 __global__ void tb_kernel(const TBArgs a)
 {
+    __shared__ int8_t mat_s[22 * 22];
+    for (int k = threadIdx.x; k < 22 * 22; k += blockDim.x) mat_s[k] = a.sp.mat[k / 22][k % 22];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -247,7 +293,7 @@ __global__ void tb_kernel(const TBArgs a)
         const PairOut &o = a.out[p];
         if ((pd.flags & (PF_SCORE_ONLY | PF_SKIP | PF_BUDGET)) || (o.status & MP_ST_ERRMASK) || o.score <= 0)
             continue;
-        trace_pair(a, p, lane);
+        trace_pair(a, mat_s, p, lane);
     }
 }
 
