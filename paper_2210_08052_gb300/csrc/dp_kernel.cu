@@ -240,6 +240,13 @@ struct Ops16 {
     {
         s.TC = 0xffffu; s.bklo = 0; s.bkhi = 0;
     }
+
+    // this chunk's maximum H of the lane's two cells (biased; 0 if none)
+    using ColMax = uint32_t;
+    static __device__ __forceinline__ ColMax chunk_max(const State &s)
+    {
+        return (s.bklo >> 16) | (s.bkhi & 0xffff0000u);
+    }
 };
 
 // ================================================================ int32 ops
@@ -272,6 +279,7 @@ struct Ops32 {
         V2 VD1, VD2, VA1, VA2;
         uint32_t X1;
         int32_t bslo, bshi, btlo, bthi, t;
+        int32_t cmlo, cmhi;                 // this chunk's maximum H per cell
     };
 
     static __device__ __forceinline__ Consts consts(const ScoreParams &sp)
@@ -298,6 +306,7 @@ struct Ops32 {
         s.VA1 = unpack16(recm1.y); s.VA2 = unpack16(recm2.y);
         s.X1 = xm1;
         s.bslo = s.bshi = 0; s.btlo = s.bthi = 0; s.t = 0;
+        s.cmlo = s.cmhi = NEG;
     }
 
     using Word = uint2;                     // [H lo, H hi] as int32
@@ -352,6 +361,8 @@ struct Ops32 {
 
         if (vlo && H0.lo > s.bslo) { s.bslo = H0.lo; s.btlo = s.t; }
         if (vhi && H0.hi > s.bshi) { s.bshi = H0.hi; s.bthi = s.t; }
+        if (vlo) s.cmlo = max(s.cmlo, H0.lo);
+        if (vhi) s.cmhi = max(s.cmhi, H0.hi);
         s.t += 1;
         return make_uint2(static_cast<uint32_t>(H0.lo), static_cast<uint32_t>(H0.hi));
     }
@@ -371,7 +382,13 @@ struct Ops32 {
         t = half ? s.bthi : s.btlo;
         if (score <= 0) score = -1;
     }
-    static __device__ __forceinline__ void reset_best(State &s) { (void)s; }
+    static __device__ __forceinline__ void reset_best(State &s) { s.cmlo = s.cmhi = NEG; }
+
+    using ColMax = uint2;
+    static __device__ __forceinline__ ColMax chunk_max(const State &s)
+    {
+        return make_uint2(static_cast<uint32_t>(s.cmlo), static_cast<uint32_t>(s.cmhi));
+    }
 };
 
 // ============================================================ strip driver
@@ -505,6 +522,9 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
         Ops::init(st, lane, w0, rm1, rm2, xm1);
     }
     uint8_t *code_strip = a.codes + pd.code_off + static_cast<size_t>(s) * strip_bytes;
+    // per-chunk column maxima of H follow the strips' streams: [strip][chunk][lane]
+    typename Ops::ColMax *colmax = reinterpret_cast<typename Ops::ColMax *>(
+        a.codes + pd.code_off + static_cast<size_t>(nstrips) * strip_bytes) + static_cast<size_t>(s) * nchunks * 32;
     Best best{0, 0x7fffffff, 0x7fffffff};
 
     for (int ch = 0; ch < nchunks; ++ch) {
@@ -541,6 +561,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
             __syncwarp();
             if (lane == 0) st_release(mine, static_cast<uint32_t>(ch + 1));
         }
+        if (store) colmax[static_cast<size_t>(ch) * 32 + lane] = Ops::chunk_max(st);
         // fold this chunk's best cells into the strip's best
 #pragma unroll
         for (int h = 0; h < 2; ++h) {

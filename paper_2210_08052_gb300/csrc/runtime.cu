@@ -52,12 +52,15 @@ constexpr uint64_t kDefaultBudget = 40ull << 30;
 
 inline uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
-// Traceback bytes of one pair: strips x padded steps x 128 B (x 2 when the
-// pair may need the int32 re-run, whose stream holds 4 B per cell).
+// Traceback bytes of one pair: strips x padded steps x 128 B plus 128 B of
+// column maxima per strip and chunk (x 2 when the pair may need the int32
+// re-run, whose stream holds 4 B per cell).
 inline uint64_t code_bytes(uint32_t m, uint32_t n, bool wide = false)
 {
     const uint64_t nchunks = div_up(static_cast<uint64_t>(n) + kStripW - 1, kChunk);
-    return div_up(m, kStripW) * nchunks * kChunk * kStepBytes * (wide ? 2 : 1);
+    const uint64_t strips = div_up(m, kStripW);
+    // H stream, then the per-chunk column maxima (one word per lane and chunk)
+    return strips * nchunks * (kChunk * kStepBytes + 32 * 4) * (wide ? 2 : 1);
 }
 
 // Residue letter -> code (ARNDCQEGHILKMFPSTWYV 0..19, '*' 20, else X 21).

@@ -100,6 +100,8 @@ struct PairView {
     const uint8_t *base;
     size_t strip_bytes;
     bool wide;               // int32 stream (4 B per cell)
+    const uint8_t *colmax;   // per strip, chunk and lane: the chunk's maximum H of the lane's two cells
+    int nchunks;
     const uint32_t *g;       // packed genome
     const uint8_t *P;        // residue codes
     int n, m;
@@ -120,6 +122,15 @@ struct PairView {
         const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(
             base + static_cast<size_t>(s) * strip_bytes + static_cast<size_t>(t >> 2) * 512 + (r >> 1) * 16 +
             (t & 3) * 4));
+        return static_cast<int>((r & 1) ? (w >> 16) : (w & 0xffffu)) - 32768;
+    }
+    // maximum H over chunk c of residue j (steps c*kChunk .. c*kChunk+kChunk-1)
+    __device__ __forceinline__ int cmax(int c, int j) const
+    {
+        const int jj = j - 1, s = jj >> 6, r = jj & 63;
+        const size_t e = (static_cast<size_t>(s) * nchunks + c) * 32 + (r >> 1);
+        if (wide) return __ldg(reinterpret_cast<const int *>(colmax) + 2 * e + (r & 1));
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(colmax) + e);
         return static_cast<int>((r & 1) ? (w >> 16) : (w & 0xffffu)) - 32768;
     }
     // base at 1-based position x (0..3), valid iff 1 <= x <= n
@@ -188,6 +199,32 @@ __device__ __forceinline__ int first_hit(int kmax, int lane, Pred pred)
     return 0;
 }
 
+// Largest row x in [1, xhi] of residue column jc with pred(x), 0 if none.
+// pred(x) may only hold where H(x, jc) >= thr: chunks whose stored maximum
+// is below thr are skipped without reading their cells.
+template <typename Pred>
+__device__ __forceinline__ int scan_column(const PairView &v, int jc, int xhi, int thr, int lane, Pred pred)
+{
+    if (xhi < 1 || jc < 1) return 0;
+    const int r = (jc - 1) & 63;
+    const int c_lo = r / kChunk, c_hi = (xhi - 1 + r) / kChunk;
+    for (int cb = c_hi; cb >= c_lo; cb -= 32) {
+        const int c = cb - lane;
+        unsigned bal = __ballot_sync(kFull, c >= c_lo && v.cmax(c, jc) >= thr);
+        while (bal) {
+            const int cc = cb - (__ffs(bal) - 1);       // highest flagged chunk first
+            bal &= bal - 1;
+            const int xa = max(1, cc * kChunk - r + 1), xb = min(xhi, cc * kChunk - r + kChunk);
+            for (int x0 = xb; x0 >= xa; x0 -= 32) {
+                const int x = x0 - lane;
+                const unsigned hit = __ballot_sync(kFull, x >= xa && pred(x));
+                if (hit) return x0 - (__ffs(hit) - 1);
+            }
+        }
+    }
+    return 0;
+}
+
 // Walk back from the best cell to the restart.  At an H cell the source is
 // the first term of Eq. 7 (M, I, D, F1, F2, G1, G2, A, B, C) whose value
 // equals H, the restart when H = 0.  The gap and intron terms use the
@@ -204,9 +241,11 @@ __device__ void trace_pair(const TBArgs &a, const int8_t *mat_s, uint32_t p, int
     const int n = static_cast<int>(pd.nt_len);
     const int nchunks = (n + kStripW - 1 + kChunk - 1) / kChunk;
     const bool wide = (o.status & kStInt32Stream) != 0;
-    const PairView v{a.codes + pd.code_off,
-                     static_cast<size_t>(nchunks) * kChunk * kStepBytes * (wide ? 2 : 1),
-                     wide, a.nt2 + pd.nt_word_off, a.prot + pd.prot_off, n, static_cast<int>(pd.prot_len),
+    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes * (wide ? 2 : 1);
+    const int nstrips = static_cast<int>(pd.n_strips);
+    const PairView v{a.codes + pd.code_off, strip_bytes, wide,
+                     a.codes + pd.code_off + static_cast<size_t>(nstrips) * strip_bytes, nchunks,
+                     a.nt2 + pd.nt_word_off, a.prot + pd.prot_off, n, static_cast<int>(pd.prot_len),
                      &a.sp, mat_s};
     const int q = a.sp.q, e = a.sp.e, f = a.sp.f, r = a.sp.r;
     const int hmax = o.score;
@@ -248,26 +287,28 @@ __device__ void trace_pair(const TBArgs &a, const int8_t *mat_s, uint32_t p, int
         if (v.H(i - 2, j - 1) - f == h) { if (lane == 0) w.push(MP_OP_F, 2); i -= 2; j -= 1; continue; }
         if (v.H(i - 1, j) - f == h) { if (lane == 0) w.push(MP_OP_G, 1); i -= 1; continue; }
         if (v.H(i - 2, j) - f == h) { if (lane == 0) w.push(MP_OP_G, 2); i -= 2; continue; }
-        // introns: the opening i' nearest to the exit i (k = i - i' + 1)
+        // introns: the opening i' nearest to the exit i; the H cell before it is
+        // x = i' - 1 (row 0 never matches since h > 0)
         const int va = h + v.a(i);
-        k = first_hit(i, lane, [&](int kk) { const int ip = i - kk + 1; return v.H(ip - 1, j) - r - v.d(ip - 1) == va; });
-        if (k) {
-            if (lane == 0) w.push(MP_OP_N, k);              // intron T[i'..i], length i - i' + 1
-            i -= k;
+        int x = scan_column(v, j, i - 1, va + r, lane, [&](int xx) { return v.H(xx, j) - r - v.d(xx) == va; });
+        if (x) {
+            if (lane == 0) w.push(MP_OP_N, i - x);          // intron T[x+1..i]
+            i = x;
             continue;
         }
         const int vb = h + v.a(i - 2), vc = h + v.a(i - 1);
         int op = MP_OP_U;
-        k = first_hit(i, lane, [&](int kk) { const int ip = i - kk + 1; return v.H(ip - 1, j - 1) - r - v.d(ip) == vb; });
-        if (!k) {
+        x = scan_column(v, j - 1, i - 1, vb + r, lane, [&](int xx) { return v.H(xx, j - 1) - r - v.d(xx + 1) == vb; });
+        if (!x) {
             op = MP_OP_V;
-            k = first_hit(i, lane, [&](int kk) { const int ip = i - kk + 1; return v.H(ip - 1, j - 1) - r - v.d(ip + 1) == vc; });
+            x = scan_column(v, j - 1, i - 1, vc + r, lane,
+                            [&](int xx) { return v.H(xx, j - 1) - r - v.d(xx + 2) == vc; });
         }
-        if (!k) { error = true; break; }
-        const int L = k - 3;                                  // intron length i - i' - 2
+        if (!x) { error = true; break; }
+        const int L = i - x - 3;                              // intron length i - i' - 2
         if (L < 1) { error = true; break; }
         if (lane == 0) w.push(op, L);
-        i -= k;
+        i = x;
         j -= 1;
     }
     if (lane == 0) {
