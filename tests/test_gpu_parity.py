@@ -261,8 +261,9 @@ def test_repeated_runs_and_graph_replay(mp, ctx):
 
 
 def _code_bytes(m, n):
-    """Traceback bytes of one pair: 64-residue strips x 96-step chunks x 128 B."""
-    return -(-m // 64) * -(-(n + 63) // 96) * 96 * 128
+    """Traceback bytes of one pair: per 64-residue strip and 96-step chunk,
+    128 B per step of H values plus 128 B of column maxima."""
+    return -(-m // 64) * -(-(n + 63) // 96) * (96 * 128 + 128)
 
 
 def test_small_budget_waves(mp, ctx, orc):
