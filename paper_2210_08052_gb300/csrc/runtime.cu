@@ -2,6 +2,7 @@
 // traceback-budgeted waves, the device pipeline (captured once per batch as
 // a CUDA graph and replayed), result download, and the serving loop.
 #include <algorithm>
+#include <cstdint>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -423,36 +424,70 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         const uint64_t cy = static_cast<uint64_t>(b->desc[y].prot_len) * b->desc[y].nt_len;
         return cx > cy;
     });
-    // ---- waves under the traceback budget; strip items in pair order
+    // ---- waves under the traceback budget
+    // Every wave gets a share of large and small pairs: pairs are taken
+    // largest first and placed in the wave with the least work (cells) whose
+    // traceback bytes still fit; a wave made only of the largest pairs would
+    // have too few strips to keep every SM busy.
     const uint64_t cap = c->budget;
+    std::vector<uint64_t> cbytes(n, 0);
+    uint64_t total_bytes = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        PairDesc &d = b->desc[k];
+        if (d.flags & (PF_SKIP | PF_SCORE_ONLY)) continue;
+        uint64_t cb = div_up(code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0), 256) * 256;
+        if (cb > cap) {
+            d.flags |= PF_BUDGET | PF_SCORE_ONLY;
+            cb = 0;
+        }
+        cbytes[k] = cb;
+        total_bytes += cb;
+    }
+    std::vector<uint32_t> wave_of(n, 0);
+    std::vector<uint64_t> wbytes, wcells;
+    const size_t nw0 = static_cast<size_t>(std::max<uint64_t>(1, div_up(total_bytes, cap)));
+    wbytes.assign(nw0, 0);
+    wcells.assign(nw0, 0);
+    for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t p = b->order[k];
+        const uint64_t cells = static_cast<uint64_t>(b->desc[p].prot_len) * b->desc[p].nt_len;
+        size_t best = SIZE_MAX;
+        for (size_t w = 0; w < wbytes.size(); ++w)
+            if (wbytes[w] + cbytes[p] <= cap && (best == SIZE_MAX || wcells[w] < wcells[best])) best = w;
+        if (best == SIZE_MAX) {
+            best = wbytes.size();
+            wbytes.push_back(0);
+            wcells.push_back(0);
+        }
+        wave_of[p] = static_cast<uint32_t>(best);
+        wbytes[best] += cbytes[p];
+        wcells[best] += cells;
+    }
+    // group the largest-first order by wave (still largest first within a wave)
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](uint32_t x, uint32_t y) { return wave_of[x] < wave_of[y]; });
+    // strip items in pair order; each wave is a contiguous range
     uint64_t cur = 0, maxw = 0;
-    uint32_t wbeg = 0, ibeg = 0;
+    uint32_t wbeg = 0, ibeg = 0, wcur = 0;
     b->h_items.clear();
     b->h_items.reserve(strips);
     b->item_off.assign(n + 1, 0);
     for (uint32_t k = 0; k < n; ++k) {
         const uint32_t p = b->order[k];
         PairDesc &d = b->desc[p];
-        b->item_off[k] = static_cast<uint32_t>(b->h_items.size());
-        if (d.flags & PF_SKIP) continue;
-        uint64_t cb = 0;
-        if (!(d.flags & PF_SCORE_ONLY)) {
-            cb = code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
-            if (cb > cap) {
-                d.flags |= PF_BUDGET | PF_SCORE_ONLY;
-                cb = 0;
-            }
-        }
-        if (cb && cur + cb > cap) {
+        if (wave_of[p] != wcur) {
             b->waves.push_back(Wave{wbeg, k, ibeg, static_cast<uint32_t>(b->h_items.size()), cur});
             maxw = std::max(maxw, cur);
             wbeg = k;
             ibeg = static_cast<uint32_t>(b->h_items.size());
             cur = 0;
+            wcur = wave_of[p];
         }
+        b->item_off[k] = static_cast<uint32_t>(b->h_items.size());
+        if (d.flags & PF_SKIP) continue;
         d.code_off = cur;
-        cur += div_up(cb, 256) * 256;
-        b->code_bytes_total += cb;
+        cur += cbytes[p];
+        if (cbytes[p]) b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
         for (uint32_t s = 0; s < d.n_strips; ++s) b->h_items.push_back(make_uint2(p, s));
     }
     b->item_off[n] = static_cast<uint32_t>(b->h_items.size());
