@@ -94,11 +94,28 @@ __device__ __forceinline__ uint4 make_record(const uint32_t *g, int n, int ii, i
 // --------------------------------------------------------------- smem
 template <typename BndT>
 struct WarpSmem {
-    uint4 ring[kRing + kRingPad];
+    // per-nt records, even and odd positions in separate halves: at a given
+    // step all lanes read records of one parity at consecutive indices, so the
+    // 16-byte loads are free of bank conflicts
+    uint4 ring[2][kRing / 2 + kRingPad / 2];
     uint32_t prof[kProfRows * 32];
     BndT bin[kChunk];
     BndT bout[kChunk];
 };
+
+template <typename BndT>
+__device__ __forceinline__ void put_record(WarpSmem<BndT> &sm, int ii, const uint4 &rec)
+{
+    const int half = ii & 1, idx = (ii >> 1) & (kRing / 2 - 1);
+    sm.ring[half][idx] = rec;
+    if (idx < kRingPad / 2) sm.ring[half][idx + kRing / 2] = rec;   // mirror: a body never wraps
+}
+
+template <typename BndT>
+__device__ __forceinline__ uint4 get_record(const WarpSmem<BndT> &sm, int ii)
+{
+    return sm.ring[ii & 1][(ii >> 1) & (kRing / 2 - 1)];
+}
 
 // ================================================================ int16 ops
 struct Ops16 {
@@ -116,7 +133,8 @@ struct Ops16 {
     struct State {
         uint32_t H1, H2, H3, L0, L1, L2, L3, IL, D1, D2, D3, A1, B1, C1;
         uint32_t VD1, VD2, VA1, VA2, X1;
-        uint32_t TC, bklo, bkhi;
+        uint32_t TC, bklo, bkhi;            // best-cell keys (pairs without a stored stream)
+        uint32_t cm;                        // this chunk's packed maximum H (pairs with a stream)
     };
 
     static __device__ __forceinline__ Consts consts(const ScoreParams &sp)
@@ -150,13 +168,16 @@ struct Ops16 {
         s.VD1 = recm1.x; s.VD2 = recm2.x;
         s.VA1 = recm1.y; s.VA2 = recm2.y;
         s.X1 = xm1;
-        s.TC = 0xffffu; s.bklo = 0; s.bkhi = 0;
+        s.TC = 0xffffu; s.bklo = 0; s.bkhi = 0; s.cm = 0;
     }
 
     using Word = uint32_t;                  // traceback word of one lane and step: [H lo, H hi]
 
     // One anti-diagonal step.  Returns the lane's two H values (biased).
-    template <bool MASKED>
+    // KEYS: track the best cell's step with keys (needed when no stream is
+    // stored); otherwise keep only the chunk's maximum, whose first position
+    // is later read back from the stream.
+    template <bool MASKED, bool KEYS>
     static __device__ __forceinline__ uint32_t step(State &s, const Consts &c, const uint4 rec,
                                                     const uint32_t *prof_lane, Bnd bin, Bnd *bout,
                                                     int lane, int ii, int n)
@@ -216,9 +237,13 @@ struct Ops16 {
         // best cell: key = H << 16 | (0xffff - step within chunk); the
         // largest key is the largest H at its first step
         const uint32_t Hm = H0 & vmask;
-        s.bklo = max(s.bklo, Hm * 65536u + s.TC);                 // [TC, H.lo]
-        s.bkhi = max(s.bkhi, (Hm & 0xffff0000u) | s.TC);         // [TC, H.hi]
-        s.TC -= 1;
+        if (KEYS) {
+            s.bklo = max(s.bklo, Hm * 65536u + s.TC);             // [TC, H.lo]
+            s.bkhi = max(s.bkhi, (Hm & 0xffff0000u) | s.TC);     // [TC, H.hi]
+            s.TC -= 1;
+        } else {
+            s.cm = vmax(s.cm, Hm);
+        }
         return H0;
     }
 
@@ -238,14 +263,22 @@ struct Ops16 {
     }
     static __device__ __forceinline__ void reset_best(State &s)
     {
-        s.TC = 0xffffu; s.bklo = 0; s.bkhi = 0;
+        s.TC = 0xffffu; s.bklo = 0; s.bkhi = 0; s.cm = 0;
     }
 
     // this chunk's maximum H of the lane's two cells (biased; 0 if none)
     using ColMax = uint32_t;
-    static __device__ __forceinline__ ColMax chunk_max(const State &s)
+    static __device__ __forceinline__ ColMax chunk_max(const State &s) { return s.cm; }
+    static constexpr bool kChunkMaxBest = true;   // with a stream, the best cell comes from chunk maxima
+    // unbiased H of half h of a stored stream word
+    static __device__ __forceinline__ int word_h(const Word &w, int h)
     {
-        return (s.bklo >> 16) | (s.bkhi & 0xffff0000u);
+        return static_cast<int>(h ? (w >> 16) : (w & 0xffffu)) - 32768;
+    }
+    static __device__ __forceinline__ Word load_word(const uint8_t *strip, int t, int lane)
+    {
+        return *reinterpret_cast<const uint32_t *>(strip + static_cast<size_t>(t >> 2) * 512 + lane * 16 +
+                                                   (t & 3) * 4);
     }
 };
 
@@ -311,7 +344,7 @@ struct Ops32 {
 
     using Word = uint2;                     // [H lo, H hi] as int32
 
-    template <bool MASKED>
+    template <bool MASKED, bool KEYS>
     static __device__ __forceinline__ uint2 step(State &s, const Consts &c, const uint4 rec,
                                                  const uint32_t *prof_lane, Bnd bin, Bnd *bout,
                                                  int lane, int ii, int n)
@@ -384,6 +417,9 @@ struct Ops32 {
     }
     static __device__ __forceinline__ void reset_best(State &s) { s.cmlo = s.cmhi = NEG; }
 
+    static constexpr bool kChunkMaxBest = false;
+    static __device__ __forceinline__ int word_h(const Word &w, int h) { return static_cast<int>(h ? w.y : w.x); }
+    static __device__ __forceinline__ Word load_word(const uint8_t *, int, int) { return make_uint2(0, 0); }
     using ColMax = uint2;
     static __device__ __forceinline__ ColMax chunk_max(const State &s)
     {
@@ -409,11 +445,16 @@ __device__ __forceinline__ void run_chunk(typename Ops::State &st, const typenam
 #pragma unroll 1
     for (int b = 0; b < kChunk / kBody; ++b) {
         const int tb = t0 + b * kBody;
-        const uint4 *recp = &sm.ring[(tb - 2 * lane) & (kRing - 1)];
+        // record of the lo cell at step tb+k: position tb+k-2l, parity k&1,
+        // index (tb+k)/2 - l within its half (tb is even)
+        const int ridx = ((tb >> 1) - lane) & (kRing / 2 - 1);
+        const uint4 *re = &sm.ring[0][ridx];
+        const uint4 *ro = &sm.ring[1][ridx];
         typename Ops::Word cw[kBody];
 #pragma unroll
         for (int k = 0; k < kBody; ++k) {
-            cw[k] = Ops::template step<MASKED>(st, c, recp[k], sm.prof + lane, sm.bin[b * kBody + k],
+            cw[k] = Ops::template step<MASKED, !STORE>(st, c, (k & 1) ? ro[k >> 1] : re[k >> 1], sm.prof + lane,
+                                                         sm.bin[b * kBody + k],
                                                &sm.bout[b * kBody + k], lane, tb + k - 2 * lane, n);
             if (STORE && (k & 3) == 3) Ops::store4(code_strip, tb + k - 3, lane, &cw[k - 3]);
         }
@@ -503,9 +544,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     // records for ii in [-max(kChunk, kStripW), kChunk)
     for (int ii = -(kChunk > kStripW ? kChunk : kStripW) + lane; ii < kChunk; ii += 32) {
         const uint4 rec = make_record(g, n, ii, a.sp.r);
-        const int slot = ii & (kRing - 1);
-        sm.ring[slot] = rec;
-        if (slot < kRingPad) sm.ring[slot + kRing] = rec;
+        put_record(sm, ii, rec);
     }
     // chunk c reads boundary entries c*kChunk+1 .. (c+1)*kChunk, which strip s-1
     // writes kStripW-1 steps later: up to its chunk c + 1 + (kStripW-1)/kChunk
@@ -515,8 +554,8 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     typename Ops::State st;
     {
         const int ii0 = -2 * lane;
-        const uint4 rm1 = sm.ring[(ii0 - 1) & (kRing - 1)];
-        const uint4 rm2 = sm.ring[(ii0 - 2) & (kRing - 1)];
+        const uint4 rm1 = get_record(sm, ii0 - 1);
+        const uint4 rm2 = get_record(sm, ii0 - 2);
         const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
         const Bnd w0 = s == 0 ? Ops::kBnd0 : ld_l2(bnd);
         Ops::init(st, lane, w0, rm1, rm2, xm1);
@@ -526,15 +565,14 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     typename Ops::ColMax *colmax = reinterpret_cast<typename Ops::ColMax *>(
         a.codes + pd.code_off + static_cast<size_t>(nstrips) * strip_bytes) + static_cast<size_t>(s) * nchunks * 32;
     Best best{0, 0x7fffffff, 0x7fffffff};
+    int cbest[2] = {0, 0}, cchunk[2] = {0, 0};      // per cell: best chunk maximum and its chunk
 
     for (int ch = 0; ch < nchunks; ++ch) {
         const int t0 = ch * kChunk;
         if (ch > 0) {
             for (int ii = t0 + lane; ii < t0 + kChunk; ii += 32) {
                 const uint4 rec = make_record(g, n, ii, a.sp.r);
-                const int slot = ii & (kRing - 1);
-                sm.ring[slot] = rec;
-                if (slot < kRingPad) sm.ring[slot + kRing] = rec;
+                put_record(sm, ii, rec);
             }
             wait_for(ch + kLag < nchunks ? ch + kLag : nchunks);
         }
@@ -562,17 +600,46 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
             if (lane == 0) st_release(mine, static_cast<uint32_t>(ch + 1));
         }
         if (store) colmax[static_cast<size_t>(ch) * 32 + lane] = Ops::chunk_max(st);
-        // fold this chunk's best cells into the strip's best
+        if (Ops::kChunkMaxBest && store) {
+            // remember the first chunk holding each cell's maximum
+            const typename Ops::ColMax cmw = Ops::chunk_max(st);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int sc, t;
-            Ops::take_best(st, h, t0, sc, t);
-            const int jj = s * kStripW + 2 * lane + h;
-            const int ii = t - 2 * lane - h;
-            if (sc > 0 && jj < m && better(sc, ii, jj, best)) best = Best{sc, ii, jj};
+            for (int h = 0; h < 2; ++h) {
+                const int v = Ops::word_h(cmw, h);
+                if (v > cbest[h]) { cbest[h] = v; cchunk[h] = ch; }
+            }
+        } else {
+            // fold this chunk's best cells into the strip's best
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int sc, t;
+                Ops::take_best(st, h, t0, sc, t);
+                const int jj = s * kStripW + 2 * lane + h;
+                const int ii = t - 2 * lane - h;
+                if (sc > 0 && jj < m && better(sc, ii, jj, best)) best = Best{sc, ii, jj};
+            }
         }
         Ops::reset_best(st);
         __syncwarp();
+    }
+    if (Ops::kChunkMaxBest && store) {
+        // first step of the best chunk holding the maximum, read back from this
+        // lane's own stored H values (valid cells only)
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = s * kStripW + 2 * lane + h;
+            if (cbest[h] <= 0 || jj >= m) continue;
+            const int tb = cchunk[h] * kChunk;
+            for (int t = tb; t < tb + kChunk; ++t) {
+                const int ii = t - 2 * lane - h;
+                if (ii < 0 || ii >= n) continue;
+                if (Ops::word_h(Ops::load_word(code_strip, t, lane), h) == cbest[h]) {
+                    if (better(cbest[h], ii, jj, best)) best = Best{cbest[h], ii, jj};
+                    break;
+                }
+            }
+        }
     }
     // warp reduction of (score desc, ii asc, jj asc)
 #pragma unroll

@@ -220,7 +220,8 @@ struct mp_dp_ctx {
     HostBuf<char> staging;
     bool timing = false;
     mp_dp_stats stats{};
-    mp_dp_batch *last = nullptr;   // batch used by mp_dp_align_batch
+    mp_dp_batch *last = nullptr;   // batch of the last run (for its counters)
+    mp_dp_batch *own = nullptr;    // buffers reused by mp_dp_align_batch from call to call
     std::vector<uint32_t> host_cig;
 
     // serving
@@ -513,10 +514,21 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     }
     // ---- host -> device
     if (c->staging.reserve(asc + 16) != cudaSuccess) return MP_ENOMEM;
-    for (size_t k = 0; k < n; ++k) {
-        const mp_pair &q = pairs[k];
-        if (q.prot_len) memcpy(c->staging.p + b->desc[k].asc_prot_off, q.prot, q.prot_len);
-        if (q.nt_len) memcpy(c->staging.p + b->desc[k].asc_nt_off, q.nt, q.nt_len);
+    auto gather = [&](size_t k0, size_t k1) {
+        for (size_t k = k0; k < k1; ++k) {
+            const mp_pair &q = pairs[k];
+            if (q.prot_len) memcpy(c->staging.p + b->desc[k].asc_prot_off, q.prot, q.prot_len);
+            if (q.nt_len) memcpy(c->staging.p + b->desc[k].asc_nt_off, q.nt, q.nt_len);
+        }
+    };
+    // large batches: gather the sequences into the pinned buffer on several threads
+    const unsigned nthr = asc > (16u << 20) ? std::min(8u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
+    if (nthr > 1) {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nthr; ++t) th.emplace_back(gather, n * t / nthr, n * (t + 1) / nthr);
+        for (auto &x : th) x.join();
+    } else {
+        gather(0, n);
     }
     cudaStream_t st = c->stream;
     CK(cudaMemcpyAsync(b->ascii.p, c->staging.p, asc, cudaMemcpyHostToDevice, st));
@@ -777,14 +789,17 @@ int mp_dp_batch_download(mp_dp_ctx *c, mp_dp_batch *b, mp_result *out)
 int mp_dp_align_batch(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *out)
 {
     if (!c || (n && (!pairs || !out))) return MP_EINVAL;
-    mp_dp_batch *b = nullptr;
-    int rc = mp_dp_batch_upload(c, pairs, n, &b);
+    // the context keeps one batch whose device buffers only grow, so repeated
+    // calls allocate nothing once the largest batch has been seen
+    if (!c->own) c->own = new (std::nothrow) mp_dp_batch();
+    if (!c->own) return MP_ENOMEM;
+    mp_dp_batch *b = c->own;
+    int rc = upload_impl(c, b, pairs, n);
     if (rc != MP_OK) return rc;
     rc = mp_dp_batch_run(c, b);
     if (rc == MP_OK) rc = mp_dp_batch_sync(c);
     if (rc == MP_OK) rc = mp_dp_batch_download(c, b, out);
     c->last = nullptr;
-    mp_dp_batch_free(c, b);
     return rc;
 }
 
@@ -1042,6 +1057,8 @@ extern "C" void mp_dp_destroy(mp_dp_ctx *c)
     if (c->server.joinable()) c->server.join();
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->own) mp_dp_batch_free(c, c->own);
+    c->own = nullptr;
     c->codes.release();
     c->staging.release();
     if (c->stream) cudaStreamDestroy(c->stream);
