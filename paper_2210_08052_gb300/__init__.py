@@ -191,11 +191,16 @@ def mp_dp_destroy(ctx) -> None:
     lib().mp_dp_destroy(ctx)
 
 
+class PairBatch(_PairArray):
+    """A C-ABI array of mp_pair built once from host sequences (what a C
+    caller passes to mp_dp_align_batch); reusable across calls."""
+
+
 def mp_dp_align_batch(ctx, pairs, raw: bool = False):
-    """Align a list of pairs end to end.  Returns a list of result dicts, or
-    with raw=True a dict of numpy arrays (scores, status, coordinates, CIGAR
-    offsets and one flat op array)."""
-    pa = _PairArray(pairs)
+    """Align pairs end to end (a list of pairs, or a PairBatch).  Returns a
+    list of result dicts, or with raw=True a structured numpy array of the
+    mp_result records."""
+    pa = pairs if isinstance(pairs, _PairArray) else _PairArray(pairs)
     res = (mp_result * max(pa.n, 1))()
     _check(lib().mp_dp_align_batch(ctx, pa.arr, pa.n, res), "mp_dp_align_batch")
     return _results(res, pa.n, raw)
@@ -212,7 +217,7 @@ def _results(res, n, raw):
 
 
 def mp_dp_batch_upload(ctx, pairs):
-    pa = _PairArray(pairs)
+    pa = pairs if isinstance(pairs, _PairArray) else _PairArray(pairs)
     b = ctypes.c_void_p()
     _check(lib().mp_dp_batch_upload(ctx, pa.arr, pa.n, ctypes.byref(b)), "mp_dp_batch_upload")
     return b, pa.n

@@ -65,14 +65,22 @@ inline uint64_t code_bytes(uint32_t m, uint32_t n, bool wide = false)
 }
 
 // Residue letter -> code (ARNDCQEGHILKMFPSTWYV 0..19, '*' 20, else X 21).
-inline int host_aa_code(unsigned char c)
-{
-    static const char order[] = "arndcqeghilkmfpstwyv";
-    const unsigned char l = c | 0x20;
-    for (int k = 0; k < 20; ++k)
-        if (order[k] == l) return k;
-    return c == '*' ? 20 : 21;
-}
+struct AACodeTable {
+    uint8_t v[256];
+    AACodeTable()
+    {
+        static const char order[] = "ARNDCQEGHILKMFPSTWYV";
+        for (int c = 0; c < 256; ++c) v[c] = 21;
+        for (int k = 0; k < 20; ++k) {
+            v[static_cast<unsigned char>(order[k])] = static_cast<uint8_t>(k);
+            v[static_cast<unsigned char>(order[k] | 0x20)] = static_cast<uint8_t>(k);
+        }
+        v[static_cast<unsigned char>('*')] = 20;
+    }
+};
+const AACodeTable kAACode;
+
+inline int host_aa_code(unsigned char c) { return kAACode.v[c]; }
 
 // Upper bound of any H of the pair: every residue scores at most its best
 // substitution and every other term of Eq. 7 is a penalty.
