@@ -206,7 +206,7 @@ void mp_dp_destroy(mp_dp_ctx *ctx);
  * allocate, free or synchronize the device afterwards.  The call runs the
  * same DP as mp_dp_align_batch (packed int16, exact int32 re-run on
  * saturation), score only, for one pair, and allocates nothing: its scratch
- * is a fixed array of about 290 KB inside this library, held by every GPU
+ * is a fixed array of about 820 KB inside this library, held by every GPU
  * that loads the library until the process exits.
  *
  *   params  scoring parameters (NULL: defaults), validated as by mp_dp_init

@@ -99,8 +99,8 @@ struct WarpSmem {
     // 16-byte loads are free of bank conflicts
     uint4 ring[2][kRing / 2 + kRingPad / 2];
     uint32_t prof[kProfRows * 32];
-    BndT bin[kChunk];
-    BndT bout[kChunk];
+    alignas(16) BndT bin[kChunk];
+    alignas(16) BndT bout[kChunk];
 };
 
 template <typename BndT>
@@ -115,6 +115,28 @@ template <typename BndT>
 __device__ __forceinline__ uint4 get_record(const WarpSmem<BndT> &sm, int ii)
 {
     return sm.ring[ii & 1][(ii >> 1) & (kRing / 2 - 1)];
+}
+
+// 16-byte asynchronous copy global -> shared (no register staging)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+// queue the records of positions [lo, lo + kChunk) into the ring
+template <typename BndT>
+__device__ __forceinline__ void fetch_records(WarpSmem<BndT> &sm, const uint4 *recs, int lo, int lane)
+{
+    for (int ii = lo + lane; ii < lo + kChunk; ii += 32) {
+        const int half = ii & 1, idx = (ii >> 1) & (kRing / 2 - 1);
+        cp_async16(&sm.ring[half][idx], recs + ii + kChunk);
+        if (idx < kRingPad / 2) cp_async16(&sm.ring[half][idx + kRing / 2], recs + ii + kChunk);
+    }
 }
 
 // ================================================================ int16 ops
@@ -179,7 +201,7 @@ struct Ops16 {
     // is later read back from the stream.
     template <bool MASKED, bool KEYS>
     static __device__ __forceinline__ uint32_t step(State &s, const Consts &c, const uint4 rec,
-                                                    const uint32_t *prof_lane, Bnd bin, Bnd *bout,
+                                                    const uint32_t *prof_lane, Bnd bin, Bnd &wout,
                                                     int lane, int ii, int n)
     {
         const uint32_t VD0 = rec.x, VA0 = rec.y;
@@ -223,7 +245,7 @@ struct Ops16 {
         const uint32_t W = prmt<0x7632>(H0, I0);
         uint32_t R = __shfl_up_sync(kFull, W, 1);
         if (lane == 0) R = bin;
-        if (lane == 31) *bout = W;
+        wout = W;
         s.L3 = s.L2; s.L2 = s.L1; s.L1 = s.L0;
         s.L0 = prmt<0x5410>(R, H0);
         s.IL = prmt<0x5432>(R, I0);
@@ -346,7 +368,7 @@ struct Ops32 {
 
     template <bool MASKED, bool KEYS>
     static __device__ __forceinline__ uint2 step(State &s, const Consts &c, const uint4 rec,
-                                                 const uint32_t *prof_lane, Bnd bin, Bnd *bout,
+                                                 const uint32_t *prof_lane, Bnd bin, Bnd &wout,
                                                  int lane, int ii, int n)
     {
         const V2 VD0 = unpack16(rec.x), VA0 = unpack16(rec.y);
@@ -381,7 +403,7 @@ struct Ops32 {
         int32_t Rh = __shfl_up_sync(kFull, Wh, 1);
         int32_t Ri = __shfl_up_sync(kFull, Wi, 1);
         if (lane == 0) { Rh = bin.h; Ri = bin.i; }
-        if (lane == 31) *bout = Bnd{Wh, Wi};
+        wout = Bnd{Wh, Wi};
         s.L3 = s.L2; s.L2 = s.L1; s.L1 = s.L0;
         s.L0 = V2{Rh, H0.lo};
         s.IL = V2{Ri, I0.lo};
@@ -451,12 +473,24 @@ __device__ __forceinline__ void run_chunk(typename Ops::State &st, const typenam
         const uint4 *re = &sm.ring[0][ridx];
         const uint4 *ro = &sm.ring[1][ridx];
         typename Ops::Word cw[kBody];
+        typename Ops::Bnd bin4[4], wout4[4];
 #pragma unroll
         for (int k = 0; k < kBody; ++k) {
+            // boundary entries move 4 steps at a time: one broadcast load for
+            // lane 0's inputs, one store of lane 31's outputs
+            if ((k & 3) == 0) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) bin4[u] = sm.bin[b * kBody + k + u];
+            }
             cw[k] = Ops::template step<MASKED, !STORE>(st, c, (k & 1) ? ro[k >> 1] : re[k >> 1], sm.prof + lane,
-                                                         sm.bin[b * kBody + k],
-                                               &sm.bout[b * kBody + k], lane, tb + k - 2 * lane, n);
-            if (STORE && (k & 3) == 3) Ops::store4(code_strip, tb + k - 3, lane, &cw[k - 3]);
+                                                         bin4[k & 3], wout4[k & 3], lane, tb + k - 2 * lane, n);
+            if ((k & 3) == 3) {
+                if (lane == 31) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) sm.bout[b * kBody + k - 3 + u] = wout4[u];
+                }
+                if (STORE) Ops::store4(code_strip, tb + k - 3, lane, &cw[k - 3]);
+            }
         }
     }
 }
@@ -542,10 +576,11 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     for (int aa = 0; aa < kProfRows; ++aa)
         sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), subst_score(a.sp, aa, phi));
     // records for ii in [-max(kChunk, kStripW), kChunk)
-    for (int ii = -(kChunk > kStripW ? kChunk : kStripW) + lane; ii < kChunk; ii += 32) {
-        const uint4 rec = make_record(g, n, ii, a.sp.r);
-        put_record(sm, ii, rec);
-    }
+    const uint4 *recs = a.recs + pd.rec_off;            // recs[ii + kChunk] is position ii
+    fetch_records(sm, recs, -kChunk, lane);
+    fetch_records(sm, recs, 0, lane);
+    cp_async_wait_all();
+    __syncwarp();
     // chunk c reads boundary entries c*kChunk+1 .. (c+1)*kChunk, which strip s-1
     // writes kStripW-1 steps later: up to its chunk c + 1 + (kStripW-1)/kChunk
     constexpr int kLag = 2 + (kStripW - 1) / kChunk;
@@ -570,10 +605,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     for (int ch = 0; ch < nchunks; ++ch) {
         const int t0 = ch * kChunk;
         if (ch > 0) {
-            for (int ii = t0 + lane; ii < t0 + kChunk; ii += 32) {
-                const uint4 rec = make_record(g, n, ii, a.sp.r);
-                put_record(sm, ii, rec);
-            }
+            cp_async_wait_all();                         // this chunk's records (queued last chunk)
             wait_for(ch + kLag < nchunks ? ch + kLag : nchunks);
         }
         if (s == 0) {
@@ -582,6 +614,8 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
             for (int k = lane; k < kChunk; k += 32) sm.bin[k] = ld_l2(bnd + t0 + 1 + k);
         }
         __syncwarp();
+        // next chunk's records land in ring slots this chunk does not read
+        if (ch + 1 < nchunks) fetch_records(sm, recs, t0 + kChunk, lane);
         const bool masked = (t0 < kStripW) || (t0 + kChunk > n);
         if (masked) {
             if (store) run_chunk<Ops, true, true>(st, c, sm, lane, t0, n, code_strip);
@@ -737,6 +771,30 @@ int dp32_blocks_per_sm()
     return nb;
 }
 
+namespace {
+// Per-nt records of every pair (see make_record), positions -kChunk upwards.
+__global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const uint32_t *nt2, int r, uint4 *recs)
+{
+    for (uint32_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
+        const PairDesc pd = pairs[p];
+        if (pd.flags & PF_SKIP) continue;
+        const int n = static_cast<int>(pd.nt_len);
+        const int cnt = static_cast<int>(records_of(pd.nt_len));
+        const uint32_t *g = nt2 + pd.nt_word_off;
+        uint4 *out = recs + pd.rec_off;
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) out[k] = make_record(g, n, k - kChunk, r);
+    }
+}
+}  // namespace
+
+cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, int r, uint4 *recs,
+                           cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    records_kernel<<<n < 8192 ? n : 8192, 256, 0, st>>>(pairs, n, nt2, r, recs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dp16(const DPArgs &a, int grid, cudaStream_t st)
 {
     dp16_blocks_per_sm();
@@ -784,11 +842,12 @@ struct NoAllocScratch {
     uint32_t progress[kNAMaxStrips];
     uint2 rerun_items[kNAMaxStrips];
     uint32_t nt2[kNANtWords];
+    uint4 recs[records_of(kNAMaxNt)];
     uint8_t prot[kNAMaxProt];
     Ops32::Bnd bnd[kNABndEntries];                   // int32 entries; the int16 pass uses the first half
 };
 
-// The scratch itself (about 290 KB).  Host code must not pass this name to a
+// The scratch itself (about 820 KB).  Host code must not pass this name to a
 // kernel: on the host it is only a stand-in for the symbol.  Its device
 // address is looked up with cudaGetSymbolAddress at set-up.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
@@ -859,9 +918,14 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
         S->nt2[kNtPadWords + w] = word;
     }
     __syncthreads();
+    // per-nt records of the pair (positions -kChunk upwards)
+    for (int k = threadIdx.x; k < static_cast<int>(records_of(static_cast<uint32_t>(n))); k += blockDim.x)
+        S->recs[k] = make_record(S->nt2 + kNtPadWords, n, k - kChunk, sp.r);
+    __syncthreads();
     if (!bad && m > 0 && n > 0) {
         DPArgs a{};
         a.pairs = &S->desc;
+        a.recs = S->recs;
         a.prot = S->prot;
         a.nt2 = S->nt2;
         a.codes = nullptr;                       // score only: no traceback codes

@@ -43,7 +43,14 @@ struct PairDesc {
     int32_t strand;
     uint32_t strip_base;    // index of strip 0 in the per-strip progress array
     uint32_t n_strips;
+    uint64_t rec_off;       // index of the record of genome position -kChunk in the record array
 };
+
+// per-nt records of a pair: positions -kChunk .. kChunk*(nchunks+1) - 1
+__host__ __device__ constexpr uint64_t records_of(uint32_t n)
+{
+    return ((static_cast<uint64_t>(n) + kStripW - 1 + kChunk - 1) / kChunk + 2) * kChunk;
+}
 
 // internal PairOut.status bit (never returned to callers): the pair's
 // traceback stream was written by the int32 kernel (4 bytes per cell)
@@ -72,6 +79,7 @@ struct ScoreParams {
 // the boundary row strip s-1 publishes chunk by chunk.
 struct DPArgs {
     const PairDesc *pairs;
+    const uint4 *recs;      // per-nt records (see make_record)
     const uint2 *items;     // processing order
     uint32_t n_items;
     uint32_t *head;         // work-queue counter
@@ -108,6 +116,8 @@ struct TBArgs {
 // kernel launchers (defined in the .cu files)
 cudaError_t launch_pack(const PairDesc *pairs, uint32_t n, const char *ascii, uint8_t *prot,
                         uint32_t *nt2, PairOut *out, cudaStream_t st);
+cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, int r, uint4 *recs,
+                           cudaStream_t st);
 cudaError_t launch_dp16(const DPArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t st);
 cudaError_t launch_tb(const TBArgs &a, int grid, cudaStream_t st);

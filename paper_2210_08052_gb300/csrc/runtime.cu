@@ -185,6 +185,7 @@ struct mp_dp_batch {
     DevBuf<PairOut> out;
     DevBuf<uint32_t> ops, cig, work;
     DevBuf<uint2> items, rerun_items;
+    DevBuf<uint4> recs;                 // per-nt records of every pair
     DevBuf<uint64_t> bnd;
     // per-run state, zeroed by one memset: counters | strips_done | progress | best_key
     DevBuf<unsigned long long> state;
@@ -356,7 +357,7 @@ static void free_batch_device(mp_dp_batch *b)
     b->events.clear();
     b->ascii.release(); b->d_desc.release(); b->prot.release(); b->nt2.release(); b->out.release();
     b->ops.release(); b->cig.release(); b->work.release(); b->items.release(); b->rerun_items.release();
-    b->bnd.release(); b->state.release();
+    b->bnd.release(); b->state.release(); b->recs.release();
 }
 
 void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
@@ -389,7 +390,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     b->cells = 0;
     b->code_bytes_total = 0;
     // ---- layout
-    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0;
+    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0, nrec = 0;
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
         PairDesc &d = b->desc[k];
@@ -407,6 +408,8 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         ntw += div_up(q.nt_len, 16) + 2 * kNtPadWords;
         d.bnd_off = bnd;
         bnd += bnd_entries(q.nt_len);
+        d.rec_off = nrec;
+        nrec += records_of(q.nt_len);
         d.cig_off = ops;
         d.cig_cap = q.prot_len + q.nt_len + 2;
         ops += d.cig_cap;
@@ -517,6 +520,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         (e = b->cig.reserve(ops + 1)) != cudaSuccess || (e = b->work.reserve(n + 1)) != cudaSuccess ||
         (e = b->items.reserve(strips + 1)) != cudaSuccess || (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess ||
         (e = b->state.reserve(b->state_bytes / 8 + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
+        (e = b->recs.reserve(nrec + 1)) != cudaSuccess ||
         (e = c->codes.reserve(std::max<uint64_t>(maxw, 256))) != cudaSuccess) {
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
@@ -579,7 +583,8 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
     CK(rec(0));
     CK(cudaMemsetAsync(state, 0, b->state_bytes, st));
     CK(launch_pack(b->d_desc.p, n, b->ascii.p, b->prot.p, b->nt2.p, b->out.p, st));
-    ++launches;
+    CK(launch_records(b->d_desc.p, n, b->nt2.p, c->sp.r, b->recs.p, st));
+    launches += 2;
     CK(rec(1));
     const int g16 = c->num_sms * dp16_blocks_per_sm();
     const int g32 = c->num_sms * dp32_blocks_per_sm();
@@ -588,6 +593,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         const Wave &wv = b->waves[w];
         DPArgs a{};
         a.pairs = b->d_desc.p;
+        a.recs = b->recs.p;
         a.prot = b->prot.p;
         a.nt2 = b->nt2.p;
         a.codes = c->codes.p;
