@@ -30,8 +30,28 @@ WORKLOAD = ("4096 (protein, region) pairs: protein log-normal median 350 aa (50-
 WORKLOAD_C3 = ("20000 (protein, region) pairs, uneven sizes: protein log-uniform 20-5000 aa; introns as the "
                "4096-pair workload plus a 2% tail of 20-100 kb; regions <= 200 kb; 5% score-only decoys; "
                "seed 3 (+1000 per rank)")
-# algorithmic integer ops per cell: 27 max/add of Eq. 7 + 16 comparisons deciding the traceback code
-OPS_PER_CELL = 43
+# algorithmic integer ops per cell of the DP pass: the 27 max/add of Eq. 7 (I 3, D 3, A/B/C 2 each,
+# H 15) and one running maximum for the best cell.  Traceback decisions are re-derived from the
+# stored H values along the path only, in the traceback kernel.
+OPS_PER_CELL = 28
+
+
+def _profile_value(key: str):
+    """A number from the committed ncu summary of the DP kernel, or None
+    unless that summary was taken on the current kernel source."""
+    import hashlib
+    import re
+
+    try:
+        src = open(os.path.join(ROOT, "paper_2210_08052_gb300", "csrc", "dp_kernel.cu"), "rb").read()
+        text = open(os.path.join(ROOT, "profiles", "dp16_c2small_full.md")).read()
+    except OSError:
+        return None
+    h = re.search(r"sha256 \(first 16 hex\): ([0-9a-f]{16})", text)
+    v = re.search(key + r": ([0-9.]+)", text)
+    if not h or not v or hashlib.sha256(src).hexdigest()[:16] != h.group(1):
+        return None
+    return float(v.group(1))
 
 
 def _profiled_traffic(cells: float):
@@ -359,6 +379,7 @@ def main():
     dp_avg_ms = statistics.mean(dp_ms) if dp_ms else None
     achieved = cells * OPS_PER_CELL / (dp_avg_ms / 1000) / 1e12 if dp_avg_ms else None
     traffic = _profiled_traffic(cells)
+    ips = _profile_value("instructions_per_step")
     line = {
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -377,6 +398,10 @@ def main():
                      "peak_basis": f"{nsm} SMs x 128 lanes x 2 int16 halves x {f_mhz:.0f} MHz (median SM clock "
                                    "under load)",
                      "hbm_write_gbs": stats["code_bytes"] / (dp_avg_ms / 1000) / 1e9 if dp_avg_ms else None,
+                     "issue_frac": (cells / 64 * ips / (dp_avg_ms / 1000) / (nsm * 4 * f_mhz * 1e6))
+                     if (dp_avg_ms and ips) else None,
+                     "issue_basis": "warp-instructions per 64-cell step from the committed ncu summary x steps/s "
+                                    "over N_SM x 4 issue slots x f_SM",
                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
         "clocks": clocks,
         "gpu_launches": stats["n_launches"] * args.steps,
