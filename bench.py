@@ -36,6 +36,25 @@ WORKLOAD_C3 = ("20000 (protein, region) pairs, uneven sizes: protein log-uniform
 OPS_PER_CELL = 28
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank aligns its own batch: the workload seed offset by 1000 per rank."""
+    return base + 1000 * rank
+
+
+def job_totals(local_units: float, local_seconds: float, dist=None, device="cpu"):
+    """(units summed over ranks, slowest rank's seconds): the whole-job
+    throughput is their ratio.  Without a process group, the local values."""
+    if dist is None:
+        return float(local_units), float(local_seconds)
+    import torch
+
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def _profile_value(key: str):
     """A number from the committed ncu summary of the DP kernel, or None
     unless that summary was taken on the current kernel source."""
@@ -290,10 +309,10 @@ def main():
     mpbuild.build()
 
     if args.workload == "c3":
-        pairs = synth.config3(seed=3 + 1000 * rank)[: args.pairs if args.pairs != 4096 else None]
+        pairs = synth.config3(seed=rank_seed(3, rank))[: args.pairs if args.pairs != 4096 else None]
         workload = WORKLOAD_C3
     else:
-        pairs = synth.config2(seed=2 + 1000 * rank)[: args.pairs]
+        pairs = synth.config2(seed=rank_seed(2, rank))[: args.pairs]
         workload = WORKLOAD
     cells = float(sum(p.cells for p in pairs))
     ctx = mp.mp_dp_init(None, local)
@@ -332,14 +351,11 @@ def main():
     res = mp.mp_dp_batch_download(ctx, batch, raw=True)
     n_rerun = int(((res["status"] & 1) != 0).sum())
     mp.mp_dp_batch_free(ctx, batch)
-    t_max = elapsed
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    all_cells, t_max = job_totals(cells, elapsed, dist, "cuda")
+    all_pairs, _ = job_totals(len(pairs), elapsed, dist, "cuda")
     ms_per_step = t_max * 1000 / args.steps
-    gcups = cells * world / (t_max / args.steps) / 1e9
-    pairs_per_s = len(pairs) * world / (t_max / args.steps)
+    gcups = all_cells / (t_max / args.steps) / 1e9
+    pairs_per_s = all_pairs / (t_max / args.steps)
 
     # ---- end to end through the C ABI with host buffers
     e2e_steps = 0 if args.skip_e2e else max(2, min(args.steps, 3))
@@ -354,16 +370,13 @@ def main():
         out = mp.mp_dp_align_batch(ctx, host_batch, raw=True)
     barrier()
     e2e_t = max(time.perf_counter() - t0, 1e-9)
-    if dist:
-        t = torch.tensor([e2e_t], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    _, e2e_t = job_totals(cells, e2e_t, dist, "cuda")
     ascii_bytes = sum(len(p.prot) + len(p.nt) for p in pairs)
     h2d = ascii_bytes + len(pairs) * (72 + 4)          # sequences + pair descriptors + work order
     d2h = len(pairs) * 32 + 4 + int(out["n_cigar"].sum()) * 4
-    e2e = {"value": cells * world / (e2e_t / e2e_steps) / 1e9 if e2e_steps else None, "unit": "GCUPS",
+    e2e = {"value": all_cells / (e2e_t / e2e_steps) / 1e9 if e2e_steps else None, "unit": "GCUPS",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "pairs_per_s": len(pairs) * world / (e2e_t / e2e_steps) if e2e_steps else None}
+           "pairs_per_s": all_pairs / (e2e_t / e2e_steps) if e2e_steps else None}
     mp.mp_dp_destroy(ctx)
 
     if rank != 0:
