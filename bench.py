@@ -281,6 +281,7 @@ def main():
     ap.add_argument("--serve-rates", default="10000")
     ap.add_argument("--pairs", type=int, default=4096, help="first N pairs of the workload (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: skip the end-to-end leg")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch configuration, no tuning runs")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
                     help="c2: the 4,096-pair batch (default); c3: the 20,000-pair uneven-size stress batch")
     args = ap.parse_args()
@@ -318,6 +319,12 @@ def main():
     ctx = mp.mp_dp_init(None, local)
     mp.mp_dp_set_timing(ctx, True)
     batch = mp.mp_dp_batch_upload(ctx, pairs)
+    tuning = None
+    if not args.no_autotune:
+        # the launch configuration is chosen by the library's autotuner on this
+        # batch (outside the timed region); the timed runs use the choice
+        best, tried = mp.mp_dp_autotune(ctx, batch)
+        tuning = {"chosen": best, "candidates": tried}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     flush.zero_()                            # first touch of the flush buffer stays outside the timed region
     torch.cuda.synchronize()
@@ -418,6 +425,7 @@ def main():
                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
         "clocks": clocks,
         "gpu_launches": stats["n_launches"] * args.steps,
+        "tuning": tuning,
         "e2e": e2e,
     }
     if not args.no_extras:

@@ -102,7 +102,9 @@ typedef struct {
                                   0: default (4e7) */
     int32_t debug_flags;       /* test hook: MP_DEBUG_NO_PUBLISH makes every strip withhold its
                                   boundary row, so the waits of the next strip run out */
-    int32_t reserved[4];
+    int32_t autotune;          /* 1: the first run of a batch whose shape class has no tuned
+                                  configuration yet runs mp_dp_autotune on it first */
+    int32_t reserved[3];
 } mp_dp_params;
 
 /* One alignment request.  prot: ASCII amino acids; nt: ASCII A/C/G/T
@@ -251,6 +253,49 @@ typedef struct {
     int32_t n_dp_launches;     /* DP kernel launches (int16 + int32) */
     uint64_t code_bytes;       /* traceback bytes written (algorithmic) */
 } mp_dp_stats;
+
+/* Launch configuration of the DP.  The paper's DP is a SIMD loop on CPU
+ * cores and has no counterpart; on the GPU the fastest configuration
+ * depends on the batch (how many pairs, how uneven, how many need int32).
+ * Every configuration computes bit-identical results: only the speed
+ * differs. */
+typedef struct {
+    int32_t dp16_variant;      /* 0: int16 DP kernel built for 3 CTAs per SM (<= 80 registers per
+                                  thread); 1: built for 2 CTAs per SM (<= 128 registers) */
+    int32_t dp16_ctas_per_sm;  /* resident 8-warp CTAs per SM in the int16 launch; 0 = all that fit */
+    int32_t dp32_ctas_per_sm;  /* the same for the int32 kernel */
+    int32_t wide_direct;       /* 1: pairs whose score bound reaches the int16 limit skip the int16
+                                  pass and run in int32 at once; 0: int16 first, int32 re-run only
+                                  if the pair saturates */
+    float ms;                  /* set by mp_dp_autotune: device time of one run of the batch */
+    int32_t reserved[3];
+} mp_dp_tuning;
+
+/* Time the candidate configurations on an uploaded batch (one warm-up run,
+ * one timed run per candidate, a second timed run of the two fastest; CUDA
+ * events on the context's stream; every run computes the batch's full
+ * results, so the batch holds valid results afterwards) and record the
+ * fastest for the batch's shape class (pair count, mean cells per pair,
+ * longest critical path and whether any pair needs int32, each on a log2
+ * scale).  Later runs of batches in that class use it unless
+ * mp_dp_set_tuning fixed a configuration.  best (may be NULL) receives the
+ * choice; tried (may be NULL) up to max_tried candidates with their times,
+ * and n_tried (may be NULL) how many were timed.  MP_EINVAL in the plain
+ * form (max_pairs_per_launch > 0); MP_ESTATE while the serving loop runs. */
+int mp_dp_autotune(mp_dp_ctx *ctx, mp_dp_batch *batch, mp_dp_tuning *best,
+                   mp_dp_tuning *tried, int max_tried, int *n_tried);
+/* Fix the configuration of every later run on the context (NULL: back to
+ * the tuned table and the defaults).  MP_EINVAL for values out of range;
+ * CTAs per SM above what fits are clamped at launch. */
+int mp_dp_set_tuning(mp_dp_ctx *ctx, const mp_dp_tuning *t);
+/* The configuration that a run of batch would use now. */
+int mp_dp_get_tuning(mp_dp_ctx *ctx, const mp_dp_batch *batch, mp_dp_tuning *t);
+/* Write / read the tuned table as text: a header naming the device and its
+ * SM count, then one line per shape class.  Load merges the entries and
+ * rejects a table made on another kind of device; a file that cannot be
+ * opened, written or parsed is MP_EINVAL as well. */
+int mp_dp_tuning_save(mp_dp_ctx *ctx, const char *path);
+int mp_dp_tuning_load(mp_dp_ctx *ctx, const char *path);
 
 int mp_dp_set_timing(mp_dp_ctx *ctx, int enable);
 int mp_dp_get_stats(mp_dp_ctx *ctx, mp_dp_stats *s);

@@ -27,7 +27,8 @@ EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_ba
             "mp_dp_batch_run", "mp_dp_batch_sync", "mp_dp_batch_download", "mp_dp_batch_free",
             "mp_dp_submit", "mp_dp_poll", "mp_dp_wait_any", "mp_dp_destroy", "mp_dp_strerror",
             "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats",
-            "mp_dp_score_pair_noalloc"]
+            "mp_dp_score_pair_noalloc", "mp_dp_autotune", "mp_dp_set_tuning", "mp_dp_get_tuning",
+            "mp_dp_tuning_save", "mp_dp_tuning_load"]
 
 
 class mp_dp_params(ctypes.Structure):
@@ -37,7 +38,8 @@ class mp_dp_params(ctypes.Structure):
                 ("splice_model", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("tb_budget_bytes", ctypes.c_uint64), ("force_int32", ctypes.c_int32),
                 ("max_pairs_per_launch", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
-                ("debug_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("debug_flags", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class mp_pair(ctypes.Structure):
@@ -58,6 +60,15 @@ class mp_dp_stats(ctypes.Structure):
                 ("tb_ms", ctypes.c_double), ("pack_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
                 ("n_waves", ctypes.c_int32), ("n_rerun", ctypes.c_int32), ("n_launches", ctypes.c_int32),
                 ("n_dp_launches", ctypes.c_int32), ("code_bytes", ctypes.c_uint64)]
+
+
+class mp_dp_tuning(ctypes.Structure):
+    _fields_ = [("dp16_variant", ctypes.c_int32), ("dp16_ctas_per_sm", ctypes.c_int32),
+                ("dp32_ctas_per_sm", ctypes.c_int32), ("wide_direct", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+
+
+TUNING_KEYS = ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct", "ms")
 
 
 class mp_dp_serve_stats(ctypes.Structure):
@@ -98,6 +109,12 @@ def lib():
             "mp_dp_get_serve_stats": (ctypes.c_int, [vp, P(mp_dp_serve_stats), ctypes.c_int]),
             "mp_dp_score_pair_noalloc": (ctypes.c_int, [P(mp_dp_params), vp, ctypes.c_uint32, vp, ctypes.c_uint32,
                                                         ctypes.c_int8, vp, vp]),
+            "mp_dp_autotune": (ctypes.c_int, [vp, vp, P(mp_dp_tuning), P(mp_dp_tuning), ctypes.c_int,
+                                              P(ctypes.c_int)]),
+            "mp_dp_set_tuning": (ctypes.c_int, [vp, P(mp_dp_tuning)]),
+            "mp_dp_get_tuning": (ctypes.c_int, [vp, vp, P(mp_dp_tuning)]),
+            "mp_dp_tuning_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+            "mp_dp_tuning_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -287,6 +304,47 @@ def mp_dp_get_serve_stats(ctx, reset: bool = False) -> dict:
     s = mp_dp_serve_stats()
     _check(lib().mp_dp_get_serve_stats(ctx, ctypes.byref(s), 1 if reset else 0), "mp_dp_get_serve_stats")
     return {k: getattr(s, k) for k, _ in mp_dp_serve_stats._fields_}
+
+
+def _tuning_dict(t) -> dict:
+    return {k: getattr(t, k) for k in TUNING_KEYS}
+
+
+def mp_dp_autotune(ctx, batch) -> tuple[dict, list[dict]]:
+    """Time the candidate launch configurations on an uploaded batch; the
+    fastest becomes the context's choice for the batch's shape class.
+    Returns (best, every candidate with its time)."""
+    best = mp_dp_tuning()
+    tried = (mp_dp_tuning * 32)()
+    n = ctypes.c_int(0)
+    _check(lib().mp_dp_autotune(ctx, batch[0], ctypes.byref(best), tried, 32, ctypes.byref(n)), "mp_dp_autotune")
+    return _tuning_dict(best), [_tuning_dict(tried[k]) for k in range(min(n.value, 32))]
+
+
+def mp_dp_set_tuning(ctx, tuning: dict | None = None) -> None:
+    """Fix the launch configuration (dict with TUNING_KEYS, missing keys 0);
+    None returns to the tuned table and the defaults."""
+    if tuning is None:
+        _check(lib().mp_dp_set_tuning(ctx, None), "mp_dp_set_tuning")
+        return
+    t = mp_dp_tuning()
+    for k, v in tuning.items():
+        setattr(t, k, v)
+    _check(lib().mp_dp_set_tuning(ctx, ctypes.byref(t)), "mp_dp_set_tuning")
+
+
+def mp_dp_get_tuning(ctx, batch) -> dict:
+    t = mp_dp_tuning()
+    _check(lib().mp_dp_get_tuning(ctx, batch[0], ctypes.byref(t)), "mp_dp_get_tuning")
+    return _tuning_dict(t)
+
+
+def mp_dp_tuning_save(ctx, path: str) -> None:
+    _check(lib().mp_dp_tuning_save(ctx, os.fsencode(path)), "mp_dp_tuning_save")
+
+
+def mp_dp_tuning_load(ctx, path: str) -> None:
+    _check(lib().mp_dp_tuning_load(ctx, os.fsencode(path)), "mp_dp_tuning_load")
 
 
 def mp_dp_num_sms(ctx) -> int:

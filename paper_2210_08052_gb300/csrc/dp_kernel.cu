@@ -33,6 +33,7 @@
 // 4 steps and no arithmetic.  The traceback kernel re-derives each decision
 // of Eq. 7 from these values (the gap and intron states in closed form),
 // with the same tie order.
+#include <atomic>
 #include <mutex>
 
 #include "mp_device.cuh"
@@ -147,7 +148,6 @@ struct Ops16 {
     static constexpr uint32_t K = 0x80008000u;
     static constexpr uint32_t SBIAS = 0x02000200u;  // profile entries hold s + 512
     static constexpr Bnd kBnd0 = 0x40008000u;       // column 0: H = 0, I = -inf
-    static constexpr int kMinBlocks = 3;             // shared memory allows 3 CTAs per SM
 
     struct Consts {
         uint32_t QE, E, F, KF;             // packed q+e, e, f and K - f
@@ -324,7 +324,6 @@ struct Ops32 {
     };
     static constexpr int32_t NEG = -(1 << 28);
     static constexpr Bnd kBnd0 = {0, NEG};
-    static constexpr int kMinBlocks = 2;
 
     struct Consts {
         int32_t qe, e, f;
@@ -717,8 +716,10 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     __syncwarp();
 }
 
-template <typename Ops>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, Ops::kMinBlocks) dp_kernel(const DPArgs a, int rerun_only)
+// MinB: CTAs per SM the build is made for (the register budget per thread
+// follows from it: 3 -> 80, 2 -> 128 for 256-thread CTAs).
+template <typename Ops, int MinB>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, MinB) dp_kernel(const DPArgs a, int rerun_only)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SM = WarpSmem<typename Ops::Bnd>;
@@ -749,27 +750,32 @@ static int blocks_per_sm(const void *fn, size_t smem)
     return nb > 0 ? nb : 1;
 }
 
-int dp16_blocks_per_sm()
+// The shared-memory opt-in is a per-device function attribute: set it, and
+// read the occupancy, once per device and build.
+template <typename Ops, int MinB>
+static int kernel_blocks_per_sm(size_t smem)
 {
-    static int nb = -1;
-    if (nb < 0) {
-        cudaFuncSetAttribute(dp_kernel<Ops16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(dp16_smem_bytes()));
-        nb = blocks_per_sm(reinterpret_cast<const void *>(dp_kernel<Ops16>), dp16_smem_bytes());
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> nb[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = 0;
+    int v = nb[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        cudaFuncSetAttribute(dp_kernel<Ops, MinB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+        v = blocks_per_sm(reinterpret_cast<const void *>(dp_kernel<Ops, MinB>), smem);
+        nb[dev].store(v, std::memory_order_relaxed);
     }
-    return nb;
+    return v;
 }
 
-int dp32_blocks_per_sm()
+int dp16_blocks_per_sm(int variant)
 {
-    static int nb = -1;
-    if (nb < 0) {
-        cudaFuncSetAttribute(dp_kernel<Ops32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(dp32_smem_bytes()));
-        nb = blocks_per_sm(reinterpret_cast<const void *>(dp_kernel<Ops32>), dp32_smem_bytes());
-    }
-    return nb;
+    return variant == 1 ? kernel_blocks_per_sm<Ops16, 2>(dp16_smem_bytes())
+                        : kernel_blocks_per_sm<Ops16, 3>(dp16_smem_bytes());
 }
+
+int dp32_blocks_per_sm() { return kernel_blocks_per_sm<Ops32, 2>(dp32_smem_bytes()); }
 
 namespace {
 // Per-nt records of every pair (see make_record), positions -kChunk upwards.
@@ -795,17 +801,18 @@ cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt
     return cudaGetLastError();
 }
 
-cudaError_t launch_dp16(const DPArgs &a, int grid, cudaStream_t st)
+cudaError_t launch_dp16(const DPArgs &a, int grid, int variant, cudaStream_t st)
 {
-    dp16_blocks_per_sm();
-    dp_kernel<Ops16><<<grid, kWarpsPerCta * 32, dp16_smem_bytes(), st>>>(a, 0);
+    dp16_blocks_per_sm(variant);
+    if (variant == 1) dp_kernel<Ops16, 2><<<grid, kWarpsPerCta * 32, dp16_smem_bytes(), st>>>(a, 0);
+    else dp_kernel<Ops16, 3><<<grid, kWarpsPerCta * 32, dp16_smem_bytes(), st>>>(a, 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t st)
 {
     dp32_blocks_per_sm();
-    dp_kernel<Ops32><<<grid, kWarpsPerCta * 32, dp32_smem_bytes(), st>>>(a, rerun_only ? 1 : 0);
+    dp_kernel<Ops32, 2><<<grid, kWarpsPerCta * 32, dp32_smem_bytes(), st>>>(a, rerun_only ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -118,12 +118,15 @@ cudaError_t launch_pack(const PairDesc *pairs, uint32_t n, const char *ascii, ui
                         uint32_t *nt2, PairOut *out, cudaStream_t st);
 cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, int r, uint4 *recs,
                            cudaStream_t st);
-cudaError_t launch_dp16(const DPArgs &a, int grid, cudaStream_t st);
+// variant 0: the int16 DP kernel built for 3 CTAs per SM (80 registers per
+// thread); 1: built for 2 CTAs per SM (up to 128).  Same results.
+constexpr int kDp16Variants = 2;
+cudaError_t launch_dp16(const DPArgs &a, int grid, int variant, cudaStream_t st);
 cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t st);
 cudaError_t launch_tb(const TBArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_compact(const PairDesc *pairs, PairOut *out, uint32_t n, const uint32_t *ops,
                            uint32_t *cig, uint32_t *total, cudaStream_t st);
-int dp16_blocks_per_sm();
+int dp16_blocks_per_sm(int variant);
 int dp32_blocks_per_sm();
 size_t dp16_smem_bytes();
 size_t dp32_smem_bytes();

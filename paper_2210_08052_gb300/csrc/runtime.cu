@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -161,6 +162,7 @@ struct Wave {
     uint32_t begin, end;    // range of the pair order
     uint32_t ibegin, iend;  // range of the strip-item order
     uint64_t code_bytes;
+    uint32_t nwide_items;   // items of PF_WIDE pairs, first in the wave's range
 };
 
 enum { EV_START = 0, EV_PACK, EV_DP, EV_RERUN, EV_TB, EV_END, EV_PER_WAVE = 3 };
@@ -192,8 +194,10 @@ struct mp_dp_batch {
     size_t state_bytes = 0, off_done = 0, off_progress = 0, off_key = 0;
     std::vector<uint2> h_items;
     std::vector<uint32_t> item_off;     // first item of each pair in the order (by order index)
+    DevBuf<uint32_t> wave_nwide;        // Wave::nwide_items of each wave, on the device
+    uint64_t shape_key = 0;             // shape class for the tuned table
     cudaGraphExec_t graph = nullptr;
-    bool graph_timed = false;
+    uint64_t graph_sig = 0;             // timing flag and configuration the graph was captured with
     int runs = 0;
     std::vector<cudaEvent_t> events;
     // host results
@@ -232,6 +236,11 @@ struct mp_dp_ctx {
     mp_dp_batch *last = nullptr;   // batch of the last run (for its counters)
     mp_dp_batch *own = nullptr;    // buffers reused by mp_dp_align_batch from call to call
     std::vector<uint32_t> host_cig;
+    // launch configuration: fixed by mp_dp_set_tuning, else tuned per shape class
+    bool has_fixed = false;
+    mp_dp_tuning fixed{};
+    std::map<uint64_t, mp_dp_tuning> tuned;
+    std::string dev_name;
 
     // serving
     std::mutex mu;
@@ -321,6 +330,9 @@ int mp_dp_init(mp_dp_ctx **out, const mp_dp_params *p, int device)
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return MP_ECUDA; }
     c->num_sms = prop.multiProcessorCount;
+    c->dev_name = prop.name;
+    for (char &ch : c->dev_name)
+        if (ch == ' ' || ch == '\t') ch = '_';
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return MP_ECUDA; }
     c->sp.q = prm.q; c->sp.e = prm.e; c->sp.f = prm.f; c->sp.r = prm.r; c->sp.stop = prm.stop;
     memcpy(c->sp.mat, prm.mat, sizeof(c->sp.mat));
@@ -357,7 +369,7 @@ static void free_batch_device(mp_dp_batch *b)
     b->events.clear();
     b->ascii.release(); b->d_desc.release(); b->prot.release(); b->nt2.release(); b->out.release();
     b->ops.release(); b->cig.release(); b->work.release(); b->items.release(); b->rerun_items.release();
-    b->bnd.release(); b->state.release(); b->recs.release();
+    b->bnd.release(); b->state.release(); b->recs.release(); b->wave_nwide.release();
 }
 
 void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
@@ -366,6 +378,33 @@ void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
     if (c) cudaSetDevice(c->device);
     free_batch_device(b);
     delete b;
+}
+
+static uint32_t log2_bucket(double v)
+{
+    uint32_t k = 0;
+    while (v >= 2.0 && k < 63) { v *= 0.5; ++k; }
+    return k;
+}
+
+// Shape class of a planned batch: pair count, mean cells per pair, the
+// longest critical path (chunks of the region plus the lag of its strips)
+// on log2 scales, whether some pair needs int32, and the wave count (1, 2,
+// 3+).  Batches of one class take the same tuned configuration.
+static uint64_t shape_key_of(const mp_dp_batch &b)
+{
+    double crit = 0;
+    uint32_t any_wide = 0;
+    for (const PairDesc &d : b.desc) {
+        if (d.flags & PF_SKIP) continue;
+        crit = std::max(crit, static_cast<double>(d.nt_len) / kChunk + 2.0 * d.n_strips);
+        if (d.flags & PF_WIDE) any_wide = 1;
+    }
+    const uint64_t nb = log2_bucket(static_cast<double>(b.n) + 1);
+    const uint64_t cb = log2_bucket(b.n ? b.cells / b.n + 1 : 1);
+    const uint64_t kb = log2_bucket(crit + 1);
+    const uint64_t wb = std::min<size_t>(b.waves.size(), 3);
+    return nb | (cb << 8) | (kb << 16) | (static_cast<uint64_t>(any_wide) << 24) | (wb << 28);
 }
 
 // (Re)fill batch b with n pairs: plan strips, waves and offsets on the host,
@@ -475,12 +514,16 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         wbytes[best] += cbytes[p];
         wcells[best] += cells;
     }
-    // group the largest-first order by wave (still largest first within a wave)
-    std::stable_sort(b->order.begin(), b->order.end(),
-                     [&](uint32_t x, uint32_t y) { return wave_of[x] < wave_of[y]; });
+    // group the largest-first order by wave, PF_WIDE pairs first within a wave
+    // (so that their items form a prefix the int32 kernel can take directly),
+    // otherwise still largest first
+    auto wide = [&](uint32_t x) { return (b->desc[x].flags & PF_WIDE) && !(b->desc[x].flags & PF_SKIP) ? 0 : 1; };
+    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
+        return wave_of[x] != wave_of[y] ? wave_of[x] < wave_of[y] : wide(x) < wide(y);
+    });
     // strip items in pair order; each wave is a contiguous range
     uint64_t cur = 0, maxw = 0;
-    uint32_t wbeg = 0, ibeg = 0, wcur = 0;
+    uint32_t wbeg = 0, ibeg = 0, wcur = 0, nwide = 0;
     b->h_items.clear();
     b->h_items.reserve(strips);
     b->item_off.assign(n + 1, 0);
@@ -488,11 +531,12 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         const uint32_t p = b->order[k];
         PairDesc &d = b->desc[p];
         if (wave_of[p] != wcur) {
-            b->waves.push_back(Wave{wbeg, k, ibeg, static_cast<uint32_t>(b->h_items.size()), cur});
+            b->waves.push_back(Wave{wbeg, k, ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
             maxw = std::max(maxw, cur);
             wbeg = k;
             ibeg = static_cast<uint32_t>(b->h_items.size());
             cur = 0;
+            nwide = 0;
             wcur = wave_of[p];
         }
         b->item_off[k] = static_cast<uint32_t>(b->h_items.size());
@@ -501,9 +545,11 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         cur += cbytes[p];
         if (cbytes[p]) b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
         for (uint32_t s = 0; s < d.n_strips; ++s) b->h_items.push_back(make_uint2(p, s));
+        if (wide(p) == 0) nwide += d.n_strips;
     }
     b->item_off[n] = static_cast<uint32_t>(b->h_items.size());
-    b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), ibeg, static_cast<uint32_t>(b->h_items.size()), cur});
+    b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
+    b->shape_key = shape_key_of(*b);
     maxw = std::max(maxw, cur);
     // per-run state block
     const size_t ncnt = 4 * b->waves.size() + 4;
@@ -520,7 +566,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         (e = b->cig.reserve(ops + 1)) != cudaSuccess || (e = b->work.reserve(n + 1)) != cudaSuccess ||
         (e = b->items.reserve(strips + 1)) != cudaSuccess || (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess ||
         (e = b->state.reserve(b->state_bytes / 8 + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
-        (e = b->recs.reserve(nrec + 1)) != cudaSuccess ||
+        (e = b->recs.reserve(nrec + 1)) != cudaSuccess || (e = b->wave_nwide.reserve(b->waves.size())) != cudaSuccess ||
         (e = c->codes.reserve(std::max<uint64_t>(maxw, 256))) != cudaSuccess) {
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
@@ -547,6 +593,9 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     CK(cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(b->items.p, b->h_items.data(), b->h_items.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    std::vector<uint32_t> nw(b->waves.size());
+    for (size_t w = 0; w < nw.size(); ++w) nw[w] = b->waves[w].nwide_items;
+    CK(cudaMemcpyAsync(b->wave_nwide.p, nw.data(), nw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     return MP_OK;
 }
@@ -566,8 +615,9 @@ int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch
     return MP_OK;
 }
 
-// Enqueue the device pipeline of a batch on stream st.
-static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool timed, bool capturing)
+// Enqueue the device pipeline of a batch on stream st with configuration t.
+static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool timed, bool capturing,
+                            const mp_dp_tuning &t)
 {
     const uint32_t n = static_cast<uint32_t>(b->n);
     int launches = 0, dp_launches = 0;
@@ -586,8 +636,11 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
     CK(launch_records(b->d_desc.p, n, b->nt2.p, c->sp.r, b->recs.p, st));
     launches += 2;
     CK(rec(1));
-    const int g16 = c->num_sms * dp16_blocks_per_sm();
-    const int g32 = c->num_sms * dp32_blocks_per_sm();
+    const int variant = t.dp16_variant == 1 ? 1 : 0;
+    const int fit16 = dp16_blocks_per_sm(variant), fit32 = dp32_blocks_per_sm();
+    const int g16 = c->num_sms * (t.dp16_ctas_per_sm > 0 ? std::min(t.dp16_ctas_per_sm, fit16) : fit16);
+    const int g32 = c->num_sms * (t.dp32_ctas_per_sm > 0 ? std::min(t.dp32_ctas_per_sm, fit32) : fit32);
+    const bool direct = t.wide_direct != 0 && !c->params.force_int32;
     const int per_launch = c->params.max_pairs_per_launch;
     for (size_t w = 0; w < W; ++w) {
         const Wave &wv = b->waves[w];
@@ -620,19 +673,27 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
                 CK(cudaMemsetAsync(a1.head, 0, sizeof(uint32_t), st));
                 const int grid = std::max(1, std::min<int>(c->num_sms, static_cast<int>((a1.n_items + kWarpsPerCta - 1) / kWarpsPerCta)));
                 if (c->params.force_int32) CK(launch_dp32(a1, grid, false, st));
-                else CK(launch_dp16(a1, grid, st));
+                else CK(launch_dp16(a1, grid, variant, st));
                 ++launches;
                 ++dp_launches;
             }
         } else {
-            a.items = b->items.p + wv.ibegin;
-            a.n_items = nitems;
+            // with wide_direct the PF_WIDE pairs' items (a prefix of the wave's
+            // range) go straight to the int32 kernel's queue
+            const uint32_t skip = direct ? wv.nwide_items : 0;
+            if (skip) {
+                CK(cudaMemcpyAsync(b->rerun_items.p + wv.ibegin, b->items.p + wv.ibegin, skip * sizeof(uint2),
+                                   cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(a.rerun_count, b->wave_nwide.p + w, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+            }
+            a.items = b->items.p + wv.ibegin + skip;
+            a.n_items = nitems - skip;
             a.head = counters + 4 * w;
-            const int want = static_cast<int>((nitems + kWarpsPerCta - 1) / kWarpsPerCta);
+            const int want = static_cast<int>((a.n_items + kWarpsPerCta - 1) / kWarpsPerCta);
             const int grid16 = std::max(1, std::min<int>(g16, want));
             const int grid32 = std::max(1, std::min<int>(g32, want));
             if (c->params.force_int32) CK(launch_dp32(a, grid32, false, st));
-            else CK(launch_dp16(a, grid16, st));
+            else CK(launch_dp16(a, grid16, variant, st));
             ++launches;
             ++dp_launches;
         }
@@ -669,12 +730,41 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
     return MP_OK;
 }
 
+static mp_dp_tuning default_tuning()
+{
+    mp_dp_tuning t{};
+    return t;     // int16 kernel for 3 CTAs/SM, all CTAs that fit, int16 first for wide pairs
+}
+
+static mp_dp_tuning tuning_for(const mp_dp_ctx *c, const mp_dp_batch *b)
+{
+    if (c->has_fixed) return c->fixed;
+    auto it = c->tuned.find(b->shape_key);
+    return it != c->tuned.end() ? it->second : default_tuning();
+}
+
+static uint64_t tuning_sig(const mp_dp_tuning &t, bool timed)
+{
+    return (static_cast<uint64_t>(t.dp16_variant & 0xff)) | (static_cast<uint64_t>(t.dp16_ctas_per_sm & 0xff) << 8) |
+           (static_cast<uint64_t>(t.dp32_ctas_per_sm & 0xff) << 16) | (static_cast<uint64_t>(t.wide_direct & 1) << 24) |
+           (static_cast<uint64_t>(timed) << 25) | (1ull << 26);
+}
+
+static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp_tuning *tried, int max_tried,
+                         int *n_tried);
+
 int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
 {
     if (!c || !b) return MP_EINVAL;
     if (cudaSetDevice(c->device) != cudaSuccess) return MP_ECUDA;
     cudaStream_t st = c->stream;
     const bool timed = c->timing;
+    if (c->params.autotune && !c->has_fixed && c->params.max_pairs_per_launch == 0 && b->n &&
+        !c->tuned.count(b->shape_key)) {
+        const int rc = autotune_impl(c, b, nullptr, nullptr, 0, nullptr);
+        if (rc != MP_OK) return rc;
+    }
+    const mp_dp_tuning t = tuning_for(c, b);
     const size_t nev = 3 + EV_PER_WAVE * b->waves.size();
     if (timed && b->events.size() < nev) {
         for (size_t k = b->events.size(); k < nev; ++k) {
@@ -684,16 +774,18 @@ int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
         }
     }
     // a batch run once is launched directly; from its second run on, the
-    // pipeline is captured once as a CUDA graph and replayed
+    // pipeline is captured once as a CUDA graph and replayed (captured again
+    // when the timing flag or the configuration changed)
     const bool use_graph = c->params.max_pairs_per_launch == 0 && ++b->runs >= 2;
-    if (use_graph && b->graph && b->graph_timed != timed) {
+    const uint64_t sig = tuning_sig(t, timed);
+    if (use_graph && b->graph && b->graph_sig != sig) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
     if (use_graph && !b->graph) {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_pipeline(c, b, st, timed, true);
+        int rc = enqueue_pipeline(c, b, st, timed, true, t);
         cudaError_t e = cudaStreamEndCapture(st, &g);
         if (rc != MP_OK) {
             if (e == cudaSuccess) cudaGraphDestroy(g);
@@ -703,14 +795,189 @@ int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
         e = cudaGraphInstantiate(&b->graph, g, 0);
         cudaGraphDestroy(g);
         CK(e);
-        b->graph_timed = timed;
+        b->graph_sig = sig;
     }
     if (use_graph) CK(cudaGraphLaunch(b->graph, st));
     else {
-        int rc = enqueue_pipeline(c, b, st, timed, false);
+        int rc = enqueue_pipeline(c, b, st, timed, false, t);
         if (rc != MP_OK) return rc;
     }
     c->last = b;
+    return MP_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+// Candidates: both int16 builds at all CTAs per SM that fit and one fewer,
+// and, when the batch has pairs that may need int32, both policies for them.
+static std::vector<mp_dp_tuning> candidates(mp_dp_ctx *c, const mp_dp_batch *b)
+{
+    bool any_wide = false;
+    for (const Wave &w : b->waves) any_wide |= w.nwide_items > 0;
+    std::vector<mp_dp_tuning> v;
+    const int fit32 = dp32_blocks_per_sm();
+    if (c->params.force_int32) {
+        for (int k = fit32; k >= std::max(1, fit32 - 1); --k) {
+            mp_dp_tuning t = default_tuning();
+            t.dp32_ctas_per_sm = k;
+            v.push_back(t);
+        }
+        return v;
+    }
+    for (int var = 0; var < kDp16Variants; ++var) {
+        const int fit = dp16_blocks_per_sm(var);
+        for (int k = fit; k >= std::max(1, fit - 1); --k)
+            for (int wd = 0; wd <= (any_wide ? 1 : 0); ++wd) {
+                mp_dp_tuning t = default_tuning();
+                t.dp16_variant = var;
+                t.dp16_ctas_per_sm = k;
+                t.dp32_ctas_per_sm = fit32;
+                t.wide_direct = wd;
+                v.push_back(t);
+            }
+    }
+    return v;
+}
+
+static int time_run(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    cudaStream_t st = c->stream;
+    CK(cudaEventRecord(e0, st));
+    const int rc = enqueue_pipeline(c, b, st, false, false, t);
+    if (rc != MP_OK) return rc;
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    return MP_OK;
+}
+
+static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp_tuning *tried, int max_tried,
+                         int *n_tried)
+{
+    std::vector<mp_dp_tuning> cand = candidates(c, b);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return MP_ECUDA;
+    }
+    int rc = MP_OK;
+    float ms = 0;
+    // warm-up: first launches of each kernel build, pages of the buffers
+    for (int var = 0; var < (c->params.force_int32 ? 1 : kDp16Variants) && rc == MP_OK; ++var) {
+        mp_dp_tuning t = cand[0];
+        t.dp16_variant = var;
+        rc = time_run(c, b, t, e0, e1, &ms);
+    }
+    for (size_t k = 0; k < cand.size() && rc == MP_OK; ++k) rc = time_run(c, b, cand[k], e0, e1, &cand[k].ms);
+    if (rc == MP_OK && cand.size() > 1) {
+        // the two fastest once more; each keeps its lower time
+        std::vector<size_t> idx(cand.size());
+        for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return cand[x].ms < cand[y].ms; });
+        for (int r = 0; r < 2 && rc == MP_OK; ++r) {
+            rc = time_run(c, b, cand[idx[r]], e0, e1, &ms);
+            cand[idx[r]].ms = std::min(cand[idx[r]].ms, ms);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MP_OK) return rc;
+    size_t bi = 0;
+    for (size_t k = 1; k < cand.size(); ++k)
+        if (cand[k].ms < cand[bi].ms) bi = k;
+    c->tuned[b->shape_key] = cand[bi];
+    c->last = b;
+    if (best) *best = cand[bi];
+    if (tried)
+        for (size_t k = 0; k < cand.size() && static_cast<int>(k) < max_tried; ++k) tried[k] = cand[k];
+    if (n_tried) *n_tried = static_cast<int>(cand.size());
+    return MP_OK;
+}
+
+int mp_dp_autotune(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp_tuning *tried, int max_tried,
+                   int *n_tried)
+{
+    if (!c || !b || (tried && max_tried < 0)) return MP_EINVAL;
+    if (c->params.max_pairs_per_launch > 0) return MP_EINVAL;
+    if (c->server_running) return MP_ESTATE;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MP_ECUDA;
+    if (b->n == 0) {
+        if (best) *best = tuning_for(c, b);
+        if (n_tried) *n_tried = 0;
+        return MP_OK;
+    }
+    return autotune_impl(c, b, best, tried, max_tried, n_tried);
+}
+
+int mp_dp_set_tuning(mp_dp_ctx *c, const mp_dp_tuning *t)
+{
+    if (!c) return MP_EINVAL;
+    if (c->server_running) return MP_ESTATE;
+    if (!t) {
+        c->has_fixed = false;
+        return MP_OK;
+    }
+    if (t->dp16_variant < 0 || t->dp16_variant >= kDp16Variants || t->dp16_ctas_per_sm < 0 ||
+        t->dp32_ctas_per_sm < 0 || t->wide_direct < 0 || t->wide_direct > 1)
+        return MP_EINVAL;
+    c->fixed = *t;
+    c->has_fixed = true;
+    return MP_OK;
+}
+
+int mp_dp_get_tuning(mp_dp_ctx *c, const mp_dp_batch *b, mp_dp_tuning *t)
+{
+    if (!c || !b || !t) return MP_EINVAL;
+    *t = tuning_for(c, b);
+    return MP_OK;
+}
+
+int mp_dp_tuning_save(mp_dp_ctx *c, const char *path)
+{
+    if (!c || !path) return MP_EINVAL;
+    FILE *f = fopen(path, "w");
+    if (!f) return MP_EINVAL;
+    bool ok = fprintf(f, "mp_dp_tuning 1 %s %d\n", c->dev_name.c_str(), c->num_sms) > 0;
+    for (const auto &kv : c->tuned) {
+        const mp_dp_tuning &t = kv.second;
+        ok = ok && fprintf(f, "%016llx %d %d %d %d %.4f\n", static_cast<unsigned long long>(kv.first), t.dp16_variant,
+                           t.dp16_ctas_per_sm, t.dp32_ctas_per_sm, t.wide_direct, static_cast<double>(t.ms)) > 0;
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? MP_OK : MP_EINVAL;
+}
+
+int mp_dp_tuning_load(mp_dp_ctx *c, const char *path)
+{
+    if (!c || !path) return MP_EINVAL;
+    if (c->server_running) return MP_ESTATE;
+    FILE *f = fopen(path, "r");
+    if (!f) return MP_EINVAL;
+    char name[256] = {0};
+    int version = 0, sms = 0;
+    if (fscanf(f, "mp_dp_tuning %d %255s %d", &version, name, &sms) != 3 || version != 1 ||
+        c->dev_name != name || sms != c->num_sms) {
+        fclose(f);
+        return MP_EINVAL;
+    }
+    std::map<uint64_t, mp_dp_tuning> got;
+    for (;;) {
+        unsigned long long key = 0;
+        mp_dp_tuning t{};
+        double ms = 0;
+        const int k = fscanf(f, "%llx %d %d %d %d %lf", &key, &t.dp16_variant, &t.dp16_ctas_per_sm,
+                             &t.dp32_ctas_per_sm, &t.wide_direct, &ms);
+        if (k == EOF) break;
+        if (k != 6 || t.dp16_variant < 0 || t.dp16_variant >= kDp16Variants || t.dp16_ctas_per_sm < 0 ||
+            t.dp32_ctas_per_sm < 0 || t.wide_direct < 0 || t.wide_direct > 1) {
+            fclose(f);
+            return MP_EINVAL;
+        }
+        t.ms = static_cast<float>(ms);
+        got[key] = t;
+    }
+    fclose(f);
+    for (const auto &kv : got) c->tuned[kv.first] = kv.second;
     return MP_OK;
 }
 
@@ -873,7 +1140,14 @@ static void serve_loop(mp_dp_ctx *c)
         mp_dp_params p = c->params;
         p.tb_budget_bytes = c->slot_budget;
         p.max_pairs_per_launch = 0;
-        if (mp_dp_init(&s.ctx, &p, c->device) != MP_OK) init_ok = false;
+        p.autotune = 0;
+        if (mp_dp_init(&s.ctx, &p, c->device) != MP_OK) {
+            init_ok = false;
+            continue;
+        }
+        s.ctx->has_fixed = c->has_fixed;
+        s.ctx->fixed = c->fixed;
+        s.ctx->tuned = c->tuned;
     }
     std::vector<Request> take;
     for (;;) {

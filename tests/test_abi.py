@@ -52,16 +52,18 @@ def test_struct_layout_matches_header(mp, tmp_path):
     src.write_text("""#include <stdio.h>
 #include <stddef.h>
 #include "mp_dp.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mp_result), sizeof(mp_pair),
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mp_result), sizeof(mp_pair),
  sizeof(mp_dp_params), sizeof(mp_dp_stats), offsetof(mp_result, cigar), offsetof(mp_pair, strand),
- offsetof(mp_dp_params, tb_budget_bytes)); return 0;}""")
+ offsetof(mp_dp_params, tb_budget_bytes), offsetof(mp_dp_params, autotune), sizeof(mp_dp_tuning),
+ offsetof(mp_dp_tuning, ms)); return 0;}""")
     exe = tmp_path / "sz"
     import subprocess
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = list(map(int, subprocess.check_output([str(exe)]).split()))
     want = [ctypes.sizeof(mp.mp_result), ctypes.sizeof(mp.mp_pair), ctypes.sizeof(mp.mp_dp_params),
             ctypes.sizeof(mp.mp_dp_stats), mp.mp_result.cigar.offset, mp.mp_pair.strand.offset,
-            mp.mp_dp_params.tb_budget_bytes.offset]
+            mp.mp_dp_params.tb_budget_bytes.offset, mp.mp_dp_params.autotune.offset,
+            ctypes.sizeof(mp.mp_dp_tuning), mp.mp_dp_tuning.ms.offset]
     assert got == want
 
 
@@ -86,4 +88,9 @@ def test_null_arguments(mp):
     assert L.mp_dp_init(None, None, 0) == mp.MP_EINVAL
     assert L.mp_dp_align_batch(None, None, 0, None) == mp.MP_EINVAL
     assert L.mp_dp_get_stats(None, None) == mp.MP_EINVAL
+    assert L.mp_dp_autotune(None, None, None, None, 0, None) == mp.MP_EINVAL
+    assert L.mp_dp_set_tuning(None, None) == mp.MP_EINVAL
+    assert L.mp_dp_get_tuning(None, None, None) == mp.MP_EINVAL
+    assert L.mp_dp_tuning_save(None, b"x") == mp.MP_EINVAL
+    assert L.mp_dp_tuning_load(None, b"x") == mp.MP_EINVAL
     L.mp_dp_destroy(None)
