@@ -30,6 +30,9 @@ WORKLOAD = ("4096 (protein, region) pairs: protein log-normal median 350 aa (50-
 WORKLOAD_C3 = ("20000 (protein, region) pairs, uneven sizes: protein log-uniform 20-5000 aa; introns as the "
                "4096-pair workload plus a 2% tail of 20-100 kb; regions <= 200 kb; 5% score-only decoys; "
                "seed 3 (+1000 per rank)")
+WORKLOAD_C5 = ("genome-scale: 500 Mb genome (40% GC) with 20000 planted genes; 200000 proteins (10% sources, "
+               "45% 50-70%-identity paralogs, 45% unrelated); host 7-mer seed + chain, top 3 chains per protein; "
+               "every candidate region aligned with traceback; seed 5 (+1000 per rank)")
 # algorithmic integer ops per cell of the DP pass: the 27 max/add of Eq. 7 (I 3, D 3, A/B/C 2 each,
 # H 15) and one running maximum for the best cell.  Traceback decisions are re-derived from the
 # stored H values along the path only, in the traceback kernel.
@@ -282,8 +285,10 @@ def main():
     ap.add_argument("--pairs", type=int, default=4096, help="first N pairs of the workload (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: skip the end-to-end leg")
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration, no tuning runs")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: the 4,096-pair batch (default); c3: the 20,000-pair uneven-size stress batch")
+    ap.add_argument("--c5-scale", type=float, default=1.0, help="shrink the genome-scale workload (tests)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+                    help="c2: the 4,096-pair batch (default); c3: the 20,000-pair uneven-size stress batch; "
+                         "c5: the candidate regions of the genome-scale workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -309,16 +314,36 @@ def main():
         dist.barrier()
     mpbuild.build()
 
-    if args.workload == "c3":
-        pairs = synth.config3(seed=rank_seed(3, rank))[: args.pairs if args.pairs != 4096 else None]
-        workload = WORKLOAD_C3
+    prep = {}
+    if args.workload == "c5":
+        # candidate regions of the genome-scale workload, as zero-copy records
+        # into the genome and protein buffers (the host seed + chain step is
+        # input preparation, outside every timed region)
+        t_gen = time.perf_counter()
+        gw = synth.config5(seed=rank_seed(5, rank), scale=args.c5_scale)
+        prep = {"genome_bp": len(gw.genome), "proteins": len(gw.prot_len), "regions": gw.n_regions,
+                "regions_per_protein": gw.n_regions / len(gw.prot_len),
+                "generate_and_seed_chain_s": time.perf_counter() - t_gen}
+        po, pl, no, nl, st_ = gw.region_arrays()
+        src = mp.RegionBatch(gw.prot_buf, po, pl, gw.genome, no, nl, st_)
+        n_pairs, cells = gw.n_regions, gw.cells()
+        ascii_bytes = int(pl.sum() + nl.sum())
+        get_pair = gw.pair
+        workload = WORKLOAD_C5 if args.c5_scale == 1.0 else WORKLOAD_C5 + f" (scaled by {args.c5_scale})"
     else:
-        pairs = synth.config2(seed=rank_seed(2, rank))[: args.pairs]
-        workload = WORKLOAD
-    cells = float(sum(p.cells for p in pairs))
+        if args.workload == "c3":
+            pairs = synth.config3(seed=rank_seed(3, rank))[: args.pairs if args.pairs != 4096 else None]
+            workload = WORKLOAD_C3
+        else:
+            pairs = synth.config2(seed=rank_seed(2, rank))[: args.pairs]
+            workload = WORKLOAD
+        src = mp.PairBatch(pairs)             # the sequences in host memory as the C ABI takes them
+        n_pairs, cells = len(pairs), float(sum(p.cells for p in pairs))
+        ascii_bytes = sum(len(p.prot) + len(p.nt) for p in pairs)
+        get_pair = pairs.__getitem__
     ctx = mp.mp_dp_init(None, local)
     mp.mp_dp_set_timing(ctx, True)
-    batch = mp.mp_dp_batch_upload(ctx, pairs)
+    batch = mp.mp_dp_batch_upload(ctx, src)
     tuning = None
     if not args.no_autotune:
         # the launch configuration is chosen by the library's autotuner on this
@@ -359,7 +384,7 @@ def main():
     n_rerun = int(((res["status"] & 1) != 0).sum())
     mp.mp_dp_batch_free(ctx, batch)
     all_cells, t_max = job_totals(cells, elapsed, dist, "cuda")
-    all_pairs, _ = job_totals(len(pairs), elapsed, dist, "cuda")
+    all_pairs, _ = job_totals(n_pairs, elapsed, dist, "cuda")
     ms_per_step = t_max * 1000 / args.steps
     gcups = all_cells / (t_max / args.steps) / 1e9
     pairs_per_s = all_pairs / (t_max / args.steps)
@@ -368,7 +393,7 @@ def main():
     e2e_steps = 0 if args.skip_e2e else max(2, min(args.steps, 3))
     mp.mp_dp_set_timing(ctx, False)
     out = res
-    host_batch = mp.PairBatch(pairs)          # the sequences in host memory as the C ABI takes them
+    host_batch = src
     if e2e_steps:
         mp.mp_dp_align_batch(ctx, host_batch, raw=True)
     barrier()
@@ -378,9 +403,8 @@ def main():
     barrier()
     e2e_t = max(time.perf_counter() - t0, 1e-9)
     _, e2e_t = job_totals(cells, e2e_t, dist, "cuda")
-    ascii_bytes = sum(len(p.prot) + len(p.nt) for p in pairs)
-    h2d = ascii_bytes + len(pairs) * (72 + 4)          # sequences + pair descriptors + work order
-    d2h = len(pairs) * 32 + 4 + int(out["n_cigar"].sum()) * 4
+    h2d = ascii_bytes + n_pairs * (72 + 4)          # sequences + pair descriptors + work order
+    d2h = n_pairs * 32 + 4 + int(out["n_cigar"].sum()) * 4
     e2e = {"value": all_cells / (e2e_t / e2e_steps) / 1e9 if e2e_steps else None, "unit": "GCUPS",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "pairs_per_s": all_pairs / (e2e_t / e2e_steps) if e2e_steps else None}
@@ -404,7 +428,7 @@ def main():
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
-        "config": {"workload": workload, "pairs": len(pairs), "cells": cells, "waves": stats["n_waves"],
+        "config": {"workload": workload, "pairs": n_pairs, "cells": cells, "waves": stats["n_waves"], **prep,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps; each step also writes "
                          f"{stats['code_bytes'] / 1e9:.1f} GB of traceback codes"},
@@ -432,7 +456,7 @@ def main():
         # plain form: one pair per kernel launch, on a sample
         ctxp = mp.mp_dp_init(mp.mp_dp_default_params(max_pairs_per_launch=1), local)
         rng = np.random.default_rng(0)
-        sample = [pairs[k] for k in rng.choice(len(pairs), 48, replace=False)]
+        sample = [get_pair(int(k)) for k in rng.choice(n_pairs, 48, replace=False)]
         mp.mp_dp_align_batch(ctxp, sample[:2], raw=True)
         bp = mp.mp_dp_batch_upload(ctxp, sample)
         mp.mp_dp_batch_run(ctxp, bp)
@@ -455,7 +479,9 @@ def main():
                                for r in args.serve_rates.split(",")]
         except Exception as exc:  # noqa: BLE001
             line["serving"] = {"error": str(exc)}
-        line["cpu_baseline"] = cpu_baseline(pairs)
+        cpu_pairs = pairs if args.workload != "c5" else \
+            [get_pair(int(k)) for k in np.random.default_rng(1).choice(n_pairs, min(n_pairs, 4000), replace=False)]
+        line["cpu_baseline"] = cpu_baseline(cpu_pairs)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

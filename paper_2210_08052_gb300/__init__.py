@@ -213,6 +213,38 @@ class PairBatch(_PairArray):
     caller passes to mp_dp_align_batch); reusable across calls."""
 
 
+class RegionBatch(_PairArray):
+    """mp_pair records pointing into two host buffers without copying: the
+    proteins (ASCII, concatenated) and a genome (ASCII), with one record per
+    (protein, genome interval, strand).  The buffers must stay alive and
+    unchanged while the batch is in use (the object keeps references)."""
+
+    def __init__(self, prot_buf, prot_off, prot_len, nt_buf, nt_off, nt_len, strand, flags=None):
+        prot_buf = np.ascontiguousarray(prot_buf, dtype=np.uint8)
+        nt_buf = np.ascontiguousarray(nt_buf, dtype=np.uint8)
+        n = len(prot_off)
+        prot_off, prot_len = np.asarray(prot_off, np.int64), np.asarray(prot_len, np.int64)
+        nt_off, nt_len = np.asarray(nt_off, np.int64), np.asarray(nt_len, np.int64)
+        if n and (prot_off.min() < 0 or (prot_off + prot_len).max() > len(prot_buf) or nt_off.min() < 0 or
+                  (nt_off + nt_len).max() > len(nt_buf) or prot_len.max() >= 1 << 32 or nt_len.max() >= 1 << 32):
+            raise ValueError("a record lies outside its buffer")
+        dt = np.dtype({"names": ["prot", "prot_len", "nt", "nt_len", "strand", "flags"],
+                       "formats": [np.uint64, np.uint32, np.uint64, np.uint32, np.int8, np.uint32],
+                       "offsets": [mp_pair.prot.offset, mp_pair.prot_len.offset, mp_pair.nt.offset,
+                                   mp_pair.nt_len.offset, mp_pair.strand.offset, mp_pair.flags.offset],
+                       "itemsize": ctypes.sizeof(mp_pair)})
+        rec = np.zeros(max(n, 1), dtype=dt)
+        rec["prot"][:n] = prot_buf.ctypes.data + prot_off
+        rec["prot_len"][:n] = prot_len
+        rec["nt"][:n] = nt_buf.ctypes.data + nt_off
+        rec["nt_len"][:n] = nt_len
+        rec["strand"][:n] = np.asarray(strand, np.int8)
+        rec["flags"][:n] = 0 if flags is None else np.asarray(flags, np.uint32)
+        self.keep = [prot_buf, nt_buf, rec]
+        self.arr = ctypes.cast(rec.ctypes.data, ctypes.POINTER(mp_pair))
+        self.n = n
+
+
 def mp_dp_align_batch(ctx, pairs, raw: bool = False):
     """Align pairs end to end (a list of pairs, or a PairBatch).  Returns a
     list of result dicts, or with raw=True a structured numpy array of the
