@@ -186,14 +186,16 @@ struct mp_dp_batch {
     DevBuf<uint32_t> nt2;
     DevBuf<PairOut> out;
     DevBuf<uint32_t> ops, cig, work;
-    DevBuf<uint2> items, rerun_items;
+    DevBuf<uint2> items, items0, rerun_items;   // all strip items; strip-0 items; re-run list
     DevBuf<uint4> recs;                 // per-nt records of every pair
     DevBuf<uint64_t> bnd;
-    // per-run state, zeroed by one memset: counters | strips_done | progress | best_key
+    // per-run state, zeroed by one memset: counters | strips_done | progress |
+    // best_key | successor slots
     DevBuf<unsigned long long> state;
-    size_t state_bytes = 0, off_done = 0, off_progress = 0, off_key = 0;
-    std::vector<uint2> h_items;
+    size_t state_bytes = 0, off_done = 0, off_progress = 0, off_key = 0, off_ready = 0;
+    std::vector<uint2> h_items, h_items0;
     std::vector<uint32_t> item_off;     // first item of each pair in the order (by order index)
+    std::vector<uint32_t> item0_off;    // first strip-0 item of each pair in the order
     DevBuf<uint32_t> wave_nwide;        // Wave::nwide_items of each wave, on the device
     uint64_t shape_key = 0;             // shape class for the tuned table
     cudaGraphExec_t graph = nullptr;
@@ -369,7 +371,7 @@ static void free_batch_device(mp_dp_batch *b)
     b->events.clear();
     b->ascii.release(); b->d_desc.release(); b->prot.release(); b->nt2.release(); b->out.release();
     b->ops.release(); b->cig.release(); b->work.release(); b->items.release(); b->rerun_items.release();
-    b->bnd.release(); b->state.release(); b->recs.release(); b->wave_nwide.release();
+    b->bnd.release(); b->state.release(); b->recs.release(); b->wave_nwide.release(); b->items0.release();
 }
 
 void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
@@ -379,6 +381,10 @@ void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
     free_batch_device(b);
     delete b;
 }
+
+// index of the compacted-CIGAR length among the state counters (after the
+// 8 counters of every wave)
+static size_t cig_total_index(const mp_dp_batch *b) { return 8 * b->waves.size(); }
 
 static uint32_t log2_bucket(double v)
 {
@@ -526,7 +532,9 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     uint32_t wbeg = 0, ibeg = 0, wcur = 0, nwide = 0;
     b->h_items.clear();
     b->h_items.reserve(strips);
+    b->h_items0.clear();
     b->item_off.assign(n + 1, 0);
+    b->item0_off.assign(n + 1, 0);
     for (uint32_t k = 0; k < n; ++k) {
         const uint32_t p = b->order[k];
         PairDesc &d = b->desc[p];
@@ -540,7 +548,9 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
             wcur = wave_of[p];
         }
         b->item_off[k] = static_cast<uint32_t>(b->h_items.size());
+        b->item0_off[k] = static_cast<uint32_t>(b->h_items0.size());
         if (d.flags & PF_SKIP) continue;
+        b->h_items0.push_back(make_uint2(p, 0));
         d.code_off = cur;
         cur += cbytes[p];
         if (cbytes[p]) b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
@@ -548,15 +558,20 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         if (wide(p) == 0) nwide += d.n_strips;
     }
     b->item_off[n] = static_cast<uint32_t>(b->h_items.size());
+    b->item0_off[n] = static_cast<uint32_t>(b->h_items0.size());
     b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
     b->shape_key = shape_key_of(*b);
     maxw = std::max(maxw, cur);
     // per-run state block
-    const size_t ncnt = 4 * b->waves.size() + 4;
+    // counters: 8 per wave (main-pass queue block of 4, re-run head and
+    // count), the compaction total, and a queue block of 4 per pair for the
+    // one-launch-per-group form
+    const size_t ncnt = 8 * b->waves.size() + 8 + 4 * n;
     b->off_done = div_up(ncnt * 4, 8) * 8;
     b->off_progress = b->off_done + div_up(n * 4, 8) * 8;
     b->off_key = b->off_progress + div_up(strips * 4, 8) * 8;
-    b->state_bytes = b->off_key + n * 8 + 8;
+    b->off_ready = b->off_key + n * 8 + 8;
+    b->state_bytes = b->off_ready + strips * 8 + 8;
 
     // ---- device buffers (grown, never shrunk)
     cudaError_t e = cudaSuccess;
@@ -564,7 +579,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         (e = b->prot.reserve(pro + 16)) != cudaSuccess || (e = b->nt2.reserve(ntw + 32)) != cudaSuccess ||
         (e = b->out.reserve(n + 1)) != cudaSuccess || (e = b->ops.reserve(ops + 1)) != cudaSuccess ||
         (e = b->cig.reserve(ops + 1)) != cudaSuccess || (e = b->work.reserve(n + 1)) != cudaSuccess ||
-        (e = b->items.reserve(strips + 1)) != cudaSuccess || (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess ||
+        (e = b->items.reserve(strips + 1)) != cudaSuccess || (e = b->items0.reserve(n + 1)) != cudaSuccess || (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess ||
         (e = b->state.reserve(b->state_bytes / 8 + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
         (e = b->recs.reserve(nrec + 1)) != cudaSuccess || (e = b->wave_nwide.reserve(b->waves.size())) != cudaSuccess ||
         (e = c->codes.reserve(std::max<uint64_t>(maxw, 256))) != cudaSuccess) {
@@ -593,6 +608,8 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     CK(cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(b->items.p, b->h_items.data(), b->h_items.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->items0.p, b->h_items0.data(), b->h_items0.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                       st));
     std::vector<uint32_t> nw(b->waves.size());
     for (size_t w = 0; w < nw.size(); ++w) nw[w] = b->waves[w].nwide_items;
     CK(cudaMemcpyAsync(b->wave_nwide.p, nw.data(), nw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
@@ -656,7 +673,8 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         a.best_key = reinterpret_cast<unsigned long long *>(state + b->off_key);
         a.strips_done = reinterpret_cast<uint32_t *>(state + b->off_done);
         a.rerun_items = b->rerun_items.p + wv.ibegin;
-        a.rerun_count = counters + 4 * w + 2;
+        a.rerun_count = counters + 8 * w + 5;
+        unsigned long long *ready = reinterpret_cast<unsigned long long *>(state + b->off_ready);
         a.sp = c->sp;
         a.spin_limit = c->params.wait_limit > 0 ? static_cast<uint32_t>(c->params.wait_limit) : 0u;
         a.no_publish = (c->params.debug_flags & MP_DEBUG_NO_PUBLISH) ? 1u : 0u;
@@ -666,12 +684,13 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
             for (uint32_t k = wv.begin; k < wv.end; k += per_launch) {
                 const uint32_t k2 = std::min<uint32_t>(wv.end, k + per_launch);
                 DPArgs a1 = a;
-                a1.items = b->items.p + b->item_off[k];
-                a1.n_items = b->item_off[k2] - b->item_off[k];
-                if (!a1.n_items) continue;
-                a1.head = counters + 4 * W + (k & 1);
-                CK(cudaMemsetAsync(a1.head, 0, sizeof(uint32_t), st));
-                const int grid = std::max(1, std::min<int>(c->num_sms, static_cast<int>((a1.n_items + kWarpsPerCta - 1) / kWarpsPerCta)));
+                a1.items = b->items0.p + b->item0_off[k];
+                a1.n_items = b->item0_off[k2] - b->item0_off[k];
+                a1.n_total = b->item_off[k2] - b->item_off[k];
+                if (!a1.n_total) continue;
+                a1.head = counters + 8 * W + 8 + 4 * k;
+                a1.ready = ready + b->item_off[k];
+                const int grid = std::max(1, std::min<int>(c->num_sms, static_cast<int>((a1.n_total + kWarpsPerCta - 1) / kWarpsPerCta)));
                 if (c->params.force_int32) CK(launch_dp32(a1, grid, false, st));
                 else CK(launch_dp16(a1, grid, variant, st));
                 ++launches;
@@ -686,10 +705,16 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
                                    cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(a.rerun_count, b->wave_nwide.p + w, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
             }
-            a.items = b->items.p + wv.ibegin + skip;
-            a.n_items = nitems - skip;
-            a.head = counters + 4 * w;
-            const int want = static_cast<int>((a.n_items + kWarpsPerCta - 1) / kWarpsPerCta);
+            // strip-0 items of the pairs the main pass runs (the wide prefix,
+            // if handed to the int32 queue, is skipped)
+            uint32_t k0 = wv.begin;
+            while (skip && k0 < wv.end && b->item_off[k0] < wv.ibegin + skip) ++k0;
+            a.items = b->items0.p + b->item0_off[k0];
+            a.n_items = b->item0_off[wv.end] - b->item0_off[k0];
+            a.n_total = nitems - skip;
+            a.head = counters + 8 * w;
+            a.ready = ready + wv.ibegin;
+            const int want = static_cast<int>((a.n_total + kWarpsPerCta - 1) / kWarpsPerCta);
             const int grid16 = std::max(1, std::min<int>(g16, want));
             const int grid32 = std::max(1, std::min<int>(g32, want));
             if (c->params.force_int32) CK(launch_dp32(a, grid32, false, st));
@@ -699,9 +724,10 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         }
         CK(rec(2 + EV_PER_WAVE * w));
         if (!c->params.force_int32) {
-            a.head = counters + 4 * w + 1;
+            a.head = counters + 8 * w + 4;
             a.items = nullptr;
-            a.n_items = 0;
+            a.n_items = a.n_total = 0;
+            a.ready = nullptr;
             CK(launch_dp32(a, g32, true, st));
             ++launches;
             ++dp_launches;
@@ -722,7 +748,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         ++launches;
         CK(rec(4 + EV_PER_WAVE * w));
     }
-    CK(launch_compact(b->d_desc.p, b->out.p, n, b->ops.p, b->cig.p, counters + 4 * W + 2, st));
+    CK(launch_compact(b->d_desc.p, b->out.p, n, b->ops.p, b->cig.p, counters + cig_total_index(b), st));
     launches += 2;
     CK(rec(static_cast<int>(2 + EV_PER_WAVE * W)));
     b->n_launches = launches;
@@ -1028,7 +1054,7 @@ int mp_dp_batch_download(mp_dp_ctx *c, mp_dp_batch *b, mp_result *out)
     b->h_out.resize(n);
     uint32_t total = 0;
     CK(cudaMemcpyAsync(b->h_out.data(), b->out.p, n * sizeof(PairOut), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&total, reinterpret_cast<uint32_t *>(b->state.p) + 4 * b->waves.size() + 2, sizeof(uint32_t),
+    CK(cudaMemcpyAsync(&total, reinterpret_cast<uint32_t *>(b->state.p) + cig_total_index(b), sizeof(uint32_t),
                        cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c->host_cig.resize(std::max<size_t>(total, 1));
