@@ -267,18 +267,24 @@ typedef struct {
     int32_t wide_direct;       /* 1: pairs whose score bound reaches the int16 limit skip the int16
                                   pass and run in int32 at once; 0: int16 first, int32 re-run only
                                   if the pair saturates */
+    int32_t overlap_waves;     /* 1: a batch whose traceback exceeds the budget is planned in waves of
+                                  half the budget that run alternately on two streams over two
+                                  halves of the arena (one wave's tail overlaps the next wave);
+                                  0: waves of the whole budget, one after the other */
     float ms;                  /* set by mp_dp_autotune: device time of one run of the batch */
-    int32_t reserved[3];
+    int32_t reserved[2];
 } mp_dp_tuning;
 
 /* Time the candidate configurations on an uploaded batch (one warm-up run,
  * one timed run per candidate, a second timed run of the two fastest; CUDA
  * events on the context's stream; every run computes the batch's full
  * results, so the batch holds valid results afterwards) and record the
- * fastest for the batch's shape class (pair count, mean cells per pair,
- * longest critical path and whether any pair needs int32, each on a log2
- * scale).  Later runs of batches in that class use it unless
- * mp_dp_set_tuning fixed a configuration.  best (may be NULL) receives the
+ * fastest for the batch's shape class (pair count, mean cells per pair and
+ * longest critical path on log2 scales, whether any pair needs int32,
+ * whether the batch needs several waves).  Later runs of batches in that
+ * class use it unless mp_dp_set_tuning fixed a configuration.  A candidate
+ * with the other wave policy re-plans the batch's waves first (host work
+ * and small copies outside the timed interval).  best (may be NULL) receives the
  * choice; tried (may be NULL) up to max_tried candidates with their times,
  * and n_tried (may be NULL) how many were timed.  MP_EINVAL in the plain
  * form (max_pairs_per_launch > 0); MP_ESTATE while the serving loop runs. */

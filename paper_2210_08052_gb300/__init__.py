@@ -65,10 +65,10 @@ class mp_dp_stats(ctypes.Structure):
 class mp_dp_tuning(ctypes.Structure):
     _fields_ = [("dp16_variant", ctypes.c_int32), ("dp16_ctas_per_sm", ctypes.c_int32),
                 ("dp32_ctas_per_sm", ctypes.c_int32), ("wide_direct", ctypes.c_int32),
-                ("ms", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+                ("overlap_waves", ctypes.c_int32), ("ms", ctypes.c_float), ("reserved", ctypes.c_int32 * 2)]
 
 
-TUNING_KEYS = ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct", "ms")
+TUNING_KEYS = ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct", "overlap_waves", "ms")
 
 
 class mp_dp_serve_stats(ctypes.Structure):

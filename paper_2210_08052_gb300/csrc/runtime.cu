@@ -165,7 +165,9 @@ struct Wave {
     uint32_t nwide_items;   // items of PF_WIDE pairs, first in the wave's range
 };
 
-enum { EV_START = 0, EV_PACK, EV_DP, EV_RERUN, EV_TB, EV_END, EV_PER_WAVE = 3 };
+// timing events: [0] start, [1] after packing; per wave [start, DP, re-run,
+// traceback]; then [before compaction, end]
+enum { EV_PER_WAVE = 4 };
 
 }  // namespace
 
@@ -198,6 +200,11 @@ struct mp_dp_batch {
     std::vector<uint32_t> item0_off;    // first strip-0 item of each pair in the order
     DevBuf<uint32_t> wave_nwide;        // Wave::nwide_items of each wave, on the device
     uint64_t shape_key = 0;             // shape class for the tuned table
+    bool overlap = false;               // waves alternate between two streams and two arena halves
+    uint64_t arena_half = 0;            // bytes of one arena half (overlap only)
+    bool needs_waves = false;           // the traceback bytes exceed the budget
+    int planned = -1;                   // wave policy of the current plan (0 / 1), -1 before planning
+    uint64_t strips_total = 0;
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_sig = 0;             // timing flag and configuration the graph was captured with
     int runs = 0;
@@ -228,6 +235,8 @@ struct mp_dp_ctx {
     int device = 0;
     int num_sms = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;     // second stream: odd waves of an overlapped batch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     mp_dp_params params{};
     ScoreParams sp{};
     uint64_t budget = 0;
@@ -336,6 +345,12 @@ int mp_dp_init(mp_dp_ctx **out, const mp_dp_params *p, int device)
     for (char &ch : c->dev_name)
         if (ch == ' ' || ch == '\t') ch = '_';
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return MP_ECUDA; }
+    if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        mp_dp_destroy(c);
+        return MP_ECUDA;
+    }
     c->sp.q = prm.q; c->sp.e = prm.e; c->sp.f = prm.f; c->sp.r = prm.r; c->sp.stop = prm.stop;
     memcpy(c->sp.mat, prm.mat, sizeof(c->sp.mat));
     size_t free_b = 0, total_b = 0;
@@ -395,8 +410,8 @@ static uint32_t log2_bucket(double v)
 
 // Shape class of a planned batch: pair count, mean cells per pair, the
 // longest critical path (chunks of the region plus the lag of its strips)
-// on log2 scales, whether some pair needs int32, and the wave count (1, 2,
-// 3+).  Batches of one class take the same tuned configuration.
+// on log2 scales, whether some pair needs int32, and whether the batch needs
+// several waves.  Batches of one class take the same tuned configuration.
 static uint64_t shape_key_of(const mp_dp_batch &b)
 {
     double crit = 0;
@@ -409,8 +424,178 @@ static uint64_t shape_key_of(const mp_dp_batch &b)
     const uint64_t nb = log2_bucket(static_cast<double>(b.n) + 1);
     const uint64_t cb = log2_bucket(b.n ? b.cells / b.n + 1 : 1);
     const uint64_t kb = log2_bucket(crit + 1);
-    const uint64_t wb = std::min<size_t>(b.waves.size(), 3);
+    const uint64_t wb = b.needs_waves ? 1 : 0;
     return nb | (cb << 8) | (kb << 16) | (static_cast<uint64_t>(any_wide) << 24) | (wb << 28);
+}
+
+static mp_dp_tuning default_tuning()
+{
+    mp_dp_tuning t{};
+    t.overlap_waves = 1;
+    return t;     // int16 kernel for 3 CTAs/SM, all CTAs that fit, int16 first for wide pairs, overlapped waves
+}
+
+static mp_dp_tuning tuning_for(const mp_dp_ctx *c, const mp_dp_batch *b)
+{
+    if (c->has_fixed) return c->fixed;
+    auto it = c->tuned.find(b->shape_key);
+    return it != c->tuned.end() ? it->second : default_tuning();
+}
+
+// Traceback bytes of the batch's pairs that keep a stream (pairs larger than
+// the whole budget are scored without one).
+static uint64_t plan_code_bytes(const mp_dp_ctx *c, const mp_dp_batch *b)
+{
+    uint64_t total = 0;
+    for (const PairDesc &d : b->desc) {
+        if (d.flags & (PF_SKIP | PF_SCORE_ONLY)) continue;
+        const uint64_t cb = div_up(code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0), 256) * 256;
+        if (cb <= c->budget) total += cb;
+    }
+    return total;
+}
+
+// Plan the batch's pair order, waves, strip items and per-run state for the
+// wave policy `overlap`, grow the buffers that depend on the plan, and copy
+// the plan to the device.  Called by the upload, and again when a
+// configuration with the other policy runs the batch.
+static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, bool overlap)
+{
+    const size_t n = b->n;
+    const uint64_t strips = b->strips_total;
+    b->waves.clear();
+    b->code_bytes_total = 0;
+    // ---- pair order: largest first (longest-processing-time first)
+    b->order.resize(n);
+    for (size_t k = 0; k < n; ++k) b->order[k] = static_cast<uint32_t>(k);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
+        const uint64_t cx = static_cast<uint64_t>(b->desc[x].prot_len) * b->desc[x].nt_len;
+        const uint64_t cy = static_cast<uint64_t>(b->desc[y].prot_len) * b->desc[y].nt_len;
+        return cx > cy;
+    });
+    // ---- waves under the traceback budget
+    // Every wave gets a share of large and small pairs: pairs are taken
+    // largest first and placed in the wave with the least work (cells) whose
+    // traceback bytes still fit; a wave made only of the largest pairs would
+    // have too few strips to keep every SM busy.
+    const uint64_t cap = c->budget;
+    std::vector<uint64_t> cbytes(n, 0);
+    uint64_t total_bytes = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        PairDesc &d = b->desc[k];
+        if (d.flags & (PF_SKIP | PF_SCORE_ONLY)) continue;
+        uint64_t cb = div_up(code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0), 256) * 256;
+        if (cb > cap) {
+            d.flags |= PF_BUDGET | PF_SCORE_ONLY;
+            cb = 0;
+        }
+        cbytes[k] = cb;
+        total_bytes += cb;
+    }
+    // With the overlapped-wave policy, a batch that needs several waves plans
+    // them at half the budget and runs them alternately on two streams over
+    // two halves of the arena, so one wave's tail (its longest pairs) overlaps
+    // the next wave's start and its traceback; a pair larger than half the
+    // budget keeps one wave per budget.
+    uint64_t maxcb = 0;
+    for (uint32_t k = 0; k < n; ++k) maxcb = std::max(maxcb, cbytes[k]);
+    b->overlap = overlap && c->params.max_pairs_per_launch == 0 && total_bytes > cap && maxcb <= cap / 2;
+    const uint64_t wcap = b->overlap ? cap / 2 : cap;
+    std::vector<uint32_t> wave_of(n, 0);
+    std::vector<uint64_t> wbytes, wcells;
+    const size_t nw0 = static_cast<size_t>(std::max<uint64_t>(1, div_up(total_bytes, wcap)));
+    wbytes.assign(nw0, 0);
+    wcells.assign(nw0, 0);
+    for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t p = b->order[k];
+        const uint64_t cells = static_cast<uint64_t>(b->desc[p].prot_len) * b->desc[p].nt_len;
+        size_t best = SIZE_MAX;
+        for (size_t w = 0; w < wbytes.size(); ++w)
+            if (wbytes[w] + cbytes[p] <= wcap && (best == SIZE_MAX || wcells[w] < wcells[best])) best = w;
+        if (best == SIZE_MAX) {
+            best = wbytes.size();
+            wbytes.push_back(0);
+            wcells.push_back(0);
+        }
+        wave_of[p] = static_cast<uint32_t>(best);
+        wbytes[best] += cbytes[p];
+        wcells[best] += cells;
+    }
+    // group the largest-first order by wave, PF_WIDE pairs first within a wave
+    // (so that their items form a prefix the int32 kernel can take directly),
+    // otherwise still largest first
+    auto wide = [&](uint32_t x) { return (b->desc[x].flags & PF_WIDE) && !(b->desc[x].flags & PF_SKIP) ? 0 : 1; };
+    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
+        return wave_of[x] != wave_of[y] ? wave_of[x] < wave_of[y] : wide(x) < wide(y);
+    });
+    // strip items in pair order; each wave is a contiguous range
+    uint64_t cur = 0, maxw = 0;
+    uint32_t wbeg = 0, ibeg = 0, wcur = 0, nwide = 0;
+    b->h_items.clear();
+    b->h_items.reserve(strips);
+    b->h_items0.clear();
+    b->item_off.assign(n + 1, 0);
+    b->item0_off.assign(n + 1, 0);
+    for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t p = b->order[k];
+        PairDesc &d = b->desc[p];
+        if (wave_of[p] != wcur) {
+            b->waves.push_back(Wave{wbeg, k, ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
+            maxw = std::max(maxw, cur);
+            wbeg = k;
+            ibeg = static_cast<uint32_t>(b->h_items.size());
+            cur = 0;
+            nwide = 0;
+            wcur = wave_of[p];
+        }
+        b->item_off[k] = static_cast<uint32_t>(b->h_items.size());
+        b->item0_off[k] = static_cast<uint32_t>(b->h_items0.size());
+        if (d.flags & PF_SKIP) continue;
+        b->h_items0.push_back(make_uint2(p, 0));
+        d.code_off = cur;
+        cur += cbytes[p];
+        if (cbytes[p]) b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
+        for (uint32_t s = 0; s < d.n_strips; ++s) b->h_items.push_back(make_uint2(p, s));
+        if (wide(p) == 0) nwide += d.n_strips;
+    }
+    b->item_off[n] = static_cast<uint32_t>(b->h_items.size());
+    b->item0_off[n] = static_cast<uint32_t>(b->h_items0.size());
+    b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
+    maxw = std::max(maxw, cur);
+    if (b->waves.size() < 2) b->overlap = false;
+    b->arena_half = std::max<uint64_t>(div_up(maxw, 256) * 256, 256);
+    // per-run state block
+    // counters: 8 per wave (main-pass queue block of 4, re-run head and
+    // count), the compaction total, and a queue block of 4 per pair for the
+    // one-launch-per-group form
+    const size_t ncnt = 8 * b->waves.size() + 8 + 4 * n;
+    b->off_done = div_up(ncnt * 4, 8) * 8;
+    b->off_progress = b->off_done + div_up(n * 4, 8) * 8;
+    b->off_key = b->off_progress + div_up(strips * 4, 8) * 8;
+    b->off_ready = b->off_key + n * 8 + 8;
+    b->state_bytes = b->off_ready + strips * 8 + 8;
+
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->runs = 0;
+    b->planned = overlap ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    if ((e = b->state.reserve(b->state_bytes / 8 + 1)) != cudaSuccess ||
+        (e = b->wave_nwide.reserve(b->waves.size())) != cudaSuccess ||
+        (e = c->codes.reserve(b->overlap ? 2 * b->arena_half : std::max<uint64_t>(maxw, 256))) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
+    cudaStream_t st = c->stream;
+    CK(cudaStreamSynchronize(st));      // no run of an earlier plan still reads these buffers
+    CK(cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->items.p, b->h_items.data(), b->h_items.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->items0.p, b->h_items0.data(), b->h_items0.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                       st));
+    std::vector<uint32_t> nw(b->waves.size());
+    for (size_t w = 0; w < nw.size(); ++w) nw[w] = b->waves[w].nwide_items;
+    CK(cudaMemcpyAsync(b->wave_nwide.p, nw.data(), nw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return MP_OK;
 }
 
 // (Re)fill batch b with n pairs: plan strips, waves and offsets on the host,
@@ -473,105 +658,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         return MP_EINVAL;
     b->ascii_bytes = asc; b->prot_total = pro; b->nt_words = ntw; b->bnd_total = bnd; b->ops_total = ops;
 
-    // ---- pair order: largest first (longest-processing-time first)
-    b->order.resize(n);
-    for (size_t k = 0; k < n; ++k) b->order[k] = static_cast<uint32_t>(k);
-    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
-        const uint64_t cx = static_cast<uint64_t>(b->desc[x].prot_len) * b->desc[x].nt_len;
-        const uint64_t cy = static_cast<uint64_t>(b->desc[y].prot_len) * b->desc[y].nt_len;
-        return cx > cy;
-    });
-    // ---- waves under the traceback budget
-    // Every wave gets a share of large and small pairs: pairs are taken
-    // largest first and placed in the wave with the least work (cells) whose
-    // traceback bytes still fit; a wave made only of the largest pairs would
-    // have too few strips to keep every SM busy.
-    const uint64_t cap = c->budget;
-    std::vector<uint64_t> cbytes(n, 0);
-    uint64_t total_bytes = 0;
-    for (uint32_t k = 0; k < n; ++k) {
-        PairDesc &d = b->desc[k];
-        if (d.flags & (PF_SKIP | PF_SCORE_ONLY)) continue;
-        uint64_t cb = div_up(code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0), 256) * 256;
-        if (cb > cap) {
-            d.flags |= PF_BUDGET | PF_SCORE_ONLY;
-            cb = 0;
-        }
-        cbytes[k] = cb;
-        total_bytes += cb;
-    }
-    std::vector<uint32_t> wave_of(n, 0);
-    std::vector<uint64_t> wbytes, wcells;
-    const size_t nw0 = static_cast<size_t>(std::max<uint64_t>(1, div_up(total_bytes, cap)));
-    wbytes.assign(nw0, 0);
-    wcells.assign(nw0, 0);
-    for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t p = b->order[k];
-        const uint64_t cells = static_cast<uint64_t>(b->desc[p].prot_len) * b->desc[p].nt_len;
-        size_t best = SIZE_MAX;
-        for (size_t w = 0; w < wbytes.size(); ++w)
-            if (wbytes[w] + cbytes[p] <= cap && (best == SIZE_MAX || wcells[w] < wcells[best])) best = w;
-        if (best == SIZE_MAX) {
-            best = wbytes.size();
-            wbytes.push_back(0);
-            wcells.push_back(0);
-        }
-        wave_of[p] = static_cast<uint32_t>(best);
-        wbytes[best] += cbytes[p];
-        wcells[best] += cells;
-    }
-    // group the largest-first order by wave, PF_WIDE pairs first within a wave
-    // (so that their items form a prefix the int32 kernel can take directly),
-    // otherwise still largest first
-    auto wide = [&](uint32_t x) { return (b->desc[x].flags & PF_WIDE) && !(b->desc[x].flags & PF_SKIP) ? 0 : 1; };
-    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
-        return wave_of[x] != wave_of[y] ? wave_of[x] < wave_of[y] : wide(x) < wide(y);
-    });
-    // strip items in pair order; each wave is a contiguous range
-    uint64_t cur = 0, maxw = 0;
-    uint32_t wbeg = 0, ibeg = 0, wcur = 0, nwide = 0;
-    b->h_items.clear();
-    b->h_items.reserve(strips);
-    b->h_items0.clear();
-    b->item_off.assign(n + 1, 0);
-    b->item0_off.assign(n + 1, 0);
-    for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t p = b->order[k];
-        PairDesc &d = b->desc[p];
-        if (wave_of[p] != wcur) {
-            b->waves.push_back(Wave{wbeg, k, ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
-            maxw = std::max(maxw, cur);
-            wbeg = k;
-            ibeg = static_cast<uint32_t>(b->h_items.size());
-            cur = 0;
-            nwide = 0;
-            wcur = wave_of[p];
-        }
-        b->item_off[k] = static_cast<uint32_t>(b->h_items.size());
-        b->item0_off[k] = static_cast<uint32_t>(b->h_items0.size());
-        if (d.flags & PF_SKIP) continue;
-        b->h_items0.push_back(make_uint2(p, 0));
-        d.code_off = cur;
-        cur += cbytes[p];
-        if (cbytes[p]) b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
-        for (uint32_t s = 0; s < d.n_strips; ++s) b->h_items.push_back(make_uint2(p, s));
-        if (wide(p) == 0) nwide += d.n_strips;
-    }
-    b->item_off[n] = static_cast<uint32_t>(b->h_items.size());
-    b->item0_off[n] = static_cast<uint32_t>(b->h_items0.size());
-    b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
-    b->shape_key = shape_key_of(*b);
-    maxw = std::max(maxw, cur);
-    // per-run state block
-    // counters: 8 per wave (main-pass queue block of 4, re-run head and
-    // count), the compaction total, and a queue block of 4 per pair for the
-    // one-launch-per-group form
-    const size_t ncnt = 8 * b->waves.size() + 8 + 4 * n;
-    b->off_done = div_up(ncnt * 4, 8) * 8;
-    b->off_progress = b->off_done + div_up(n * 4, 8) * 8;
-    b->off_key = b->off_progress + div_up(strips * 4, 8) * 8;
-    b->off_ready = b->off_key + n * 8 + 8;
-    b->state_bytes = b->off_ready + strips * 8 + 8;
+    b->strips_total = strips;
 
     // ---- device buffers (grown, never shrunk)
     cudaError_t e = cudaSuccess;
@@ -579,10 +666,9 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         (e = b->prot.reserve(pro + 16)) != cudaSuccess || (e = b->nt2.reserve(ntw + 32)) != cudaSuccess ||
         (e = b->out.reserve(n + 1)) != cudaSuccess || (e = b->ops.reserve(ops + 1)) != cudaSuccess ||
         (e = b->cig.reserve(ops + 1)) != cudaSuccess || (e = b->work.reserve(n + 1)) != cudaSuccess ||
-        (e = b->items.reserve(strips + 1)) != cudaSuccess || (e = b->items0.reserve(n + 1)) != cudaSuccess || (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess ||
-        (e = b->state.reserve(b->state_bytes / 8 + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
-        (e = b->recs.reserve(nrec + 1)) != cudaSuccess || (e = b->wave_nwide.reserve(b->waves.size())) != cudaSuccess ||
-        (e = c->codes.reserve(std::max<uint64_t>(maxw, 256))) != cudaSuccess) {
+        (e = b->items.reserve(strips + 1)) != cudaSuccess || (e = b->items0.reserve(n + 1)) != cudaSuccess ||
+        (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
+        (e = b->recs.reserve(nrec + 1)) != cudaSuccess) {
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
     // ---- host -> device
@@ -605,16 +691,12 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     }
     cudaStream_t st = c->stream;
     CK(cudaMemcpyAsync(b->ascii.p, c->staging.p, asc, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(b->items.p, b->h_items.data(), b->h_items.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(b->items0.p, b->h_items0.data(), b->h_items0.size() * sizeof(uint2), cudaMemcpyHostToDevice,
-                       st));
-    std::vector<uint32_t> nw(b->waves.size());
-    for (size_t w = 0; w < nw.size(); ++w) nw[w] = b->waves[w].nwide_items;
-    CK(cudaMemcpyAsync(b->wave_nwide.p, nw.data(), nw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
-    return MP_OK;
+    // ---- the batch's shape class and the wave plan its configuration asks for
+    b->needs_waves = plan_code_bytes(c, b) > c->budget;
+    b->shape_key = shape_key_of(*b);
+    b->planned = -1;
+    return plan_waves(c, b, tuning_for(c, b).overlap_waves != 0);
 }
 
 int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch **out)
@@ -638,12 +720,13 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
 {
     const uint32_t n = static_cast<uint32_t>(b->n);
     int launches = 0, dp_launches = 0;
-    auto rec = [&](int idx) -> cudaError_t {
+    auto rec_on = [&](int idx, cudaStream_t s_) -> cudaError_t {
         // inside a stream capture only an External record becomes an event-record node
         if (!timed) return cudaSuccess;
-        return capturing ? cudaEventRecordWithFlags(b->events[idx], st, cudaEventRecordExternal)
-                         : cudaEventRecord(b->events[idx], st);
+        return capturing ? cudaEventRecordWithFlags(b->events[idx], s_, cudaEventRecordExternal)
+                         : cudaEventRecord(b->events[idx], s_);
     };
+    auto rec = [&](int idx) { return rec_on(idx, st); };
     char *state = reinterpret_cast<char *>(b->state.p);
     uint32_t *counters = reinterpret_cast<uint32_t *>(state);
     const size_t W = b->waves.size();
@@ -659,14 +742,26 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
     const int g32 = c->num_sms * (t.dp32_ctas_per_sm > 0 ? std::min(t.dp32_ctas_per_sm, fit32) : fit32);
     const bool direct = t.wide_direct != 0 && !c->params.force_int32;
     const int per_launch = c->params.max_pairs_per_launch;
+    const bool overlap = b->overlap && W > 1;
+    if (overlap) {
+        // the second stream joins after packing (and, under capture, joins the graph)
+        CK(cudaEventRecord(c->ev_fork, st));
+        CK(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+    }
+    const cudaStream_t main_st = st;
     for (size_t w = 0; w < W; ++w) {
         const Wave &wv = b->waves[w];
+        // odd waves of an overlapped batch: second stream, second arena half
+        // (this `st` shadows the main stream for the wave's launches)
+        const cudaStream_t st = overlap && (w & 1) ? c->stream2 : main_st;
+        uint8_t *arena = c->codes.p + (overlap && (w & 1) ? b->arena_half : 0);
+        CK(rec_on(static_cast<int>(2 + EV_PER_WAVE * w), st));
         DPArgs a{};
         a.pairs = b->d_desc.p;
         a.recs = b->recs.p;
         a.prot = b->prot.p;
         a.nt2 = b->nt2.p;
-        a.codes = c->codes.p;
+        a.codes = arena;
         a.bnd = b->bnd.p;
         a.out = b->out.p;
         a.progress = reinterpret_cast<uint32_t *>(state + b->off_progress);
@@ -722,8 +817,10 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
             ++launches;
             ++dp_launches;
         }
-        CK(rec(2 + EV_PER_WAVE * w));
-        if (!c->params.force_int32) {
+        CK(rec_on(static_cast<int>(3 + EV_PER_WAVE * w), st));
+        // only PF_WIDE pairs can saturate int16 (others are marked MP_ST_TRACE
+        // if they ever did): a wave without them needs no re-run launch
+        if (!c->params.force_int32 && wv.nwide_items > 0) {
             a.head = counters + 8 * w + 4;
             a.items = nullptr;
             a.n_items = a.n_total = 0;
@@ -732,12 +829,12 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
             ++launches;
             ++dp_launches;
         }
-        CK(rec(3 + EV_PER_WAVE * w));
+        CK(rec_on(static_cast<int>(4 + EV_PER_WAVE * w), st));
         TBArgs t{};
         t.pairs = b->d_desc.p;
         t.work = b->work.p + wv.begin;
         t.n_work = wv.end - wv.begin;
-        t.codes = c->codes.p;
+        t.codes = arena;
         t.prot = b->prot.p;
         t.nt2 = b->nt2.p;
         t.out = b->out.p;
@@ -746,34 +843,26 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         const int tgrid = std::max(1, std::min<int>(c->num_sms * 8, static_cast<int>((t.n_work + 7) / 8)));
         CK(launch_tb(t, tgrid, st));
         ++launches;
-        CK(rec(4 + EV_PER_WAVE * w));
+        CK(rec_on(static_cast<int>(5 + EV_PER_WAVE * w), st));
     }
+    if (overlap) {
+        CK(cudaEventRecord(c->ev_join, c->stream2));
+        CK(cudaStreamWaitEvent(st, c->ev_join, 0));
+    }
+    CK(rec(static_cast<int>(2 + EV_PER_WAVE * W)));
     CK(launch_compact(b->d_desc.p, b->out.p, n, b->ops.p, b->cig.p, counters + cig_total_index(b), st));
     launches += 2;
-    CK(rec(static_cast<int>(2 + EV_PER_WAVE * W)));
+    CK(rec(static_cast<int>(3 + EV_PER_WAVE * W)));
     b->n_launches = launches;
     b->n_dp_launches = dp_launches;
     return MP_OK;
-}
-
-static mp_dp_tuning default_tuning()
-{
-    mp_dp_tuning t{};
-    return t;     // int16 kernel for 3 CTAs/SM, all CTAs that fit, int16 first for wide pairs
-}
-
-static mp_dp_tuning tuning_for(const mp_dp_ctx *c, const mp_dp_batch *b)
-{
-    if (c->has_fixed) return c->fixed;
-    auto it = c->tuned.find(b->shape_key);
-    return it != c->tuned.end() ? it->second : default_tuning();
 }
 
 static uint64_t tuning_sig(const mp_dp_tuning &t, bool timed)
 {
     return (static_cast<uint64_t>(t.dp16_variant & 0xff)) | (static_cast<uint64_t>(t.dp16_ctas_per_sm & 0xff) << 8) |
            (static_cast<uint64_t>(t.dp32_ctas_per_sm & 0xff) << 16) | (static_cast<uint64_t>(t.wide_direct & 1) << 24) |
-           (static_cast<uint64_t>(timed) << 25) | (1ull << 26);
+           (static_cast<uint64_t>(timed) << 25) | (static_cast<uint64_t>(t.overlap_waves & 1) << 26) | (1ull << 27);
 }
 
 static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp_tuning *tried, int max_tried,
@@ -791,7 +880,11 @@ int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
         if (rc != MP_OK) return rc;
     }
     const mp_dp_tuning t = tuning_for(c, b);
-    const size_t nev = 3 + EV_PER_WAVE * b->waves.size();
+    if (b->needs_waves && b->planned != (t.overlap_waves ? 1 : 0)) {
+        const int rc = plan_waves(c, b, t.overlap_waves != 0);
+        if (rc != MP_OK) return rc;
+    }
+    const size_t nev = 4 + EV_PER_WAVE * b->waves.size();
     if (timed && b->events.size() < nev) {
         for (size_t k = b->events.size(); k < nev; ++k) {
             cudaEvent_t e;
@@ -833,39 +926,51 @@ int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
 }
 
 // ------------------------------------------------------------ autotuner
-// Candidates: both int16 builds at all CTAs per SM that fit and one fewer,
-// and, when the batch has pairs that may need int32, both policies for them.
+// Candidates: both int16 builds at all CTAs per SM that fit and one fewer;
+// when the batch has pairs that may need int32, both policies for them; when
+// it needs several waves, both wave policies (the plan changes with it, so
+// candidates are grouped by wave policy).
 static std::vector<mp_dp_tuning> candidates(mp_dp_ctx *c, const mp_dp_batch *b)
 {
     bool any_wide = false;
-    for (const Wave &w : b->waves) any_wide |= w.nwide_items > 0;
+    for (const PairDesc &d : b->desc) any_wide |= (d.flags & PF_WIDE) && !(d.flags & (PF_SKIP | PF_SCORE_ONLY));
     std::vector<mp_dp_tuning> v;
     const int fit32 = dp32_blocks_per_sm();
-    if (c->params.force_int32) {
-        for (int k = fit32; k >= std::max(1, fit32 - 1); --k) {
-            mp_dp_tuning t = default_tuning();
-            t.dp32_ctas_per_sm = k;
-            v.push_back(t);
-        }
-        return v;
-    }
-    for (int var = 0; var < kDp16Variants; ++var) {
-        const int fit = dp16_blocks_per_sm(var);
-        for (int k = fit; k >= std::max(1, fit - 1); --k)
-            for (int wd = 0; wd <= (any_wide ? 1 : 0); ++wd) {
+    const int n_ov = b->needs_waves ? 2 : 1;
+    for (int ov = 0; ov < n_ov; ++ov) {
+        const int overlap = b->needs_waves ? 1 - ov : 1;
+        if (c->params.force_int32) {
+            for (int k = fit32; k >= std::max(1, fit32 - 1); --k) {
                 mp_dp_tuning t = default_tuning();
-                t.dp16_variant = var;
-                t.dp16_ctas_per_sm = k;
-                t.dp32_ctas_per_sm = fit32;
-                t.wide_direct = wd;
+                t.dp32_ctas_per_sm = k;
+                t.overlap_waves = overlap;
                 v.push_back(t);
             }
+            continue;
+        }
+        for (int var = 0; var < kDp16Variants; ++var) {
+            const int fit = dp16_blocks_per_sm(var);
+            for (int k = fit; k >= std::max(1, fit - 1); --k)
+                for (int wd = 0; wd <= (any_wide ? 1 : 0); ++wd) {
+                    mp_dp_tuning t = default_tuning();
+                    t.dp16_variant = var;
+                    t.dp16_ctas_per_sm = k;
+                    t.dp32_ctas_per_sm = fit32;
+                    t.wide_direct = wd;
+                    t.overlap_waves = overlap;
+                    v.push_back(t);
+                }
+        }
     }
     return v;
 }
 
 static int time_run(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, cudaEvent_t e0, cudaEvent_t e1, float *ms)
 {
+    if (b->needs_waves && b->planned != (t.overlap_waves ? 1 : 0)) {
+        const int rc = plan_waves(c, b, t.overlap_waves != 0);      // outside the timed interval
+        if (rc != MP_OK) return rc;
+    }
     cudaStream_t st = c->stream;
     CK(cudaEventRecord(e0, st));
     const int rc = enqueue_pipeline(c, b, st, false, false, t);
@@ -912,6 +1017,14 @@ static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp
     for (size_t k = 1; k < cand.size(); ++k)
         if (cand[k].ms < cand[bi].ms) bi = k;
     c->tuned[b->shape_key] = cand[bi];
+    if (b->needs_waves && b->planned != (cand[bi].overlap_waves ? 1 : 0)) {
+        // re-plan for the choice and run once more, so that the batch's
+        // results (whose counters sit where the plan puts them) match its plan
+        int rc = plan_waves(c, b, cand[bi].overlap_waves != 0);
+        if (rc == MP_OK) rc = enqueue_pipeline(c, b, c->stream, false, false, cand[bi]);
+        if (rc != MP_OK) return rc;
+        CK(cudaStreamSynchronize(c->stream));
+    }
     c->last = b;
     if (best) *best = cand[bi];
     if (tried)
@@ -944,7 +1057,8 @@ int mp_dp_set_tuning(mp_dp_ctx *c, const mp_dp_tuning *t)
         return MP_OK;
     }
     if (t->dp16_variant < 0 || t->dp16_variant >= kDp16Variants || t->dp16_ctas_per_sm < 0 ||
-        t->dp32_ctas_per_sm < 0 || t->wide_direct < 0 || t->wide_direct > 1)
+        t->dp32_ctas_per_sm < 0 || t->wide_direct < 0 || t->wide_direct > 1 || t->overlap_waves < 0 ||
+        t->overlap_waves > 1)
         return MP_EINVAL;
     c->fixed = *t;
     c->has_fixed = true;
@@ -963,11 +1077,12 @@ int mp_dp_tuning_save(mp_dp_ctx *c, const char *path)
     if (!c || !path) return MP_EINVAL;
     FILE *f = fopen(path, "w");
     if (!f) return MP_EINVAL;
-    bool ok = fprintf(f, "mp_dp_tuning 1 %s %d\n", c->dev_name.c_str(), c->num_sms) > 0;
+    bool ok = fprintf(f, "mp_dp_tuning 2 %s %d\n", c->dev_name.c_str(), c->num_sms) > 0;
     for (const auto &kv : c->tuned) {
         const mp_dp_tuning &t = kv.second;
-        ok = ok && fprintf(f, "%016llx %d %d %d %d %.4f\n", static_cast<unsigned long long>(kv.first), t.dp16_variant,
-                           t.dp16_ctas_per_sm, t.dp32_ctas_per_sm, t.wide_direct, static_cast<double>(t.ms)) > 0;
+        ok = ok && fprintf(f, "%016llx %d %d %d %d %d %.4f\n", static_cast<unsigned long long>(kv.first),
+                           t.dp16_variant, t.dp16_ctas_per_sm, t.dp32_ctas_per_sm, t.wide_direct, t.overlap_waves,
+                           static_cast<double>(t.ms)) > 0;
     }
     ok = (fclose(f) == 0) && ok;
     return ok ? MP_OK : MP_EINVAL;
@@ -981,7 +1096,7 @@ int mp_dp_tuning_load(mp_dp_ctx *c, const char *path)
     if (!f) return MP_EINVAL;
     char name[256] = {0};
     int version = 0, sms = 0;
-    if (fscanf(f, "mp_dp_tuning %d %255s %d", &version, name, &sms) != 3 || version != 1 ||
+    if (fscanf(f, "mp_dp_tuning %d %255s %d", &version, name, &sms) != 3 || version != 2 ||
         c->dev_name != name || sms != c->num_sms) {
         fclose(f);
         return MP_EINVAL;
@@ -991,11 +1106,12 @@ int mp_dp_tuning_load(mp_dp_ctx *c, const char *path)
         unsigned long long key = 0;
         mp_dp_tuning t{};
         double ms = 0;
-        const int k = fscanf(f, "%llx %d %d %d %d %lf", &key, &t.dp16_variant, &t.dp16_ctas_per_sm,
-                             &t.dp32_ctas_per_sm, &t.wide_direct, &ms);
+        const int k = fscanf(f, "%llx %d %d %d %d %d %lf", &key, &t.dp16_variant, &t.dp16_ctas_per_sm,
+                             &t.dp32_ctas_per_sm, &t.wide_direct, &t.overlap_waves, &ms);
         if (k == EOF) break;
-        if (k != 6 || t.dp16_variant < 0 || t.dp16_variant >= kDp16Variants || t.dp16_ctas_per_sm < 0 ||
-            t.dp32_ctas_per_sm < 0 || t.wide_direct < 0 || t.wide_direct > 1) {
+        if (k != 7 || t.dp16_variant < 0 || t.dp16_variant >= kDp16Variants || t.dp16_ctas_per_sm < 0 ||
+            t.dp32_ctas_per_sm < 0 || t.wide_direct < 0 || t.wide_direct > 1 || t.overlap_waves < 0 ||
+            t.overlap_waves > 1) {
             fclose(f);
             return MP_EINVAL;
         }
@@ -1020,17 +1136,17 @@ static int collect_stats(mp_dp_ctx *c, mp_dp_batch *b)
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, b->events[0], b->events[1]));
         s.pack_ms = ms;
-        cudaEvent_t prev = b->events[1];
+        // per wave on its own stream (overlapped waves: the sums exceed the wall time)
         for (size_t w = 0; w < b->waves.size(); ++w) {
             const size_t base = 2 + EV_PER_WAVE * w;
-            CK(cudaEventElapsedTime(&ms, prev, b->events[base])); s.dp_ms += ms;
-            CK(cudaEventElapsedTime(&ms, b->events[base], b->events[base + 1])); s.rerun_ms += ms;
-            CK(cudaEventElapsedTime(&ms, b->events[base + 1], b->events[base + 2])); s.tb_ms += ms;
-            prev = b->events[base + 2];
+            CK(cudaEventElapsedTime(&ms, b->events[base], b->events[base + 1])); s.dp_ms += ms;
+            CK(cudaEventElapsedTime(&ms, b->events[base + 1], b->events[base + 2])); s.rerun_ms += ms;
+            CK(cudaEventElapsedTime(&ms, b->events[base + 2], b->events[base + 3])); s.tb_ms += ms;
         }
-        CK(cudaEventElapsedTime(&ms, prev, b->events[2 + EV_PER_WAVE * b->waves.size()]));
+        const size_t end = 2 + EV_PER_WAVE * b->waves.size();
+        CK(cudaEventElapsedTime(&ms, b->events[end], b->events[end + 1]));
         s.tb_ms += ms;
-        CK(cudaEventElapsedTime(&ms, b->events[0], b->events[2 + EV_PER_WAVE * b->waves.size()]));
+        CK(cudaEventElapsedTime(&ms, b->events[0], b->events[end + 1]));
         s.total_ms = ms;
     }
     return MP_OK;
@@ -1375,6 +1491,10 @@ extern "C" void mp_dp_destroy(mp_dp_ctx *c)
     c->own = nullptr;
     c->codes.release();
     c->staging.release();
+    if (c->stream2) cudaStreamSynchronize(c->stream2);
     if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->stream2) cudaStreamDestroy(c->stream2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }

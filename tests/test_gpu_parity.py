@@ -290,6 +290,39 @@ def test_small_budget_waves(mp, ctx, orc):
         mp.mp_dp_destroy(c)
 
 
+def test_overlapped_waves(mp, ctx):
+    """A batch needing several waves, with every pair under half the budget:
+    with overlapped waves (the default) they alternate between two streams
+    over two arena halves; without, they run one after the other at the
+    whole budget.  Either way, and switching between the two on one batch
+    (which re-plans it), the results equal the one-wave run, direct and
+    replayed as a graph, with timing on."""
+    pairs = _gene_pairs(63, 60, 300, 900)
+    need = [_code_bytes(len(p.prot), len(p.nt)) for p in pairs]
+    budget = max(3 * max(need), sum(need) // 3)
+    ref = mp.mp_dp_align_batch(ctx, pairs)
+    want = [{k: r[k] for k in KEYS} for r in ref]
+    c = mp.mp_dp_init(mp.mp_dp_default_params(tb_budget_bytes=budget), 0)
+    try:
+        mp.mp_dp_set_timing(c, True)
+        b = mp.mp_dp_batch_upload(c, pairs)
+        waves = {}
+        for ov in (1, 0, 1):
+            mp.mp_dp_set_tuning(c, dict(overlap_waves=ov))
+            for _ in range(3):
+                mp.mp_dp_batch_run(c, b)
+                mp.mp_dp_batch_sync(c)
+                got = mp.mp_dp_batch_download(c, b)
+                assert [{k: g[k] for k in KEYS} for g in got] == want
+                st = mp.mp_dp_get_stats(c)
+                assert st["total_ms"] > 0 and st["dp_ms"] > 0
+                waves[ov] = st["n_waves"]
+        assert waves[1] >= 4 and 2 <= waves[0] < waves[1]
+        mp.mp_dp_batch_free(c, b)
+    finally:
+        mp.mp_dp_destroy(c)
+
+
 def test_serving_alone_and_in_mix(mp, ctx):
     """Each request's result is the same served alone, in a burst with
     others in flight, and from the batch call."""

@@ -93,7 +93,8 @@ def test_autotune_picks_a_timed_candidate_and_keeps_results(mp, mixed, tmp_path)
         best, tried = mp.mp_dp_autotune(ctx, b)
         assert len(tried) >= 4 and all(t["ms"] > 0 for t in tried)
         assert best["ms"] == min(t["ms"] for t in tried)
-        strip = lambda t: {k: t[k] for k in ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct")}
+        strip = lambda t: {k: t[k] for k in ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct",
+                                             "overlap_waves")}
         assert strip(best) in [strip(t) for t in tried]
         assert {t["wide_direct"] for t in tried} == {0, 1}         # the batch has wide pairs
         # the batch holds the results of the tuning runs
@@ -140,7 +141,7 @@ def test_tuning_arguments_checked(mp, tmp_path):
     L = mp.lib()
     try:
         for bad in (dict(dp16_variant=2), dict(dp16_variant=-1), dict(wide_direct=2), dict(dp16_ctas_per_sm=-1),
-                    dict(dp32_ctas_per_sm=-3)):
+                    dict(dp32_ctas_per_sm=-3), dict(overlap_waves=2)):
             with pytest.raises(mp.MPError):
                 mp.mp_dp_set_tuning(ctx, bad)
         mp.mp_dp_set_tuning(ctx, dict(dp16_ctas_per_sm=99))       # clamped at launch
@@ -149,7 +150,7 @@ def test_tuning_arguments_checked(mp, tmp_path):
         assert all(g["status"] & 0xF0 == 0 for g in got)
         mp.mp_dp_set_tuning(ctx, None)
         bad_file = tmp_path / "other.txt"
-        bad_file.write_text("mp_dp_tuning 1 Some_Other_GPU 7\n0000000000000001 0 3 2 0 1.0\n")
+        bad_file.write_text("mp_dp_tuning 2 Some_Other_GPU 7\n0000000000000001 0 3 2 0 1 1.0\n")
         assert L.mp_dp_tuning_load(ctx, str(bad_file).encode()) == mp.MP_EINVAL
         assert L.mp_dp_tuning_load(ctx, str(tmp_path / "missing.txt").encode()) == mp.MP_EINVAL
     finally:
