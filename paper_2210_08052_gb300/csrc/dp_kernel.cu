@@ -505,32 +505,6 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// queue strip s+1 of pair p (its first boundary rows are published)
-__device__ __forceinline__ void push_successor(const DPArgs &a, uint32_t p, int s)
-{
-    const uint32_t slot = atomicAdd(&a.head[2], 1u);
-    st_relaxed64(&a.ready[slot], (static_cast<unsigned long long>(s + 2) << 32) | p);
-}
-
 template <typename T>
 __device__ __forceinline__ T ld_l2(const T *p);
 template <>
@@ -657,9 +631,6 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
             __syncwarp();
             if (lane == 0) st_release(mine, static_cast<uint32_t>(ch + 1));
         }
-        // strip s+1 starts once kLag chunks are out: queue it now
-        if (lane == 0 && a.ready && !rerun && s + 1 < nstrips && ch + 1 == (nchunks < kLag ? nchunks : kLag))
-            push_successor(a, p, s);
         if (store) colmax[static_cast<size_t>(ch) * 32 + lane] = Ops::chunk_max(st);
         if (Ops::kChunkMaxBest && store) {
             // remember the first chunk holding each cell's maximum
@@ -753,57 +724,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinB) dp_kernel(const DPArg
     using SM = WarpSmem<typename Ops::Bnd>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     SM &sm = reinterpret_cast<SM *>(smem_raw)[warp];
-    if (rerun_only) {
-        const uint32_t count = *a.rerun_count;
-        for (;;) {
-            uint32_t idx = 0;
-            if (lane == 0) idx = atomicAdd(a.head, 1u);
-            idx = __shfl_sync(kFull, idx, 0);
-            if (idx >= count) break;
-            const uint2 it = a.rerun_items[idx];
-            run_strip<Ops>(a, sm, it.x, static_cast<int>(it.y), lane, true);
-        }
-        return;
-    }
-    const uint32_t spin_limit = a.spin_limit ? a.spin_limit : kSpinLimit;
+    // a fixed list (the wave's interleaved strip items, or the re-run list):
+    // a strip's warp waits, bounded, for its predecessor's rows
+    const uint2 *list = rerun_only ? a.rerun_items : a.items;
+    const uint32_t count = rerun_only ? *a.rerun_count : a.n_items;
     for (;;) {
-        // lane 0 takes a queued successor strip first, else the next strip-0
-        // item; with neither, it waits while strips are still to be queued
-        uint2 it = make_uint2(0, 0);
-        uint32_t got = 0;
-        if (lane == 0) {
-            uint32_t nap = 128;                          // idle polling backs off to 2 us
-            for (uint32_t spins = 0;;) {
-                const uint32_t h = ld_relaxed(&a.head[1]);
-                if (h < ld_relaxed(&a.head[2])) {
-                    if (atomicCAS(&a.head[1], h, h + 1) != h) continue;
-                    // the slot was claimed by its producer before the tail moved
-                    unsigned long long v = 0;
-                    for (uint32_t k = 0; (v = ld_relaxed64(&a.ready[h])) == 0 && k < spin_limit; ++k) __nanosleep(32);
-                    if (v == 0) break;                       // cannot happen; give up the warp
-                    it = make_uint2(static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32) - 1u);
-                    got = 1;
-                    break;
-                }
-                if (ld_relaxed(&a.head[0]) < a.n_items) {
-                    const uint32_t idx = atomicAdd(&a.head[0], 1u);
-                    if (idx < a.n_items) {
-                        it = a.items[idx];
-                        got = 1;
-                        break;
-                    }
-                }
-                if (ld_relaxed(&a.head[3]) >= a.n_total || ++spins > spin_limit) break;
-                __nanosleep(nap);
-                nap = nap < 2048 ? 2 * nap : 2048;
-            }
-            if (got) atomicAdd(&a.head[3], 1u);
-        }
-        got = __shfl_sync(kFull, got, 0);
-        if (!got) break;
-        it.x = __shfl_sync(kFull, it.x, 0);
-        it.y = __shfl_sync(kFull, it.y, 0);
-        run_strip<Ops>(a, sm, it.x, static_cast<int>(it.y), lane, false);
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(a.head, 1u);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= count) break;
+        const uint2 it = list[idx];
+        run_strip<Ops>(a, sm, it.x, static_cast<int>(it.y), lane, rerun_only != 0);
     }
 }
 

@@ -80,18 +80,9 @@ struct ScoreParams {
 struct DPArgs {
     const PairDesc *pairs;
     const uint4 *recs;      // per-nt records (see make_record)
-    // Main pass: items lists the strip-0 items (pair, 0) of the launch in
-    // processing order; strip s+1 of a pair is queued in `ready` by strip s
-    // once the boundary rows it needs first are published, so a warp never
-    // takes a strip that would have to wait for its start.  head[0]: next
-    // strip-0 item, head[1] / head[2]: ready-queue head / tail, head[3]:
-    // items taken; n_total: every strip item of the launch.  Re-run pass:
-    // head[0] indexes rerun_items.
-    const uint2 *items;
+    const uint2 *items;     // processing order (strip s+1 of a pair some items after strip s)
     uint32_t n_items;
-    uint32_t n_total;
-    uint32_t *head;
-    unsigned long long *ready;   // (s + 1) << 32 | pair per slot, 0 until written; null: no successors queued
+    uint32_t *head;         // work-queue counter
     const uint8_t *prot;    // residue codes
     const uint32_t *nt2;    // packed genome (base k at bits 2(k%16) of word k/16)
     uint8_t *codes;         // traceback code arena

@@ -188,16 +188,14 @@ struct mp_dp_batch {
     DevBuf<uint32_t> nt2;
     DevBuf<PairOut> out;
     DevBuf<uint32_t> ops, cig, work;
-    DevBuf<uint2> items, items0, rerun_items;   // all strip items; strip-0 items; re-run list
+    DevBuf<uint2> items, rerun_items;   // strip items in processing order; re-run list
     DevBuf<uint4> recs;                 // per-nt records of every pair
     DevBuf<uint64_t> bnd;
-    // per-run state, zeroed by one memset: counters | strips_done | progress |
-    // best_key | successor slots
+    // per-run state, zeroed by one memset: counters | strips_done | progress | best_key
     DevBuf<unsigned long long> state;
-    size_t state_bytes = 0, off_done = 0, off_progress = 0, off_key = 0, off_ready = 0;
-    std::vector<uint2> h_items, h_items0;
+    size_t state_bytes = 0, off_done = 0, off_progress = 0, off_key = 0;
+    std::vector<uint2> h_items;
     std::vector<uint32_t> item_off;     // first item of each pair in the order (by order index)
-    std::vector<uint32_t> item0_off;    // first strip-0 item of each pair in the order
     DevBuf<uint32_t> wave_nwide;        // Wave::nwide_items of each wave, on the device
     uint64_t shape_key = 0;             // shape class for the tuned table
     bool overlap = false;               // waves alternate between two streams and two arena halves
@@ -386,7 +384,7 @@ static void free_batch_device(mp_dp_batch *b)
     b->events.clear();
     b->ascii.release(); b->d_desc.release(); b->prot.release(); b->nt2.release(); b->out.release();
     b->ops.release(); b->cig.release(); b->work.release(); b->items.release(); b->rerun_items.release();
-    b->bnd.release(); b->state.release(); b->recs.release(); b->wave_nwide.release(); b->items0.release();
+    b->bnd.release(); b->state.release(); b->recs.release(); b->wave_nwide.release();
 }
 
 void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
@@ -453,6 +451,42 @@ static uint64_t plan_code_bytes(const mp_dp_ctx *c, const mp_dp_batch *b)
         if (cb <= c->budget) total += cb;
     }
     return total;
+}
+
+// Order each wave's strip items so that a warp rarely takes a strip whose
+// predecessor has not yet published the boundary rows it starts with: the
+// first items are the strip-0 items (largest pairs first), and strip s+1 of
+// a pair follows strip s by about as many items as the warps pop while the
+// predecessor runs kLag = 2 chunks.  PF_WIDE pairs' items stay a prefix of
+// the wave (the int32 queue may take them as a block).
+static void interleave_items(const mp_dp_ctx *c, mp_dp_batch *b)
+{
+    const double warps = static_cast<double>(c->num_sms) * 2 * kWarpsPerCta;
+    std::vector<std::pair<double, uint2>> keyed;
+    auto segment = [&](uint32_t lo, uint32_t hi) {
+        if (hi - lo < 2) return;
+        double chunks = 0;
+        for (uint32_t k = lo; k < hi; ++k)
+            chunks += static_cast<double>((b->desc[b->h_items[k].x].nt_len + kStripW - 1 + kChunk - 1) / kChunk);
+        const double D = std::max(1.0, 2.0 * warps / (chunks / (hi - lo)));
+        keyed.clear();
+        uint32_t rank = 0;
+        for (uint32_t k = lo; k < hi; ++k) {
+            const uint2 it = b->h_items[k];
+            if (k > lo && it.x != b->h_items[k - 1].x) ++rank;
+            const double key = it.y == 0 ? rank : rank + it.y * D + warps;
+            keyed.emplace_back(key, it);
+        }
+        std::stable_sort(keyed.begin(), keyed.end(),
+                         [](const std::pair<double, uint2> &x, const std::pair<double, uint2> &y) {
+                             return x.first < y.first;
+                         });
+        for (uint32_t k = lo; k < hi; ++k) b->h_items[k] = keyed[k - lo].second;
+    };
+    for (const Wave &w : b->waves) {
+        segment(w.ibegin, w.ibegin + w.nwide_items);
+        segment(w.ibegin + w.nwide_items, w.iend);
+    }
 }
 
 // Plan the batch's pair order, waves, strip items and per-run state for the
@@ -533,9 +567,7 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, bool overlap)
     uint32_t wbeg = 0, ibeg = 0, wcur = 0, nwide = 0;
     b->h_items.clear();
     b->h_items.reserve(strips);
-    b->h_items0.clear();
     b->item_off.assign(n + 1, 0);
-    b->item0_off.assign(n + 1, 0);
     for (uint32_t k = 0; k < n; ++k) {
         const uint32_t p = b->order[k];
         PairDesc &d = b->desc[p];
@@ -549,9 +581,7 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, bool overlap)
             wcur = wave_of[p];
         }
         b->item_off[k] = static_cast<uint32_t>(b->h_items.size());
-        b->item0_off[k] = static_cast<uint32_t>(b->h_items0.size());
         if (d.flags & PF_SKIP) continue;
-        b->h_items0.push_back(make_uint2(p, 0));
         d.code_off = cur;
         cur += cbytes[p];
         if (cbytes[p]) b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
@@ -559,21 +589,20 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, bool overlap)
         if (wide(p) == 0) nwide += d.n_strips;
     }
     b->item_off[n] = static_cast<uint32_t>(b->h_items.size());
-    b->item0_off[n] = static_cast<uint32_t>(b->h_items0.size());
     b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
+    if (c->params.max_pairs_per_launch == 0) interleave_items(c, b);
     maxw = std::max(maxw, cur);
     if (b->waves.size() < 2) b->overlap = false;
     b->arena_half = std::max<uint64_t>(div_up(maxw, 256) * 256, 256);
     // per-run state block
-    // counters: 8 per wave (main-pass queue block of 4, re-run head and
-    // count), the compaction total, and a queue block of 4 per pair for the
+    // counters: 8 per wave ([0] main-pass head, [4] re-run head, [5] re-run
+    // count), the compaction total, and a head per pair group for the
     // one-launch-per-group form
     const size_t ncnt = 8 * b->waves.size() + 8 + 4 * n;
     b->off_done = div_up(ncnt * 4, 8) * 8;
     b->off_progress = b->off_done + div_up(n * 4, 8) * 8;
     b->off_key = b->off_progress + div_up(strips * 4, 8) * 8;
-    b->off_ready = b->off_key + n * 8 + 8;
-    b->state_bytes = b->off_ready + strips * 8 + 8;
+    b->state_bytes = b->off_key + n * 8 + 8;
 
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -589,8 +618,6 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, bool overlap)
     CK(cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(b->items.p, b->h_items.data(), b->h_items.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(b->items0.p, b->h_items0.data(), b->h_items0.size() * sizeof(uint2), cudaMemcpyHostToDevice,
-                       st));
     std::vector<uint32_t> nw(b->waves.size());
     for (size_t w = 0; w < nw.size(); ++w) nw[w] = b->waves[w].nwide_items;
     CK(cudaMemcpyAsync(b->wave_nwide.p, nw.data(), nw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
@@ -666,7 +693,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         (e = b->prot.reserve(pro + 16)) != cudaSuccess || (e = b->nt2.reserve(ntw + 32)) != cudaSuccess ||
         (e = b->out.reserve(n + 1)) != cudaSuccess || (e = b->ops.reserve(ops + 1)) != cudaSuccess ||
         (e = b->cig.reserve(ops + 1)) != cudaSuccess || (e = b->work.reserve(n + 1)) != cudaSuccess ||
-        (e = b->items.reserve(strips + 1)) != cudaSuccess || (e = b->items0.reserve(n + 1)) != cudaSuccess ||
+        (e = b->items.reserve(strips + 1)) != cudaSuccess ||
         (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
         (e = b->recs.reserve(nrec + 1)) != cudaSuccess) {
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
@@ -769,7 +796,6 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         a.strips_done = reinterpret_cast<uint32_t *>(state + b->off_done);
         a.rerun_items = b->rerun_items.p + wv.ibegin;
         a.rerun_count = counters + 8 * w + 5;
-        unsigned long long *ready = reinterpret_cast<unsigned long long *>(state + b->off_ready);
         a.sp = c->sp;
         a.spin_limit = c->params.wait_limit > 0 ? static_cast<uint32_t>(c->params.wait_limit) : 0u;
         a.no_publish = (c->params.debug_flags & MP_DEBUG_NO_PUBLISH) ? 1u : 0u;
@@ -779,13 +805,11 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
             for (uint32_t k = wv.begin; k < wv.end; k += per_launch) {
                 const uint32_t k2 = std::min<uint32_t>(wv.end, k + per_launch);
                 DPArgs a1 = a;
-                a1.items = b->items0.p + b->item0_off[k];
-                a1.n_items = b->item0_off[k2] - b->item0_off[k];
-                a1.n_total = b->item_off[k2] - b->item_off[k];
-                if (!a1.n_total) continue;
+                a1.items = b->items.p + b->item_off[k];
+                a1.n_items = b->item_off[k2] - b->item_off[k];
+                if (!a1.n_items) continue;
                 a1.head = counters + 8 * W + 8 + 4 * k;
-                a1.ready = ready + b->item_off[k];
-                const int grid = std::max(1, std::min<int>(c->num_sms, static_cast<int>((a1.n_total + kWarpsPerCta - 1) / kWarpsPerCta)));
+                const int grid = std::max(1, std::min<int>(c->num_sms, static_cast<int>((a1.n_items + kWarpsPerCta - 1) / kWarpsPerCta)));
                 if (c->params.force_int32) CK(launch_dp32(a1, grid, false, st));
                 else CK(launch_dp16(a1, grid, variant, st));
                 ++launches;
@@ -800,16 +824,12 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
                                    cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(a.rerun_count, b->wave_nwide.p + w, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
             }
-            // strip-0 items of the pairs the main pass runs (the wide prefix,
-            // if handed to the int32 queue, is skipped)
-            uint32_t k0 = wv.begin;
-            while (skip && k0 < wv.end && b->item_off[k0] < wv.ibegin + skip) ++k0;
-            a.items = b->items0.p + b->item0_off[k0];
-            a.n_items = b->item0_off[wv.end] - b->item0_off[k0];
-            a.n_total = nitems - skip;
+            // the wave's interleaved strip items (the wide prefix, if handed
+            // to the int32 queue, is skipped)
+            a.items = b->items.p + wv.ibegin + skip;
+            a.n_items = nitems - skip;
             a.head = counters + 8 * w;
-            a.ready = ready + wv.ibegin;
-            const int want = static_cast<int>((a.n_total + kWarpsPerCta - 1) / kWarpsPerCta);
+            const int want = static_cast<int>((a.n_items + kWarpsPerCta - 1) / kWarpsPerCta);
             const int grid16 = std::max(1, std::min<int>(g16, want));
             const int grid32 = std::max(1, std::min<int>(g32, want));
             if (c->params.force_int32) CK(launch_dp32(a, grid32, false, st));
@@ -823,8 +843,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         if (!c->params.force_int32 && wv.nwide_items > 0) {
             a.head = counters + 8 * w + 4;
             a.items = nullptr;
-            a.n_items = a.n_total = 0;
-            a.ready = nullptr;
+            a.n_items = 0;
             CK(launch_dp32(a, g32, true, st));
             ++launches;
             ++dp_launches;
