@@ -285,7 +285,7 @@ def main():
     ap.add_argument("--pairs", type=int, default=4096, help="first N pairs of the workload (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: skip the end-to-end leg")
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration, no tuning runs")
-    ap.add_argument("--tuning", default="", help="fixed launch configuration 'variant,ctas16,ctas32,wide_direct[,overlap_waves]'")
+    ap.add_argument("--tuning", default="", help="fixed launch configuration 'variant,ctas16,ctas32,wide_direct[,overlap_waves[,item_order]]'")
     ap.add_argument("--c5-scale", type=float, default=1.0, help="shrink the genome-scale workload (tests)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
                     help="c2: the 4,096-pair batch (default); c3: the 20,000-pair uneven-size stress batch; "
@@ -348,9 +348,9 @@ def main():
     tuning = None
     if args.tuning:
         # a fixed launch configuration: int16 build, CTAs/SM (int16, int32), wide pairs direct
-        v, c16, c32, wd, ov = (int(x) for x in (args.tuning + ",1").split(",")[:5])
+        v, c16, c32, wd, ov, io = (int(x) for x in (args.tuning + ",1,1").split(",")[:6])
         fixed = {"dp16_variant": v, "dp16_ctas_per_sm": c16, "dp32_ctas_per_sm": c32, "wide_direct": wd,
-                 "overlap_waves": ov}
+                 "overlap_waves": ov, "item_order": io}
         mp.mp_dp_set_tuning(ctx, fixed)
         tuning = {"fixed": fixed}
     elif not args.no_autotune:

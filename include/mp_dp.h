@@ -271,20 +271,25 @@ typedef struct {
                                   half the budget that run alternately on two streams over two
                                   halves of the arena (one wave's tail overlaps the next wave);
                                   0: waves of the whole budget, one after the other */
+    int32_t item_order;        /* 1: a wave's strip items interleaved so that strip s+1 of a pair is
+                                  taken about two chunks after strip s; 0: pairs' strips back to
+                                  back (a strip's warp first waits for its predecessor) */
     float ms;                  /* set by mp_dp_autotune: device time of one run of the batch */
-    int32_t reserved[2];
+    int32_t reserved[1];
 } mp_dp_tuning;
 
-/* Time the candidate configurations on an uploaded batch (one warm-up run,
- * one timed run per candidate, a second timed run of the two fastest; CUDA
- * events on the context's stream; every run computes the batch's full
- * results, so the batch holds valid results afterwards) and record the
+/* Time the candidate configurations on an uploaded batch (warm-up runs;
+ * one timed run per kernel configuration under the default plan, then one
+ * per plan option under the fastest of those; a second timed run of the two
+ * fastest overall; CUDA events on the context's stream; every run computes
+ * the batch's full results, so the batch holds valid results afterwards)
+ * and record the
  * fastest for the batch's shape class (pair count, mean cells per pair and
  * longest critical path on log2 scales, whether any pair needs int32,
  * whether the batch needs several waves).  Later runs of batches in that
  * class use it unless mp_dp_set_tuning fixed a configuration.  A candidate
- * with the other wave policy re-plans the batch's waves first (host work
- * and small copies outside the timed interval).  best (may be NULL) receives the
+ * with another plan (wave policy, item order) re-plans the batch first (host
+ * work and small copies outside the timed interval).  best (may be NULL) receives the
  * choice; tried (may be NULL) up to max_tried candidates with their times,
  * and n_tried (may be NULL) how many were timed.  MP_EINVAL in the plain
  * form (max_pairs_per_launch > 0); MP_ESTATE while the serving loop runs. */

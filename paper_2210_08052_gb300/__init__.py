@@ -65,10 +65,12 @@ class mp_dp_stats(ctypes.Structure):
 class mp_dp_tuning(ctypes.Structure):
     _fields_ = [("dp16_variant", ctypes.c_int32), ("dp16_ctas_per_sm", ctypes.c_int32),
                 ("dp32_ctas_per_sm", ctypes.c_int32), ("wide_direct", ctypes.c_int32),
-                ("overlap_waves", ctypes.c_int32), ("ms", ctypes.c_float), ("reserved", ctypes.c_int32 * 2)]
+                ("overlap_waves", ctypes.c_int32), ("item_order", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
-TUNING_KEYS = ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct", "overlap_waves", "ms")
+TUNING_KEYS = ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct", "overlap_waves", "item_order",
+               "ms")
 
 
 class mp_dp_serve_stats(ctypes.Structure):

@@ -201,7 +201,7 @@ struct mp_dp_batch {
     bool overlap = false;               // waves alternate between two streams and two arena halves
     uint64_t arena_half = 0;            // bytes of one arena half (overlap only)
     bool needs_waves = false;           // the traceback bytes exceed the budget
-    int planned = -1;                   // wave policy of the current plan (0 / 1), -1 before planning
+    int planned = -1;                   // plan_key() the current plan was made for, -1 before planning
     uint64_t strips_total = 0;
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_sig = 0;             // timing flag and configuration the graph was captured with
@@ -430,6 +430,7 @@ static mp_dp_tuning default_tuning()
 {
     mp_dp_tuning t{};
     t.overlap_waves = 1;
+    t.item_order = 1;
     return t;     // int16 kernel for 3 CTAs/SM, all CTAs that fit, int16 first for wide pairs, overlapped waves
 }
 
@@ -438,6 +439,21 @@ static mp_dp_tuning tuning_for(const mp_dp_ctx *c, const mp_dp_batch *b)
     if (c->has_fixed) return c->fixed;
     auto it = c->tuned.find(b->shape_key);
     return it != c->tuned.end() ? it->second : default_tuning();
+}
+
+// What a plan depends on in a configuration: the wave policy (only for a
+// batch that needs several waves) and the item order.
+static int plan_key(const mp_dp_batch *b, const mp_dp_tuning &t)
+{
+    return (b->needs_waves && t.overlap_waves ? 1 : 0) | (t.item_order ? 2 : 0);
+}
+
+static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t);
+
+// Re-plan the batch if its plan was made for another configuration.
+static int ensure_plan(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t)
+{
+    return b->planned == plan_key(b, t) ? MP_OK : plan_waves(c, b, t);
 }
 
 // Traceback bytes of the batch's pairs that keep a stream (pairs larger than
@@ -454,11 +470,12 @@ static uint64_t plan_code_bytes(const mp_dp_ctx *c, const mp_dp_batch *b)
 }
 
 // Order each wave's strip items so that a warp rarely takes a strip whose
-// predecessor has not yet published the boundary rows it starts with: the
-// first items are the strip-0 items (largest pairs first), and strip s+1 of
-// a pair follows strip s by about as many items as the warps pop while the
-// predecessor runs kLag = 2 chunks.  PF_WIDE pairs' items stay a prefix of
-// the wave (the int32 queue may take them as a block).
+// predecessor has not yet published the boundary rows it starts with: pairs
+// in order (largest first), strip s+1 of a pair placed after strip s by
+// about as many items as the warps pop while the predecessor runs kLag = 2
+// chunks (the strips of a pair still run close together, so its per-nt
+// records and boundary rows are read from L2).  PF_WIDE pairs' items stay a
+// prefix of the wave (the int32 queue may take them as a block).
 static void interleave_items(const mp_dp_ctx *c, mp_dp_batch *b)
 {
     const double warps = static_cast<double>(c->num_sms) * 2 * kWarpsPerCta;
@@ -474,7 +491,7 @@ static void interleave_items(const mp_dp_ctx *c, mp_dp_batch *b)
         for (uint32_t k = lo; k < hi; ++k) {
             const uint2 it = b->h_items[k];
             if (k > lo && it.x != b->h_items[k - 1].x) ++rank;
-            const double key = it.y == 0 ? rank : rank + it.y * D + warps;
+            const double key = rank + it.y * D;
             keyed.emplace_back(key, it);
         }
         std::stable_sort(keyed.begin(), keyed.end(),
@@ -493,8 +510,9 @@ static void interleave_items(const mp_dp_ctx *c, mp_dp_batch *b)
 // wave policy `overlap`, grow the buffers that depend on the plan, and copy
 // the plan to the device.  Called by the upload, and again when a
 // configuration with the other policy runs the batch.
-static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, bool overlap)
+static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t)
 {
+    const bool overlap = t.overlap_waves != 0;
     const size_t n = b->n;
     const uint64_t strips = b->strips_total;
     b->waves.clear();
@@ -590,7 +608,7 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, bool overlap)
     }
     b->item_off[n] = static_cast<uint32_t>(b->h_items.size());
     b->waves.push_back(Wave{wbeg, static_cast<uint32_t>(n), ibeg, static_cast<uint32_t>(b->h_items.size()), cur, nwide});
-    if (c->params.max_pairs_per_launch == 0) interleave_items(c, b);
+    if (c->params.max_pairs_per_launch == 0 && t.item_order) interleave_items(c, b);
     maxw = std::max(maxw, cur);
     if (b->waves.size() < 2) b->overlap = false;
     b->arena_half = std::max<uint64_t>(div_up(maxw, 256) * 256, 256);
@@ -607,7 +625,7 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, bool overlap)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     b->runs = 0;
-    b->planned = overlap ? 1 : 0;
+    b->planned = plan_key(b, t);
     cudaError_t e = cudaSuccess;
     if ((e = b->state.reserve(b->state_bytes / 8 + 1)) != cudaSuccess ||
         (e = b->wave_nwide.reserve(b->waves.size())) != cudaSuccess ||
@@ -723,7 +741,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     b->needs_waves = plan_code_bytes(c, b) > c->budget;
     b->shape_key = shape_key_of(*b);
     b->planned = -1;
-    return plan_waves(c, b, tuning_for(c, b).overlap_waves != 0);
+    return plan_waves(c, b, tuning_for(c, b));
 }
 
 int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch **out)
@@ -881,7 +899,7 @@ static uint64_t tuning_sig(const mp_dp_tuning &t, bool timed)
 {
     return (static_cast<uint64_t>(t.dp16_variant & 0xff)) | (static_cast<uint64_t>(t.dp16_ctas_per_sm & 0xff) << 8) |
            (static_cast<uint64_t>(t.dp32_ctas_per_sm & 0xff) << 16) | (static_cast<uint64_t>(t.wide_direct & 1) << 24) |
-           (static_cast<uint64_t>(timed) << 25) | (static_cast<uint64_t>(t.overlap_waves & 1) << 26) | (1ull << 27);
+           (static_cast<uint64_t>(timed) << 25) | (static_cast<uint64_t>(t.overlap_waves & 1) << 26) | (static_cast<uint64_t>(t.item_order & 1) << 27) | (1ull << 28);
 }
 
 static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp_tuning *tried, int max_tried,
@@ -899,8 +917,8 @@ int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
         if (rc != MP_OK) return rc;
     }
     const mp_dp_tuning t = tuning_for(c, b);
-    if (b->needs_waves && b->planned != (t.overlap_waves ? 1 : 0)) {
-        const int rc = plan_waves(c, b, t.overlap_waves != 0);
+    {
+        const int rc = ensure_plan(c, b, t);
         if (rc != MP_OK) return rc;
     }
     const size_t nev = 4 + EV_PER_WAVE * b->waves.size();
@@ -945,49 +963,58 @@ int mp_dp_batch_run(mp_dp_ctx *c, mp_dp_batch *b)
 }
 
 // ------------------------------------------------------------ autotuner
-// Candidates: both int16 builds at all CTAs per SM that fit and one fewer;
-// when the batch has pairs that may need int32, both policies for them; when
-// it needs several waves, both wave policies (the plan changes with it, so
-// candidates are grouped by wave policy).
-static std::vector<mp_dp_tuning> candidates(mp_dp_ctx *c, const mp_dp_batch *b)
+// Kernel candidates: both int16 builds at all CTAs per SM that fit and one
+// fewer, and, when the batch has pairs that may need int32, both policies
+// for them; each with the default plan (overlapped waves, interleaved items).
+static std::vector<mp_dp_tuning> kernel_candidates(mp_dp_ctx *c, const mp_dp_batch *b)
 {
     bool any_wide = false;
     for (const PairDesc &d : b->desc) any_wide |= (d.flags & PF_WIDE) && !(d.flags & (PF_SKIP | PF_SCORE_ONLY));
     std::vector<mp_dp_tuning> v;
     const int fit32 = dp32_blocks_per_sm();
-    const int n_ov = b->needs_waves ? 2 : 1;
-    for (int ov = 0; ov < n_ov; ++ov) {
-        const int overlap = b->needs_waves ? 1 - ov : 1;
-        if (c->params.force_int32) {
-            for (int k = fit32; k >= std::max(1, fit32 - 1); --k) {
+    if (c->params.force_int32) {
+        for (int k = fit32; k >= std::max(1, fit32 - 1); --k) {
+            mp_dp_tuning t = default_tuning();
+            t.dp32_ctas_per_sm = k;
+            v.push_back(t);
+        }
+        return v;
+    }
+    for (int var = 0; var < kDp16Variants; ++var) {
+        const int fit = dp16_blocks_per_sm(var);
+        for (int k = fit; k >= std::max(1, fit - 1); --k)
+            for (int wd = 0; wd <= (any_wide ? 1 : 0); ++wd) {
                 mp_dp_tuning t = default_tuning();
-                t.dp32_ctas_per_sm = k;
-                t.overlap_waves = overlap;
+                t.dp16_variant = var;
+                t.dp16_ctas_per_sm = k;
+                t.dp32_ctas_per_sm = fit32;
+                t.wide_direct = wd;
                 v.push_back(t);
             }
-            continue;
-        }
-        for (int var = 0; var < kDp16Variants; ++var) {
-            const int fit = dp16_blocks_per_sm(var);
-            for (int k = fit; k >= std::max(1, fit - 1); --k)
-                for (int wd = 0; wd <= (any_wide ? 1 : 0); ++wd) {
-                    mp_dp_tuning t = default_tuning();
-                    t.dp16_variant = var;
-                    t.dp16_ctas_per_sm = k;
-                    t.dp32_ctas_per_sm = fit32;
-                    t.wide_direct = wd;
-                    t.overlap_waves = overlap;
-                    v.push_back(t);
-                }
-        }
     }
+    return v;
+}
+
+// Plan candidates around a kernel configuration: the other item order and,
+// for a batch that needs several waves, the other wave policy.
+static std::vector<mp_dp_tuning> plan_candidates(const mp_dp_batch *b, const mp_dp_tuning &k)
+{
+    std::vector<mp_dp_tuning> v;
+    for (int ord = 0; ord <= 1; ++ord)
+        for (int ov = 0; ov <= (b->needs_waves ? 1 : 0); ++ov) {
+            mp_dp_tuning t = k;
+            t.item_order = ord;
+            t.overlap_waves = b->needs_waves ? ov : k.overlap_waves;
+            if (t.item_order == k.item_order && t.overlap_waves == k.overlap_waves) continue;
+            v.push_back(t);
+        }
     return v;
 }
 
 static int time_run(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, cudaEvent_t e0, cudaEvent_t e1, float *ms)
 {
-    if (b->needs_waves && b->planned != (t.overlap_waves ? 1 : 0)) {
-        const int rc = plan_waves(c, b, t.overlap_waves != 0);      // outside the timed interval
+    {
+        const int rc = ensure_plan(c, b, t);        // outside the timed interval
         if (rc != MP_OK) return rc;
     }
     cudaStream_t st = c->stream;
@@ -1003,7 +1030,9 @@ static int time_run(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, cudaEve
 static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp_tuning *tried, int max_tried,
                          int *n_tried)
 {
-    std::vector<mp_dp_tuning> cand = candidates(c, b);
+    // two stages: the kernel configurations under the default plan, then the
+    // plan options (item order, wave policy) under the fastest of those
+    std::vector<mp_dp_tuning> cand = kernel_candidates(c, b);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1019,6 +1048,15 @@ static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp
         rc = time_run(c, b, t, e0, e1, &ms);
     }
     for (size_t k = 0; k < cand.size() && rc == MP_OK; ++k) rc = time_run(c, b, cand[k], e0, e1, &cand[k].ms);
+    if (rc == MP_OK) {
+        size_t k1 = 0;
+        for (size_t k = 1; k < cand.size(); ++k)
+            if (cand[k].ms < cand[k1].ms) k1 = k;
+        for (const mp_dp_tuning &t : plan_candidates(b, cand[k1])) {
+            cand.push_back(t);
+            if ((rc = time_run(c, b, cand.back(), e0, e1, &cand.back().ms)) != MP_OK) break;
+        }
+    }
     if (rc == MP_OK && cand.size() > 1) {
         // the two fastest once more; each keeps its lower time
         std::vector<size_t> idx(cand.size());
@@ -1036,10 +1074,10 @@ static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp
     for (size_t k = 1; k < cand.size(); ++k)
         if (cand[k].ms < cand[bi].ms) bi = k;
     c->tuned[b->shape_key] = cand[bi];
-    if (b->needs_waves && b->planned != (cand[bi].overlap_waves ? 1 : 0)) {
+    if (b->planned != plan_key(b, cand[bi])) {
         // re-plan for the choice and run once more, so that the batch's
         // results (whose counters sit where the plan puts them) match its plan
-        int rc = plan_waves(c, b, cand[bi].overlap_waves != 0);
+        int rc = plan_waves(c, b, cand[bi]);
         if (rc == MP_OK) rc = enqueue_pipeline(c, b, c->stream, false, false, cand[bi]);
         if (rc != MP_OK) return rc;
         CK(cudaStreamSynchronize(c->stream));
@@ -1077,7 +1115,7 @@ int mp_dp_set_tuning(mp_dp_ctx *c, const mp_dp_tuning *t)
     }
     if (t->dp16_variant < 0 || t->dp16_variant >= kDp16Variants || t->dp16_ctas_per_sm < 0 ||
         t->dp32_ctas_per_sm < 0 || t->wide_direct < 0 || t->wide_direct > 1 || t->overlap_waves < 0 ||
-        t->overlap_waves > 1)
+        t->overlap_waves > 1 || t->item_order < 0 || t->item_order > 1)
         return MP_EINVAL;
     c->fixed = *t;
     c->has_fixed = true;
@@ -1096,12 +1134,12 @@ int mp_dp_tuning_save(mp_dp_ctx *c, const char *path)
     if (!c || !path) return MP_EINVAL;
     FILE *f = fopen(path, "w");
     if (!f) return MP_EINVAL;
-    bool ok = fprintf(f, "mp_dp_tuning 2 %s %d\n", c->dev_name.c_str(), c->num_sms) > 0;
+    bool ok = fprintf(f, "mp_dp_tuning 3 %s %d\n", c->dev_name.c_str(), c->num_sms) > 0;
     for (const auto &kv : c->tuned) {
         const mp_dp_tuning &t = kv.second;
-        ok = ok && fprintf(f, "%016llx %d %d %d %d %d %.4f\n", static_cast<unsigned long long>(kv.first),
+        ok = ok && fprintf(f, "%016llx %d %d %d %d %d %d %.4f\n", static_cast<unsigned long long>(kv.first),
                            t.dp16_variant, t.dp16_ctas_per_sm, t.dp32_ctas_per_sm, t.wide_direct, t.overlap_waves,
-                           static_cast<double>(t.ms)) > 0;
+                           t.item_order, static_cast<double>(t.ms)) > 0;
     }
     ok = (fclose(f) == 0) && ok;
     return ok ? MP_OK : MP_EINVAL;
@@ -1115,7 +1153,7 @@ int mp_dp_tuning_load(mp_dp_ctx *c, const char *path)
     if (!f) return MP_EINVAL;
     char name[256] = {0};
     int version = 0, sms = 0;
-    if (fscanf(f, "mp_dp_tuning %d %255s %d", &version, name, &sms) != 3 || version != 2 ||
+    if (fscanf(f, "mp_dp_tuning %d %255s %d", &version, name, &sms) != 3 || version != 3 ||
         c->dev_name != name || sms != c->num_sms) {
         fclose(f);
         return MP_EINVAL;
@@ -1125,10 +1163,10 @@ int mp_dp_tuning_load(mp_dp_ctx *c, const char *path)
         unsigned long long key = 0;
         mp_dp_tuning t{};
         double ms = 0;
-        const int k = fscanf(f, "%llx %d %d %d %d %d %lf", &key, &t.dp16_variant, &t.dp16_ctas_per_sm,
-                             &t.dp32_ctas_per_sm, &t.wide_direct, &t.overlap_waves, &ms);
+        const int k = fscanf(f, "%llx %d %d %d %d %d %d %lf", &key, &t.dp16_variant, &t.dp16_ctas_per_sm,
+                             &t.dp32_ctas_per_sm, &t.wide_direct, &t.overlap_waves, &t.item_order, &ms);
         if (k == EOF) break;
-        if (k != 7 || t.dp16_variant < 0 || t.dp16_variant >= kDp16Variants || t.dp16_ctas_per_sm < 0 ||
+        if (k != 8 || t.item_order < 0 || t.item_order > 1 || t.dp16_variant < 0 || t.dp16_variant >= kDp16Variants || t.dp16_ctas_per_sm < 0 ||
             t.dp32_ctas_per_sm < 0 || t.wide_direct < 0 || t.wide_direct > 1 || t.overlap_waves < 0 ||
             t.overlap_waves > 1) {
             fclose(f);

@@ -294,9 +294,9 @@ def test_overlapped_waves(mp, ctx):
     """A batch needing several waves, with every pair under half the budget:
     with overlapped waves (the default) they alternate between two streams
     over two arena halves; without, they run one after the other at the
-    whole budget.  Either way, and switching between the two on one batch
-    (which re-plans it), the results equal the one-wave run, direct and
-    replayed as a graph, with timing on."""
+    whole budget.  Either way, with either item order, and switching between
+    them on one batch (which re-plans it), the results equal the one-wave
+    run, direct and replayed as a graph, with timing on."""
     pairs = _gene_pairs(63, 60, 300, 900)
     need = [_code_bytes(len(p.prot), len(p.nt)) for p in pairs]
     budget = max(3 * max(need), sum(need) // 3)
@@ -307,8 +307,8 @@ def test_overlapped_waves(mp, ctx):
         mp.mp_dp_set_timing(c, True)
         b = mp.mp_dp_batch_upload(c, pairs)
         waves = {}
-        for ov in (1, 0, 1):
-            mp.mp_dp_set_tuning(c, dict(overlap_waves=ov))
+        for ov, io in ((1, 1), (0, 1), (1, 0), (0, 0), (1, 1)):
+            mp.mp_dp_set_tuning(c, dict(overlap_waves=ov, item_order=io))
             for _ in range(3):
                 mp.mp_dp_batch_run(c, b)
                 mp.mp_dp_batch_sync(c)
