@@ -66,7 +66,8 @@ def blosum62_22() -> np.ndarray:
 class Params(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("e", ctypes.c_int32), ("f", ctypes.c_int32),
                 ("r", ctypes.c_int32), ("stop", ctypes.c_int32),
-                ("mat", (ctypes.c_int32 * 22) * 22)]
+                ("mat", (ctypes.c_int32 * 22) * 22),
+                ("splice_model", ctypes.c_int32), ("splice_p", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -80,8 +81,11 @@ class Result(ctypes.Structure):
 DEFAULTS = dict(q=11, e=1, f=23, r=29, stop=23)
 
 
-def make_params(q=None, e=None, f=None, r=None, stop=None, mat=None) -> Params:
+def make_params(q=None, e=None, f=None, r=None, stop=None, mat=None, splice_model=0, splice_p=30) -> Params:
+    """Scoring parameters; splice_model 0 is the final model, 1 the simple
+    GT-AG model with cost splice_p."""
     p = Params()
+    p.splice_model, p.splice_p = splice_model, splice_p
     d = dict(DEFAULTS)
     for k, v in (("q", q), ("e", e), ("f", f), ("r", r), ("stop", stop)):
         if v is not None:
@@ -128,6 +132,9 @@ def lib():
             L.orc_translate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.orc_translate.restype = ctypes.c_int
             L.orc_donor.argtypes = [ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.c_int]
+            L.orc_donor_simple.argtypes = [ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_acceptor_simple.argtypes = [ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int]
             L.orc_donor.restype = ctypes.c_int
             L.orc_acceptor.argtypes = [ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.c_int]
             L.orc_acceptor.restype = ctypes.c_int
@@ -202,6 +209,19 @@ def acceptor(nt: str, x: int) -> int:
     codes = [0] + ["ACGT".index(c) for c in nt.upper()]
     arr = (ctypes.c_int8 * len(codes))(*codes)
     return lib().orc_acceptor(arr, len(nt), x)
+
+
+def donor_simple(nt: str, x: int, p: int) -> int:
+    """d(x) of the simple GT-AG model with cost p; x is 1-based."""
+    codes = [0] + ["ACGT".index(c) for c in nt.upper()]
+    arr = (ctypes.c_int8 * len(codes))(*codes)
+    return lib().orc_donor_simple(arr, len(nt), x, p)
+
+
+def acceptor_simple(nt: str, x: int, p: int) -> int:
+    codes = [0] + ["ACGT".index(c) for c in nt.upper()]
+    arr = (ctypes.c_int8 * len(codes))(*codes)
+    return lib().orc_acceptor_simple(arr, len(nt), x, p)
 
 
 def revcomp(s: str) -> str:

@@ -13,7 +13,8 @@
  *     with the match term read as H[i-3][j-1] + s(i,j) (the printed
  *     H[i-3][j] cannot advance j; the worked example and Eq. 5 both consume
  *     one residue per codon).
- *   - The final splice model d(i), a(i) (Methods, "Splice models").
+ *   - The final splice model d(i), a(i) (Methods, "Splice models"), or the
+ *     simple GT-AG model with cost p defined right after Eq. 7.
  *   - Local mode: H restarts at 0; the best cell is the largest H, ties to
  *     the smallest i and then the smallest j.
  *   - Ties inside every max go to the earliest term in the printed order of
@@ -45,6 +46,8 @@ static const char ORC_CODE_TCAG[] =
 typedef struct {
     int32_t q, e, f, r, stop;   /* gap open, gap extend, frameshift, intron, stop codon */
     int32_t mat[22][22];        /* [translated aa][protein residue], ORC_AA order */
+    int32_t splice_model;       /* 0: the final model; 1: the simple GT-AG model */
+    int32_t splice_p;           /* simple model: cost p of a donor without GT / acceptor without AG */
 } orc_params;
 
 typedef struct {
@@ -127,6 +130,30 @@ int orc_acceptor(const int8_t *T, int n, int x)
     return 30;
 }
 
+/* Simple model (Methods, "DP for protein-to-genome alignment", the
+ * definitions right after Eq. 7): d(x) = 0 if T[x+1..x+2] is GT, else p;
+ * a(x) = 0 if T[x-1..x] is AG, else p.  Bases outside T match nothing. */
+int orc_donor_simple(const int8_t *T, int n, int x, int p)
+{
+    return (base_at(T, n, x + 1) == G_ && base_at(T, n, x + 2) == T_) ? 0 : p;
+}
+
+int orc_acceptor_simple(const int8_t *T, int n, int x, int p)
+{
+    return (base_at(T, n, x - 1) == A_ && base_at(T, n, x) == G_) ? 0 : p;
+}
+
+/* d(x) and a(x) under the model the parameters select. */
+static int32_t splice_d(const orc_params *p, const int8_t *T, int n, int x)
+{
+    return p->splice_model == 1 ? orc_donor_simple(T, n, x, p->splice_p) : orc_donor(T, n, x);
+}
+
+static int32_t splice_a(const orc_params *p, const int8_t *T, int n, int x)
+{
+    return p->splice_model == 1 ? orc_acceptor_simple(T, n, x, p->splice_p) : orc_acceptor(T, n, x);
+}
+
 /* ------------------------------------------------------------- the DP */
 
 typedef struct {
@@ -163,8 +190,8 @@ static int32_t subst(const dp_t *dp, int i, int j)
     return dp->p->mat[aa][dp->P[j]];
 }
 
-static int32_t dfun(const dp_t *dp, int x) { return orc_donor(dp->T, dp->n, x); }
-static int32_t afun(const dp_t *dp, int x) { return orc_acceptor(dp->T, dp->n, x); }
+static int32_t dfun(const dp_t *dp, int x) { return splice_d(dp->p, dp->T, dp->n, x); }
+static int32_t afun(const dp_t *dp, int x) { return splice_a(dp->p, dp->T, dp->n, x); }
 
 /* The ten H terms of Eq. 7 at (i, j) in printed order:
  * 0 M, 1 I, 2 D, 3 F1, 4 F2, 5 G1, 6 G2, 7 A, 8 B, 9 C. */
@@ -402,10 +429,10 @@ int32_t orc_rescore(const orc_params *p, const char *prot, int32_t plen, const c
         case OP_D: sc -= p->q + (int64_t)p->e * len; i += 3 * len; break;
         case OP_F: sc -= p->f; i += len; j += 1; break;
         case OP_G: sc -= p->f; i += len; break;
-        case OP_N: sc -= p->r + orc_donor(T, tlen, i) + orc_acceptor(T, tlen, i + len); i += len; break;
-        case OP_U: sc -= p->r + orc_donor(T, tlen, i + 1) + orc_acceptor(T, tlen, i + len + 1);
+        case OP_N: sc -= p->r + splice_d(p, T, tlen, i) + splice_a(p, T, tlen, i + len); i += len; break;
+        case OP_U: sc -= p->r + splice_d(p, T, tlen, i + 1) + splice_a(p, T, tlen, i + len + 1);
                    i += len + 3; j += 1; break;
-        case OP_V: sc -= p->r + orc_donor(T, tlen, i + 2) + orc_acceptor(T, tlen, i + len + 2);
+        case OP_V: sc -= p->r + splice_d(p, T, tlen, i + 2) + splice_a(p, T, tlen, i + len + 2);
                    i += len + 3; j += 1; break;
         default: bad = 1;
         }

@@ -32,16 +32,35 @@ import oracle
 ORDER = {"M": 0, "I": 1, "D": 2, "F1": 3, "F2": 4, "G1": 5, "G2": 6, "N": 7, "U": 8, "V": 9}
 
 
+def _simple_d(nt: str, x: int, p: int) -> int:
+    """Simple GT-AG model: d(x) = 0 when the two bases after x (1-based
+    x+1, x+2; 0-based x, x+1) spell GT, else p."""
+    return 0 if 0 <= x and x + 2 <= len(nt) and nt[x:x + 2] == "GT" else p
+
+
+def _simple_a(nt: str, x: int, p: int) -> int:
+    """a(x) = 0 when the bases at 1-based x-1, x (0-based x-2, x-1) spell AG."""
+    return 0 if 2 <= x <= len(nt) and nt[x - 2:x] == "AG" else p
+
+
 class Problem:
-    def __init__(self, prot: str, nt: str, q=11, e=1, f=23, r=29, stop=23, mat=None):
+    def __init__(self, prot: str, nt: str, q=11, e=1, f=23, r=29, stop=23, mat=None, splice_p=None):
+        """splice_p None: the final splice model (the oracle's tables, pinned
+        on their own); an integer: the simple GT-AG model with that cost,
+        written out here from its definition."""
         self.P = [oracle.AA.index(c) if c in oracle.AA else 21 for c in prot]
         self.T = ["ACGT".index(c) for c in nt]
         self.nt = nt
         self.n, self.m = len(nt), len(prot)
         self.q, self.e, self.f, self.r, self.stop = q, e, f, r, stop
         self.mat = oracle.blosum62_22() if mat is None else mat
-        self._d = [oracle.donor(nt, x) if nt else 30 for x in range(-3, self.n + 4)]
-        self._a = [oracle.acceptor(nt, x) if nt else 30 for x in range(-3, self.n + 4)]
+        xs = range(-3, self.n + 4)
+        if splice_p is None:
+            self._d = [oracle.donor(nt, x) if nt else 30 for x in xs]
+            self._a = [oracle.acceptor(nt, x) if nt else 30 for x in xs]
+        else:
+            self._d = [_simple_d(nt, x, splice_p) for x in xs]
+            self._a = [_simple_a(nt, x, splice_p) for x in xs]
 
     def d(self, x):
         return self._d[x + 3]

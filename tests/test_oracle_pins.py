@@ -86,6 +86,22 @@ def test_splice_out_of_range(orc):
     assert orc.acceptor("CAG", 3) == 0 and orc.acceptor("CAG", 4) == 30
 
 
+@pytest.mark.parametrize("p", [0, 7, 30])
+def test_simple_model_rows(orc, p):
+    """Simple GT-AG model (the definitions right after Eq. 7): every
+    dinucleotide after a donor position or ending at an acceptor position;
+    only GT and AG cost nothing."""
+    for b1 in "ACGT":
+        for b2 in "ACGT":
+            dn = b1 + b2
+            assert orc.donor_simple("A" + dn + "A", 1, p) == (0 if dn == "GT" else p), dn
+            assert orc.acceptor_simple("A" + dn + "A", 3, p) == (0 if dn == "AG" else p), dn
+    # bases outside T match nothing
+    assert orc.donor_simple("AAG", 2, p) == p and orc.donor_simple("GT", 0, p) == 0
+    assert orc.donor_simple("GT", -1, p) == p and orc.acceptor_simple("AG", 2, p) == 0
+    assert orc.acceptor_simple("AG", 1, p) == p and orc.acceptor_simple("AG", 3, p) == p
+
+
 # ----------------------------------------------------------- brute force
 
 def _random_case(rng, n, m, valid=True):
@@ -128,6 +144,52 @@ def test_segment_recursion_equals_oracle(orc):
         want = bf.segment_best(bf.Problem(prot, nt, **params))
         got = orc.align(prot, nt, 1, orc.make_params(**params))["score"]
         assert got == want, (prot, nt, params)
+
+
+def test_simple_model_against_enumeration(orc):
+    """With the simple GT-AG model the oracle's score is the best path score
+    of the enumerations (all three intron phases, with GT/AG and other
+    splice sites), for several costs p."""
+    rng = random.Random(17)
+    for k in range(120):
+        n, m = rng.randint(0, 20), rng.randint(0, 5)
+        prot, nt, params = _random_case(rng, n, m, valid=True)
+        if nt and rng.random() < 0.6:
+            # plant splice signals so that cheap introns exist
+            i = rng.randint(0, len(nt))
+            nt = (nt[:i] + "GT" + "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 4))) + "AG" + nt[i:])[:22]
+        p = rng.choice([0, 3, 9, 30])
+        want = bf.segment_best(bf.Problem(prot, nt, splice_p=p, **params))
+        got = orc.align(prot, nt, 1, orc.make_params(splice_model=1, splice_p=p, **params))["score"]
+        assert got == want, (prot, nt, params, p)
+        if len(nt) <= 6 and m <= 2:
+            assert got == bf.best_by_enumeration(bf.all_paths(bf.Problem(prot, nt, splice_p=p, **params)))
+
+
+def test_simple_model_intron_costs(orc):
+    """A GT...AG intron costs r under the simple model and r + 2p when the
+    same intron has neither signal."""
+    rng = random.Random(44)
+    prot, nt, intron = _intron_case(rng, 0)
+    for p in (0, 5, 30):
+        r = orc.align(prot, nt, 1, orc.make_params(splice_model=1, splice_p=p))
+        assert r["score"] == _diag_sum(orc, prot) - 29 and r["cigar"][1] == ("N", len(intron))
+    # CA...TC instead of GT...AG: the intron pays r + 2p while that stays cheaper than the alternatives
+    bad = nt.replace(intron, "CA" + intron[2:-2] + "TC")
+    r = orc.align(prot, bad, 1, orc.make_params(splice_model=1, splice_p=3))
+    assert r["score"] == _diag_sum(orc, prot) - 29 - 6 and r["cigar"][1] == ("N", len(intron))
+
+
+def test_simple_model_rescoring(orc):
+    """Op-sum rescoring under the simple model reproduces the DP score."""
+    rng = random.Random(45)
+    for _ in range(30):
+        prot, nt, intron = _intron_case(rng, rng.randint(0, 2))
+        p = rng.choice([0, 4, 30])
+        params = orc.make_params(splice_model=1, splice_p=p)
+        r = orc.align(prot, nt, 1, params)
+        sc, pe, te = orc.rescore(prot, nt, 1, r["prot_st"], r["nt_st"], r["cigar_raw"], params)
+        assert (sc, pe, te) == (r["score"], r["prot_en"], r["nt_en"])
 
 
 def test_segment_recursion_default_params(orc):
