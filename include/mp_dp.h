@@ -74,6 +74,8 @@ extern "C" {
 
 /* ------------------------------------------------------------- params */
 #define MP_SPLICE_FINAL 0   /* the final splice model of the "Splice models" section */
+#define MP_SPLICE_SIMPLE 1  /* the simple model defined right after Eq. 7: d(x) = 0 if T[x+1..x+2]
+                               is GT, else splice_p; a(x) = 0 if T[x-1..x] is AG, else splice_p */
 #define MP_MODE_LOCAL 0     /* local alignment (the only mode of this version) */
 
 #define MP_PAIR_SCORE_ONLY 0x1u  /* mp_pair.flags: score and end cell only, no CIGAR */
@@ -91,7 +93,7 @@ extern "C" {
 typedef struct {
     int32_t q, e, f, r, stop;  /* gap open, gap extend, frameshift, intron, stop codon */
     int8_t mat[22][22];
-    int32_t splice_model;      /* MP_SPLICE_FINAL */
+    int32_t splice_model;      /* MP_SPLICE_FINAL or MP_SPLICE_SIMPLE */
     int32_t mode;              /* MP_MODE_LOCAL */
     uint64_t tb_budget_bytes;  /* device bytes for traceback codes (default 40 GiB, capped
                                   by free device memory at init) */
@@ -104,7 +106,9 @@ typedef struct {
                                   boundary row, so the waits of the next strip run out */
     int32_t autotune;          /* 1: the first run of a batch whose shape class has no tuned
                                   configuration yet runs mp_dp_autotune on it first */
-    int32_t reserved[3];
+    int32_t splice_p;          /* MP_SPLICE_SIMPLE: cost p of a donor without GT or an acceptor
+                                  without AG (0..1000; the paper gives no value; default 30) */
+    int32_t reserved[2];
 } mp_dp_params;
 
 /* One alignment request.  prot: ASCII amino acids; nt: ASCII A/C/G/T

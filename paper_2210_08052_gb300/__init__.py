@@ -20,6 +20,7 @@ MP_OK, MP_EINVAL, MP_ENOMEM, MP_EBUDGET, MP_ETIMEOUT = 0, -1, -2, -3, -4
 MP_ECUDA, MP_EPENDING, MP_EAGAIN, MP_ETICKET, MP_ESTATE, MP_ETOOLARGE = -5, -6, -7, -8, -9, -10
 MP_ST_RERUN, MP_ST_BADSEQ, MP_ST_BUDGET, MP_ST_TRACE, MP_ST_TIMEOUT, MP_ST_ERRMASK = 0x1, 0x10, 0x20, 0x40, 0x80, 0xF0
 MP_PAIR_SCORE_ONLY = 0x1
+MP_SPLICE_FINAL, MP_SPLICE_SIMPLE = 0, 1
 MP_DEBUG_NO_PUBLISH = 0x1
 OP_NAMES = "MIDFGNUV"
 
@@ -39,7 +40,7 @@ class mp_dp_params(ctypes.Structure):
                 ("tb_budget_bytes", ctypes.c_uint64), ("force_int32", ctypes.c_int32),
                 ("max_pairs_per_launch", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
                 ("debug_flags", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("splice_p", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class mp_pair(ctypes.Structure):

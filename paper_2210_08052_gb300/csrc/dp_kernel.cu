@@ -65,7 +65,7 @@ __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b)
 //   x = [r + d(i+1), r + d(i)]   (16-bit halves, lo first)
 //   y = [a(i), a(i-1)]
 //   z = byte offset of the profile row of the codon ending at i
-__device__ __forceinline__ uint4 make_record(const uint32_t *g, int n, int ii, int r)
+__device__ __forceinline__ uint4 make_record(const uint32_t *g, int n, int ii, const ScoreParams &sp)
 {
     const int s = ii - 3;                  // window T0[ii-3 .. ii+4]
     const int w = s >> 4;                  // floor division (s may be negative)
@@ -80,10 +80,11 @@ __device__ __forceinline__ uint4 make_record(const uint32_t *g, int n, int ii, i
         v[k] = static_cast<unsigned>(s + k) < static_cast<unsigned>(n);
     }
     const int aa = (v[1] && v[3]) ? c_code.v[b[1] * 16 + b[2] * 4 + b[3]] : 21;
-    const int dC = donor_score(b[5], b[6], b[7], v[5], v[6], v[7]);     // d(i+1)
-    const int dB = donor_score(b[4], b[5], b[6], v[4], v[5], v[6]);     // d(i)
-    const int aA = acceptor_score(b[1], b[2], b[3], v[1], v[2], v[3]);  // a(i)
-    const int aC = acceptor_score(b[0], b[1], b[2], v[0], v[1], v[2]);  // a(i-1)
+    const int r = sp.r;
+    const int dC = splice_donor(sp, b[5], b[6], b[7], v[5], v[6], v[7]);     // d(i+1)
+    const int dB = splice_donor(sp, b[4], b[5], b[6], v[4], v[5], v[6]);     // d(i)
+    const int aA = splice_acceptor(sp, b[1], b[2], b[3], v[1], v[2], v[3]);  // a(i)
+    const int aC = splice_acceptor(sp, b[0], b[1], b[2], v[0], v[1], v[2]);  // a(i-1)
     uint4 rec;
     rec.x = static_cast<uint32_t>(r + dC) | (static_cast<uint32_t>(r + dB) << 16);
     rec.y = static_cast<uint32_t>(aA) | (static_cast<uint32_t>(aC) << 16);
@@ -780,7 +781,8 @@ int dp32_blocks_per_sm() { return kernel_blocks_per_sm<Ops32, 2>(dp32_smem_bytes
 
 namespace {
 // Per-nt records of every pair (see make_record), positions -kChunk upwards.
-__global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const uint32_t *nt2, int r, uint4 *recs)
+__global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const uint32_t *nt2, const ScoreParams sp,
+                               uint4 *recs)
 {
     for (uint32_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
         const PairDesc pd = pairs[p];
@@ -789,16 +791,16 @@ __global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const ui
         const int cnt = static_cast<int>(records_of(pd.nt_len));
         const uint32_t *g = nt2 + pd.nt_word_off;
         uint4 *out = recs + pd.rec_off;
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) out[k] = make_record(g, n, k - kChunk, r);
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) out[k] = make_record(g, n, k - kChunk, sp);
     }
 }
 }  // namespace
 
-cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, int r, uint4 *recs,
+cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, const ScoreParams &sp, uint4 *recs,
                            cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    records_kernel<<<n < 8192 ? n : 8192, 256, 0, st>>>(pairs, n, nt2, r, recs);
+    records_kernel<<<n < 8192 ? n : 8192, 256, 0, st>>>(pairs, n, nt2, sp, recs);
     return cudaGetLastError();
 }
 
@@ -928,7 +930,7 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
     __syncthreads();
     // per-nt records of the pair (positions -kChunk upwards)
     for (int k = threadIdx.x; k < static_cast<int>(records_of(static_cast<uint32_t>(n))); k += blockDim.x)
-        S->recs[k] = make_record(S->nt2 + kNtPadWords, n, k - kChunk, sp.r);
+        S->recs[k] = make_record(S->nt2 + kNtPadWords, n, k - kChunk, sp);
     __syncthreads();
     if (!bad && m > 0 && n > 0) {
         DPArgs a{};
@@ -999,7 +1001,9 @@ extern "C" int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *
     for (int x = 0; x < 20; ++x)
         for (int y = 0; y < 22; ++y) mn = p.mat[x][y] < mn ? p.mat[x][y] : mn;
     if (p.q < 0 || p.e < 1 || p.f < 0 || p.r < 0 || p.stop < 0 || p.q + p.e > 1000 || p.f > 1000 ||
-        p.r > 1000 || p.stop > 512 || !(p.r > p.f && p.r > p.stop && p.r > -mn))
+        p.r > 1000 || p.stop > 512 || !(p.r > p.f && p.r > p.stop && p.r > -mn) ||
+        (p.splice_model != MP_SPLICE_FINAL && p.splice_model != MP_SPLICE_SIMPLE) || p.splice_p < 0 ||
+        p.splice_p > 1000)
         return MP_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return MP_ECUDA;
@@ -1022,6 +1026,8 @@ extern "C" int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *
     if (setup_err != cudaSuccess || !scratch_ptr[dev]) return MP_ECUDA;
     ScoreParams sp;
     sp.q = p.q; sp.e = p.e; sp.f = p.f; sp.r = p.r; sp.stop = p.stop;
+    sp.splice_model = p.splice_model;
+    sp.splice_p = p.splice_p;
     for (int x = 0; x < 22; ++x)
         for (int y = 0; y < 22; ++y) sp.mat[x][y] = p.mat[x][y];
     dp_noalloc_kernel<<<1, kWarpsPerCta * 32, kNASmem, static_cast<cudaStream_t>(stream)>>>(

@@ -61,6 +61,23 @@ __device__ __forceinline__ int acceptor_score(int b1, int b2, int b3, bool v1, b
     return 30;
 }
 
+// d(x) and a(x) under the parameters' splice model; for the simple model
+// (defined right after Eq. 7) a donor needs GT at T[x+1..x+2] and an
+// acceptor AG at T[x-1..x], else they cost splice_p.  Arguments as above.
+__device__ __forceinline__ int splice_donor(const ScoreParams &sp, int b1, int b2, int b3, bool v1, bool v2,
+                                            bool v3)
+{
+    if (sp.splice_model == MP_SPLICE_SIMPLE) return (v1 && v2 && b1 == 2 && b2 == 3) ? 0 : sp.splice_p;
+    return donor_score(b1, b2, b3, v1, v2, v3);
+}
+
+__device__ __forceinline__ int splice_acceptor(const ScoreParams &sp, int b1, int b2, int b3, bool v1, bool v2,
+                                               bool v3)
+{
+    if (sp.splice_model == MP_SPLICE_SIMPLE) return (v2 && v3 && b2 == 0 && b3 == 2) ? 0 : sp.splice_p;
+    return acceptor_score(b1, b2, b3, v1, v2, v3);
+}
+
 __device__ __forceinline__ int subst_score(const ScoreParams &sp, int aa, int pc)
 {
     if (aa == 21) return -512;             // no complete codon (i < 3)

@@ -72,6 +72,8 @@ struct PairOut {
 struct ScoreParams {
     int32_t q, e, f, r, stop;
     int8_t mat[22][22];
+    int32_t splice_model;   // MP_SPLICE_FINAL / MP_SPLICE_SIMPLE
+    int32_t splice_p;       // simple model: cost of a donor without GT / acceptor without AG
 };
 
 // A work item is one 64-residue strip of one pair: x = pair, y = strip.
@@ -116,7 +118,7 @@ struct TBArgs {
 // kernel launchers (defined in the .cu files)
 cudaError_t launch_pack(const PairDesc *pairs, uint32_t n, const char *ascii, uint8_t *prot,
                         uint32_t *nt2, PairOut *out, cudaStream_t st);
-cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, int r, uint4 *recs,
+cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, const ScoreParams &sp, uint4 *recs,
                            cudaStream_t st);
 // variant 0: the int16 DP kernel built for 3 CTAs per SM (80 registers per
 // thread); 1: built for 2 CTAs per SM (up to 128).  Same results.

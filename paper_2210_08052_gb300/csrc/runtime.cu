@@ -285,6 +285,7 @@ void mp_dp_default_params(mp_dp_params *p)
     }
     p->mat[20][20] = 1;
     p->splice_model = MP_SPLICE_FINAL;
+    p->splice_p = 30;
     p->mode = MP_MODE_LOCAL;
     p->tb_budget_bytes = kDefaultBudget;
 }
@@ -316,7 +317,9 @@ static int validate_params(const mp_dp_params *p)
         for (int b = 0; b < 22; ++b) mn = std::min<int>(mn, p->mat[a][b]);
     // an intron of length <= 0 must lose to a frameshift or a match from the same cell
     if (!(p->r > p->f && p->r > p->stop && p->r > -mn)) return MP_EINVAL;
-    if (p->splice_model != MP_SPLICE_FINAL || p->mode != MP_MODE_LOCAL) return MP_EINVAL;
+    if ((p->splice_model != MP_SPLICE_FINAL && p->splice_model != MP_SPLICE_SIMPLE) || p->mode != MP_MODE_LOCAL)
+        return MP_EINVAL;
+    if (p->splice_p < 0 || p->splice_p > 1000) return MP_EINVAL;
     if (p->max_pairs_per_launch < 0 || p->wait_limit < 0) return MP_EINVAL;
     return MP_OK;
 }
@@ -351,6 +354,8 @@ int mp_dp_init(mp_dp_ctx **out, const mp_dp_params *p, int device)
     }
     c->sp.q = prm.q; c->sp.e = prm.e; c->sp.f = prm.f; c->sp.r = prm.r; c->sp.stop = prm.stop;
     memcpy(c->sp.mat, prm.mat, sizeof(c->sp.mat));
+    c->sp.splice_model = prm.splice_model;
+    c->sp.splice_p = prm.splice_p;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     uint64_t budget = prm.tb_budget_bytes ? prm.tb_budget_bytes : kDefaultBudget;
@@ -778,7 +783,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
     CK(rec(0));
     CK(cudaMemsetAsync(state, 0, b->state_bytes, st));
     CK(launch_pack(b->d_desc.p, n, b->ascii.p, b->prot.p, b->nt2.p, b->out.p, st));
-    CK(launch_records(b->d_desc.p, n, b->nt2.p, c->sp.r, b->recs.p, st));
+    CK(launch_records(b->d_desc.p, n, b->nt2.p, c->sp, b->recs.p, st));
     launches += 2;
     CK(rec(1));
     const int variant = t.dp16_variant == 1 ? 1 : 0;

@@ -139,16 +139,16 @@ struct PairView {
         return (__ldg(g + ((x - 1) >> 4)) >> (2 * ((x - 1) & 15))) & 3;
     }
     __device__ __forceinline__ bool in(int x) const { return x >= 1 && x <= n; }
-    // final splice model: d(x) looks at T[x+1..x+3], a(x) at T[x-2..x]
+    // splice model: d(x) looks at T[x+1..x+3], a(x) at T[x-2..x]
     __device__ __forceinline__ int d(int x) const
     {
         const bool v1 = in(x + 1), v2 = in(x + 2), v3 = in(x + 3);
-        return donor_score(v1 ? b(x + 1) : 0, v2 ? b(x + 2) : 0, v3 ? b(x + 3) : 0, v1, v2, v3);
+        return splice_donor(*sp, v1 ? b(x + 1) : 0, v2 ? b(x + 2) : 0, v3 ? b(x + 3) : 0, v1, v2, v3);
     }
     __device__ __forceinline__ int a(int x) const
     {
         const bool v1 = in(x - 2), v2 = in(x - 1), v3 = in(x);
-        return acceptor_score(v1 ? b(x - 2) : 0, v2 ? b(x - 1) : 0, v3 ? b(x) : 0, v1, v2, v3);
+        return splice_acceptor(*sp, v1 ? b(x - 2) : 0, v2 ? b(x - 1) : 0, v3 ? b(x) : 0, v1, v2, v3);
     }
     // s(i, j): codon T[i-2..i] against residue P[j]
     __device__ __forceinline__ int s(int i, int j) const

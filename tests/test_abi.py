@@ -44,6 +44,7 @@ def test_default_params_match_oracle_tables(mp, orc):
     om = orc.blosum62_22()
     assert (lm[:20, :] == om[:20, :]).all()          # rows the DP reads
     assert p.tb_budget_bytes == 40 << 30
+    assert p.splice_model == mp.MP_SPLICE_FINAL and p.splice_p == 30
 
 
 def test_struct_layout_matches_header(mp, tmp_path):
@@ -74,7 +75,7 @@ def test_strerror(mp):
 
 
 @pytest.mark.parametrize("bad", [dict(r=20), dict(r=23), dict(e=0), dict(q=-1), dict(stop=40),
-                                 dict(splice_model=1), dict(mode=2)])
+                                 dict(splice_model=2), dict(splice_p=-1), dict(splice_p=1001), dict(mode=2)])
 def test_init_rejects_degenerate_params(mp, bad):
     """r must exceed f, stop and -min(mat) so that no intron of length <= 0
     beats a frameshift or a match (validated before any device access)."""

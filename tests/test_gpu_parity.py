@@ -45,7 +45,8 @@ def ctx32(mp):
 
 def _orc_params(orc, p):
     return orc.make_params(q=p.q, e=p.e, f=p.f, r=p.r, stop=p.stop,
-                           mat=np.array([[p.mat[a][b] for b in range(22)] for a in range(22)]))
+                           mat=np.array([[p.mat[a][b] for b in range(22)] for a in range(22)]),
+                           splice_model=p.splice_model, splice_p=p.splice_p)
 
 
 def _compare(orc, pairs, got, params=None, limit=5):
@@ -321,6 +322,52 @@ def test_overlapped_waves(mp, ctx):
         mp.mp_dp_batch_free(c, b)
     finally:
         mp.mp_dp_destroy(c)
+
+
+@pytest.mark.parametrize("splice_p", [0, 12, 30])
+def test_simple_splice_model(mp, orc, splice_p):
+    """The simple GT-AG splice model (cost p for a donor without GT or an
+    acceptor without AG): gene pairs whose introns keep GT...AG or have their
+    signals replaced, both strands, plus an int16-saturating pair (int32
+    re-run), against the oracle under the same model."""
+    rng = np.random.default_rng(80 + splice_p)
+    pairs = []
+    for k in range(40):
+        m = int(rng.integers(20, 260))
+        prot = synth.random_protein(rng, m)
+        lens = [int(rng.integers(40, 700)) for _ in range(int(rng.integers(1, 4)))]
+        if k % 2 == 0:
+            region, _ = synth.gen.plant_gene(rng, prot, float(rng.uniform(0.05, 0.3)), int(rng.integers(0, 2)),
+                                             lens, int(rng.integers(0, 200)), int(rng.integers(0, 200)), 0.45)
+        else:
+            # introns whose ends are neither GT nor AG
+            cds = synth.reverse_translate(rng, prot)
+            cuts = sorted(int(x) for x in rng.choice(np.arange(1, len(cds)), size=len(lens), replace=False))
+            pieces, prev = [synth.random_dna(rng, int(rng.integers(0, 200)))], 0
+            for cut, L in zip(cuts, lens):
+                ends = [str(x) for x in rng.choice(["CA", "TC", "AA", "CC", "TT"], size=2)]
+                pieces += [cds[prev:cut], ends[0] + synth.random_dna(rng, L - 4) + ends[1]]
+                prev = cut
+            pieces += [cds[prev:], synth.random_dna(rng, int(rng.integers(0, 200)))]
+            region = "".join(pieces)
+        strand = 1
+        if rng.random() < 0.5:
+            region, strand = synth.revcomp(region), -1
+        pairs.append(synth.Pair(prot, region, strand))
+    prot = "".join("W" if rng.random() < 0.9 else "C" for _ in range(3200))
+    cds = synth.reverse_translate(rng, prot)
+    pairs.append(synth.Pair(prot, synth.random_dna(rng, 60) + cds[:4800] + "GTAAGT" + synth.random_dna(rng, 120) +
+                            "TAG" + cds[4800:] + synth.random_dna(rng, 40), 1))
+    params = mp.mp_dp_default_params(splice_model=mp.MP_SPLICE_SIMPLE, splice_p=splice_p)
+    c = mp.mp_dp_init(params, 0)
+    try:
+        got = mp.mp_dp_align_batch(c, pairs)
+        got2 = mp.mp_dp_align_batch(c, pairs)             # graph replay
+    finally:
+        mp.mp_dp_destroy(c)
+    assert got[-1]["status"] & 1                          # re-run in int32
+    _compare(orc, pairs, got, _orc_params(orc, params))
+    assert [{k: g[k] for k in KEYS} for g in got2] == [{k: g[k] for k in KEYS} for g in got]
 
 
 def test_serving_alone_and_in_mix(mp, ctx):
