@@ -85,16 +85,32 @@ inline int host_aa_code(unsigned char c) { return kAACode.v[c]; }
 
 // Upper bound of any H of the pair: every residue scores at most its best
 // substitution and every other term of Eq. 7 is a penalty.
-inline int64_t score_bound(const ScoreParams &sp, const char *prot, uint32_t m)
-{
+// Per residue code, the best score any codon can earn against it (at least
+// 0), and the largest of these: the table behind score_bound.
+struct BoundTable {
     int best[22];
-    for (int pc = 0; pc < 22; ++pc) {
-        int b = -sp.stop;
-        for (int t = 0; t < 20; ++t) b = std::max<int>(b, sp.mat[t][pc]);
-        best[pc] = std::max(b, 0);
+    int top;
+    explicit BoundTable(const ScoreParams &sp)
+    {
+        top = 0;
+        for (int pc = 0; pc < 22; ++pc) {
+            int b = -sp.stop;
+            for (int t = 0; t < 20; ++t) b = std::max<int>(b, sp.mat[t][pc]);
+            best[pc] = std::max(b, 0);
+            top = std::max(top, best[pc]);
+        }
     }
+};
+
+// An upper bound of the pair's local score: the sum over residues of their
+// best codon score.  Proteins too short to reach `limit` even at the
+// largest per-residue score are not scanned (the returned bound is then
+// m * top, below the limit).
+inline int64_t score_bound(const BoundTable &bt, const char *prot, uint32_t m, int64_t limit)
+{
+    if (static_cast<int64_t>(m) * bt.top < limit) return static_cast<int64_t>(m) * bt.top;
     int64_t s = 0;
-    for (uint32_t k = 0; k < m; ++k) s += best[host_aa_code(static_cast<unsigned char>(prot[k]))];
+    for (uint32_t k = 0; k < m; ++k) s += bt.best[host_aa_code(static_cast<unsigned char>(prot[k]))];
     return s;
 }
 
@@ -670,6 +686,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     b->cells = 0;
     b->code_bytes_total = 0;
     // ---- layout
+    const BoundTable bt(c->sp);
     uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0, nrec = 0;
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
@@ -698,7 +715,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         strips += d.n_strips;
         if (q.flags & MP_PAIR_SCORE_ONLY) d.flags |= PF_SCORE_ONLY;
         if (q.prot_len == 0 || q.nt_len == 0) d.flags |= PF_SKIP;
-        if (c->params.force_int32 || (q.prot_len && score_bound(c->sp, q.prot, q.prot_len) >= kOverflowT))
+        if (c->params.force_int32 || (q.prot_len && score_bound(bt, q.prot, q.prot_len, kOverflowT) >= kOverflowT))
             d.flags |= PF_WIDE;
         b->nt_len[k] = q.nt_len;
         b->strand[k] = q.strand;
@@ -740,8 +757,9 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         gather(0, n);
     }
     cudaStream_t st = c->stream;
+    // the sequences travel while the host plans the waves (plan_waves waits
+    // for the stream before it returns, so the staging buffer is free again)
     CK(cudaMemcpyAsync(b->ascii.p, c->staging.p, asc, cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
     // ---- the batch's shape class and the wave plan its configuration asks for
     b->needs_waves = plan_code_bytes(c, b) > c->budget;
     b->shape_key = shape_key_of(*b);
@@ -1364,6 +1382,7 @@ static void serve_loop(mp_dp_ctx *c)
             }
         }
         // admit queued requests into free slots
+        const BoundTable bt(c->sp);
         for (auto &s : slots) {
             if (s.busy || !init_ok) continue;
             take.clear();
@@ -1375,7 +1394,7 @@ static void serve_loop(mp_dp_ctx *c)
                     const uint64_t cb = (r.flags & MP_PAIR_SCORE_ONLY)
                                             ? 0
                                             : code_bytes(r.prot.size(), r.nt.size(),
-                                                         score_bound(c->sp, r.prot.data(), r.prot.size()) >= kOverflowT);
+                                                         score_bound(bt, r.prot.data(), r.prot.size(), kOverflowT) >= kOverflowT);
                     if (!take.empty() && bytes + cb > c->slot_budget) break;
                     bytes += cb;
                     take.push_back(std::move(c->queue.front()));
@@ -1434,8 +1453,10 @@ extern "C" int mp_dp_submit(mp_dp_ctx *c, const mp_pair *q, uint64_t *ticket)
         return MP_EINVAL;
     std::unique_lock<std::mutex> lk(c->mu);
     if (c->slot_budget == 0) c->slot_budget = c->budget / static_cast<uint64_t>(c->n_slots);
+    const BoundTable bt(c->sp);
     if (!(q->flags & MP_PAIR_SCORE_ONLY) &&
-        code_bytes(q->prot_len, q->nt_len, score_bound(c->sp, q->prot, q->prot_len) >= kOverflowT) > c->slot_budget)
+        code_bytes(q->prot_len, q->nt_len, score_bound(bt, q->prot, q->prot_len, kOverflowT) >= kOverflowT) >
+            c->slot_budget)
         return MP_EBUDGET;
     if (c->stopping) return MP_ESTATE;
     if (c->queue.size() >= c->ring_cap) return MP_EAGAIN;
