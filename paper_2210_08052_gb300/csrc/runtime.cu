@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
@@ -500,26 +501,29 @@ static uint64_t plan_code_bytes(const mp_dp_ctx *c, const mp_dp_batch *b)
 static void interleave_items(const mp_dp_ctx *c, mp_dp_batch *b)
 {
     const double warps = static_cast<double>(c->num_sms) * 2 * kWarpsPerCta;
-    std::vector<std::pair<double, uint2>> keyed;
+    std::vector<uint32_t> key, count;
+    std::vector<uint2> out;
     auto segment = [&](uint32_t lo, uint32_t hi) {
         if (hi - lo < 2) return;
         double chunks = 0;
         for (uint32_t k = lo; k < hi; ++k)
             chunks += static_cast<double>((b->desc[b->h_items[k].x].nt_len + kStripW - 1 + kChunk - 1) / kChunk);
-        const double D = std::max(1.0, 2.0 * warps / (chunks / (hi - lo)));
-        keyed.clear();
-        uint32_t rank = 0;
+        const uint32_t D = static_cast<uint32_t>(std::max(1.0, std::round(2.0 * warps / (chunks / (hi - lo)))));
+        // key = rank of the pair + D * strip; a stable counting sort by key
+        key.resize(hi - lo);
+        uint32_t rank = 0, top = 0;
         for (uint32_t k = lo; k < hi; ++k) {
             const uint2 it = b->h_items[k];
             if (k > lo && it.x != b->h_items[k - 1].x) ++rank;
-            const double key = rank + it.y * D;
-            keyed.emplace_back(key, it);
+            key[k - lo] = rank + it.y * D;
+            top = std::max(top, key[k - lo]);
         }
-        std::stable_sort(keyed.begin(), keyed.end(),
-                         [](const std::pair<double, uint2> &x, const std::pair<double, uint2> &y) {
-                             return x.first < y.first;
-                         });
-        for (uint32_t k = lo; k < hi; ++k) b->h_items[k] = keyed[k - lo].second;
+        count.assign(static_cast<size_t>(top) + 2, 0);
+        for (uint32_t k = 0; k < hi - lo; ++k) ++count[key[k] + 1];
+        for (size_t v = 1; v < count.size(); ++v) count[v] += count[v - 1];
+        out.resize(hi - lo);
+        for (uint32_t k = 0; k < hi - lo; ++k) out[count[key[k]]++] = b->h_items[lo + k];
+        std::copy(out.begin(), out.end(), b->h_items.begin() + lo);
     };
     for (const Wave &w : b->waves) {
         segment(w.ibegin, w.ibegin + w.nwide_items);
