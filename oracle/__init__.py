@@ -185,6 +185,43 @@ def rescore(prot: str, nt: str, strand: int, prot_st: int, nt_st_aligned: int, c
     return s, pe.value, te.value
 
 
+def exon_sequence(nt: str, strand: int, res: dict) -> str:
+    """The genome an alignment covers with its introns cut out, in the
+    aligned orientation (Methods, "Avoiding pseudogenes": the translated
+    coding region without introns).  Codons (M, D) and frameshift bases
+    (F, G) are kept; an N intron is dropped; a U or V intron is dropped but
+    the split codon's 3 bases around it are kept."""
+    t = nt.upper() if strand > 0 else revcomp(nt)
+    i = res["nt_st"] if strand > 0 else len(nt) - res["nt_en"]
+    out = []
+    for op, n in res["cigar"]:
+        if op in "MD":
+            out.append(t[i:i + 3 * n]); i += 3 * n
+        elif op in "FG":
+            out.append(t[i:i + n]); i += n
+        elif op == "N":
+            i += n
+        elif op == "U":
+            out.append(t[i:i + 1]); out.append(t[i + 1 + n:i + 3 + n]); i += n + 3
+        elif op == "V":
+            out.append(t[i:i + 2]); out.append(t[i + 2 + n:i + 3 + n]); i += n + 3
+    return "".join(out)
+
+
+def exon_score(prot: str, nt: str, strand: int = 1, params: Params | None = None, res: dict | None = None) -> int:
+    """Pseudogene-aware score (Methods, "Avoiding pseudogenes"): the local DP
+    score of the protein against the alignment's coding region without
+    introns, less the intron cost r when the alignment has no intron.  An
+    alignment of score 0 (none) keeps 0."""
+    p = params if params is not None else make_params()
+    r = res if res is not None else align(prot, nt, strand, p)
+    if r["score"] <= 0 or not r["cigar"]:
+        return r["score"]
+    s2 = align(prot, exon_sequence(nt, strand, r), 1, p)["score"]
+    single = not any(op in "NUV" for op, _ in r["cigar"])
+    return s2 - (p.r if single else 0)
+
+
 def encode_cigar(ops) -> list:
     """[(letter, len), ...] -> packed op words (len << 4 | code)."""
     return [(int(n) << 4) | OP_NAMES.index(c) for c, n in ops]

@@ -378,6 +378,37 @@ def test_hand_single_intron(orc, phase, op):
         assert r["cigar"] == [("M", 20), (op, len(intron)), ("M", 19)]
 
 
+# ------------------------------------------------------- pseudogenes
+
+@pytest.mark.parametrize("phase", [0, 1, 2])
+def test_exon_sequence_rebuilds_the_cds(orc, phase):
+    """For an exact spliced copy the alignment's coding region without
+    introns is the coding sequence itself (split codon kept for phases 1, 2),
+    on either strand."""
+    rng = random.Random(60 + phase)
+    prot, nt, intron = _intron_case(rng, phase)
+    cds = nt.replace(intron, "")
+    for strand, t in ((1, nt), (-1, orc.revcomp(nt))):
+        r = orc.align(prot, t, strand)
+        assert orc.exon_sequence(t, strand, r) == cds
+
+
+def test_exon_score_prefers_the_spliced_gene(orc):
+    """Avoiding pseudogenes: against its spliced gene a protein pays the
+    intron in the DP score but not in the exon score; against an unspliced
+    copy (a processed pseudogene) the exon score pays r once more."""
+    rng = random.Random(64)
+    prot, gene, intron = _intron_case(rng, 0)
+    pseudo = gene.replace(intron, "")
+    diag = _diag_sum(orc, prot)
+    rg, rp = orc.align(prot, gene), orc.align(prot, pseudo)
+    assert rg["score"] == diag - 29 and rp["score"] == diag            # the DP favours the pseudogene
+    assert orc.exon_score(prot, gene) == diag                             # intron-free region: Σ diag
+    assert orc.exon_score(prot, pseudo) == diag - 29                      # single exon pays r
+    assert orc.exon_score(prot, gene) > orc.exon_score(prot, pseudo)
+    assert orc.exon_score("WWWW", "AAAAAAAAAAAA") == 0                    # no alignment
+
+
 # ---------------------------------------------------------------- ties
 
 def test_best_cell_tie_smallest_i(orc):
