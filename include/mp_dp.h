@@ -108,7 +108,8 @@ typedef struct {
                                   configuration yet runs mp_dp_autotune on it first */
     int32_t splice_p;          /* MP_SPLICE_SIMPLE: cost p of a donor without GT or an acceptor
                                   without AG (0..1000; the paper gives no value; default 30) */
-    int32_t reserved[2];
+    int32_t exon_rescore;      /* 1: mp_dp_align_batch also fills mp_result.exon_score */
+    int32_t reserved[1];
 } mp_dp_params;
 
 /* One alignment request.  prot: ASCII amino acids; nt: ASCII A/C/G/T
@@ -133,6 +134,9 @@ typedef struct {
     int32_t prot_st, prot_en;  /* 0-based half-open on the protein */
     int32_t nt_st, nt_en;      /* 0-based half-open on the input's forward strand */
     uint32_t n_cigar;
+    int32_t exon_score;        /* pseudogene-aware score (Methods, "Avoiding pseudogenes"): set by
+                                  mp_dp_exon_rescore (or mp_dp_align_batch with
+                                  params.exon_rescore); otherwise equal to score */
     const uint32_t *cigar;
 } mp_result;
 
@@ -240,6 +244,19 @@ int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *d_prot, uin
 
 /* Static string for a return code. */
 const char *mp_dp_strerror(int code);
+
+/* Pseudogene-aware rescoring (Methods, "Avoiding pseudogenes").  An
+ * unspliced pseudogene of a spliced gene can outscore the gene because it
+ * pays no intron costs.  For every result that carries a CIGAR, this runs
+ * the local DP of the pair's protein against the alignment's coding region
+ * with the introns cut out (codons, frameshift bases and the split codon of
+ * a phase-1/2 intron kept, in the aligned orientation) and sets exon_score
+ * to that score, less the intron cost r when the alignment has no intron.
+ * Results without a CIGAR keep exon_score = score.  results must come from
+ * aligning these pairs with this context (same order, CIGARs still valid);
+ * the rescoring runs on the GPU as a score-only batch of its own and does
+ * not disturb the CIGARs.  MP_ESTATE while the serving loop runs. */
+int mp_dp_exon_rescore(mp_dp_ctx *ctx, const mp_pair *pairs, size_t n, mp_result *results);
 
 /* Counters of the last mp_dp_batch_run / mp_dp_align_batch on the context.
  * Kernel times come from CUDA events recorded on the context's stream

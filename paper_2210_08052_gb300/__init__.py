@@ -29,7 +29,7 @@ EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_ba
             "mp_dp_submit", "mp_dp_poll", "mp_dp_wait_any", "mp_dp_destroy", "mp_dp_strerror",
             "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats",
             "mp_dp_score_pair_noalloc", "mp_dp_autotune", "mp_dp_set_tuning", "mp_dp_get_tuning",
-            "mp_dp_tuning_save", "mp_dp_tuning_load"]
+            "mp_dp_tuning_save", "mp_dp_tuning_load", "mp_dp_exon_rescore"]
 
 
 class mp_dp_params(ctypes.Structure):
@@ -40,7 +40,7 @@ class mp_dp_params(ctypes.Structure):
                 ("tb_budget_bytes", ctypes.c_uint64), ("force_int32", ctypes.c_int32),
                 ("max_pairs_per_launch", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
                 ("debug_flags", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("splice_p", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("splice_p", ctypes.c_int32), ("exon_rescore", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class mp_pair(ctypes.Structure):
@@ -53,7 +53,8 @@ class mp_result(ctypes.Structure):
     _fields_ = [("score", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("prot_st", ctypes.c_int32), ("prot_en", ctypes.c_int32),
                 ("nt_st", ctypes.c_int32), ("nt_en", ctypes.c_int32),
-                ("n_cigar", ctypes.c_uint32), ("cigar", ctypes.POINTER(ctypes.c_uint32))]
+                ("n_cigar", ctypes.c_uint32), ("exon_score", ctypes.c_int32),
+                ("cigar", ctypes.POINTER(ctypes.c_uint32))]
 
 
 class mp_dp_stats(ctypes.Structure):
@@ -117,6 +118,7 @@ def lib():
             "mp_dp_set_tuning": (ctypes.c_int, [vp, P(mp_dp_tuning)]),
             "mp_dp_get_tuning": (ctypes.c_int, [vp, vp, P(mp_dp_tuning)]),
             "mp_dp_tuning_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+            "mp_dp_exon_rescore": (ctypes.c_int, [vp, P(mp_pair), ctypes.c_size_t, P(mp_result)]),
             "mp_dp_tuning_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
         }
         for name, (res, args) in sig.items():
@@ -196,7 +198,7 @@ def result_dict(r: mp_result) -> dict:
     cig = [(OP_NAMES[r.cigar[k] & 0xF], r.cigar[k] >> 4) for k in range(r.n_cigar)] if r.n_cigar else []
     raw = [r.cigar[k] for k in range(r.n_cigar)] if r.n_cigar else []
     return dict(score=r.score, status=r.status, prot_st=r.prot_st, prot_en=r.prot_en,
-                nt_st=r.nt_st, nt_en=r.nt_en, cigar=cig, cigar_raw=raw)
+                nt_st=r.nt_st, nt_en=r.nt_en, cigar=cig, cigar_raw=raw, exon_score=r.exon_score)
 
 
 # ------------------------------------------------------------- C-ABI mirror
@@ -263,7 +265,7 @@ def _results(res, n, raw):
         return [result_dict(res[k]) for k in range(n)]
     buf = np.frombuffer(res, dtype=np.dtype([("score", "<i4"), ("status", "<i4"), ("prot_st", "<i4"),
                                              ("prot_en", "<i4"), ("nt_st", "<i4"), ("nt_en", "<i4"),
-                                             ("n_cigar", "<u4"), ("pad", "<u4"), ("cigar", "<u8")]),
+                                             ("n_cigar", "<u4"), ("exon_score", "<i4"), ("cigar", "<u8")]),
                         count=n)
     return buf.copy()
 
@@ -380,6 +382,24 @@ def mp_dp_tuning_save(ctx, path: str) -> None:
 
 def mp_dp_tuning_load(ctx, path: str) -> None:
     _check(lib().mp_dp_tuning_load(ctx, os.fsencode(path)), "mp_dp_tuning_load")
+
+
+def mp_dp_exon_rescore(ctx, pairs, results) -> list:
+    """Pseudogene-aware scores of alignments (result dicts from aligning the
+    same pairs with this context).  Returns the exon_score of each pair."""
+    pa = pairs if isinstance(pairs, _PairArray) else _PairArray(pairs)
+    res = (mp_result * max(pa.n, 1))()
+    keep = []
+    for k, r in enumerate(results):
+        for key in ("score", "status", "prot_st", "prot_en", "nt_st", "nt_en"):
+            setattr(res[k], key, int(r[key]))
+        raw = (ctypes.c_uint32 * max(1, len(r["cigar_raw"])))(*r["cigar_raw"])
+        keep.append(raw)
+        res[k].n_cigar = len(r["cigar_raw"])
+        res[k].cigar = ctypes.cast(raw, ctypes.POINTER(ctypes.c_uint32))
+        res[k].exon_score = int(r["score"])
+    _check(lib().mp_dp_exon_rescore(ctx, pa.arr, pa.n, res), "mp_dp_exon_rescore")
+    return [res[k].exon_score for k in range(pa.n)]
 
 
 def mp_dp_num_sms(ctx) -> int:

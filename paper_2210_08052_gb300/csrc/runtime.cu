@@ -261,6 +261,7 @@ struct mp_dp_ctx {
     mp_dp_stats stats{};
     mp_dp_batch *last = nullptr;   // batch of the last run (for its counters)
     mp_dp_batch *own = nullptr;    // buffers reused by mp_dp_align_batch from call to call
+    mp_dp_batch *aux = nullptr;    // score-only batch of mp_dp_exon_rescore
     std::vector<uint32_t> host_cig;
     // launch configuration: fixed by mp_dp_set_tuning, else tuned per shape class
     bool has_fixed = false;
@@ -1272,6 +1273,7 @@ int mp_dp_batch_download(mp_dp_ctx *c, mp_dp_batch *b, mp_result *out)
         if (o.status & MP_ST_RERUN) ++nrerun;
         if ((o.status & MP_ST_ERRMASK) & ~MP_ST_BUDGET) continue;
         r.score = o.score > 0 ? o.score : 0;
+        r.exon_score = r.score;
         const int32_t tn = static_cast<int32_t>(d.nt_len);
         if (r.score <= 0) continue;
         const bool score_only = (d.flags & (PF_SCORE_ONLY | PF_BUDGET)) != 0;
@@ -1306,8 +1308,101 @@ int mp_dp_align_batch(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *o
     rc = mp_dp_batch_run(c, b);
     if (rc == MP_OK) rc = mp_dp_batch_sync(c);
     if (rc == MP_OK) rc = mp_dp_batch_download(c, b, out);
+    if (rc == MP_OK && c->params.exon_rescore) rc = mp_dp_exon_rescore(c, pairs, n, out);
     c->last = nullptr;
     return rc;
+}
+
+// The genome an alignment covers with its introns cut out, in the aligned
+// orientation: codons and frameshift bases kept, an N intron dropped, a U or
+// V intron dropped with the 3 bases of its split codon kept.  False if the
+// CIGAR runs outside the region.
+static bool exon_region(const mp_pair &q, const mp_result &r, std::string &out)
+{
+    const int32_t n = static_cast<int32_t>(q.nt_len);
+    std::string t(q.nt, q.nt_len);
+    if (q.strand < 0) {
+        std::reverse(t.begin(), t.end());
+        for (char &ch : t) {
+            switch (ch | 0x20) {
+            case 'a': ch = 'T'; break;
+            case 'c': ch = 'G'; break;
+            case 'g': ch = 'C'; break;
+            case 't': ch = 'A'; break;
+            default: return false;
+            }
+        }
+    }
+    int64_t i = q.strand > 0 ? r.nt_st : n - r.nt_en;
+    out.clear();
+    auto take = [&](int64_t len) {
+        if (i < 0 || i + len > n) return false;
+        out.append(t, static_cast<size_t>(i), static_cast<size_t>(len));
+        i += len;
+        return true;
+    };
+    for (uint32_t k = 0; k < r.n_cigar; ++k) {
+        const uint32_t op = r.cigar[k] & 0xf;
+        const int64_t len = r.cigar[k] >> 4;
+        bool ok = true;
+        switch (op) {
+        case MP_OP_M: case MP_OP_D: ok = take(3 * len); break;
+        case MP_OP_I: break;
+        case MP_OP_F: case MP_OP_G: ok = take(len); break;
+        case MP_OP_N: i += len; break;
+        case MP_OP_U: ok = take(1); i += len; ok = ok && take(2); break;
+        case MP_OP_V: ok = take(2); i += len; ok = ok && take(1); break;
+        default: ok = false;
+        }
+        if (!ok || i > n) return false;
+    }
+    return true;
+}
+
+int mp_dp_exon_rescore(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *res)
+{
+    if (!c || (n && (!pairs || !res))) return MP_EINVAL;
+    if (c->server_running) return MP_ESTATE;
+    std::vector<std::string> seqs;
+    std::vector<size_t> idx;
+    std::vector<char> intron;
+    for (size_t k = 0; k < n; ++k) {
+        const mp_result &r = res[k];
+        if (r.score <= 0 || !r.n_cigar || !r.cigar || (r.status & MP_ST_ERRMASK)) continue;
+        std::string s;
+        if (!exon_region(pairs[k], r, s)) continue;
+        bool has_intron = false;
+        for (uint32_t j = 0; j < r.n_cigar; ++j) {
+            const uint32_t op = r.cigar[j] & 0xf;
+            has_intron |= op == MP_OP_N || op == MP_OP_U || op == MP_OP_V;
+        }
+        seqs.push_back(std::move(s));
+        idx.push_back(k);
+        intron.push_back(has_intron ? 1 : 0);
+    }
+    if (idx.empty()) return MP_OK;
+    std::vector<mp_pair> sub(idx.size());
+    for (size_t i = 0; i < idx.size(); ++i) {
+        const mp_pair &q = pairs[idx[i]];
+        sub[i] = mp_pair{q.prot, q.prot_len, seqs[i].data(), static_cast<uint32_t>(seqs[i].size()), 1,
+                         MP_PAIR_SCORE_ONLY};
+    }
+    if (!c->aux) c->aux = new (std::nothrow) mp_dp_batch();
+    if (!c->aux) return MP_ENOMEM;
+    mp_dp_batch *b = c->aux;
+    int rc = upload_impl(c, b, sub.data(), sub.size());
+    if (rc == MP_OK) rc = mp_dp_batch_run(c, b);
+    if (rc != MP_OK) return rc;
+    b->h_out.resize(sub.size());
+    CK(cudaMemcpyAsync(b->h_out.data(), b->out.p, sub.size() * sizeof(PairOut), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < idx.size(); ++i) {
+        const PairOut &o = b->h_out[i];
+        if (o.status & MP_ST_ERRMASK) continue;
+        const int32_t s2 = o.score > 0 ? o.score : 0;
+        res[idx[i]].exon_score = s2 - (intron[i] ? 0 : c->params.r);
+    }
+    return MP_OK;
 }
 
 }  // extern "C"
@@ -1575,6 +1670,8 @@ extern "C" void mp_dp_destroy(mp_dp_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->own) mp_dp_batch_free(c, c->own);
+    if (c->aux) mp_dp_batch_free(c, c->aux);
+    c->aux = nullptr;
     c->own = nullptr;
     c->codes.release();
     c->staging.release();

@@ -370,6 +370,40 @@ def test_simple_splice_model(mp, orc, splice_p):
     assert [{k: g[k] for k in KEYS} for g in got2] == [{k: g[k] for k in KEYS} for g in got]
 
 
+def test_exon_rescore(mp, ctx, orc):
+    """Pseudogene-aware scores: spliced genes, their processed (intron-free)
+    copies, both strands, and pairs without an alignment; the library's
+    exon_score equals the oracle's, from mp_dp_align_batch with
+    params.exon_rescore and from mp_dp_exon_rescore on earlier results."""
+    rng = np.random.default_rng(90)
+    pairs = _gene_pairs(91, 24, 300, 900)
+    for k in range(8):
+        prot = synth.random_protein(rng, int(rng.integers(40, 300)))
+        cds_only, _ = synth.gen.plant_gene(rng, prot, float(rng.uniform(0.05, 0.3)), 0, [],
+                                           int(rng.integers(0, 200)), int(rng.integers(0, 200)), 0.45)
+        strand = 1 if k % 2 == 0 else -1
+        pairs.append(synth.Pair(prot, cds_only if strand > 0 else synth.revcomp(cds_only), strand))
+    pairs.append(synth.Pair("WWWWWW", "A" * 60, 1))
+    want = [orc.exon_score(p.prot, p.nt, p.strand) for p in pairs]
+    c = mp.mp_dp_init(mp.mp_dp_default_params(exon_rescore=1), 0)
+    try:
+        got = mp.mp_dp_align_batch(c, pairs)
+        got2 = mp.mp_dp_align_batch(c, pairs)
+    finally:
+        mp.mp_dp_destroy(c)
+    assert [g["exon_score"] for g in got] == want
+    assert [g["exon_score"] for g in got2] == want
+    _compare(orc, pairs[:6], got[:6])                     # the alignments themselves are untouched
+    plain = mp.mp_dp_align_batch(ctx, pairs)
+    assert [g["exon_score"] for g in plain] == [g["score"] for g in plain]
+    assert mp.mp_dp_exon_rescore(ctx, pairs, plain) == want
+    # a single-exon alignment is also the best one inside its own region: its
+    # exon score is its score less r
+    for k in range(24, 32):
+        assert got[k]["score"] == 0 or (not any(op in "NUV" for op, _ in got[k]["cigar"]) and
+                                        want[k] == got[k]["score"] - 29)
+
+
 def test_serving_alone_and_in_mix(mp, ctx):
     """Each request's result is the same served alone, in a burst with
     others in flight, and from the batch call."""
