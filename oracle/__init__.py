@@ -67,7 +67,7 @@ class Params(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("e", ctypes.c_int32), ("f", ctypes.c_int32),
                 ("r", ctypes.c_int32), ("stop", ctypes.c_int32),
                 ("mat", (ctypes.c_int32 * 22) * 22),
-                ("splice_model", ctypes.c_int32), ("splice_p", ctypes.c_int32)]
+                ("splice_model", ctypes.c_int32), ("splice_p", ctypes.c_int32), ("mode", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -81,11 +81,13 @@ class Result(ctypes.Structure):
 DEFAULTS = dict(q=11, e=1, f=23, r=29, stop=23)
 
 
-def make_params(q=None, e=None, f=None, r=None, stop=None, mat=None, splice_model=0, splice_p=30) -> Params:
+def make_params(q=None, e=None, f=None, r=None, stop=None, mat=None, splice_model=0, splice_p=30,
+                mode=0) -> Params:
     """Scoring parameters; splice_model 0 is the final model, 1 the simple
-    GT-AG model with cost splice_p."""
+    GT-AG model with cost splice_p; mode 0 local, 1 global (cell (0, 0) to
+    (|T|, |P|)), 2 extension (from (0, 0), ending anywhere)."""
     p = Params()
-    p.splice_model, p.splice_p = splice_model, splice_p
+    p.splice_model, p.splice_p, p.mode = splice_model, splice_p, mode
     d = dict(DEFAULTS)
     for k, v in (("q", q), ("e", e), ("f", f), ("r", r), ("stop", stop)):
         if v is not None:

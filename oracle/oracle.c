@@ -48,6 +48,8 @@ typedef struct {
     int32_t mat[22][22];        /* [translated aa][protein residue], ORC_AA order */
     int32_t splice_model;       /* 0: the final model; 1: the simple GT-AG model */
     int32_t splice_p;           /* simple model: cost p of a donor without GT / acceptor without AG */
+    int32_t mode;               /* 0 local; 1 global (from cell (0,0) to (|T|,|P|)); 2 extension
+                                   (from (0,0), ending anywhere) */
 } orc_params;
 
 typedef struct {
@@ -198,7 +200,7 @@ static int32_t afun(const dp_t *dp, int x) { return splice_a(dp->p, dp->T, dp->n
 static void h_terms(const dp_t *dp, int i, int j, int32_t t[10])
 {
     const orc_params *p = dp->p;
-    t[0] = (i >= 3) ? getH(dp, i - 3, j - 1) + subst(dp, i, j) : ORC_NEG_INF;
+    t[0] = (i >= 3 && j >= 1) ? getH(dp, i - 3, j - 1) + subst(dp, i, j) : ORC_NEG_INF;
     t[1] = dp->I[IDX(dp, i, j)];
     t[2] = dp->D[IDX(dp, i, j)];
     t[3] = getH(dp, i - 1, j - 1) - p->f;
@@ -210,11 +212,45 @@ static void h_terms(const dp_t *dp, int i, int j, int32_t t[10])
     t[9] = dp->C[IDX(dp, i, j)] - afun(dp, i - 1);
 }
 
+/* Fill all six matrices by Eq. 7 in global or extension mode: the path
+ * starts at cell (0, 0) (H = 0, every other state -inf there), so row 0 and
+ * column 0 follow the recurrence too (row 0 only through I, column 0
+ * through D, G and the phase-0 intron state A), and H has no restart. */
+static void fill_anchored(dp_t *dp)
+{
+    const orc_params *p = dp->p;
+    int n = dp->n, m = dp->m;
+    for (int i = 0; i <= n; ++i) {
+        for (int j = 0; j <= m; ++j) {
+            size_t c = IDX(dp, i, j);
+            if (i == 0 && j == 0) {
+                dp->H[c] = 0;
+                dp->I[c] = dp->D[c] = dp->A[c] = dp->B[c] = dp->C[c] = ORC_NEG_INF;
+                continue;
+            }
+            dp->I[c] = j >= 1 ? max2(getH(dp, i, j - 1) - p->q, getS(dp, dp->I, i, j - 1)) - p->e : ORC_NEG_INF;
+            dp->D[c] = max2(getH(dp, i - 3, j) - p->q, getS(dp, dp->D, i - 3, j)) - p->e;
+            dp->A[c] = max2(getH(dp, i - 1, j) - p->r - dfun(dp, i - 1), getS(dp, dp->A, i - 1, j));
+            dp->B[c] = max2(getH(dp, i - 1, j - 1) - p->r - dfun(dp, i), getS(dp, dp->B, i - 1, j));
+            dp->C[c] = max2(getH(dp, i - 1, j - 1) - p->r - dfun(dp, i + 1), getS(dp, dp->C, i - 1, j));
+            int32_t t[10];
+            h_terms(dp, i, j, t);
+            int32_t h = t[0];
+            for (int k = 1; k < 10; ++k) h = max2(h, t[k]);
+            dp->H[c] = h;
+        }
+    }
+}
+
 /* Fill all six matrices by Eq. 7 (local mode). */
 static void fill(dp_t *dp)
 {
     const orc_params *p = dp->p;
     int n = dp->n, m = dp->m;
+    if (p->mode != 0) {
+        fill_anchored(dp);
+        return;
+    }
     for (int j = 0; j <= m; ++j) {
         dp->H[IDX(dp, 0, j)] = 0;
         dp->I[IDX(dp, 0, j)] = dp->D[IDX(dp, 0, j)] = ORC_NEG_INF;
@@ -262,10 +298,11 @@ static int traceback(const dp_t *dp, int bi, int bj, oplist *L, int *si, int *sj
 {
     const orc_params *p = dp->p;
     int i = bi, j = bj, degenerate = 0;
+    const int anchored = p->mode != 0;               /* global / extension: the path ends at (0, 0) */
     for (;;) {
-        if (i <= 0 || j <= 0) break;                 /* row/column 0: H = 0 */
+        if (anchored ? (i == 0 && j == 0) : (i <= 0 || j <= 0)) break;   /* local: row/column 0 hold H = 0 */
         int32_t h = dp->H[IDX(dp, i, j)];
-        if (h == 0) break;                           /* restart wins ties at 0 */
+        if (!anchored && h == 0) break;              /* restart wins ties at 0 */
         int32_t t[10];
         h_terms(dp, i, j, t);
         int src = -1;
@@ -357,15 +394,22 @@ int orc_align(const orc_params *p, const char *prot, int32_t plen, const char *n
     dp.A = buf + 3 * cells; dp.B = buf + 4 * cells; dp.C = buf + 5 * cells;
     fill(&dp);
 
-    /* best cell: largest H, then smallest i, then smallest j */
+    /* best cell: largest H, then smallest i, then smallest j (local: over
+     * cells after a residue and a base; extension: over every cell, (0, 0)
+     * with H = 0 included); global: the cell (|T|, |P|) */
     int32_t best = 0;
     int bi = 0, bj = 0;
-    for (int i = 1; i <= tlen; ++i)
-        for (int j = 1; j <= plen; ++j)
-            if (dp.H[IDX(&dp, i, j)] > best) { best = dp.H[IDX(&dp, i, j)]; bi = i; bj = j; }
+    if (p->mode == 1) {
+        bi = tlen; bj = plen;
+        best = dp.H[IDX(&dp, tlen, plen)];
+    } else {
+        for (int i = p->mode == 2 ? 0 : 1; i <= tlen; ++i)
+            for (int j = p->mode == 2 ? 0 : 1; j <= plen; ++j)
+                if (dp.H[IDX(&dp, i, j)] > best) { best = dp.H[IDX(&dp, i, j)]; bi = i; bj = j; }
+    }
 
     res->score = best;
-    if (best > 0) {
+    if (best > 0 || p->mode == 1) {
         uint32_t *rev = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
         oplist L = {rev, 0, cap, 0};
         int si = 0, sj = 0;

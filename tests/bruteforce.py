@@ -112,6 +112,29 @@ def segment_best(pb: Problem) -> int:
     return max(max(row) for row in best)
 
 
+NEG = float("-inf")
+
+
+def anchored_best(pb: Problem, mode: str) -> int:
+    """Best score of a path from cell (0, 0): ending at (n, m) ("global") or
+    anywhere, the empty path included ("extend").  A Bellman recursion over
+    whole operations, with unreachable cells at -inf."""
+    n, m = pb.n, pb.m
+    best = [[NEG] * (m + 1) for _ in range(n + 1)]
+    best[0][0] = 0
+    for i in range(n + 1):
+        for j in range(m + 1):
+            b = best[i][j]
+            if b == NEG:
+                continue
+            for _, _, di, dj, c in pb.ops_from(i, j):
+                if b + c > best[i + di][j + dj]:
+                    best[i + di][j + dj] = b + c
+    if mode == "global":
+        return best[n][m]
+    return max(max(row) for row in best)
+
+
 def all_paths(pb: Problem, limit: int = 2_000_000):
     """Every (start, ops, end, score) path, by exhaustive depth-first walk."""
     out = []

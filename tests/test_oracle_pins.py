@@ -378,6 +378,72 @@ def test_hand_single_intron(orc, phase, op):
         assert r["cigar"] == [("M", 20), (op, len(intron)), ("M", 19)]
 
 
+# ------------------------------------------- global and extension modes
+
+def test_anchored_modes_against_segment_recursion(orc):
+    """Global mode (path from cell (0, 0) to (|T|, |P|)) and extension mode
+    (from (0, 0), ending anywhere): the oracle's score is the best op-sum over
+    paths from (0, 0), with random penalties and both splice models."""
+    rng = random.Random(71)
+    for k in range(150):
+        n, m = rng.randint(0, 14), rng.randint(0, 4)
+        prot, nt, params = _random_case(rng, n, m, valid=True)
+        simple = rng.random() < 0.3
+        sp = dict(splice_p=rng.choice([0, 5, 30])) if simple else {}
+        for mode, name in ((1, "global"), (2, "extend")):
+            want = bf.anchored_best(bf.Problem(prot, nt, **params, **sp), name)
+            got = orc.align(prot, nt, 1, orc.make_params(mode=mode, splice_model=1 if simple else 0, **params, **sp))
+            assert got["score"] == want, (mode, prot, nt, params, sp)
+
+
+def test_anchored_modes_against_enumeration(orc):
+    """The same against every enumerated path from (0, 0) on tiny inputs."""
+    rng = random.Random(72)
+    for _ in range(60):
+        prot, nt, params = _random_case(rng, rng.randint(0, 6), rng.randint(0, 2), valid=True)
+        paths = [p for p in bf.all_paths(bf.Problem(prot, nt, **params)) if p[0] == 0 and p[1] == 0]
+        g = max(p[5] for p in paths if (p[3], p[4]) == (len(nt), len(prot)))
+        x = max(p[5] for p in paths)
+        assert orc.align(prot, nt, 1, orc.make_params(mode=1, **params))["score"] == g
+        assert orc.align(prot, nt, 1, orc.make_params(mode=2, **params))["score"] == x
+
+
+def test_anchored_paths_rescore_and_span(orc):
+    """Anchored alignments start at (0, 0); global ones end at (|T|, |P|);
+    their CIGARs rescore to the score (negative scores included), on both
+    strands."""
+    rng = random.Random(73)
+    for _ in range(40):
+        prot, nt, params = _random_case(rng, rng.randint(3, 40), rng.randint(1, 8), valid=True)
+        for mode in (1, 2):
+            pp = orc.make_params(mode=mode, **params)
+            for strand, t in ((1, nt), (-1, orc.revcomp(nt))):
+                r = orc.align(prot, t, strand, pp)
+                if mode == 2 and r["score"] == 0 and not r["cigar"]:
+                    continue                                  # the empty extension
+                st = 0 if strand > 0 else len(t) - r["nt_en"]
+                assert r["prot_st"] == 0 and (r["nt_st"] == 0 if strand > 0 else r["nt_en"] == len(t))
+                if mode == 1:
+                    assert r["prot_en"] == len(prot) and (r["nt_en"] if strand > 0 else len(t) - r["nt_st"]) == len(t)
+                if r["cigar"]:
+                    sc, pe, te = orc.rescore(prot, t, strand, r["prot_st"], st, r["cigar_raw"], pp)
+                    assert (sc, pe) == (r["score"], r["prot_en"])
+
+
+def test_anchored_exact_cds(orc):
+    """An exact coding sequence: global and extension scores equal the local
+    one (Σ diag); with one extra codon before it, global pays one deletion
+    q + e and extension too (the path must start at the genome's start)."""
+    rng = random.Random(74)
+    prot = _rand_prot(rng, 30)
+    cds = _cds(rng, prot)
+    diag = _diag_sum(orc, prot)
+    for mode in (1, 2):
+        assert orc.align(prot, cds, 1, orc.make_params(mode=mode))["score"] == diag
+        r = orc.align(prot, "CCC" + cds, 1, orc.make_params(mode=mode))
+        assert r["score"] == diag - 12 and r["cigar"] == [("D", 1), ("M", 30)]
+
+
 # ------------------------------------------------------- pseudogenes
 
 @pytest.mark.parametrize("phase", [0, 1, 2])
