@@ -76,7 +76,11 @@ extern "C" {
 #define MP_SPLICE_FINAL 0   /* the final splice model of the "Splice models" section */
 #define MP_SPLICE_SIMPLE 1  /* the simple model defined right after Eq. 7: d(x) = 0 if T[x+1..x+2]
                                is GT, else splice_p; a(x) = 0 if T[x-1..x] is AG, else splice_p */
-#define MP_MODE_LOCAL 0     /* local alignment (the only mode of this version) */
+#define MP_MODE_LOCAL 0     /* local alignment: the path may start and end at any cell */
+#define MP_MODE_GLOBAL 1    /* gap closing between two anchors: the path runs from the start of the
+                               protein and region to both their ends; the score may be negative */
+#define MP_MODE_EXTEND 2    /* extension from an anchor: the path starts at the start of the protein
+                               and region and ends anywhere (score >= 0; 0: the empty extension) */
 
 #define MP_PAIR_SCORE_ONLY 0x1u  /* mp_pair.flags: score and end cell only, no CIGAR */
 #define MP_DEBUG_NO_PUBLISH 0x1  /* mp_dp_params.debug_flags (tests only) */
@@ -94,7 +98,12 @@ typedef struct {
     int32_t q, e, f, r, stop;  /* gap open, gap extend, frameshift, intron, stop codon */
     int8_t mat[22][22];
     int32_t splice_model;      /* MP_SPLICE_FINAL or MP_SPLICE_SIMPLE */
-    int32_t mode;              /* MP_MODE_LOCAL */
+    int32_t mode;              /* MP_MODE_LOCAL, MP_MODE_GLOBAL or MP_MODE_EXTEND.  In the two
+                                  anchored modes the alignment starts at position 0 of the protein
+                                  and of the aligned strand (strand -1: the input's end); in global
+                                  mode every pair keeps its traceback (MP_PAIR_SCORE_ONLY is
+                                  ignored) since the score is read at the end cell.  A pair
+                                  with an empty protein or region scores 0 in every mode */
     uint64_t tb_budget_bytes;  /* device bytes for traceback codes (default 40 GiB, capped
                                   by free device memory at init) */
     int32_t force_int32;       /* 1: skip the packed int16 pass and run every pair in int32 */
@@ -230,7 +239,7 @@ void mp_dp_destroy(mp_dp_ctx *ctx);
  *   stream  CUDA stream (cudaStream_t) to launch on; NULL = default stream
  *
  * Returns MP_ETOOLARGE beyond the size limits, MP_EINVAL for bad arguments
- * or parameters, MP_ECUDA if a CUDA call fails; otherwise MP_OK once the
+ * or parameters (local mode only), MP_ECUDA if a CUDA call fails; otherwise MP_OK once the
  * work is enqueued (the result is ready when the stream reaches it).
  * The first call on a device looks up the scratch address and sets a kernel
  * attribute (once per device, with that device current); make that first

@@ -21,6 +21,7 @@ MP_ECUDA, MP_EPENDING, MP_EAGAIN, MP_ETICKET, MP_ESTATE, MP_ETOOLARGE = -5, -6, 
 MP_ST_RERUN, MP_ST_BADSEQ, MP_ST_BUDGET, MP_ST_TRACE, MP_ST_TIMEOUT, MP_ST_ERRMASK = 0x1, 0x10, 0x20, 0x40, 0x80, 0xF0
 MP_PAIR_SCORE_ONLY = 0x1
 MP_SPLICE_FINAL, MP_SPLICE_SIMPLE = 0, 1
+MP_MODE_LOCAL, MP_MODE_GLOBAL, MP_MODE_EXTEND = 0, 1, 2
 MP_DEBUG_NO_PUBLISH = 0x1
 OP_NAMES = "MIDFGNUV"
 

@@ -152,6 +152,8 @@ struct Ops16 {
 
     struct Consts {
         uint32_t QE, E, F, KF;             // packed q+e, e, f and K - f
+        uint32_t FLOOR;                    // local: biased 0 (the restart); anchored modes: 0 (none)
+        uint32_t ROW0;                     // H in row 0 of the lane's two columns (biased)
     };
     struct State {
         uint32_t H1, H2, H3, L0, L1, L2, L3, IL, D1, D2, D3, A1, B1, C1;
@@ -168,7 +170,24 @@ struct Ops16 {
         c.E = static_cast<uint32_t>(sp.e) | (static_cast<uint32_t>(sp.e) << 16);
         c.F = static_cast<uint32_t>(sp.f) | (static_cast<uint32_t>(sp.f) << 16);
         c.KF = K - c.F;
+        c.FLOOR = sp.mode == MP_MODE_LOCAL ? Z : 0u;
+        c.ROW0 = Z;
         return c;
+    }
+
+    // biased pair [lo, hi] of H values (clamped to the int16 range)
+    static __device__ __forceinline__ uint32_t pack2(int lo, int hi)
+    {
+        lo = min(max(lo, -32768), 32767);
+        hi = min(max(hi, -32768), 32767);
+        return static_cast<uint32_t>(lo + 32768) | (static_cast<uint32_t>(hi + 32768) << 16);
+    }
+    static __device__ __forceinline__ void set_row0(Consts &c, int lo, int hi) { c.ROW0 = pack2(lo, hi); }
+    // boundary entry of column 0 in the anchored modes: [H, I = -inf]
+    static __device__ __forceinline__ Bnd col0_entry(int h)
+    {
+        h = max(h, -16384);
+        return static_cast<uint32_t>(h + 32768) | 0x40000000u;
     }
 
     static __device__ __forceinline__ uint32_t prof_entry(int slo, int shi)
@@ -179,11 +198,13 @@ struct Ops16 {
     // State before step 0: every cell not yet reached is outside the matrix
     // (-inf) except the row-0 cell at ii = -1, where H = 0.  w0 is the
     // boundary entry at ii = 0 (used by lane 0).
+    // h1: H in row 0 of the lane's columns; l1: H in row 0 of the columns to
+    // their left (both biased 0 in local mode)
     static __device__ __forceinline__ void init(State &s, int lane, Bnd w0, uint4 recm1, uint4 recm2,
-                                                uint32_t xm1)
+                                                uint32_t xm1, uint32_t h1, uint32_t l1)
     {
-        s.H1 = Z; s.H2 = NEGV; s.H3 = NEGV;
-        s.L1 = Z; s.L2 = NEGV; s.L3 = NEGV;
+        s.H1 = h1; s.H2 = NEGV; s.H3 = NEGV;
+        s.L1 = l1; s.L2 = NEGV; s.L3 = NEGV;
         s.L0 = (lane == 0) ? ((w0 & 0xffffu) | 0x80000000u) : NEGV;
         s.IL = (lane == 0) ? ((w0 >> 16) | 0x40000000u) : NEGV;
         s.D1 = s.D2 = s.D3 = NEGV;
@@ -225,14 +246,14 @@ struct Ops16 {
         const uint32_t Ap = A0 - VA0;                     // A - a(i)
         const uint32_t Bp = B0 - s.VA2;                   // B - a(i-2)
         const uint32_t Cp = C0 - s.VA1;                   // C - a(i-1)
-        uint32_t H0 = vmax(vmax(vmax(M, I0), vmax(D0, FG)), vmax(vmax(Ap, Bp), vmax(Cp, Z)));
+        uint32_t H0 = vmax(vmax(vmax(M, I0), vmax(D0, FG)), vmax(vmax(Ap, Bp), vmax(Cp, c.FLOOR)));
 
         uint32_t vmask = 0xffffffffu;
         if (MASKED) {
             // cells before row 1 are outside the matrix; ii = -1 is row 0
             const uint32_t kill = (ii < 0 ? 0x0000ffffu : 0u) | (ii < 1 ? 0xffff0000u : 0u);
             const uint32_t row0 = (ii == -1 ? 0x0000ffffu : 0u) | (ii == 0 ? 0xffff0000u : 0u);
-            const uint32_t hforce = (row0 & Z) | (~row0 & NEGV);
+            const uint32_t hforce = (row0 & c.ROW0) | (~row0 & NEGV);
             H0 = (H0 & ~kill) | (hforce & kill);
             I0 = (I0 & ~kill) | (NEGV & kill);
             D0 = (D0 & ~kill) | (NEGV & kill);
@@ -328,6 +349,8 @@ struct Ops32 {
 
     struct Consts {
         int32_t qe, e, f;
+        int32_t floor;                      // local: 0 (the restart); anchored modes: NEG (none)
+        int32_t row0lo, row0hi;             // H in row 0 of the lane's two columns
     };
     struct State {
         V2 H1, H2, H3, L0, L1, L2, L3, IL, D1, D2, D3, A1, B1, C1;
@@ -339,8 +362,12 @@ struct Ops32 {
 
     static __device__ __forceinline__ Consts consts(const ScoreParams &sp)
     {
-        return Consts{sp.q + sp.e, sp.e, sp.f};
+        return Consts{sp.q + sp.e, sp.e, sp.f, sp.mode == MP_MODE_LOCAL ? 0 : NEG, 0, 0};
     }
+
+    static __device__ __forceinline__ V2 pack2(int lo, int hi) { return V2{lo, hi}; }
+    static __device__ __forceinline__ void set_row0(Consts &c, int lo, int hi) { c.row0lo = lo; c.row0hi = hi; }
+    static __device__ __forceinline__ Bnd col0_entry(int h) { return Bnd{h, NEG}; }
 
     static __device__ __forceinline__ uint32_t prof_entry(int slo, int shi)
     {
@@ -348,11 +375,11 @@ struct Ops32 {
     }
 
     static __device__ __forceinline__ void init(State &s, int lane, Bnd w0, uint4 recm1, uint4 recm2,
-                                                uint32_t xm1)
+                                                uint32_t xm1, V2 h1, V2 l1)
     {
         const V2 ng{NEG, NEG};
-        s.H1 = V2{0, 0}; s.H2 = ng; s.H3 = ng;
-        s.L1 = V2{0, 0}; s.L2 = ng; s.L3 = ng;
+        s.H1 = h1; s.H2 = ng; s.H3 = ng;
+        s.L1 = l1; s.L2 = ng; s.L3 = ng;
         s.L0 = (lane == 0) ? V2{w0.h, 0} : ng;
         s.IL = (lane == 0) ? V2{w0.i, NEG} : ng;
         s.D1 = s.D2 = s.D3 = ng;
@@ -388,12 +415,12 @@ struct Ops32 {
         V2 C0 = mx(Copen, s.C1);
         const V2 FG = subc(mx(mx(s.L1, s.L2), mx(s.H1, s.H2)), c.f);
         const V2 Ap = sub(A0, VA0), Bp = sub(B0, s.VA2), Cp = sub(C0, s.VA1);
-        V2 H0 = mx(mx(mx(M, I0), mx(D0, FG)), mx(mx(Ap, Bp), mx(Cp, V2{0, 0})));
+        V2 H0 = mx(mx(mx(M, I0), mx(D0, FG)), mx(mx(Ap, Bp), mx(Cp, V2{c.floor, c.floor})));
 
         bool vlo = true, vhi = true;
         if (MASKED) {
-            if (ii < 0) { H0.lo = (ii == -1) ? 0 : NEG; I0.lo = D0.lo = A0.lo = B0.lo = C0.lo = NEG; }
-            if (ii < 1) { H0.hi = (ii == 0) ? 0 : NEG; I0.hi = D0.hi = A0.hi = B0.hi = C0.hi = NEG; }
+            if (ii < 0) { H0.lo = (ii == -1) ? c.row0lo : NEG; I0.lo = D0.lo = A0.lo = B0.lo = C0.lo = NEG; }
+            if (ii < 1) { H0.hi = (ii == 0) ? c.row0hi : NEG; I0.hi = D0.hi = A0.hi = B0.hi = C0.hi = NEG; }
             vlo = ii >= 0 && ii < n;
             vhi = ii >= 1 && ii <= n;
         }
@@ -542,7 +569,14 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
     const uint32_t *g = a.nt2 + pd.nt_word_off;
     const uint8_t *P = a.prot + pd.prot_off;
     Bnd *bnd = reinterpret_cast<Bnd *>(a.bnd) + pd.bnd_off + kBndPad;   // bnd[ii], ii >= -64
-    const typename Ops::Consts c = Ops::consts(a.sp);
+    typename Ops::Consts c = Ops::consts(a.sp);
+    // anchored modes: row 0 holds H[0][j] = -(q + e j) (an I run from cell
+    // (0, 0)) and column 0 the values of the column-0 array; local: both 0
+    const bool anchored = a.sp.mode != MP_MODE_LOCAL;
+    const int32_t *c0 = anchored ? a.col0 + pd.col0_off : nullptr;      // c0[i] = H[i][0]
+    const int jcol = s * kStripW + 2 * lane + 1;                         // 1-based column of the lo cell
+    auto row0 = [&](int j) { return (!anchored || j == 0) ? 0 : -(a.sp.q + a.sp.e * j); };
+    Ops::set_row0(c, row0(jcol), row0(jcol + 1));
     const int nsteps = n + kStripW - 1;
     const int nchunks = (nsteps + kChunk - 1) / kChunk;
     // 2 bytes per cell in the int16 path, 4 in the int32 path
@@ -591,8 +625,9 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
         const uint4 rm1 = get_record(sm, ii0 - 1);
         const uint4 rm2 = get_record(sm, ii0 - 2);
         const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
-        const Bnd w0 = s == 0 ? Ops::kBnd0 : ld_l2(bnd);
-        Ops::init(st, lane, w0, rm1, rm2, xm1);
+        const Bnd w0 = s > 0 ? ld_l2(bnd) : (anchored ? Ops::col0_entry(__ldg(c0 + 1)) : Ops::kBnd0);
+        Ops::init(st, lane, w0, rm1, rm2, xm1, Ops::pack2(row0(jcol), row0(jcol + 1)),
+                  Ops::pack2(row0(jcol - 1), row0(jcol)));
     }
     uint8_t *code_strip = a.codes + pd.code_off + static_cast<size_t>(s) * strip_bytes;
     // per-chunk column maxima of H follow the strips' streams: [strip][chunk][lane]
@@ -607,7 +642,10 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
             cp_async_wait_all();                         // this chunk's records (queued last chunk)
             wait_for(ch + kLag < nchunks ? ch + kLag : nchunks);
         }
-        if (s == 0) {
+        if (s == 0 && anchored) {
+            // column 0 of the anchored modes; bin[k] is genome position t0 + 1 + k (row t0 + 2 + k)
+            for (int k = lane; k < kChunk; k += 32) sm.bin[k] = Ops::col0_entry(__ldg(c0 + t0 + 2 + k));
+        } else if (s == 0) {
             for (int k = lane; k < kChunk; k += 32) sm.bin[k] = Ops::kBnd0;   // column 0: H = 0, I = -inf
         } else {
             for (int k = lane; k < kChunk; k += 32) sm.bin[k] = ld_l2(bnd + t0 + 1 + k);
@@ -1003,7 +1041,7 @@ extern "C" int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *
     if (p.q < 0 || p.e < 1 || p.f < 0 || p.r < 0 || p.stop < 0 || p.q + p.e > 1000 || p.f > 1000 ||
         p.r > 1000 || p.stop > 512 || !(p.r > p.f && p.r > p.stop && p.r > -mn) ||
         (p.splice_model != MP_SPLICE_FINAL && p.splice_model != MP_SPLICE_SIMPLE) || p.splice_p < 0 ||
-        p.splice_p > 1000)
+        p.splice_p > 1000 || p.mode != MP_MODE_LOCAL)
         return MP_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return MP_ECUDA;
@@ -1028,6 +1066,7 @@ extern "C" int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *
     sp.q = p.q; sp.e = p.e; sp.f = p.f; sp.r = p.r; sp.stop = p.stop;
     sp.splice_model = p.splice_model;
     sp.splice_p = p.splice_p;
+    sp.mode = MP_MODE_LOCAL;
     for (int x = 0; x < 22; ++x)
         for (int y = 0; y < 22; ++y) sp.mat[x][y] = p.mat[x][y];
     dp_noalloc_kernel<<<1, kWarpsPerCta * 32, kNASmem, static_cast<cudaStream_t>(stream)>>>(

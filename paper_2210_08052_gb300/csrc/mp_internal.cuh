@@ -44,6 +44,7 @@ struct PairDesc {
     uint32_t strip_base;    // index of strip 0 in the per-strip progress array
     uint32_t n_strips;
     uint64_t rec_off;       // index of the record of genome position -kChunk in the record array
+    uint64_t col0_off;      // anchored modes: index of H[0][0] in the column-0 array (H[i][0] at +i)
 };
 
 // per-nt records of a pair: positions -kChunk .. kChunk*(nchunks+1) - 1
@@ -74,7 +75,12 @@ struct ScoreParams {
     int8_t mat[22][22];
     int32_t splice_model;   // MP_SPLICE_FINAL / MP_SPLICE_SIMPLE
     int32_t splice_p;       // simple model: cost of a donor without GT / acceptor without AG
+    int32_t mode;           // MP_MODE_LOCAL / MP_MODE_GLOBAL / MP_MODE_EXTEND
 };
+
+// anchored modes: entries of the column-0 array beyond row |T| (the DP's
+// boundary loads run up to 64 + 2 chunks past the last row)
+constexpr int kCol0Pad = kStripW + 2 * kChunk + 2;
 
 // A work item is one 64-residue strip of one pair: x = pair, y = strip.
 // The warp running strip s consumes the boundary row strip s-1 publishes
@@ -89,6 +95,7 @@ struct DPArgs {
     const uint32_t *nt2;    // packed genome (base k at bits 2(k%16) of word k/16)
     uint8_t *codes;         // traceback code arena
     void *bnd;              // boundary arena
+    const int32_t *col0;    // anchored modes: column 0 of every pair (H[i][0]); null in local mode
     PairOut *out;
     uint32_t *progress;     // per strip: chunks whose boundary row is published
     unsigned long long *best_key;   // per pair: max of (score, -ii, -jj)
@@ -112,6 +119,7 @@ struct TBArgs {
     const uint32_t *nt2;    // packed genome
     PairOut *out;
     uint32_t *ops;          // reversed-op slots
+    const int32_t *col0;    // anchored modes: column 0 of every pair (H[i][0])
     ScoreParams sp;
 };
 
@@ -126,6 +134,10 @@ constexpr int kDp16Variants = 2;
 cudaError_t launch_dp16(const DPArgs &a, int grid, int variant, cudaStream_t st);
 cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t st);
 cudaError_t launch_tb(const TBArgs &a, int grid, cudaStream_t st);
+// anchored modes: column 0 of every pair, H[i][0] for i = 0..|T| (then
+// padding), by the recurrence restricted to the D, G and A terms
+cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, const ScoreParams &sp, int32_t *col0,
+                        cudaStream_t st);
 cudaError_t launch_compact(const PairDesc *pairs, PairOut *out, uint32_t n, const uint32_t *ops,
                            uint32_t *cig, uint32_t *total, cudaStream_t st);
 int dp16_blocks_per_sm(int variant);

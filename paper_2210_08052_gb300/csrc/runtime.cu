@@ -207,6 +207,7 @@ struct mp_dp_batch {
     DevBuf<uint32_t> ops, cig, work;
     DevBuf<uint2> items, rerun_items;   // strip items in processing order; re-run list
     DevBuf<uint4> recs;                 // per-nt records of every pair
+    DevBuf<int32_t> col0;               // anchored modes: column 0 of every pair
     DevBuf<uint64_t> bnd;
     // per-run state, zeroed by one memset: counters | strips_done | progress | best_key
     DevBuf<unsigned long long> state;
@@ -335,7 +336,8 @@ static int validate_params(const mp_dp_params *p)
         for (int b = 0; b < 22; ++b) mn = std::min<int>(mn, p->mat[a][b]);
     // an intron of length <= 0 must lose to a frameshift or a match from the same cell
     if (!(p->r > p->f && p->r > p->stop && p->r > -mn)) return MP_EINVAL;
-    if ((p->splice_model != MP_SPLICE_FINAL && p->splice_model != MP_SPLICE_SIMPLE) || p->mode != MP_MODE_LOCAL)
+    if ((p->splice_model != MP_SPLICE_FINAL && p->splice_model != MP_SPLICE_SIMPLE) ||
+        (p->mode != MP_MODE_LOCAL && p->mode != MP_MODE_GLOBAL && p->mode != MP_MODE_EXTEND))
         return MP_EINVAL;
     if (p->splice_p < 0 || p->splice_p > 1000) return MP_EINVAL;
     if (p->max_pairs_per_launch < 0 || p->wait_limit < 0) return MP_EINVAL;
@@ -374,6 +376,7 @@ int mp_dp_init(mp_dp_ctx **out, const mp_dp_params *p, int device)
     memcpy(c->sp.mat, prm.mat, sizeof(c->sp.mat));
     c->sp.splice_model = prm.splice_model;
     c->sp.splice_p = prm.splice_p;
+    c->sp.mode = prm.mode;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     uint64_t budget = prm.tb_budget_bytes ? prm.tb_budget_bytes : kDefaultBudget;
@@ -407,7 +410,7 @@ static void free_batch_device(mp_dp_batch *b)
     b->events.clear();
     b->ascii.release(); b->d_desc.release(); b->prot.release(); b->nt2.release(); b->out.release();
     b->ops.release(); b->cig.release(); b->work.release(); b->items.release(); b->rerun_items.release();
-    b->bnd.release(); b->state.release(); b->recs.release(); b->wave_nwide.release();
+    b->bnd.release(); b->state.release(); b->recs.release(); b->wave_nwide.release(); b->col0.release();
 }
 
 void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
@@ -692,7 +695,8 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     b->code_bytes_total = 0;
     // ---- layout
     const BoundTable bt(c->sp);
-    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0, nrec = 0;
+    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0, nrec = 0, nc0 = 0;
+    const bool anchored = c->params.mode != MP_MODE_LOCAL;
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
         PairDesc &d = b->desc[k];
@@ -712,15 +716,25 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         bnd += bnd_entries(q.nt_len);
         d.rec_off = nrec;
         nrec += records_of(q.nt_len);
+        d.col0_off = nc0;
+        if (anchored) nc0 += static_cast<uint64_t>(q.nt_len) + 1 + kCol0Pad;
         d.cig_off = ops;
         d.cig_cap = q.prot_len + q.nt_len + 2;
         ops += d.cig_cap;
         d.n_strips = static_cast<uint32_t>(div_up(q.prot_len, kStripW));
         d.strip_base = static_cast<uint32_t>(strips);
         strips += d.n_strips;
-        if (q.flags & MP_PAIR_SCORE_ONLY) d.flags |= PF_SCORE_ONLY;
+        // global mode reads its score at the end cell from the traceback stream
+        if ((q.flags & MP_PAIR_SCORE_ONLY) && c->params.mode != MP_MODE_GLOBAL) d.flags |= PF_SCORE_ONLY;
         if (q.prot_len == 0 || q.nt_len == 0) d.flags |= PF_SKIP;
         if (c->params.force_int32 || (q.prot_len && score_bound(bt, q.prot, q.prot_len, kOverflowT) >= kOverflowT))
+            d.flags |= PF_WIDE;
+        // anchored modes: H may go negative; a path through row 0 and one
+        // column (I run, D run, a frameshift) bounds it from below.  Pairs whose
+        // bound leaves the int16 range safely run in int32 (PF_WIDE pairs of
+        // these modes skip the int16 pass).
+        if (anchored && 2 * static_cast<int64_t>(c->params.q) + c->params.f +
+                                static_cast<int64_t>(c->params.e) * (q.prot_len + q.nt_len / 3 + 2) >= 12000)
             d.flags |= PF_WIDE;
         b->nt_len[k] = q.nt_len;
         b->strand[k] = q.strand;
@@ -740,6 +754,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         (e = b->cig.reserve(ops + 1)) != cudaSuccess || (e = b->work.reserve(n + 1)) != cudaSuccess ||
         (e = b->items.reserve(strips + 1)) != cudaSuccess ||
         (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
+        (anchored && (e = b->col0.reserve(nc0 + 1)) != cudaSuccess) ||
         (e = b->recs.reserve(nrec + 1)) != cudaSuccess) {
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
@@ -808,12 +823,18 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
     CK(launch_pack(b->d_desc.p, n, b->ascii.p, b->prot.p, b->nt2.p, b->out.p, st));
     CK(launch_records(b->d_desc.p, n, b->nt2.p, c->sp, b->recs.p, st));
     launches += 2;
+    const bool anchored = c->params.mode != MP_MODE_LOCAL;
+    if (anchored) {
+        CK(launch_col0(b->d_desc.p, n, b->nt2.p, c->sp, b->col0.p, st));
+        ++launches;
+    }
     CK(rec(1));
     const int variant = t.dp16_variant == 1 ? 1 : 0;
     const int fit16 = dp16_blocks_per_sm(variant), fit32 = dp32_blocks_per_sm();
     const int g16 = c->num_sms * (t.dp16_ctas_per_sm > 0 ? std::min(t.dp16_ctas_per_sm, fit16) : fit16);
     const int g32 = c->num_sms * (t.dp32_ctas_per_sm > 0 ? std::min(t.dp32_ctas_per_sm, fit32) : fit32);
-    const bool direct = t.wide_direct != 0 && !c->params.force_int32;
+    // in the anchored modes PF_WIDE pairs never take the int16 pass
+    const bool direct = (t.wide_direct != 0 || anchored) && !c->params.force_int32;
     const int per_launch = c->params.max_pairs_per_launch;
     const bool overlap = b->overlap && W > 1;
     if (overlap) {
@@ -836,6 +857,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         a.nt2 = b->nt2.p;
         a.codes = arena;
         a.bnd = b->bnd.p;
+        a.col0 = anchored ? b->col0.p : nullptr;
         a.out = b->out.p;
         a.progress = reinterpret_cast<uint32_t *>(state + b->off_progress);
         a.best_key = reinterpret_cast<unsigned long long *>(state + b->off_key);
@@ -904,6 +926,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         t.nt2 = b->nt2.p;
         t.out = b->out.p;
         t.ops = b->ops.p;
+        t.col0 = anchored ? b->col0.p : nullptr;
         t.sp = c->sp;
         const int tgrid = std::max(1, std::min<int>(c->num_sms * 8, static_cast<int>((t.n_work + 7) / 8)));
         CK(launch_tb(t, tgrid, st));
@@ -1272,10 +1295,12 @@ int mp_dp_batch_download(mp_dp_ctx *c, mp_dp_batch *b, mp_result *out)
         r.status = o.status & 0xff;
         if (o.status & MP_ST_RERUN) ++nrerun;
         if ((o.status & MP_ST_ERRMASK) & ~MP_ST_BUDGET) continue;
-        r.score = o.score > 0 ? o.score : 0;
+        const bool global = c->params.mode == MP_MODE_GLOBAL;
+        if (global && (d.flags & PF_BUDGET)) continue;                // no stream: no end-cell score
+        r.score = global ? o.score : (o.score > 0 ? o.score : 0);    // global scores may be negative
         r.exon_score = r.score;
         const int32_t tn = static_cast<int32_t>(d.nt_len);
-        if (r.score <= 0) continue;
+        if (!global && r.score <= 0) continue;
         const bool score_only = (d.flags & (PF_SCORE_ONLY | PF_BUDGET)) != 0;
         const int32_t en_al = o.best_ii + 1;
         r.prot_en = o.best_jj + 1;

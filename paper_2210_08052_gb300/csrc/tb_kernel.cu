@@ -107,11 +107,18 @@ struct PairView {
     int n, m;
     const ScoreParams *sp;
     const int8_t *mat;       // shared-memory copy of sp->mat
+    const int32_t *c0;       // anchored modes: column 0 (H[i][0]); null in local mode
 
     __device__ __forceinline__ int H(int i, int j) const
     {
-        if (i < 0) return kNeg;
-        if (i == 0 || j == 0) return 0;
+        if (i < 0 || j < 0) return kNeg;
+        if (c0) {
+            // anchored modes: row 0 is an I run from (0, 0); column 0 precomputed
+            if (i == 0) return j == 0 ? 0 : -(sp->q + sp->e * j);
+            if (j == 0) return __ldg(c0 + i);
+        } else if (i == 0 || j == 0) {
+            return 0;
+        }
         const int ii = i - 1, jj = j - 1;
         const int s = jj >> 6, r = jj & 63, t = ii + r;
         if (wide) {
@@ -239,28 +246,66 @@ __device__ void trace_pair(const TBArgs &a, const int8_t *mat_s, uint32_t p, int
     const PairDesc pd = a.pairs[p];
     PairOut &o = a.out[p];
     const int n = static_cast<int>(pd.nt_len);
+    const int m = static_cast<int>(pd.prot_len);
     const int nchunks = (n + kStripW - 1 + kChunk - 1) / kChunk;
     const bool wide = (o.status & kStInt32Stream) != 0;
     const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes * (wide ? 2 : 1);
     const int nstrips = static_cast<int>(pd.n_strips);
+    // anchored modes: the path ends at cell (0, 0), whose row and column
+    // follow the recurrence (PairView returns them) and H has no restart
+    const bool anchored = a.sp.mode != MP_MODE_LOCAL;
     const PairView v{a.codes + pd.code_off, strip_bytes, wide,
                      a.codes + pd.code_off + static_cast<size_t>(nstrips) * strip_bytes, nchunks,
-                     a.nt2 + pd.nt_word_off, a.prot + pd.prot_off, n, static_cast<int>(pd.prot_len),
-                     &a.sp, mat_s};
+                     a.nt2 + pd.nt_word_off, a.prot + pd.prot_off, n, m,
+                     &a.sp, mat_s, anchored ? a.col0 + pd.col0_off : nullptr};
     const int q = a.sp.q, e = a.sp.e, f = a.sp.f, r = a.sp.r;
-    const int hmax = o.score;
+    const int hmax = o.score > 0 ? o.score : 0;             // no H exceeds it (H[0][0] = 0 included)
     int i = o.best_ii + 1, j = o.best_jj + 1;
+    if (a.sp.mode == MP_MODE_GLOBAL) {
+        // global: the alignment ends at (|T|, |P|)
+        i = n;
+        j = m;
+        const int hend = v.H(n, m);
+        __syncwarp();
+        if (lane == 0) {
+            o.score = hend;
+            o.best_ii = n - 1;
+            o.best_jj = m - 1;
+        }
+    }
+    // the opening row x of an intron in column jc at or above xhi, or -1:
+    // rows from 1 by the pruned scan, then column 0 / row 0 in the anchored modes
+    auto find_open = [&](int jc, int xhi, int thr, auto pred) -> int {
+        if (xhi < 0 || jc < 0) return -1;
+        if (jc >= 1) {
+            const int x = scan_column(v, jc, xhi, thr, lane, pred);
+            if (x) return x;
+        } else if (anchored) {
+            // column 0 (no stored maxima): a plain scan
+            for (int x0 = xhi; x0 >= 1; x0 -= 32) {
+                const int x = x0 - lane;
+                const unsigned hit = __ballot_sync(kFull, x >= 1 && pred(x));
+                if (hit) return x0 - (__ffs(hit) - 1);
+            }
+        }
+        return (anchored && pred(0)) ? 0 : -1;
+    };
     OpWriter w{a.ops + pd.cig_off, pd.cig_cap, 0, 0, 0, false};
     bool error = false;
     for (;;) {
-        if (i <= 0 || j <= 0) break;
+        if (anchored) {
+            if (i == 0 && j == 0) break;
+            if (i < 0 || j < 0) { error = true; break; }
+        } else if (i <= 0 || j <= 0) {
+            break;
+        }
         // M runs: cells (i - 3k, j - k) along the codon diagonal
         const int ik = i - 3 * lane, jk = j - lane;
         const bool inside = ik >= 1 && jk >= 1;
-        const int hk = inside ? v.H(ik, jk) : 0;
+        const int hk = (inside || (anchored && ik >= 0 && jk >= 0)) ? v.H(ik, jk) : 0;
         int hn = __shfl_down_sync(kFull, hk, 1);
         if (lane == 31) hn = (ik >= 3 && jk >= 1) ? v.H(ik - 3, jk - 1) : kNeg;
-        const bool is_m = inside && hk > 0 && ik >= 3 && hk == hn + v.s(ik, jk);
+        const bool is_m = inside && (anchored || hk > 0) && ik >= 3 && hk == hn + v.s(ik, jk);
         const unsigned nonm = __ballot_sync(kFull, !is_m);
         const int cnt = nonm ? __ffs(nonm) - 1 : 32;
         if (cnt > 0) {
@@ -270,7 +315,11 @@ __device__ void trace_pair(const TBArgs &a, const int8_t *mat_s, uint32_t p, int
         }
         if (cnt == 32) continue;
         const int h = __shfl_sync(kFull, hk, cnt);
-        if (i <= 0 || j <= 0 || h <= 0) break;                 // restart wins a tie at 0
+        if (anchored) {
+            if (i == 0 && j == 0) break;
+        } else if (i <= 0 || j <= 0 || h <= 0) {
+            break;                                           // restart wins a tie at 0
+        }
         // I: residues against no genome
         const int kgap = (hmax - q - h) / e;
         int k = kgap >= 1 ? first_hit(j < kgap ? j : kgap, lane,
@@ -288,23 +337,22 @@ __device__ void trace_pair(const TBArgs &a, const int8_t *mat_s, uint32_t p, int
         if (v.H(i - 1, j) - f == h) { if (lane == 0) w.push(MP_OP_G, 1); i -= 1; continue; }
         if (v.H(i - 2, j) - f == h) { if (lane == 0) w.push(MP_OP_G, 2); i -= 2; continue; }
         // introns: the opening i' nearest to the exit i; the H cell before it is
-        // x = i' - 1 (row 0 never matches since h > 0)
+        // x = i' - 1 (in local mode row 0 never matches since h > 0)
         const int va = h + v.a(i);
-        int x = scan_column(v, j, i - 1, va + r, lane, [&](int xx) { return v.H(xx, j) - r - v.d(xx) == va; });
-        if (x) {
+        int x = find_open(j, i - 1, va + r, [&](int xx) { return v.H(xx, j) - r - v.d(xx) == va; });
+        if (x >= 0) {
             if (lane == 0) w.push(MP_OP_N, i - x);          // intron T[x+1..i]
             i = x;
             continue;
         }
         const int vb = h + v.a(i - 2), vc = h + v.a(i - 1);
         int op = MP_OP_U;
-        x = scan_column(v, j - 1, i - 1, vb + r, lane, [&](int xx) { return v.H(xx, j - 1) - r - v.d(xx + 1) == vb; });
-        if (!x) {
+        x = find_open(j - 1, i - 1, vb + r, [&](int xx) { return v.H(xx, j - 1) - r - v.d(xx + 1) == vb; });
+        if (x < 0) {
             op = MP_OP_V;
-            x = scan_column(v, j - 1, i - 1, vc + r, lane,
-                            [&](int xx) { return v.H(xx, j - 1) - r - v.d(xx + 2) == vc; });
+            x = find_open(j - 1, i - 1, vc + r, [&](int xx) { return v.H(xx, j - 1) - r - v.d(xx + 2) == vc; });
         }
-        if (!x) { error = true; break; }
+        if (x < 0) { error = true; break; }
         const int L = i - x - 3;                              // intron length i - i' - 2
         if (L < 1) { error = true; break; }
         if (lane == 0) w.push(op, L);
@@ -332,7 +380,8 @@ __global__ void tb_kernel(const TBArgs a)
         const uint32_t p = a.work[k];
         const PairDesc &pd = a.pairs[p];
         const PairOut &o = a.out[p];
-        if ((pd.flags & (PF_SCORE_ONLY | PF_SKIP | PF_BUDGET)) || (o.status & MP_ST_ERRMASK) || o.score <= 0)
+        if ((pd.flags & (PF_SCORE_ONLY | PF_SKIP | PF_BUDGET)) || (o.status & MP_ST_ERRMASK) ||
+            (o.score <= 0 && a.sp.mode != MP_MODE_GLOBAL))
             continue;
         trace_pair(a, mat_s, p, lane);
     }
@@ -392,6 +441,58 @@ __global__ void copy_ops_kernel(const PairDesc *pairs, const PairOut *out, uint3
 }
 
 }  // namespace
+
+namespace {
+// Column 0 in the anchored modes, where the path starts at cell (0, 0):
+// H[0][0] = 0 and, for i >= 1, Eq. 7 with no residue consumed -- a codon
+// deletion run (D), the frameshift insertions G1, G2 and the phase-0 intron
+// state A (M, I, F1, F2, B and C need column -1).  One thread per pair,
+// sequential in i; rows past |T| hold -inf.
+__global__ void col0_kernel(const PairDesc *pairs, uint32_t n_pairs, const uint32_t *nt2, const ScoreParams sp,
+                            int32_t *col0)
+{
+    constexpr int32_t NEG = -(1 << 28);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs; p += gridDim.x * blockDim.x) {
+        const PairDesc pd = pairs[p];
+        if (pd.flags & PF_SKIP) continue;
+        const int n = static_cast<int>(pd.nt_len);
+        const uint32_t *g = nt2 + pd.nt_word_off;
+        int32_t *h = col0 + pd.col0_off;
+        auto base = [&](int x) { return static_cast<int>((g[(x - 1) >> 4] >> (2 * ((x - 1) & 15))) & 3); };
+        auto in = [&](int x) { return x >= 1 && x <= n; };
+        auto dsc = [&](int x) {
+            const bool v1 = in(x + 1), v2 = in(x + 2), v3 = in(x + 3);
+            return splice_donor(sp, v1 ? base(x + 1) : 0, v2 ? base(x + 2) : 0, v3 ? base(x + 3) : 0, v1, v2, v3);
+        };
+        auto asc = [&](int x) {
+            const bool v1 = in(x - 2), v2 = in(x - 1), v3 = in(x);
+            return splice_acceptor(sp, v1 ? base(x - 2) : 0, v2 ? base(x - 1) : 0, v3 ? base(x) : 0, v1, v2, v3);
+        };
+        // H[i-1], H[i-2], H[i-3]; D[i-1], D[i-2], D[i-3]; A[i-1]
+        int32_t h1 = 0, h2 = NEG, h3 = NEG, d1 = NEG, d2 = NEG, d3 = NEG, av = NEG;
+        h[0] = 0;
+        for (int i = 1; i <= n; ++i) {
+            const int32_t dv = max(max(h3 - sp.q, d3) - sp.e, NEG);
+            av = max(max(h1 - sp.r - dsc(i - 1), av), NEG);
+            int32_t hv = max(dv, max(h1, h2) - sp.f);
+            hv = max(max(hv, av - asc(i)), NEG);
+            h[i] = hv;
+            d3 = d2; d2 = d1; d1 = dv;
+            h3 = h2; h2 = h1; h1 = hv;
+        }
+        for (int i = n + 1; i <= n + kCol0Pad; ++i) h[i] = NEG;
+    }
+}
+}  // namespace
+
+cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, const ScoreParams &sp, int32_t *col0,
+                        cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const uint32_t grid = (n + 127) / 128 < 2048 ? (n + 127) / 128 : 2048;
+    col0_kernel<<<grid, 128, 0, st>>>(pairs, n, nt2, sp, col0);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack(const PairDesc *pairs, uint32_t n, const char *ascii, uint8_t *prot, uint32_t *nt2,
                         PairOut *out, cudaStream_t st)

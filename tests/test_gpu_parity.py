@@ -404,6 +404,77 @@ def test_exon_rescore(mp, ctx, orc):
                                         want[k] == got[k]["score"] - 29)
 
 
+def _anchored_pairs(seed, count, mmax):
+    """Gene pairs with short flanks (the gap-closing and extension regions
+    between anchors are short), several strips and chunks, both strands."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(rng.integers(1, mmax + 1))
+        prot = synth.random_protein(rng, m)
+        lens = [int(rng.integers(40, 600)) for _ in range(int(rng.integers(0, 3)))]
+        region, _ = synth.gen.plant_gene(rng, prot, float(rng.uniform(0.0, 0.35)), int(rng.integers(0, 3)), lens,
+                                         int(rng.integers(0, 40)), int(rng.integers(0, 40)), 0.45)
+        strand = 1
+        if rng.random() < 0.5:
+            region, strand = synth.revcomp(region), -1
+        out.append(synth.Pair(prot, region, strand))
+    # unrelated protein and region: negative global scores
+    for _ in range(3):
+        m = int(rng.integers(20, 150))
+        out.append(synth.Pair(synth.random_protein(rng, m), synth.random_dna(rng, int(rng.integers(50, 900))), 1))
+    return out
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("splice_model", [0, 1])
+def test_anchored_modes(mp, orc, mode, splice_model):
+    """Global (gap closing: from the start of protein and region to both
+    ends) and extension (from the start, ending anywhere) against the oracle:
+    score, coordinates and CIGAR, with both splice models, the graph replay
+    and score-only requests (which global mode still traces)."""
+    pairs = _anchored_pairs(100 + mode + 10 * splice_model, 30, 300)
+    params = mp.mp_dp_default_params(mode=mode, splice_model=splice_model, splice_p=15)
+    c = mp.mp_dp_init(params, 0)
+    try:
+        got = mp.mp_dp_align_batch(c, pairs)
+        got2 = mp.mp_dp_align_batch(c, pairs)
+        so = mp.mp_dp_align_batch(c, [synth.Pair(p.prot, p.nt, p.strand, True) for p in pairs[:6]])
+    finally:
+        mp.mp_dp_destroy(c)
+    op = _orc_params(orc, params)
+    op.mode = mode
+    _compare(orc, pairs, got, op)
+    assert [{k: g[k] for k in KEYS} for g in got2] == [{k: g[k] for k in KEYS} for g in got]
+    if mode == 1:
+        assert min(g["score"] for g in got) < 0
+        assert [g["score"] for g in so] == [g["score"] for g in got[:6]]
+    else:
+        assert [g["score"] for g in so] == [g["score"] for g in got[:6]]
+
+
+def test_anchored_int32_pairs(mp, orc):
+    """Anchored pairs whose lower bound leaves the int16 range run in int32
+    at once (here by a large gap extension e), against the oracle."""
+    rng = np.random.default_rng(120)
+    pairs = []
+    for k in range(4):
+        m = int(rng.integers(900, 1100))
+        prot = synth.random_protein(rng, m)
+        region, _ = synth.gen.plant_gene(rng, prot, 0.2, 1, [300], 500, 500, 0.45)
+        pairs.append(synth.Pair(prot, region, 1 if k % 2 == 0 else -1))
+    for mode in (1, 2):
+        params = mp.mp_dp_default_params(mode=mode, e=6, q=9)
+        c = mp.mp_dp_init(params, 0)
+        try:
+            got = mp.mp_dp_align_batch(c, pairs)
+        finally:
+            mp.mp_dp_destroy(c)
+        op = _orc_params(orc, params)
+        op.mode = mode
+        _compare(orc, pairs, got, op)
+
+
 def test_serving_alone_and_in_mix(mp, ctx):
     """Each request's result is the same served alone, in a burst with
     others in flight, and from the batch call."""
