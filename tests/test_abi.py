@@ -75,7 +75,7 @@ def test_strerror(mp):
 
 
 @pytest.mark.parametrize("bad", [dict(r=20), dict(r=23), dict(e=0), dict(q=-1), dict(stop=40),
-                                 dict(splice_model=2), dict(splice_p=-1), dict(splice_p=1001), dict(mode=2)])
+                                 dict(splice_model=2), dict(splice_p=-1), dict(splice_p=1001), dict(mode=3), dict(mode=-1)])
 def test_init_rejects_degenerate_params(mp, bad):
     """r must exceed f, stop and -min(mat) so that no intron of length <= 0
     beats a frameshift or a match (validated before any device access)."""
