@@ -250,6 +250,20 @@ def acceptor(nt: str, x: int) -> int:
     return lib().orc_acceptor(arr, len(nt), x)
 
 
+def fill_h(prot: str, nt: str, strand: int = 1, params: Params | None = None) -> np.ndarray:
+    """The oracle's H matrix, (|T|+1) x (|P|+1), aligned orientation."""
+    L = lib()
+    p = params if params is not None else make_params()
+    pb = prot.encode()
+    tb = nt.encode()
+    out = np.zeros((len(tb) + 1) * (len(pb) + 1), dtype=np.int32)
+    L.orc_fill_h.argtypes = [ctypes.POINTER(Params), ctypes.c_char_p, ctypes.c_int32, ctypes.c_char_p,
+                             ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+    if L.orc_fill_h(ctypes.byref(p), pb, len(pb), tb, len(tb), int(strand), out.ctypes.data) != 0:
+        raise ValueError("oracle rejected the input")
+    return out.reshape(len(tb) + 1, len(pb) + 1)
+
+
 def donor_simple(nt: str, x: int, p: int) -> int:
     """d(x) of the simple GT-AG model with cost p; x is 1-based."""
     codes = [0] + ["ACGT".index(c) for c in nt.upper()]

@@ -430,6 +430,38 @@ int orc_align(const orc_params *p, const char *prot, int32_t plen, const char *n
     return 0;
 }
 
+/* The filled H matrix ((tlen+1) x (plen+1), row-major, aligned
+ * orientation) for tests that inspect the DP values themselves. */
+int orc_fill_h(const orc_params *p, const char *prot, int32_t plen, const char *nt, int32_t tlen, int32_t strand,
+               int32_t *h_out)
+{
+    dp_t dp;
+    memset(&dp, 0, sizeof(dp));
+    dp.n = tlen;
+    dp.m = plen;
+    dp.p = p;
+    dp.T = (int8_t *)malloc((size_t)tlen + 1);
+    dp.P = (int8_t *)malloc((size_t)plen + 1);
+    if (!dp.T || !dp.P) { free(dp.T); free(dp.P); return -1; }
+    for (int i = 1; i <= tlen; ++i) {
+        int b = orc_nt_code(nt[strand < 0 ? tlen - i : i - 1]);
+        if (b < 0) { free(dp.T); free(dp.P); return -1; }
+        dp.T[i] = (int8_t)(strand < 0 ? 3 - b : b);
+    }
+    for (int j = 1; j <= plen; ++j) dp.P[j] = (int8_t)orc_aa_code(prot[j - 1]);
+    size_t cells = (size_t)(tlen + 1) * (size_t)(plen + 1);
+    int32_t *buf = (int32_t *)malloc(cells * 6 * sizeof(int32_t));
+    if (!buf) { free(dp.T); free(dp.P); return -1; }
+    dp.H = buf; dp.I = buf + cells; dp.D = buf + 2 * cells;
+    dp.A = buf + 3 * cells; dp.B = buf + 4 * cells; dp.C = buf + 5 * cells;
+    fill(&dp);
+    memcpy(h_out, dp.H, cells * sizeof(int32_t));
+    free(buf);
+    free(dp.T);
+    free(dp.P);
+    return 0;
+}
+
 /* Score only: the same fill, returning the best H (for large cases). */
 int32_t orc_score(const orc_params *p, const char *prot, int32_t plen, const char *nt, int32_t tlen,
                   int32_t strand)

@@ -195,17 +195,21 @@ struct Ops16 {
         return static_cast<uint32_t>(slo + 512) | (static_cast<uint32_t>(shi + 512) << 16);
     }
 
-    // State before step 0: every cell not yet reached is outside the matrix
-    // (-inf) except the row-0 cell at ii = -1, where H = 0.  w0 is the
-    // boundary entry at ii = 0 (used by lane 0).
-    // h1: H in row 0 of the lane's columns; l1: H in row 0 of the columns to
-    // their left (both biased 0 in local mode)
+    // State before step 0, i.e. the history of steps -1 .. -4.  At step tau
+    // lane l holds rows ii = tau - 2l (lo), tau - 2l - 1 (hi) and sees its
+    // left column at ii = tau - 2l + 1, so only lane 0 touches the matrix
+    // there: its lo column in row 0 at step -1 (H1.lo, L0.hi = h_self), its
+    // left column at ii = 0 at step -1 (L0.lo, the boundary entry w0) and in
+    // row 0 at step -2 (L1.lo = h_left).  Every other slot is outside (-inf).
+    // h_self, h_left: H in row 0 of the lane's lo column and of the column to
+    // its left (0 in local mode)
     static __device__ __forceinline__ void init(State &s, int lane, Bnd w0, uint4 recm1, uint4 recm2,
-                                                uint32_t xm1, uint32_t h1, uint32_t l1)
+                                                uint32_t xm1, int h_self, int h_left)
     {
-        s.H1 = h1; s.H2 = NEGV; s.H3 = NEGV;
-        s.L1 = l1; s.L2 = NEGV; s.L3 = NEGV;
-        s.L0 = (lane == 0) ? ((w0 & 0xffffu) | 0x80000000u) : NEGV;
+        const uint32_t hs = pack2(h_self, -16384), hl = pack2(h_left, -16384);   // [H, -inf]
+        s.H1 = (lane == 0) ? hs : NEGV; s.H2 = NEGV; s.H3 = NEGV;
+        s.L1 = (lane == 0) ? hl : NEGV; s.L2 = NEGV; s.L3 = NEGV;
+        s.L0 = (lane == 0) ? ((w0 & 0xffffu) | (hs << 16)) : NEGV;
         s.IL = (lane == 0) ? ((w0 >> 16) | 0x40000000u) : NEGV;
         s.D1 = s.D2 = s.D3 = NEGV;
         s.A1 = s.B1 = s.C1 = NEGV;
@@ -375,12 +379,13 @@ struct Ops32 {
     }
 
     static __device__ __forceinline__ void init(State &s, int lane, Bnd w0, uint4 recm1, uint4 recm2,
-                                                uint32_t xm1, V2 h1, V2 l1)
+                                                uint32_t xm1, int h_self, int h_left)
     {
+        // the same history as the int16 state (see Ops16::init)
         const V2 ng{NEG, NEG};
-        s.H1 = h1; s.H2 = ng; s.H3 = ng;
-        s.L1 = l1; s.L2 = ng; s.L3 = ng;
-        s.L0 = (lane == 0) ? V2{w0.h, 0} : ng;
+        s.H1 = (lane == 0) ? V2{h_self, NEG} : ng; s.H2 = ng; s.H3 = ng;
+        s.L1 = (lane == 0) ? V2{h_left, NEG} : ng; s.L2 = ng; s.L3 = ng;
+        s.L0 = (lane == 0) ? V2{w0.h, h_self} : ng;
         s.IL = (lane == 0) ? V2{w0.i, NEG} : ng;
         s.D1 = s.D2 = s.D3 = ng;
         s.A1 = s.B1 = s.C1 = ng;
@@ -626,8 +631,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
         const uint4 rm2 = get_record(sm, ii0 - 2);
         const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
         const Bnd w0 = s > 0 ? ld_l2(bnd) : (anchored ? Ops::col0_entry(__ldg(c0 + 1)) : Ops::kBnd0);
-        Ops::init(st, lane, w0, rm1, rm2, xm1, Ops::pack2(row0(jcol), row0(jcol + 1)),
-                  Ops::pack2(row0(jcol - 1), row0(jcol)));
+        Ops::init(st, lane, w0, rm1, rm2, xm1, row0(jcol), row0(jcol - 1));
     }
     uint8_t *code_strip = a.codes + pd.code_off + static_cast<size_t>(s) * strip_bytes;
     // per-chunk column maxima of H follow the strips' streams: [strip][chunk][lane]

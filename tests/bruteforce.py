@@ -29,6 +29,7 @@ from functools import lru_cache
 
 import oracle
 
+NEG = float("-inf")
 ORDER = {"M": 0, "I": 1, "D": 2, "F1": 3, "F2": 4, "G1": 5, "G2": 6, "N": 7, "U": 8, "V": 9}
 
 
@@ -98,30 +99,18 @@ class Problem:
                 yield ("V", L, L + 3, 1, -(r + self.d(i + 2) + self.a(i + L + 2)))
 
 
-def segment_best(pb: Problem) -> int:
-    """Best local score: max over start cells and operation sequences."""
+def best_table(pb: Problem, mode: str = "local"):
+    """best[i][j]: the best score of a path ending at cell (i, j), by a
+    Bellman recursion over whole operations.  "local": paths start at any
+    cell (the empty path scores 0, so no entry is below 0); "global" and
+    "extend": paths start at (0, 0), unreachable cells stay at -inf."""
     n, m = pb.n, pb.m
-    best = [[0] * (m + 1) for _ in range(n + 1)]   # best path score ending at (i, j); empty path = 0
+    if mode == "local":
+        best = [[0] * (m + 1) for _ in range(n + 1)]
+    else:
+        best = [[NEG] * (m + 1) for _ in range(n + 1)]
+        best[0][0] = 0
     # process cells in order of i, then j (every op advances i or j)
-    for i in range(n + 1):
-        for j in range(m + 1):
-            b = best[i][j]
-            for _, _, di, dj, c in pb.ops_from(i, j):
-                if b + c > best[i + di][j + dj]:
-                    best[i + di][j + dj] = b + c
-    return max(max(row) for row in best)
-
-
-NEG = float("-inf")
-
-
-def anchored_best(pb: Problem, mode: str) -> int:
-    """Best score of a path from cell (0, 0): ending at (n, m) ("global") or
-    anywhere, the empty path included ("extend").  A Bellman recursion over
-    whole operations, with unreachable cells at -inf."""
-    n, m = pb.n, pb.m
-    best = [[NEG] * (m + 1) for _ in range(n + 1)]
-    best[0][0] = 0
     for i in range(n + 1):
         for j in range(m + 1):
             b = best[i][j]
@@ -130,8 +119,20 @@ def anchored_best(pb: Problem, mode: str) -> int:
             for _, _, di, dj, c in pb.ops_from(i, j):
                 if b + c > best[i + di][j + dj]:
                     best[i + di][j + dj] = b + c
+    return best
+
+
+def segment_best(pb: Problem) -> int:
+    """Best local score: max over start cells and operation sequences."""
+    return max(max(row) for row in best_table(pb, "local"))
+
+
+def anchored_best(pb: Problem, mode: str) -> int:
+    """Best score of a path from cell (0, 0): ending at (n, m) ("global") or
+    anywhere, the empty path included ("extend")."""
+    best = best_table(pb, mode)
     if mode == "global":
-        return best[n][m]
+        return best[pb.n][pb.m]
     return max(max(row) for row in best)
 
 

@@ -396,6 +396,27 @@ def test_anchored_modes_against_segment_recursion(orc):
             assert got["score"] == want, (mode, prot, nt, params, sp)
 
 
+def test_every_h_cell_against_segment_tables(orc):
+    """Every cell of the oracle's H matrix is the best score of a path ending
+    there (H is the maximum of Eq. 7's states, and each state the best over
+    its paths): local mode against paths from any cell with the empty path at
+    0, the anchored modes against paths from (0, 0).  A wrong boundary value
+    (row 0, column 0) or a dropped term shows up in the cell it reaches."""
+    rng = random.Random(73)
+    for k in range(90):
+        n, m = rng.randint(0, 16), rng.randint(0, 5)
+        prot, nt, params = _random_case(rng, n, m, valid=rng.random() < 0.7)
+        simple = rng.random() < 0.3
+        sp = dict(splice_p=rng.choice([0, 5, 30])) if simple else {}
+        pb = bf.Problem(prot, nt, **params, **sp)
+        for mode, name in ((0, "local"), (1, "global"), (2, "extend")):
+            want = np.array(bf.best_table(pb, name), dtype=np.float64)
+            op = orc.make_params(mode=mode, splice_model=1 if simple else 0, **params, **sp)
+            got = orc.fill_h(prot, nt, 1, op)
+            assert got.shape == (n + 1, m + 1)
+            assert np.array_equal(got.astype(np.float64), want), (mode, prot, nt, params, sp)
+
+
 def test_anchored_modes_against_enumeration(orc):
     """The same against every enumerated path from (0, 0) on tiny inputs."""
     rng = random.Random(72)
