@@ -344,6 +344,19 @@ int mp_dp_get_stats(mp_dp_ctx *ctx, mp_dp_stats *s);
 /* Number of streaming multiprocessors of the context's device. */
 int mp_dp_num_sms(mp_dp_ctx *ctx);
 
+/* Test hook (no counterpart in the method): the H values of Eq. 7 the DP
+ * stored for pair k of `batch`, read back through the traceback's view of
+ * the stream.  h (host, caller-owned) receives (|T|+1) x (|P|+1) int32,
+ * row-major, H[i][j] at i*(|P|+1)+j, in the aligned orientation (the
+ * reverse complement for strand -1); row 0 and column 0 hold the boundary
+ * of the context's mode.  Valid after mp_dp_batch_run + mp_dp_batch_sync of
+ * `batch` as the context's last run, in one wave (a batch within the
+ * traceback budget).  MP_EINVAL: null argument, k out of range, or a pair
+ * with no stored stream (score-only, empty, over budget); MP_ESTATE: another
+ * run since, or a batch run in several waves; MP_ENOMEM: the cell buffer
+ * could not be allocated (this hook allocates device memory per call). */
+int mp_dp_debug_h(mp_dp_ctx *ctx, mp_dp_batch *batch, size_t k, int32_t *h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_ba
             "mp_dp_submit", "mp_dp_poll", "mp_dp_wait_any", "mp_dp_destroy", "mp_dp_strerror",
             "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats",
             "mp_dp_score_pair_noalloc", "mp_dp_autotune", "mp_dp_set_tuning", "mp_dp_get_tuning",
-            "mp_dp_tuning_save", "mp_dp_tuning_load", "mp_dp_exon_rescore"]
+            "mp_dp_tuning_save", "mp_dp_tuning_load", "mp_dp_exon_rescore", "mp_dp_debug_h"]
 
 
 class mp_dp_params(ctypes.Structure):
@@ -121,6 +121,7 @@ def lib():
             "mp_dp_tuning_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
             "mp_dp_exon_rescore": (ctypes.c_int, [vp, P(mp_pair), ctypes.c_size_t, P(mp_result)]),
             "mp_dp_tuning_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
+            "mp_dp_debug_h": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -405,6 +406,14 @@ def mp_dp_exon_rescore(ctx, pairs, results) -> list:
 
 def mp_dp_num_sms(ctx) -> int:
     return lib().mp_dp_num_sms(ctx)
+
+
+def mp_dp_debug_h(ctx, batch, k: int, nt_len: int, prot_len: int) -> np.ndarray:
+    """Test hook: the stored H matrix of pair k ((nt_len+1) x (prot_len+1),
+    aligned orientation) after mp_dp_batch_run + mp_dp_batch_sync."""
+    h = np.empty((nt_len + 1) * (prot_len + 1), dtype=np.int32)
+    _check(lib().mp_dp_debug_h(ctx, batch[0], k, h.ctypes.data), "mp_dp_debug_h")
+    return h.reshape(nt_len + 1, prot_len + 1)
 
 
 def mp_dp_score_pair_noalloc(params, d_prot: int, prot_len: int, d_nt: int, nt_len: int, strand: int,

@@ -134,6 +134,7 @@ constexpr int kDp16Variants = 2;
 cudaError_t launch_dp16(const DPArgs &a, int grid, int variant, cudaStream_t st);
 cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t st);
 cudaError_t launch_tb(const TBArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_dump_h(const TBArgs &a, uint32_t p, size_t cells, int32_t *h, cudaStream_t st);
 // anchored modes: column 0 of every pair, H[i][0] for i = 0..|T| (then
 // padding), by the recurrence restricted to the D, G and A terms
 cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, const ScoreParams &sp, int32_t *col0,

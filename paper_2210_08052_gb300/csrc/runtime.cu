@@ -388,6 +388,34 @@ int mp_dp_init(mp_dp_ctx **out, const mp_dp_params *p, int device)
 
 int mp_dp_num_sms(mp_dp_ctx *c) { return c ? c->num_sms : 0; }
 
+int mp_dp_debug_h(mp_dp_ctx *c, mp_dp_batch *b, size_t k, int32_t *h)
+{
+    if (!c || !b || !h || k >= b->n) return MP_EINVAL;
+    const PairDesc &d = b->desc[k];
+    if (d.flags & (PF_SCORE_ONLY | PF_SKIP | PF_BUDGET)) return MP_EINVAL;      // no stream kept
+    // the arena holds the stream of the context's last run, whole only in one wave
+    if (c->last != b || b->waves.size() != 1) return MP_ESTATE;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MP_ECUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    const size_t cells = (static_cast<size_t>(d.nt_len) + 1) * (static_cast<size_t>(d.prot_len) + 1);
+    DevBuf<int32_t> tmp;
+    if (tmp.reserve(cells) != cudaSuccess) return MP_ENOMEM;
+    TBArgs t{};
+    t.pairs = b->d_desc.p;
+    t.codes = c->codes.p;
+    t.prot = b->prot.p;
+    t.nt2 = b->nt2.p;
+    t.out = b->out.p;
+    t.col0 = c->params.mode != MP_MODE_LOCAL ? b->col0.p : nullptr;
+    t.sp = c->sp;
+    cudaError_t e = launch_dump_h(t, static_cast<uint32_t>(k), cells, tmp.p, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, tmp.p, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    tmp.release();
+    return e == cudaSuccess ? MP_OK : MP_ECUDA;
+}
+
 int mp_dp_set_timing(mp_dp_ctx *c, int enable)
 {
     if (!c) return MP_EINVAL;

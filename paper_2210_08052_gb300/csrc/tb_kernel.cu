@@ -241,23 +241,31 @@ __device__ __forceinline__ int scan_column(const PairView &v, int jc, int xhi, i
 //   B[i][j] = max_{i'<=i} H[i'-1][j-1] - r - d(i'),  C: the same with d(i'+1),
 // each bounded above by H[i][j]; the run length the tie rule picks (open
 // before extend) is the shortest one reaching H.
+// The view of pair pd whose DP has run (o holds its stream width).
+__device__ __forceinline__ PairView make_view(const TBArgs &a, const PairDesc &pd, const PairOut &o,
+                                              const int8_t *mat_s)
+{
+    const int n = static_cast<int>(pd.nt_len);
+    const int nchunks = (n + kStripW - 1 + kChunk - 1) / kChunk;
+    const bool wide = (o.status & kStInt32Stream) != 0;
+    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes * (wide ? 2 : 1);
+    const bool anchored = a.sp.mode != MP_MODE_LOCAL;
+    return PairView{a.codes + pd.code_off, strip_bytes, wide,
+                    a.codes + pd.code_off + static_cast<size_t>(pd.n_strips) * strip_bytes, nchunks,
+                    a.nt2 + pd.nt_word_off, a.prot + pd.prot_off, n, static_cast<int>(pd.prot_len),
+                    &a.sp, mat_s, anchored ? a.col0 + pd.col0_off : nullptr};
+}
+
 __device__ void trace_pair(const TBArgs &a, const int8_t *mat_s, uint32_t p, int lane)
 {
     const PairDesc pd = a.pairs[p];
     PairOut &o = a.out[p];
     const int n = static_cast<int>(pd.nt_len);
     const int m = static_cast<int>(pd.prot_len);
-    const int nchunks = (n + kStripW - 1 + kChunk - 1) / kChunk;
-    const bool wide = (o.status & kStInt32Stream) != 0;
-    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes * (wide ? 2 : 1);
-    const int nstrips = static_cast<int>(pd.n_strips);
     // anchored modes: the path ends at cell (0, 0), whose row and column
     // follow the recurrence (PairView returns them) and H has no restart
     const bool anchored = a.sp.mode != MP_MODE_LOCAL;
-    const PairView v{a.codes + pd.code_off, strip_bytes, wide,
-                     a.codes + pd.code_off + static_cast<size_t>(nstrips) * strip_bytes, nchunks,
-                     a.nt2 + pd.nt_word_off, a.prot + pd.prot_off, n, m,
-                     &a.sp, mat_s, anchored ? a.col0 + pd.col0_off : nullptr};
+    const PairView v = make_view(a, pd, o, mat_s);
     const int q = a.sp.q, e = a.sp.e, f = a.sp.f, r = a.sp.r;
     const int hmax = o.score > 0 ? o.score : 0;             // no H exceeds it (H[0][0] = 0 included)
     int i = o.best_ii + 1, j = o.best_jj + 1;
@@ -387,6 +395,22 @@ __global__ void tb_kernel(const TBArgs a)
     }
 }
 
+// Test hook: H of every cell (i, j), 0 <= i <= |T|, 0 <= j <= |P|, of pair
+// p, row-major, read through the traceback's own view of the stream.
+__global__ void dump_h_kernel(const TBArgs a, uint32_t p, int32_t *h)
+{
+    __shared__ int8_t mat_s[22 * 22];
+    for (int k = threadIdx.x; k < 22 * 22; k += blockDim.x) mat_s[k] = a.sp.mat[k / 22][k % 22];
+    __syncthreads();
+    const PairDesc pd = a.pairs[p];
+    const PairView v = make_view(a, pd, a.out[p], mat_s);
+    const size_t cols = static_cast<size_t>(pd.prot_len) + 1;
+    const size_t cells = (static_cast<size_t>(pd.nt_len) + 1) * cols;
+    for (size_t k = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; k < cells;
+         k += static_cast<size_t>(gridDim.x) * blockDim.x)
+        h[k] = v.H(static_cast<int>(k / cols), static_cast<int>(k % cols));
+}
+
 // ------------------------------------------------------------ compaction
 // Exclusive scan of per-pair op counts (one CTA), then a reversed copy of
 // each pair's ops into the compact array.
@@ -500,6 +524,13 @@ cudaError_t launch_pack(const PairDesc *pairs, uint32_t n, const char *ascii, ui
     if (n == 0) return cudaSuccess;
     const uint32_t grid = n < 8192 ? n : 8192;
     pack_kernel<<<grid, 256, 0, st>>>(pairs, n, ascii, prot, nt2, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dump_h(const TBArgs &a, uint32_t p, size_t cells, int32_t *h, cudaStream_t st)
+{
+    const size_t blocks = (cells + 255) / 256;
+    dump_h_kernel<<<static_cast<unsigned>(blocks < 1024 ? (blocks ? blocks : 1) : 1024), 256, 0, st>>>(a, p, h);
     return cudaGetLastError();
 }
 

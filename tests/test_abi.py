@@ -94,4 +94,5 @@ def test_null_arguments(mp):
     assert L.mp_dp_get_tuning(None, None, None) == mp.MP_EINVAL
     assert L.mp_dp_tuning_save(None, b"x") == mp.MP_EINVAL
     assert L.mp_dp_tuning_load(None, b"x") == mp.MP_EINVAL
+    assert L.mp_dp_debug_h(None, None, 0, None) == mp.MP_EINVAL
     L.mp_dp_destroy(None)

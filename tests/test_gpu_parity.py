@@ -426,6 +426,33 @@ def _anchored_pairs(seed, count, mmax):
     return out
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("force_int32", [0, 1])
+def test_stored_h_matches_oracle(mp, orc, mode, force_int32):
+    """Every stored H value of Eq. 7 (read back from the traceback stream,
+    with the mode's row 0 and column 0) equals the oracle's H matrix, cell
+    by cell, for pairs spanning several strips and chunks, both strands,
+    in the int16 and int32 kernels."""
+    pairs = _anchored_pairs(140 + mode, 6, 150)
+    params = mp.mp_dp_default_params(mode=mode, force_int32=force_int32)
+    op = _orc_params(orc, params)
+    op.mode = mode
+    c = mp.mp_dp_init(params, 0)
+    try:
+        b = mp.mp_dp_batch_upload(c, pairs)
+        mp.mp_dp_batch_run(c, b)
+        mp.mp_dp_batch_sync(c)
+        for k, p in enumerate(pairs):
+            got = mp.mp_dp_debug_h(c, b, k, len(p.nt), len(p.prot))
+            want = orc.fill_h(p.prot, p.nt, p.strand, op)
+            bad = np.argwhere(got != want)
+            assert bad.size == 0, (k, len(p.nt), len(p.prot), p.strand,
+                                   [(int(i), int(j), int(got[i, j]), int(want[i, j])) for i, j in bad[:8]])
+        mp.mp_dp_batch_free(c, b)
+    finally:
+        mp.mp_dp_destroy(c)
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("splice_model", [0, 1])
 def test_anchored_modes(mp, orc, mode, splice_model):
