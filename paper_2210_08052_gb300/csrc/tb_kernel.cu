@@ -492,15 +492,19 @@ __global__ void col0_kernel(const PairDesc *pairs, uint32_t n_pairs, const uint3
             const bool v1 = in(x - 2), v2 = in(x - 1), v3 = in(x);
             return splice_acceptor(sp, v1 ? base(x - 2) : 0, v2 ? base(x - 1) : 0, v3 ? base(x) : 0, v1, v2, v3);
         };
-        // H[i-1], H[i-2], H[i-3]; D[i-1], D[i-2], D[i-3]; A[i-1]
-        int32_t h1 = 0, h2 = NEG, h3 = NEG, d1 = NEG, d2 = NEG, d3 = NEG, av = NEG;
+        // H[i-1], H[i-2], H[i-3]; D[i-1], D[i-2], D[i-3]; A[i-1].  The state is
+        // carried in 64 bits: ptxas 13.0 at -O1 and above turned the same loop
+        // with 32-bit state into code that returns +f for H[1][0] (correct at
+        // -O0); the 64-bit form compiles to the recurrence as written.
+        constexpr int64_t N64 = NEG;
+        int64_t h1 = 0, h2 = N64, h3 = N64, d1 = N64, d2 = N64, d3 = N64, av = N64;
         h[0] = 0;
         for (int i = 1; i <= n; ++i) {
-            const int32_t dv = max(max(h3 - sp.q, d3) - sp.e, NEG);
-            av = max(max(h1 - sp.r - dsc(i - 1), av), NEG);
-            int32_t hv = max(dv, max(h1, h2) - sp.f);
-            hv = max(max(hv, av - asc(i)), NEG);
-            h[i] = hv;
+            const int64_t dv = max(max(h3 - sp.q, d3) - sp.e, N64);
+            av = max(max(h1 - sp.r - dsc(i - 1), av), N64);
+            int64_t hv = max(dv, max(h1, h2) - sp.f);
+            hv = max(max(hv, av - asc(i)), N64);
+            h[i] = static_cast<int32_t>(hv);
             d3 = d2; d2 = d1; d1 = dv;
             h3 = h2; h2 = h1; h1 = hv;
         }

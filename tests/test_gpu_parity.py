@@ -448,11 +448,12 @@ def test_stored_h_matches_oracle(mp, orc, mode, force_int32):
             want = orc.fill_h(p.prot, p.nt, p.strand, op)
             bad = np.argwhere(got != want)
             if bad.size:
-                report.append((k, len(p.nt), len(p.prot), p.strand, len(bad),
-                               "col0 got", got[:6, 0].tolist(), "want", want[:6, 0].tolist(),
-                               [(int(i), int(j), int(got[i, j]), int(want[i, j])) for i, j in bad[:4]]))
+                report.append(f"pair {k} |T|={len(p.nt)} |P|={len(p.prot)} strand={p.strand} bad={len(bad)} "
+                              f"col0 {got[:10, 0].tolist()} want {want[:10, 0].tolist()} "
+                              f"row1 {got[1, :6].tolist()} want {want[1, :6].tolist()} "
+                              f"first {[(int(i), int(j), int(got[i, j]), int(want[i, j])) for i, j in bad[:4]]}")
         mp.mp_dp_batch_free(c, b)
-        assert not report, report
+        assert not report, "\n".join(report)
     finally:
         mp.mp_dp_destroy(c)
 
