@@ -495,6 +495,33 @@ def main():
         line["exon_rescore"] = {"value": cells / te / 1e9, "unit": "GCUPS (alignment cells; end to end)",
                                 "ms_per_call": te * 1000,
                                 "extra_ms_over_e2e": te * 1000 - (e2e_t / e2e_steps * 1000 if e2e_steps else 0.0)}
+        # anchored modes on the same batch (gap closing between anchors, and
+        # extension from an anchor): device-resident inputs, pipeline time by
+        # CUDA events, the L2 flushed before each timed run
+        anchored = {}
+        for mode, name in ((1, "global"), (2, "extension")):
+            ctxa = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode), local)
+            mp.mp_dp_set_timing(ctxa, True)
+            ba = mp.mp_dp_batch_upload(ctxa, src)
+            for _ in range(2):                    # autotune on the first run, then a warm-up
+                mp.mp_dp_batch_run(ctxa, ba)
+                mp.mp_dp_batch_sync(ctxa)
+            ams, ars = [], []
+            for _ in range(2):
+                flush.zero_()
+                torch.cuda.synchronize()
+                mp.mp_dp_batch_run(ctxa, ba)
+                mp.mp_dp_batch_sync(ctxa)
+                sa = mp.mp_dp_get_stats(ctxa)
+                ams.append(sa["total_ms"])
+                ars.append(sa["rerun_ms"])
+            ra = mp.mp_dp_batch_download(ctxa, ba, raw=True)
+            mp.mp_dp_batch_free(ctxa, ba)
+            mp.mp_dp_destroy(ctxa)
+            anchored[name] = {"value": cells / (statistics.mean(ams) / 1000) / 1e9, "unit": "GCUPS",
+                              "pipeline_ms": statistics.mean(ams), "int32_ms": statistics.mean(ars),
+                              "pairs_with_error_status": int(((ra["status"] & 0xF0) != 0).sum())}
+        line["anchored_modes"] = anchored
         line["plain"] = {"value": pc / tp / 1e9, "unit": "GCUPS", "pairs_per_s": len(sample) / tp,
                          "sample": f"{len(sample)} random pairs of the workload, one kernel launch per pair",
                          "batched_over_plain": gcups / (pc / tp / 1e9)}
