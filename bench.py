@@ -506,7 +506,7 @@ def main():
             for _ in range(2):                    # autotune on the first run, then a warm-up
                 mp.mp_dp_batch_run(ctxa, ba)
                 mp.mp_dp_batch_sync(ctxa)
-            ams, ars = [], []
+            ams, ars, ads, ats = [], [], [], []
             for _ in range(2):
                 flush.zero_()
                 torch.cuda.synchronize()
@@ -515,11 +515,14 @@ def main():
                 sa = mp.mp_dp_get_stats(ctxa)
                 ams.append(sa["total_ms"])
                 ars.append(sa["rerun_ms"])
+                ads.append(sa["dp_ms"])
+                ats.append(sa["tb_ms"])
             ra = mp.mp_dp_batch_download(ctxa, ba, raw=True)
             mp.mp_dp_batch_free(ctxa, ba)
             mp.mp_dp_destroy(ctxa)
             anchored[name] = {"value": cells / (statistics.mean(ams) / 1000) / 1e9, "unit": "GCUPS",
-                              "pipeline_ms": statistics.mean(ams), "int32_ms": statistics.mean(ars),
+                              "pipeline_ms": statistics.mean(ams), "dp_int16_ms": statistics.mean(ads),
+                              "int32_ms": statistics.mean(ars), "traceback_ms": statistics.mean(ats),
                               "pairs_with_error_status": int(((ra["status"] & 0xF0) != 0).sum())}
         line["anchored_modes"] = anchored
         line["plain"] = {"value": pc / tp / 1e9, "unit": "GCUPS", "pairs_per_s": len(sample) / tp,

@@ -470,45 +470,66 @@ namespace {
 // Column 0 in the anchored modes, where the path starts at cell (0, 0):
 // H[0][0] = 0 and, for i >= 1, Eq. 7 with no residue consumed -- a codon
 // deletion run (D), the frameshift insertions G1, G2 and the phase-0 intron
-// state A (M, I, F1, F2, B and C need column -1).  One thread per pair,
-// sequential in i; rows past |T| hold -inf.
-__global__ void col0_kernel(const PairDesc *pairs, uint32_t n_pairs, const uint32_t *nt2, const ScoreParams sp,
-                            int32_t *col0)
+// state A (M, I, F1, F2, B and C need column -1).  One warp per pair, in
+// tiles of kCol0Tile rows: the lanes evaluate the splice terms d(i-1),
+// a(i) of the tile into shared memory, lane 0 runs the sequential
+// recurrence over it, and the lanes write the tile out.  Rows past |T| hold
+// -inf.
+constexpr int kCol0Tile = 256;
+constexpr int kCol0Warps = 4;
+
+__global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *pairs, uint32_t n_pairs,
+                                                                 const uint32_t *nt2, const ScoreParams sp,
+                                                                 int32_t *col0)
 {
     constexpr int32_t NEG = -(1 << 28);
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs; p += gridDim.x * blockDim.x) {
+    __shared__ int32_t s_d[kCol0Warps][kCol0Tile], s_a[kCol0Warps][kCol0Tile], s_h[kCol0Warps][kCol0Tile];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const uint32_t nwarps = gridDim.x * kCol0Warps;
+    for (uint32_t p = blockIdx.x * kCol0Warps + wl; p < n_pairs; p += nwarps) {
         const PairDesc pd = pairs[p];
         if (pd.flags & PF_SKIP) continue;
         const int n = static_cast<int>(pd.nt_len);
         const uint32_t *g = nt2 + pd.nt_word_off;
         int32_t *h = col0 + pd.col0_off;
-        auto base = [&](int x) { return static_cast<int>((g[(x - 1) >> 4] >> (2 * ((x - 1) & 15))) & 3); };
+        auto base = [&](int x) { return static_cast<int>((__ldg(g + ((x - 1) >> 4)) >> (2 * ((x - 1) & 15))) & 3); };
         auto in = [&](int x) { return x >= 1 && x <= n; };
-        auto dsc = [&](int x) {
-            const bool v1 = in(x + 1), v2 = in(x + 2), v3 = in(x + 3);
-            return splice_donor(sp, v1 ? base(x + 1) : 0, v2 ? base(x + 2) : 0, v3 ? base(x + 3) : 0, v1, v2, v3);
-        };
-        auto asc = [&](int x) {
-            const bool v1 = in(x - 2), v2 = in(x - 1), v3 = in(x);
-            return splice_acceptor(sp, v1 ? base(x - 2) : 0, v2 ? base(x - 1) : 0, v3 ? base(x) : 0, v1, v2, v3);
-        };
-        // H[i-1], H[i-2], H[i-3]; D[i-1], D[i-2], D[i-3]; A[i-1].  The state is
-        // carried in 64 bits: ptxas 13.0 at -O1 and above turned the same loop
-        // with 32-bit state into code that returns +f for H[1][0] (correct at
-        // -O0); the 64-bit form compiles to the recurrence as written.
+        // lane 0's recurrence state: H[i-1], H[i-2], H[i-3]; D[i-1], D[i-2],
+        // D[i-3]; A[i-1].  It is carried in 64 bits: ptxas 13.0 at -O1 and
+        // above turned an earlier form of this recurrence with 32-bit state
+        // into code that returned +f for H[1][0] (correct at -O0).
         constexpr int64_t N64 = NEG;
         int64_t h1 = 0, h2 = N64, h3 = N64, d1 = N64, d2 = N64, d3 = N64, av = N64;
-        h[0] = 0;
-        for (int i = 1; i <= n; ++i) {
-            const int64_t dv = max(max(h3 - sp.q, d3) - sp.e, N64);
-            av = max(max(h1 - sp.r - dsc(i - 1), av), N64);
-            int64_t hv = max(dv, max(h1, h2) - sp.f);
-            hv = max(max(hv, av - asc(i)), N64);
-            h[i] = static_cast<int32_t>(hv);
-            d3 = d2; d2 = d1; d1 = dv;
-            h3 = h2; h2 = h1; h1 = hv;
+        if (lane == 0) h[0] = 0;
+        for (int i0 = 1; i0 <= n; i0 += kCol0Tile) {
+            const int cnt = min(kCol0Tile, n - i0 + 1);
+            for (int k = lane; k < cnt; k += 32) {
+                const int i = i0 + k;
+                // d(i-1) from T[i..i+2], a(i) from T[i-2..i]
+                const bool dv1 = in(i), dv2 = in(i + 1), dv3 = in(i + 2);
+                s_d[wl][k] = splice_donor(sp, dv1 ? base(i) : 0, dv2 ? base(i + 1) : 0, dv3 ? base(i + 2) : 0,
+                                          dv1, dv2, dv3);
+                const bool av1 = in(i - 2), av2 = in(i - 1);
+                s_a[wl][k] = splice_acceptor(sp, av1 ? base(i - 2) : 0, av2 ? base(i - 1) : 0, base(i), av1, av2,
+                                             true);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                for (int k = 0; k < cnt; ++k) {
+                    const int64_t dv = max(max(h3 - sp.q, d3) - sp.e, N64);
+                    av = max(max(h1 - sp.r - s_d[wl][k], av), N64);
+                    int64_t hv = max(dv, max(h1, h2) - sp.f);
+                    hv = max(max(hv, av - s_a[wl][k]), N64);
+                    s_h[wl][k] = static_cast<int32_t>(hv);
+                    d3 = d2; d2 = d1; d1 = dv;
+                    h3 = h2; h2 = h1; h1 = hv;
+                }
+            }
+            __syncwarp();
+            for (int k = lane; k < cnt; k += 32) h[i0 + k] = s_h[wl][k];
+            __syncwarp();
         }
-        for (int i = n + 1; i <= n + kCol0Pad; ++i) h[i] = NEG;
+        for (int i = n + 1 + lane; i <= n + kCol0Pad; i += 32) h[i] = NEG;
     }
 }
 }  // namespace
@@ -517,8 +538,8 @@ cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, 
                         cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    const uint32_t grid = (n + 127) / 128 < 2048 ? (n + 127) / 128 : 2048;
-    col0_kernel<<<grid, 128, 0, st>>>(pairs, n, nt2, sp, col0);
+    const uint32_t blocks = (n + kCol0Warps - 1) / kCol0Warps;
+    col0_kernel<<<blocks < 4096 ? blocks : 4096, kCol0Warps * 32, 0, st>>>(pairs, n, nt2, sp, col0);
     return cudaGetLastError();
 }
 
