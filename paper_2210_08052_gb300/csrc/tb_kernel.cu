@@ -470,66 +470,148 @@ namespace {
 // Column 0 in the anchored modes, where the path starts at cell (0, 0):
 // H[0][0] = 0 and, for i >= 1, Eq. 7 with no residue consumed -- a codon
 // deletion run (D), the frameshift insertions G1, G2 and the phase-0 intron
-// state A (M, I, F1, F2, B and C need column -1).  One warp per pair, in
-// tiles of kCol0Tile rows: the lanes evaluate the splice terms d(i-1),
-// a(i) of the tile into shared memory, lane 0 runs the sequential
-// recurrence over it, and the lanes write the tile out.  Rows past |T| hold
-// -inf.
-constexpr int kCol0Tile = 256;
+// state A (M, I, F1, F2, B and C need column -1):
+//   D[i] = max(H[i-3] - q - e, D[i-3] - e)
+//   A[i] = max(H[i-1] - r - d(i-1), A[i-1])
+//   H[i] = max(D[i], H[i-1] - f, H[i-2] - f, A[i] - a(i)).
+// Each row is a (max, +)-linear map of the state
+//   s = (H[i], H[i-1], H[i-2], D[i], D[i-1], D[i-2], A[i]),
+// so one warp per pair splits the rows into 32 segments: each lane composes
+// the 7x7 transfer matrix of its segment, the segments' incoming states are
+// then chained across the lanes (32 matrix-vector products), and each lane
+// re-runs its segment from its incoming state, writing H.  The critical
+// path is |T|/32 rows instead of |T|.  Rows past |T| hold -inf.
 constexpr int kCol0Warps = 4;
+constexpr int kS = 7;   // state size
+
+struct Col0Ctx {
+    const uint32_t *g;
+    int n;
+    int qe, e, f, r;
+};
+
+// base at 1-based position x (1 <= x <= n)
+__device__ __forceinline__ int col0_base(const uint32_t *g, int x)
+{
+    return static_cast<int>((__ldg(g + ((x - 1) >> 4)) >> (2 * ((x - 1) & 15))) & 3);
+}
+
+// Sliding window of the bases T[i-2..i+2] around row i, giving d(i-1)
+// (from T[i..i+2]) and a(i) (from T[i-2..i]).
+struct SpliceWindow {
+    int b[5];      // T[i-2], T[i-1], T[i], T[i+1], T[i+2] (0 where outside)
+    int i;
+    __device__ __forceinline__ void start(const Col0Ctx &c, int i0)
+    {
+        i = i0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int x = i0 - 2 + k;
+            b[k] = (x >= 1 && x <= c.n) ? col0_base(c.g, x) : 0;
+        }
+    }
+    __device__ __forceinline__ void advance(const Col0Ctx &c)
+    {
+        ++i;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b[k] = b[k + 1];
+        b[4] = (i + 2 <= c.n) ? col0_base(c.g, i + 2) : 0;
+    }
+    __device__ __forceinline__ int donor(const ScoreParams &sp, const Col0Ctx &c) const
+    {
+        return splice_donor(sp, b[2], b[3], b[4], true, i + 1 <= c.n, i + 2 <= c.n);
+    }
+    __device__ __forceinline__ int acceptor(const ScoreParams &sp) const
+    {
+        return splice_acceptor(sp, b[0], b[1], b[2], i - 2 >= 1, i - 1 >= 1, true);
+    }
+};
+
+// One row applied to a state vector v (in place); every value stays >= NEG.
+template <typename T>
+__device__ __forceinline__ void col0_row(T *v, const Col0Ctx &c, int dd, int aa)
+{
+    const T neg = static_cast<T>(kNeg);
+    const T dn = max(max(v[2] - c.qe, v[5] - c.e), neg);
+    const T an = max(max(v[0] - c.r - dd, v[6]), neg);
+    const T hn = max(max(dn, max(v[0], v[1]) - c.f), max(an - aa, neg));
+    v[5] = v[4]; v[4] = v[3]; v[3] = dn;
+    v[2] = v[1]; v[1] = v[0]; v[0] = hn;
+    v[6] = an;
+}
 
 __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *pairs, uint32_t n_pairs,
                                                                  const uint32_t *nt2, const ScoreParams sp,
                                                                  int32_t *col0)
 {
-    constexpr int32_t NEG = -(1 << 28);
-    __shared__ int32_t s_d[kCol0Warps][kCol0Tile], s_a[kCol0Warps][kCol0Tile], s_h[kCol0Warps][kCol0Tile];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kCol0Warps;
-    for (uint32_t p = blockIdx.x * kCol0Warps + wl; p < n_pairs; p += nwarps) {
+    for (uint32_t p = blockIdx.x * kCol0Warps + (threadIdx.x >> 5); p < n_pairs; p += nwarps) {
         const PairDesc pd = pairs[p];
         if (pd.flags & PF_SKIP) continue;
         const int n = static_cast<int>(pd.nt_len);
-        const uint32_t *g = nt2 + pd.nt_word_off;
+        const Col0Ctx c{nt2 + pd.nt_word_off, n, sp.q + sp.e, sp.e, sp.f, sp.r};
         int32_t *h = col0 + pd.col0_off;
-        auto base = [&](int x) { return static_cast<int>((__ldg(g + ((x - 1) >> 4)) >> (2 * ((x - 1) & 15))) & 3); };
-        auto in = [&](int x) { return x >= 1 && x <= n; };
-        // lane 0's recurrence state: H[i-1], H[i-2], H[i-3]; D[i-1], D[i-2],
-        // D[i-3]; A[i-1].  It is carried in 64 bits: ptxas 13.0 at -O1 and
-        // above turned an earlier form of this recurrence with 32-bit state
-        // into code that returned +f for H[1][0] (correct at -O0).
-        constexpr int64_t N64 = NEG;
-        int64_t h1 = 0, h2 = N64, h3 = N64, d1 = N64, d2 = N64, d3 = N64, av = N64;
-        if (lane == 0) h[0] = 0;
-        for (int i0 = 1; i0 <= n; i0 += kCol0Tile) {
-            const int cnt = min(kCol0Tile, n - i0 + 1);
-            for (int k = lane; k < cnt; k += 32) {
-                const int i = i0 + k;
-                // d(i-1) from T[i..i+2], a(i) from T[i-2..i]
-                const bool dv1 = in(i), dv2 = in(i + 1), dv3 = in(i + 2);
-                s_d[wl][k] = splice_donor(sp, dv1 ? base(i) : 0, dv2 ? base(i + 1) : 0, dv3 ? base(i + 2) : 0,
-                                          dv1, dv2, dv3);
-                const bool av1 = in(i - 2), av2 = in(i - 1);
-                s_a[wl][k] = splice_acceptor(sp, av1 ? base(i - 2) : 0, av2 ? base(i - 1) : 0, base(i), av1, av2,
-                                             true);
-            }
-            __syncwarp();
-            if (lane == 0) {
-                for (int k = 0; k < cnt; ++k) {
-                    const int64_t dv = max(max(h3 - sp.q, d3) - sp.e, N64);
-                    av = max(max(h1 - sp.r - s_d[wl][k], av), N64);
-                    int64_t hv = max(dv, max(h1, h2) - sp.f);
-                    hv = max(max(hv, av - s_a[wl][k]), N64);
-                    s_h[wl][k] = static_cast<int32_t>(hv);
-                    d3 = d2; d2 = d1; d1 = dv;
-                    h3 = h2; h2 = h1; h1 = hv;
-                }
-            }
-            __syncwarp();
-            for (int k = lane; k < cnt; k += 32) h[i0 + k] = s_h[wl][k];
-            __syncwarp();
+        const int L = (n + 31) / 32;
+        const int r0 = lane * L + 1, r1 = min(n, (lane + 1) * L);     // this lane's rows (none if r0 > r1)
+
+        // 1. transfer matrix of the segment: column k is the state reached
+        //    from the k-th unit state (0 at k, -inf elsewhere)
+        int32_t t[kS][kS];
+#pragma unroll
+        for (int k = 0; k < kS; ++k) {
+#pragma unroll
+            for (int j = 0; j < kS; ++j) t[k][j] = j == k ? 0 : kNeg;
         }
-        for (int i = n + 1 + lane; i <= n + kCol0Pad; i += 32) h[i] = NEG;
+        SpliceWindow w;
+        if (r0 <= r1) {
+            w.start(c, r0);
+            for (int i = r0; i <= r1; ++i) {
+                const int dd = w.donor(sp, c), aa = w.acceptor(sp);
+#pragma unroll
+                for (int k = 0; k < kS; ++k) col0_row(t[k], c, dd, aa);
+                if (i < r1) w.advance(c);
+            }
+        }
+        // 2. incoming state of every segment, chained across the lanes from
+        //    s_0 = (0, -inf, ...); entries are sums of two values >= NEG, so
+        //    no 32-bit overflow before the clamp
+        int32_t s[kS], sin[kS];
+#pragma unroll
+        for (int k = 0; k < kS; ++k) s[k] = sin[k] = k == 0 ? 0 : kNeg;
+        for (int l = 0; l < 32; ++l) {
+            if (lane == l) {
+#pragma unroll
+                for (int k = 0; k < kS; ++k) sin[k] = s[k];
+            }
+            int32_t ns[kS];
+#pragma unroll
+            for (int j = 0; j < kS; ++j) ns[j] = kNeg;
+#pragma unroll
+            for (int k = 0; k < kS; ++k) {
+#pragma unroll
+                for (int j = 0; j < kS; ++j) ns[j] = max(ns[j], __shfl_sync(kFull, t[k][j], l) + s[k]);
+            }
+#pragma unroll
+            for (int j = 0; j < kS; ++j) s[j] = max(ns[j], kNeg);
+        }
+        // 3. re-run the segment from its incoming state (64-bit state: ptxas
+        //    13.0 at -O1 and above turned an earlier 32-bit form of this
+        //    recurrence into code returning +f for H[1][0]; correct at -O0)
+        if (lane == 0) h[0] = 0;
+        if (r0 <= r1) {
+            int64_t v[kS];
+#pragma unroll
+            for (int k = 0; k < kS; ++k) v[k] = sin[k];
+            w.start(c, r0);
+            for (int i = r0; i <= r1; ++i) {
+                const int dd = w.donor(sp, c), aa = w.acceptor(sp);
+                col0_row(v, c, dd, aa);
+                h[i] = static_cast<int32_t>(v[0]);
+                if (i < r1) w.advance(c);
+            }
+        }
+        for (int i = n + 1 + lane; i <= n + kCol0Pad; i += 32) h[i] = kNeg;
     }
 }
 }  // namespace
