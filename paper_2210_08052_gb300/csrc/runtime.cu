@@ -1372,25 +1372,29 @@ int mp_dp_align_batch(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *o
 // CIGAR runs outside the region.
 static bool exon_region(const mp_pair &q, const mp_result &r, std::string &out)
 {
-    const int32_t n = static_cast<int32_t>(q.nt_len);
-    std::string t(q.nt, q.nt_len);
-    if (q.strand < 0) {
-        std::reverse(t.begin(), t.end());
-        for (char &ch : t) {
-            switch (ch | 0x20) {
-            case 'a': ch = 'T'; break;
-            case 'c': ch = 'G'; break;
-            case 'g': ch = 'C'; break;
-            case 't': ch = 'A'; break;
-            default: return false;
-            }
-        }
-    }
+    // segments of the aligned orientation are taken straight from the
+    // caller's buffer: as they are for strand +1, reverse-complemented for
+    // strand -1 (aligned position i is base n-1-i of the buffer)
+    const int64_t n = static_cast<int64_t>(q.nt_len);
     int64_t i = q.strand > 0 ? r.nt_st : n - r.nt_en;
     out.clear();
     auto take = [&](int64_t len) {
         if (i < 0 || i + len > n) return false;
-        out.append(t, static_cast<size_t>(i), static_cast<size_t>(len));
+        if (q.strand > 0) {
+            out.append(q.nt + i, static_cast<size_t>(len));
+        } else {
+            for (int64_t k = 0; k < len; ++k) {
+                char ch;
+                switch (q.nt[n - 1 - (i + k)] | 0x20) {
+                case 'a': ch = 'T'; break;
+                case 'c': ch = 'G'; break;
+                case 'g': ch = 'C'; break;
+                case 't': ch = 'A'; break;
+                default: return false;
+                }
+                out.push_back(ch);
+            }
+        }
         i += len;
         return true;
     };
