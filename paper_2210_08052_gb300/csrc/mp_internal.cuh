@@ -135,6 +135,24 @@ cudaError_t launch_dp16(const DPArgs &a, int grid, int variant, cudaStream_t st)
 cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t st);
 cudaError_t launch_tb(const TBArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_dump_h(const TBArgs &a, uint32_t p, size_t cells, int32_t *h, cudaStream_t st);
+
+// One pair of a pseudogene-rescoring batch: where its protein and region
+// sit in the source ASCII (as the caller passed them), and its alignment's
+// ops (protein order) and start in the aligned orientation.  The gather
+// writes the protein and the alignment's intron-free coding region into the
+// rescoring batch's ASCII at the offsets of that batch's descriptor.
+struct ExonJob {
+    uint64_t src_nt_off;
+    uint64_t op_off;
+    uint32_t src_prot_off;
+    uint32_t src_nt_len;
+    uint32_t n_ops;
+    int32_t strand;
+    int32_t i0;
+    uint32_t pad;
+};
+cudaError_t launch_exon_gather(const ExonJob *jobs, uint32_t n, const PairDesc *aux, const char *src,
+                               const uint32_t *ops, char *dst, cudaStream_t st);
 // anchored modes: column 0 of every pair, H[i][0] for i = 0..|T| (then
 // padding), by the recurrence restricted to the D, G and A terms
 cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, const ScoreParams &sp, int32_t *col0,

@@ -263,6 +263,7 @@ struct mp_dp_ctx {
     mp_dp_batch *last = nullptr;   // batch of the last run (for its counters)
     mp_dp_batch *own = nullptr;    // buffers reused by mp_dp_align_batch from call to call
     mp_dp_batch *aux = nullptr;    // score-only batch of mp_dp_exon_rescore
+    DevBuf<uint8_t> exbuf;         // rescoring jobs (and, for earlier results, their regions and ops)
     std::vector<uint32_t> host_cig;
     // launch configuration: fixed by mp_dp_set_tuning, else tuned per shape class
     bool has_fixed = false;
@@ -702,11 +703,14 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t)
 
 // (Re)fill batch b with n pairs: plan strips, waves and offsets on the host,
 // grow the device buffers when needed, and copy the inputs to the device.
-static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_t n)
+// ascii_on_device: the caller writes the batch's ASCII into b->ascii on the
+// context's stream itself (the pairs' nt pointers are unused and may be null;
+// the protein pointers still serve the score bound).
+static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_t n, bool ascii_on_device = false)
 {
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
-        if ((q.prot_len && !q.prot) || (q.nt_len && !q.nt)) return MP_EINVAL;
+        if ((q.prot_len && !q.prot) || (q.nt_len && !q.nt && !ascii_on_device)) return MP_EINVAL;
         if (q.strand != 1 && q.strand != -1) return MP_EINVAL;
         if (q.prot_len >= (1u << 20) || q.nt_len >= (1u << 20) - 1024) return MP_EINVAL;
     }
@@ -786,6 +790,13 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         (e = b->recs.reserve(nrec + 1)) != cudaSuccess) {
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
+    cudaStream_t st = c->stream;
+    if (ascii_on_device) {
+        b->needs_waves = plan_code_bytes(c, b) > c->budget;
+        b->shape_key = shape_key_of(*b);
+        b->planned = -1;
+        return plan_waves(c, b, tuning_for(c, b));
+    }
     // ---- host -> device
     if (c->staging.reserve(asc + 16) != cudaSuccess) return MP_ENOMEM;
     auto gather = [&](size_t k0, size_t k1) {
@@ -804,7 +815,6 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     } else {
         gather(0, n);
     }
-    cudaStream_t st = c->stream;
     // the sequences travel while the host plans the waves (plan_waves waits
     // for the stream before it returns, so the staging buffer is free again)
     CK(cudaMemcpyAsync(b->ascii.p, c->staging.p, asc, cudaMemcpyHostToDevice, st));
@@ -1348,6 +1358,8 @@ int mp_dp_batch_download(mp_dp_ctx *c, mp_dp_batch *b, mp_result *out)
     return MP_OK;
 }
 
+static int exon_rescore_impl(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *res, const mp_dp_batch *src);
+
 int mp_dp_align_batch(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *out)
 {
     if (!c || (n && (!pairs || !out))) return MP_EINVAL;
@@ -1361,105 +1373,153 @@ int mp_dp_align_batch(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *o
     rc = mp_dp_batch_run(c, b);
     if (rc == MP_OK) rc = mp_dp_batch_sync(c);
     if (rc == MP_OK) rc = mp_dp_batch_download(c, b, out);
-    if (rc == MP_OK && c->params.exon_rescore) rc = mp_dp_exon_rescore(c, pairs, n, out);
+    if (rc == MP_OK && c->params.exon_rescore) rc = exon_rescore_impl(c, pairs, n, out, b);
     c->last = nullptr;
     return rc;
 }
 
 // The genome an alignment covers with its introns cut out, in the aligned
 // orientation: codons and frameshift bases kept, an N intron dropped, a U or
-// V intron dropped with the 3 bases of its split codon kept.  False if the
-// CIGAR runs outside the region.
-static bool exon_region(const mp_pair &q, const mp_result &r, std::string &out)
+// V intron dropped with the 3 bases of its split codon kept.  The host only
+// walks the ops for the region's length (and checks that the walk stays in
+// the region); the bases are gathered on the device (exon_gather_kernel).
+static bool exon_walk(const mp_result &r, int64_t n, int64_t i0, uint64_t &len, bool &has_intron)
 {
-    // segments of the aligned orientation are taken straight from the
-    // caller's buffer: as they are for strand +1, reverse-complemented for
-    // strand -1 (aligned position i is base n-1-i of the buffer)
-    const int64_t n = static_cast<int64_t>(q.nt_len);
-    int64_t i = q.strand > 0 ? r.nt_st : n - r.nt_en;
-    out.clear();
-    auto take = [&](int64_t len) {
-        if (i < 0 || i + len > n) return false;
-        if (q.strand > 0) {
-            out.append(q.nt + i, static_cast<size_t>(len));
-        } else {
-            for (int64_t k = 0; k < len; ++k) {
-                char ch;
-                switch (q.nt[n - 1 - (i + k)] | 0x20) {
-                case 'a': ch = 'T'; break;
-                case 'c': ch = 'G'; break;
-                case 'g': ch = 'C'; break;
-                case 't': ch = 'A'; break;
-                default: return false;
-                }
-                out.push_back(ch);
-            }
-        }
-        i += len;
-        return true;
-    };
+    int64_t i = i0;
+    len = 0;
+    has_intron = false;
+    if (i < 0 || i > n) return false;
+    auto take = [&](int64_t l) { i += l; len += static_cast<uint64_t>(l); return i <= n; };
     for (uint32_t k = 0; k < r.n_cigar; ++k) {
-        const uint32_t op = r.cigar[k] & 0xf;
-        const int64_t len = r.cigar[k] >> 4;
+        const int64_t l = r.cigar[k] >> 4;
         bool ok = true;
-        switch (op) {
-        case MP_OP_M: case MP_OP_D: ok = take(3 * len); break;
+        switch (r.cigar[k] & 0xf) {
+        case MP_OP_M: case MP_OP_D: ok = take(3 * l); break;
         case MP_OP_I: break;
-        case MP_OP_F: case MP_OP_G: ok = take(len); break;
-        case MP_OP_N: i += len; break;
-        case MP_OP_U: ok = take(1); i += len; ok = ok && take(2); break;
-        case MP_OP_V: ok = take(2); i += len; ok = ok && take(1); break;
+        case MP_OP_F: case MP_OP_G: ok = take(l); break;
+        case MP_OP_N: i += l; has_intron = true; ok = i <= n; break;
+        case MP_OP_U: ok = take(1); i += l; ok = ok && take(2); has_intron = true; break;
+        case MP_OP_V: ok = take(2); i += l; ok = ok && take(1); has_intron = true; break;
         default: ok = false;
         }
-        if (!ok || i > n) return false;
+        if (!ok) return false;
     }
     return true;
 }
 
-int mp_dp_exon_rescore(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *res)
+// src: the batch whose run produced res (its ASCII and compacted ops are
+// still on the device), or null for results from elsewhere (their regions,
+// proteins and ops are uploaded).
+static int exon_rescore_impl(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *res, const mp_dp_batch *src)
 {
-    if (!c || (n && (!pairs || !res))) return MP_EINVAL;
     if (c->server_running) return MP_ESTATE;
-    std::vector<std::string> seqs;
     std::vector<size_t> idx;
     std::vector<char> intron;
+    std::vector<ExonJob> jobs;
+    std::vector<mp_pair> sub;
+    const uint32_t *hc = c->host_cig.data();
+    const size_t hc_n = c->host_cig.size();
     for (size_t k = 0; k < n; ++k) {
         const mp_result &r = res[k];
         if (r.score <= 0 || !r.n_cigar || !r.cigar || (r.status & MP_ST_ERRMASK)) continue;
-        std::string s;
-        if (!exon_region(pairs[k], r, s)) continue;
+        const mp_pair &q = pairs[k];
+        if (q.strand != 1 && q.strand != -1) continue;
+        const int64_t nl = q.nt_len;
+        const int64_t i0 = q.strand > 0 ? r.nt_st : nl - r.nt_en;
+        uint64_t len = 0;
         bool has_intron = false;
-        for (uint32_t j = 0; j < r.n_cigar; ++j) {
-            const uint32_t op = r.cigar[j] & 0xf;
-            has_intron |= op == MP_OP_N || op == MP_OP_U || op == MP_OP_V;
-        }
-        seqs.push_back(std::move(s));
+        if (!exon_walk(r, nl, i0, len, has_intron) || len >= (1u << 20) - 1024) continue;
+        ExonJob j{};
+        j.src_nt_len = q.nt_len;
+        j.n_ops = r.n_cigar;
+        j.strand = q.strand;
+        j.i0 = static_cast<int32_t>(i0);
+        jobs.push_back(j);
+        sub.push_back(mp_pair{q.prot, q.prot_len, nullptr, static_cast<uint32_t>(len), 1, MP_PAIR_SCORE_ONLY});
         idx.push_back(k);
         intron.push_back(has_intron ? 1 : 0);
     }
     if (idx.empty()) return MP_OK;
-    std::vector<mp_pair> sub(idx.size());
-    for (size_t i = 0; i < idx.size(); ++i) {
-        const mp_pair &q = pairs[idx[i]];
-        sub[i] = mp_pair{q.prot, q.prot_len, seqs[i].data(), static_cast<uint32_t>(seqs[i].size()), 1,
-                         MP_PAIR_SCORE_ONLY};
+    // a source batch serves only if every result's ops lie in the context's
+    // copy of that batch's compacted CIGARs
+    bool resident = src != nullptr && src->n == n;
+    for (size_t i = 0; resident && i < idx.size(); ++i) {
+        const mp_result &r = res[idx[i]];
+        resident = r.cigar >= hc && r.cigar + r.n_cigar <= hc + hc_n;
     }
     if (!c->aux) c->aux = new (std::nothrow) mp_dp_batch();
     if (!c->aux) return MP_ENOMEM;
     mp_dp_batch *b = c->aux;
-    int rc = upload_impl(c, b, sub.data(), sub.size());
-    if (rc == MP_OK) rc = mp_dp_batch_run(c, b);
+    int rc = upload_impl(c, b, sub.data(), sub.size(), true);
     if (rc != MP_OK) return rc;
-    b->h_out.resize(sub.size());
-    CK(cudaMemcpyAsync(b->h_out.data(), b->out.p, sub.size() * sizeof(PairOut), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    for (size_t i = 0; i < idx.size(); ++i) {
+    // device buffer: [jobs][ops][ASCII of the source pairs] (the last two only
+    // without a resident source), each part 16-byte aligned
+    const size_t nj = jobs.size();
+    const size_t jobs_bytes = div_up(nj * sizeof(ExonJob), 16) * 16;
+    size_t ops_bytes = 0, asc_bytes = 0;
+    if (resident) {
+        for (size_t i = 0; i < nj; ++i) {
+            const size_t k = idx[i];
+            jobs[i].src_nt_off = src->desc[k].asc_nt_off;
+            jobs[i].src_prot_off = src->desc[k].asc_prot_off;
+            jobs[i].op_off = static_cast<uint64_t>(res[k].cigar - hc);
+        }
+    } else {
+        uint64_t ops = 0, asc = 0;
+        for (size_t i = 0; i < nj; ++i) {
+            const size_t k = idx[i];
+            jobs[i].op_off = ops;
+            ops += res[k].n_cigar;
+            jobs[i].src_prot_off = static_cast<uint32_t>(asc);
+            asc += pairs[k].prot_len;
+            jobs[i].src_nt_off = asc;
+            asc += pairs[k].nt_len;
+            asc = div_up(asc, 16) * 16;
+        }
+        if (asc > 0xffffffffull) return MP_EINVAL;
+        ops_bytes = div_up(ops * sizeof(uint32_t), 16) * 16;
+        asc_bytes = asc;
+    }
+    const size_t total = jobs_bytes + ops_bytes + asc_bytes;
+    if (c->staging.reserve(total + 16) != cudaSuccess || c->exbuf.reserve(total + 16) != cudaSuccess)
+        return MP_ENOMEM;
+    char *h = c->staging.p;
+    memcpy(h, jobs.data(), nj * sizeof(ExonJob));
+    if (!resident) {
+        uint32_t *hops = reinterpret_cast<uint32_t *>(h + jobs_bytes);
+        char *hasc = h + jobs_bytes + ops_bytes;
+        for (size_t i = 0; i < nj; ++i) {
+            const size_t k = idx[i];
+            memcpy(hops + jobs[i].op_off, res[k].cigar, res[k].n_cigar * sizeof(uint32_t));
+            const mp_pair &q = pairs[k];
+            if (q.prot_len) memcpy(hasc + jobs[i].src_prot_off, q.prot, q.prot_len);
+            if (q.nt_len) memcpy(hasc + jobs[i].src_nt_off, q.nt, q.nt_len);
+        }
+    }
+    cudaStream_t st = c->stream;
+    CK(cudaMemcpyAsync(c->exbuf.p, h, total, cudaMemcpyHostToDevice, st));
+    const ExonJob *d_jobs = reinterpret_cast<const ExonJob *>(c->exbuf.p);
+    const uint32_t *d_ops = resident ? src->cig.p : reinterpret_cast<const uint32_t *>(c->exbuf.p + jobs_bytes);
+    const char *d_src = resident ? src->ascii.p : reinterpret_cast<const char *>(c->exbuf.p + jobs_bytes + ops_bytes);
+    CK(launch_exon_gather(d_jobs, static_cast<uint32_t>(nj), b->d_desc.p, d_src, d_ops, b->ascii.p, st));
+    rc = mp_dp_batch_run(c, b);
+    if (rc != MP_OK) return rc;
+    b->h_out.resize(nj);
+    CK(cudaMemcpyAsync(b->h_out.data(), b->out.p, nj * sizeof(PairOut), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < nj; ++i) {
         const PairOut &o = b->h_out[i];
         if (o.status & MP_ST_ERRMASK) continue;
         const int32_t s2 = o.score > 0 ? o.score : 0;
         res[idx[i]].exon_score = s2 - (intron[i] ? 0 : c->params.r);
     }
     return MP_OK;
+}
+
+int mp_dp_exon_rescore(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *res)
+{
+    if (!c || (n && (!pairs || !res))) return MP_EINVAL;
+    return exon_rescore_impl(c, pairs, n, res, nullptr);
 }
 
 }  // extern "C"
@@ -1732,6 +1792,7 @@ extern "C" void mp_dp_destroy(mp_dp_ctx *c)
     c->own = nullptr;
     c->codes.release();
     c->staging.release();
+    c->exbuf.release();
     if (c->stream2) cudaStreamSynchronize(c->stream2);
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->stream2) cudaStreamDestroy(c->stream2);

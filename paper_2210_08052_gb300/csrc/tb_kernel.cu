@@ -625,6 +625,72 @@ cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, 
     return cudaGetLastError();
 }
 
+namespace {
+// Complement of one ASCII base (either case); anything else becomes N,
+// which the pack step reports as a bad sequence.
+__device__ __forceinline__ char complement_base(char ch)
+{
+    switch (ch | 0x20) {
+    case 'a': return 'T';
+    case 'c': return 'G';
+    case 'g': return 'C';
+    case 't': return 'A';
+    default: return 'N';
+    }
+}
+
+// One warp per rescoring pair: the protein, then the bases the alignment
+// keeps (codons of M and D, the bases of F and G, the split codon around a
+// U or V intron; an N intron and the intron of U or V are skipped), in the
+// aligned orientation (reverse complement of the caller's region on strand
+// -1).  Every copy is bounded by both the source region and the
+// destination length.
+__global__ void exon_gather_kernel(const ExonJob *jobs, uint32_t n, const PairDesc *aux, const char *src,
+                                   const uint32_t *ops, char *dst)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nwarps) {
+        const ExonJob J = jobs[j];
+        const PairDesc d = aux[j];
+        for (uint32_t k = lane; k < d.prot_len; k += 32) dst[d.asc_prot_off + k] = src[J.src_prot_off + k];
+        const int64_t nl = J.src_nt_len, out_len = d.nt_len;
+        int64_t i = J.i0, o = 0;
+        auto copy = [&](int64_t len) {
+            for (int64_t t = lane; t < len; t += 32) {
+                const int64_t a = i + t;
+                if (a < 0 || a >= nl || o + t >= out_len) continue;
+                dst[d.asc_nt_off + o + t] =
+                    J.strand > 0 ? src[J.src_nt_off + a] : complement_base(src[J.src_nt_off + nl - 1 - a]);
+            }
+            i += len;
+            o += len;
+        };
+        for (uint32_t u = 0; u < J.n_ops; ++u) {
+            const uint32_t w = ops[J.op_off + u];
+            const int64_t len = w >> 4;
+            switch (w & 0xf) {
+            case MP_OP_M: case MP_OP_D: copy(3 * len); break;
+            case MP_OP_F: case MP_OP_G: copy(len); break;
+            case MP_OP_N: i += len; break;
+            case MP_OP_U: copy(1); i += len; copy(2); break;
+            case MP_OP_V: copy(2); i += len; copy(1); break;
+            default: break;                                   // I: residues only
+            }
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_exon_gather(const ExonJob *jobs, uint32_t n, const PairDesc *aux, const char *src,
+                               const uint32_t *ops, char *dst, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const uint32_t blocks = (n + 7) / 8;
+    exon_gather_kernel<<<blocks < 4096 ? blocks : 4096, 256, 0, st>>>(jobs, n, aux, src, ops, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const PairDesc *pairs, uint32_t n, const char *ascii, uint8_t *prot, uint32_t *nt2,
                         PairOut *out, cudaStream_t st)
 {
