@@ -485,6 +485,54 @@ def test_anchored_modes(mp, orc, mode, splice_model):
         assert [g["score"] for g in so] == [g["score"] for g in got[:6]]
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_anchored_modes_across_configurations(mp, orc, mode):
+    """The global and extension modes under both int16 builds, both item
+    orders and both wave policies, in a budget that needs several waves:
+    results equal the oracle's, direct and replayed as a graph."""
+    pairs = _anchored_pairs(130 + mode, 36, 260)
+    need = [_code_bytes(len(p.prot), len(p.nt)) for p in pairs]
+    budget = max(3 * max(need), sum(need) // 3)
+    params = mp.mp_dp_default_params(mode=mode, tb_budget_bytes=budget)
+    op = _orc_params(orc, params)
+    op.mode = mode
+    want = [orc.align(p.prot, p.nt, p.strand, op) for p in pairs]
+    c = mp.mp_dp_init(params, 0)
+    try:
+        for v, ov, io in ((0, 1, 1), (1, 1, 0), (0, 0, 1), (1, 0, 0)):
+            mp.mp_dp_set_tuning(c, dict(dp16_variant=v, overlap_waves=ov, item_order=io))
+            for _ in range(2):
+                got = mp.mp_dp_align_batch(c, pairs)
+                bad = [k for k, (g, w) in enumerate(zip(got, want))
+                       if any(g[key] != w[key] for key in KEYS) or g["status"] & 0xF0]
+                assert not bad, (v, ov, io, bad[:5])
+            assert mp.mp_dp_get_stats(c)["n_waves"] >= 2
+    finally:
+        mp.mp_dp_destroy(c)
+
+
+def test_anchored_serving(mp, orc):
+    """Requests served in global mode give the batch call's results."""
+    pairs = _anchored_pairs(150, 24, 200)
+    params = mp.mp_dp_default_params(mode=1)
+    c = mp.mp_dp_init(params, 0)
+    try:
+        ref = mp.mp_dp_align_batch(c, pairs)
+        tickets = [mp.mp_dp_submit(c, p) for p in pairs]
+        got = {}
+        while len(got) < len(tickets):
+            r = mp.mp_dp_wait_any(c, 5_000_000)
+            assert r is not None
+            got[r[0]] = r[1]
+        for t, r in zip(tickets, ref):
+            assert {x: got[t][x] for x in KEYS} == {x: r[x] for x in KEYS}
+    finally:
+        mp.mp_dp_destroy(c)
+    op = _orc_params(orc, params)
+    op.mode = 1
+    _compare(orc, pairs[:8], ref[:8], op)
+
+
 def test_anchored_int32_pairs(mp, orc):
     """Anchored pairs whose lower bound leaves the int16 range run in int32
     at once (here by a large gap extension e), against the oracle."""
