@@ -225,6 +225,44 @@ def test_edge_cases(mp, ctx, orc):
     assert bad[1]["status"] == 0 and bad[1]["score"] == 11
 
 
+def test_maximum_sizes(mp, ctx, orc):
+    """A region of the largest accepted length (1,047,551 nt) around a
+    planted gene, and a protein of the largest accepted length (1,048,575
+    residues) against a region carrying a slice of it on the minus strand:
+    each aligns as the oracle aligns a window holding the planted copy
+    (score, CIGAR, coordinates shifted back), and each CIGAR rescores by
+    op-sum to the score.  One past either limit is rejected."""
+    rng = np.random.default_rng(170)
+    nmax, pmax = (1 << 20) - 1025, (1 << 20) - 1
+    prot = synth.random_protein(rng, 220)
+    gene, _ = synth.gen.plant_gene(rng, prot, 0.2, 1, [400, 900], 600, 600, 0.45)
+    left = 400_000
+    region = synth.random_dna(rng, left) + gene + synth.random_dna(rng, nmax - left - len(gene))
+    big = synth.random_protein(rng, pmax)
+    k0 = 700_000
+    gene2, _ = synth.gen.plant_gene(rng, big[k0:k0 + 150], 0.15, 0, [300], 200, 200, 0.45)
+    pairs = [synth.Pair(prot, region, 1), synth.Pair(big, synth.revcomp(gene2), -1)]
+    assert len(region) == nmax and len(big) == pmax
+    got = mp.mp_dp_align_batch(ctx, pairs)
+    w0 = orc.align(prot, gene, 1)
+    p0 = k0 - 300
+    w1 = orc.align(big[p0:k0 + 450], synth.revcomp(gene2), -1)
+    want = [dict(w0, nt_st=w0["nt_st"] + left, nt_en=w0["nt_en"] + left),
+            dict(w1, prot_st=w1["prot_st"] + p0, prot_en=w1["prot_en"] + p0)]
+    for p, g, w in zip(pairs, got, want):
+        assert g["status"] & 0xF0 == 0
+        assert w["score"] > 300
+        assert {k: g[k] for k in KEYS} == {k: w[k] for k in KEYS}
+        n = len(p.nt)
+        st = g["nt_st"] if p.strand > 0 else n - g["nt_en"]
+        en = g["nt_en"] if p.strand > 0 else n - g["nt_st"]
+        assert orc.rescore(p.prot, p.nt, p.strand, g["prot_st"], st, g["cigar_raw"]) == \
+            (g["score"], g["prot_en"], en)
+    for bad in (synth.Pair(prot, region + "A", 1), synth.Pair(big + "W", gene2, 1)):
+        with pytest.raises(mp.MPError):
+            mp.mp_dp_align_batch(ctx, [bad])
+
+
 def test_score_only_pairs(mp, ctx, orc):
     pairs = _gene_pairs(31, 30, 150, 400)
     so = [synth.Pair(p.prot, p.nt, p.strand, True) for p in pairs]
