@@ -500,7 +500,7 @@ def main():
         # CUDA events, the L2 flushed before each timed run
         anchored = {}
         for mode, name in ((1, "global"), (2, "extension")):
-            ctxa = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode), local)
+            ctxa = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode, autotune=1), local)
             mp.mp_dp_set_timing(ctxa, True)
             ba = mp.mp_dp_batch_upload(ctxa, src)
             for _ in range(2):                    # autotune on the first run, then a warm-up
