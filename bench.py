@@ -154,7 +154,7 @@ def cpu_baseline(pairs, seconds: float = 15.0, single_core: bool = True):
     pairs drawn in a fixed shuffled order until the time budget is spent;
     with single_core, also one thread alone for a fifth of that time."""
     import random
-    from concurrent.futures import ThreadPoolExecutor
+    from concurrent.futures import FIRST_COMPLETED, ThreadPoolExecutor, wait
 
     import oracle
 
@@ -169,26 +169,27 @@ def cpu_baseline(pairs, seconds: float = 15.0, single_core: bool = True):
     deadline = t0 + seconds
     with ThreadPoolExecutor(max_workers=cores) as ex:
         it = iter(idx)
-        futs = set()
+        futs = {}
 
         def submit():
             k = next(it, None)
             if k is None or time.perf_counter() > deadline:
                 return False
             p = pairs[k]
-            futs.add((ex.submit(oracle.align, p.prot, p.nt, p.strand), p.cells))
+            futs[ex.submit(oracle.align, p.prot, p.nt, p.strand)] = p.cells
             return True
 
         for _ in range(cores):
             if not submit():
                 break
         while futs:
-            f, c = next(iter(futs))
-            f.result()
-            futs.discard((f, c))
-            done_cells += c
-            n_done += 1
-            submit()
+            # refill each thread as soon as its pair is done
+            done, _ = wait(list(futs), return_when=FIRST_COMPLETED)
+            for f in done:
+                f.result()
+                done_cells += futs.pop(f)
+                n_done += 1
+                submit()
     dt = time.perf_counter() - t0
     # one core: the same order, one pair after another, for a fifth of the time
     c1 = 0
