@@ -303,6 +303,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration, no tuning runs")
     ap.add_argument("--tuning", default="", help="fixed launch configuration 'variant,ctas16,ctas32,wide_direct[,overlap_waves[,item_order]]'")
     ap.add_argument("--c5-scale", type=float, default=1.0, help="shrink the genome-scale workload (tests)")
+    ap.add_argument("--mode", default="local", choices=["local", "global", "extension"],
+                    help="DP mode of the main leg (profiling runs; the bench line reports local mode)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
                     help="c2: the 4,096-pair batch (default); c3: the 20,000-pair uneven-size stress batch; "
                          "c5: the candidate regions of the genome-scale workload")
@@ -358,7 +360,8 @@ def main():
         n_pairs, cells = len(pairs), float(sum(p.cells for p in pairs))
         ascii_bytes = sum(len(p.prot) + len(p.nt) for p in pairs)
         get_pair = pairs.__getitem__
-    ctx = mp.mp_dp_init(None, local)
+    mode = {"local": 0, "global": 1, "extension": 2}[args.mode]
+    ctx = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode), local)
     mp.mp_dp_set_timing(ctx, True)
     batch = mp.mp_dp_batch_upload(ctx, src)
     tuning = None
@@ -458,7 +461,8 @@ def main():
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
-        "config": {"workload": workload, "pairs": n_pairs, "cells": cells, "waves": stats["n_waves"], **prep,
+        "config": {"workload": workload + ("" if mode == 0 else f" ({args.mode} mode)"), "pairs": n_pairs,
+                   "cells": cells, "waves": stats["n_waves"], **prep,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps; each step also writes "
                          f"{stats['code_bytes'] / 1e9:.1f} GB of traceback codes"},
