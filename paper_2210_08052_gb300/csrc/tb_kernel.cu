@@ -497,10 +497,13 @@ __device__ __forceinline__ int col0_base(const uint32_t *g, int x)
 }
 
 // Sliding window of the bases T[i-2..i+2] around row i, giving d(i-1)
-// (from T[i..i+2]) and a(i) (from T[i-2..i]).
+// (from T[i..i+2]) and a(i) (from T[i-2..i]).  The packed words ahead of
+// the window are held in registers, the next one loaded 16 rows before its
+// first base is needed (reads past the region fall in its zero padding).
 struct SpliceWindow {
     int b[5];      // T[i-2], T[i-1], T[i], T[i+1], T[i+2] (0 where outside)
     int i;
+    uint32_t w0, w1;   // the word holding T[i+3] and the one after it
     __device__ __forceinline__ void start(const Col0Ctx &c, int i0)
     {
         i = i0;
@@ -509,13 +512,21 @@ struct SpliceWindow {
             const int x = i0 - 2 + k;
             b[k] = (x >= 1 && x <= c.n) ? col0_base(c.g, x) : 0;
         }
+        const int wi = (i0 + 2) >> 4;                  // word of position i0 + 3
+        w0 = __ldg(c.g + wi);
+        w1 = __ldg(c.g + wi + 1);
     }
     __device__ __forceinline__ void advance(const Col0Ctx &c)
     {
         ++i;
 #pragma unroll
         for (int k = 0; k < 4; ++k) b[k] = b[k + 1];
-        b[4] = (i + 2 <= c.n) ? col0_base(c.g, i + 2) : 0;
+        const int x = i + 2;                           // the base entering the window
+        b[4] = x <= c.n ? static_cast<int>((w0 >> (2 * ((x - 1) & 15))) & 3) : 0;
+        if (((x - 1) & 15) == 15) {                   // x ends its word: the next word comes in
+            w0 = w1;
+            w1 = __ldg(c.g + ((x - 1) >> 4) + 2);
+        }
     }
     __device__ __forceinline__ int donor(const ScoreParams &sp, const Col0Ctx &c) const
     {
