@@ -496,12 +496,18 @@ __device__ __forceinline__ int col0_base(const uint32_t *g, int x)
     return static_cast<int>((__ldg(g + ((x - 1) >> 4)) >> (2 * ((x - 1) & 15))) & 3);
 }
 
-// Sliding window of the bases T[i-2..i+2] around row i, giving d(i-1)
-// (from T[i..i+2]) and a(i) (from T[i-2..i]).  The packed words ahead of
-// the window are held in registers, the next one loaded 16 rows before its
-// first base is needed (reads past the region fall in its zero padding).
+// Splice terms as table lookups: a base is coded 0..3, a position outside
+// the region 4; d(i-1) is kDon[T[i]][T[i+1]][T[i+2]] and a(i) is
+// kAcc[T[i-2]][T[i-1]][T[i]], both 5 x 5 x 5, filled at launch from the
+// splice model's own functions (so no data-dependent branch per row).
+constexpr int kOut = 4;
+
+// Sliding window of the codes of T[i-2..i+2] around row i.  The packed words
+// ahead of the window are held in registers, the next one loaded 16 rows
+// before its first base is needed (reads past the region fall in its zero
+// padding).
 struct SpliceWindow {
-    int b[5];      // T[i-2], T[i-1], T[i], T[i+1], T[i+2] (0 where outside)
+    int b[5];          // codes of T[i-2], T[i-1], T[i], T[i+1], T[i+2]
     int i;
     uint32_t w0, w1;   // the word holding T[i+3] and the one after it
     __device__ __forceinline__ void start(const Col0Ctx &c, int i0)
@@ -510,7 +516,7 @@ struct SpliceWindow {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const int x = i0 - 2 + k;
-            b[k] = (x >= 1 && x <= c.n) ? col0_base(c.g, x) : 0;
+            b[k] = (x >= 1 && x <= c.n) ? col0_base(c.g, x) : kOut;
         }
         const int wi = (i0 + 2) >> 4;                  // word of position i0 + 3
         w0 = __ldg(c.g + wi);
@@ -522,39 +528,73 @@ struct SpliceWindow {
 #pragma unroll
         for (int k = 0; k < 4; ++k) b[k] = b[k + 1];
         const int x = i + 2;                           // the base entering the window
-        b[4] = x <= c.n ? static_cast<int>((w0 >> (2 * ((x - 1) & 15))) & 3) : 0;
+        b[4] = x <= c.n ? static_cast<int>((w0 >> (2 * ((x - 1) & 15))) & 3) : kOut;
         if (((x - 1) & 15) == 15) {                   // x ends its word: the next word comes in
             w0 = w1;
             w1 = __ldg(c.g + ((x - 1) >> 4) + 2);
         }
     }
-    __device__ __forceinline__ int donor(const ScoreParams &sp, const Col0Ctx &c) const
+    // r + d(i-1) and a(i) of the current row
+    __device__ __forceinline__ void terms(const int16_t *don, const int16_t *acc, int r, int &rd, int &aa) const
     {
-        return splice_donor(sp, b[2], b[3], b[4], true, i + 1 <= c.n, i + 2 <= c.n);
-    }
-    __device__ __forceinline__ int acceptor(const ScoreParams &sp) const
-    {
-        return splice_acceptor(sp, b[0], b[1], b[2], i - 2 >= 1, i - 1 >= 1, true);
+        rd = r + don[(b[2] * 5 + b[3]) * 5 + b[4]];
+        aa = acc[(b[0] * 5 + b[1]) * 5 + b[2]];
     }
 };
 
-// One row applied to a state vector v (in place); every value stays >= NEG.
-template <typename T>
-__device__ __forceinline__ void col0_row(T *v, const Col0Ctx &c, int dd, int aa)
+// One row on a state vector v = (H[i], H[i-1], H[i-2], D[i], D[i-1], D[i-2],
+// A[i]) in place; rd = r + d(i), aa = a(i+1).  With clamp, every value stays
+// >= NEG; without, values below NEG only drift further down (by at most a few
+// thousand per row), which the 32-bit matrix phase absorbs.
+template <typename T, bool CLAMP>
+__device__ __forceinline__ void col0_row(T *v, const Col0Ctx &c, int rd, int aa)
 {
     const T neg = static_cast<T>(kNeg);
-    const T dn = max(max(v[2] - c.qe, v[5] - c.e), neg);
-    const T an = max(max(v[0] - c.r - dd, v[6]), neg);
-    const T hn = max(max(dn, max(v[0], v[1]) - c.f), max(an - aa, neg));
+    T dn = max(v[2] - c.qe, v[5] - c.e);
+    T an = max(v[0] - rd, v[6]);
+    T hn = max(max(dn, max(v[0], v[1]) - c.f), an - aa);
+    if (CLAMP) {
+        dn = max(dn, neg);
+        an = max(an, neg);
+        hn = max(hn, neg);
+    }
     v[5] = v[4]; v[4] = v[3]; v[3] = dn;
     v[2] = v[1]; v[1] = v[0]; v[0] = hn;
     v[6] = an;
+}
+
+// Three rows at once (H and D step back by three rows, so after three rows
+// every register holds its own role again and no value moves).
+template <typename T>
+__device__ __forceinline__ void col0_row3(T *v, const Col0Ctx &c, const int *rd, const int *aa)
+{
+    const T d1 = max(v[2] - c.qe, v[5] - c.e);
+    const T a1 = max(v[0] - rd[0], v[6]);
+    const T h1 = max(max(d1, max(v[0], v[1]) - c.f), a1 - aa[0]);
+    const T d2 = max(v[1] - c.qe, v[4] - c.e);
+    const T a2 = max(h1 - rd[1], a1);
+    const T h2 = max(max(d2, max(h1, v[0]) - c.f), a2 - aa[1]);
+    const T d3 = max(v[0] - c.qe, v[3] - c.e);
+    const T a3 = max(h2 - rd[2], a2);
+    const T h3 = max(max(d3, max(h2, h1) - c.f), a3 - aa[2]);
+    v[0] = h3; v[1] = h2; v[2] = h1;
+    v[3] = d3; v[4] = d2; v[5] = d1;
+    v[6] = a3;
 }
 
 __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *pairs, uint32_t n_pairs,
                                                                  const uint32_t *nt2, const ScoreParams sp,
                                                                  int32_t *col0)
 {
+    __shared__ int16_t s_don[125], s_acc[125];
+    for (int k = threadIdx.x; k < 125; k += blockDim.x) {
+        const int c1 = k / 25, c2 = (k / 5) % 5, c3 = k % 5;
+        const bool v1 = c1 != kOut, v2 = c2 != kOut, v3 = c3 != kOut;
+        const int b1 = v1 ? c1 : 0, b2 = v2 ? c2 : 0, b3 = v3 ? c3 : 0;
+        s_don[k] = static_cast<int16_t>(splice_donor(sp, b1, b2, b3, v1, v2, v3));
+        s_acc[k] = static_cast<int16_t>(splice_acceptor(sp, b1, b2, b3, v1, v2, v3));
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kCol0Warps;
     for (uint32_t p = blockIdx.x * kCol0Warps + (threadIdx.x >> 5); p < n_pairs; p += nwarps) {
@@ -565,9 +605,11 @@ __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *p
         int32_t *h = col0 + pd.col0_off;
         const int L = (n + 31) / 32;
         const int r0 = lane * L + 1, r1 = min(n, (lane + 1) * L);     // this lane's rows (none if r0 > r1)
+        const int cnt = r1 >= r0 ? r1 - r0 + 1 : 0;
 
         // 1. transfer matrix of the segment: column k is the state reached
-        //    from the k-th unit state (0 at k, -inf elsewhere)
+        //    from the k-th unit state (0 at k, -inf elsewhere); the last
+        //    segment's matrix is never used
         int32_t t[kS][kS];
 #pragma unroll
         for (int k = 0; k < kS; ++k) {
@@ -575,22 +617,34 @@ __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *p
             for (int j = 0; j < kS; ++j) t[k][j] = j == k ? 0 : kNeg;
         }
         SpliceWindow w;
-        if (r0 <= r1) {
+        if (cnt > 0 && lane < 31) {
             w.start(c, r0);
-            for (int i = r0; i <= r1; ++i) {
-                const int dd = w.donor(sp, c), aa = w.acceptor(sp);
+            int done = 0;
+            for (; done + 3 <= cnt; done += 3) {
+                int rd[3], aa[3];
 #pragma unroll
-                for (int k = 0; k < kS; ++k) col0_row(t[k], c, dd, aa);
-                if (i < r1) w.advance(c);
+                for (int u = 0; u < 3; ++u) {
+                    w.terms(s_don, s_acc, c.r, rd[u], aa[u]);
+                    if (done + u + 1 < cnt) w.advance(c);
+                }
+#pragma unroll
+                for (int k = 0; k < kS; ++k) col0_row3(t[k], c, rd, aa);
+            }
+            for (; done < cnt; ++done) {
+                int rd, aa;
+                w.terms(s_don, s_acc, c.r, rd, aa);
+                if (done + 1 < cnt) w.advance(c);
+#pragma unroll
+                for (int k = 0; k < kS; ++k) col0_row<int32_t, false>(t[k], c, rd, aa);
             }
         }
         // 2. incoming state of every segment, chained across the lanes from
-        //    s_0 = (0, -inf, ...); entries are sums of two values >= NEG, so
-        //    no 32-bit overflow before the clamp
+        //    s_0 = (0, -inf, ...); matrix entries are >= NEG less the drift of
+        //    one segment and s is clamped, so the sums stay inside 32 bits
         int32_t s[kS], sin[kS];
 #pragma unroll
         for (int k = 0; k < kS; ++k) s[k] = sin[k] = k == 0 ? 0 : kNeg;
-        for (int l = 0; l < 32; ++l) {
+        for (int l = 0; l < 31; ++l) {
             if (lane == l) {
 #pragma unroll
                 for (int k = 0; k < kS; ++k) sin[k] = s[k];
@@ -606,20 +660,25 @@ __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *p
 #pragma unroll
             for (int j = 0; j < kS; ++j) s[j] = max(ns[j], kNeg);
         }
+        if (lane == 31) {
+#pragma unroll
+            for (int k = 0; k < kS; ++k) sin[k] = s[k];
+        }
         // 3. re-run the segment from its incoming state (64-bit state: ptxas
         //    13.0 at -O1 and above turned an earlier 32-bit form of this
         //    recurrence into code returning +f for H[1][0]; correct at -O0)
         if (lane == 0) h[0] = 0;
-        if (r0 <= r1) {
+        if (cnt > 0) {
             int64_t v[kS];
 #pragma unroll
             for (int k = 0; k < kS; ++k) v[k] = sin[k];
             w.start(c, r0);
-            for (int i = r0; i <= r1; ++i) {
-                const int dd = w.donor(sp, c), aa = w.acceptor(sp);
-                col0_row(v, c, dd, aa);
-                h[i] = static_cast<int32_t>(v[0]);
-                if (i < r1) w.advance(c);
+            for (int done = 0; done < cnt; ++done) {
+                int rd, aa;
+                w.terms(s_don, s_acc, c.r, rd, aa);
+                if (done + 1 < cnt) w.advance(c);
+                col0_row<int64_t, true>(v, c, rd, aa);
+                h[r0 + done] = static_cast<int32_t>(v[0]);
             }
         }
         for (int i = n + 1 + lane; i <= n + kCol0Pad; i += 32) h[i] = kNeg;
