@@ -563,25 +563,6 @@ __device__ __forceinline__ void col0_row(T *v, const Col0Ctx &c, int rd, int aa)
     v[6] = an;
 }
 
-// Three rows at once (H and D step back by three rows, so after three rows
-// every register holds its own role again and no value moves).
-template <typename T>
-__device__ __forceinline__ void col0_row3(T *v, const Col0Ctx &c, const int *rd, const int *aa)
-{
-    const T d1 = max(v[2] - c.qe, v[5] - c.e);
-    const T a1 = max(v[0] - rd[0], v[6]);
-    const T h1 = max(max(d1, max(v[0], v[1]) - c.f), a1 - aa[0]);
-    const T d2 = max(v[1] - c.qe, v[4] - c.e);
-    const T a2 = max(h1 - rd[1], a1);
-    const T h2 = max(max(d2, max(h1, v[0]) - c.f), a2 - aa[1]);
-    const T d3 = max(v[0] - c.qe, v[3] - c.e);
-    const T a3 = max(h2 - rd[2], a2);
-    const T h3 = max(max(d3, max(h2, h1) - c.f), a3 - aa[2]);
-    v[0] = h3; v[1] = h2; v[2] = h1;
-    v[3] = d3; v[4] = d2; v[5] = d1;
-    v[6] = a3;
-}
-
 __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *pairs, uint32_t n_pairs,
                                                                  const uint32_t *nt2, const ScoreParams sp,
                                                                  int32_t *col0)
@@ -616,21 +597,13 @@ __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *p
 #pragma unroll
             for (int j = 0; j < kS; ++j) t[k][j] = j == k ? 0 : kNeg;
         }
+        // (one row per step: ptxas 13.0 at -O1 and above gave wrong matrices
+        // for a three-rows-per-step form of this loop, correct at -O0 and in
+        // 64 bits; the column-0 tests compare every value with the oracle)
         SpliceWindow w;
         if (cnt > 0 && lane < 31) {
             w.start(c, r0);
-            int done = 0;
-            for (; done + 3 <= cnt; done += 3) {
-                int rd[3], aa[3];
-#pragma unroll
-                for (int u = 0; u < 3; ++u) {
-                    w.terms(s_don, s_acc, c.r, rd[u], aa[u]);
-                    if (done + u + 1 < cnt) w.advance(c);
-                }
-#pragma unroll
-                for (int k = 0; k < kS; ++k) col0_row3(t[k], c, rd, aa);
-            }
-            for (; done < cnt; ++done) {
+            for (int done = 0; done < cnt; ++done) {
                 int rd, aa;
                 w.terms(s_don, s_acc, c.r, rd, aa);
                 if (done + 1 < cnt) w.advance(c);

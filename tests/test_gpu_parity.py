@@ -496,6 +496,44 @@ def test_stored_h_matches_oracle(mp, orc, mode, force_int32):
         mp.mp_dp_destroy(c)
 
 
+@pytest.mark.parametrize("pset", [dict(), dict(q=3, e=2, f=5, r=9, splice_model=1, splice_p=7),
+                                  dict(q=0, e=1, f=9, r=12), dict(q=11, e=3, f=17, r=40, splice_model=1)])
+def test_column0_against_oracle(mp, orc, pset):
+    """Column 0 of the anchored modes (Eq. 7 with no residue consumed: D
+    runs, G1, G2 and introns from row 0) against the oracle's, for regions of
+    1 to 9,000 nt dense in GT and AG (so that the intron terms compete), with
+    several penalty sets and both splice models; column 0 is the kernel that
+    splits its rows into 32 segments and chains them."""
+    rng = np.random.default_rng(171)
+    pairs = []
+    for n in (1, 2, 3, 5, 31, 32, 33, 95, 96, 97, 200, 511, 700, 1500, 4000, 9000):
+        t = list(synth.random_dna(rng, n))
+        i = 0
+        while i + 1 < n:
+            t[i:i + 2] = "AG" if rng.random() < 0.5 else "GT"
+            i += int(rng.integers(7, 18))
+        pairs.append(synth.Pair("M", "".join(t), 1))
+    params = mp.mp_dp_default_params(mode=1, **pset)
+    op = _orc_params(orc, params)
+    op.mode = 1
+    c = mp.mp_dp_init(params, 0)
+    try:
+        b = mp.mp_dp_batch_upload(c, pairs)
+        mp.mp_dp_batch_run(c, b)
+        mp.mp_dp_batch_sync(c)
+        bad = []
+        for k, p in enumerate(pairs):
+            got = mp.mp_dp_debug_h(c, b, k, len(p.nt), 1)[:, 0]
+            want = orc.fill_h(p.prot, p.nt, 1, op)[:, 0]
+            rows = np.nonzero(got != want)[0]
+            if rows.size:
+                bad.append((len(p.nt), int(rows[0]), int(got[rows[0]]), int(want[rows[0]]), int(rows.size)))
+        mp.mp_dp_batch_free(c, b)
+    finally:
+        mp.mp_dp_destroy(c)
+    assert not bad, bad
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("splice_model", [0, 1])
 def test_anchored_modes(mp, orc, mode, splice_model):
