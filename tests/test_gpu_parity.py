@@ -496,8 +496,8 @@ def test_stored_h_matches_oracle(mp, orc, mode, force_int32):
         mp.mp_dp_destroy(c)
 
 
-@pytest.mark.parametrize("pset", [dict(), dict(q=3, e=2, f=5, r=9, splice_model=1, splice_p=7),
-                                  dict(q=0, e=1, f=9, r=12), dict(q=11, e=3, f=17, r=40, splice_model=1)])
+@pytest.mark.parametrize("pset", [dict(), dict(q=3, e=2, f=5, r=9, stop=4, splice_model=1, splice_p=7),
+                                  dict(q=0, e=1, f=9, r=12, stop=4), dict(q=11, e=3, f=17, r=40, splice_model=1)])
 def test_column0_against_oracle(mp, orc, pset):
     """Column 0 of the anchored modes (Eq. 7 with no residue consumed: D
     runs, G1, G2 and introns from row 0) against the oracle's, for regions of
