@@ -38,6 +38,7 @@
 
 #include "mp_device.cuh"
 #include "mp_internal.cuh"
+#include "traceback.cuh"
 
 namespace mpdp {
 namespace {
@@ -485,6 +486,22 @@ struct Best {
     int score, ii, jj;
 };
 
+// Traceback of pair p by the warp that finished its last strip (a call, not
+// inlined, so the traceback's registers stay out of the DP loop's budget).
+__device__ __noinline__ void trace_inline(const DPArgs &a, uint32_t p, int lane)
+{
+    TBArgs t{};
+    t.pairs = a.pairs;
+    t.codes = a.codes;
+    t.prot = a.prot;
+    t.nt2 = a.nt2;
+    t.out = a.out;
+    t.ops = a.ops;
+    t.col0 = a.col0;
+    t.sp = a.sp;
+    trace_pair<true>(t, a.mat, p, lane);
+}
+
 __device__ __forceinline__ bool better(int s, int i, int j, const Best &b)
 {
     return s > b.score || (s == b.score && (i < b.ii || (i == b.ii && j < b.jj)));
@@ -725,6 +742,7 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
         o.jj = __shfl_xor_sync(kFull, best.jj, off);
         if (better(o.score, o.ii, o.jj, best)) best = o;
     }
+    int trace_now = 0;
     if (lane == 0) {
         if (best.score > 0) atomicMax(a.best_key + p, best_key(best.score, best.ii, best.jj));
         if (timed_out) atomicOr(&a.out[p].status, MP_ST_TIMEOUT);
@@ -753,7 +771,21 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
                 const uint32_t slot = atomicAdd(a.rerun_count, static_cast<uint32_t>(nstrips));
                 for (int k = 0; k < nstrips; ++k) a.rerun_items[slot + k] = make_uint2(p, k);
             }
+            // the pair is final (not queued for the int32 kernel): trace it now,
+            // while other warps run other strips
+            trace_now = a.mat != nullptr && !(o.status & MP_ST_ERRMASK) &&
+                        !(pd.flags & (PF_SCORE_ONLY | PF_SKIP | PF_BUDGET)) &&
+                        (!(o.status & MP_ST_RERUN) || sizeof(Bnd) == 8) &&
+                        (score > 0 || a.sp.mode == MP_MODE_GLOBAL);
         }
+    }
+    trace_now = __shfl_sync(kFull, trace_now, 0);
+    __syncwarp();
+    if (trace_now) {
+        __threadfence();        // the other strips' streams (published before their count) are visible
+        trace_inline(a, p, lane);
+        __syncwarp();
+        if (lane == 0) a.out[p].status |= kStTraced;
     }
     __syncwarp();
 }

@@ -56,6 +56,9 @@ __host__ __device__ constexpr uint64_t records_of(uint32_t n)
 // internal PairOut.status bit (never returned to callers): the pair's
 // traceback stream was written by the int32 kernel (4 bytes per cell)
 constexpr int32_t kStInt32Stream = 0x100;
+// internal PairOut.status bit: the pair was traced by the DP kernel right
+// after its last strip (the traceback kernel skips it)
+constexpr int32_t kStTraced = 0x200;
 
 // PF_WIDE: the pair's score could exceed the int16 range, so its traceback
 // region is sized for the int32 re-run (4 bytes per cell)
@@ -105,6 +108,8 @@ struct DPArgs {
     ScoreParams sp;
     uint32_t spin_limit;    // polls before a wait gives up (0: kSpinLimit)
     uint32_t no_publish;    // test hook: withhold boundary rows
+    uint32_t *ops;          // reversed-op slots, for the traceback of a pair right after its last strip
+    const int8_t *mat;      // the substitution matrix (22 x 22) in device memory; null: no such traceback
 };
 
 // bounded wait of a consumer strip for its producer (iterations of ~0.25 us)

@@ -264,6 +264,7 @@ struct mp_dp_ctx {
     mp_dp_batch *own = nullptr;    // buffers reused by mp_dp_align_batch from call to call
     mp_dp_batch *aux = nullptr;    // score-only batch of mp_dp_exon_rescore
     DevBuf<uint8_t> exbuf;         // rescoring jobs (and, for earlier results, their regions and ops)
+    DevBuf<int8_t> d_mat;          // the substitution matrix for the DP kernel's own tracebacks
     std::vector<uint32_t> host_cig;
     // launch configuration: fixed by mp_dp_set_tuning, else tuned per shape class
     bool has_fixed = false;
@@ -378,6 +379,11 @@ int mp_dp_init(mp_dp_ctx **out, const mp_dp_params *p, int device)
     c->sp.splice_model = prm.splice_model;
     c->sp.splice_p = prm.splice_p;
     c->sp.mode = prm.mode;
+    if (c->d_mat.reserve(sizeof(c->sp.mat)) != cudaSuccess ||
+        cudaMemcpy(c->d_mat.p, c->sp.mat, sizeof(c->sp.mat), cudaMemcpyHostToDevice) != cudaSuccess) {
+        mp_dp_destroy(c);
+        return MP_ECUDA;
+    }
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     uint64_t budget = prm.tb_budget_bytes ? prm.tb_budget_bytes : kDefaultBudget;
@@ -905,6 +911,8 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         a.sp = c->sp;
         a.spin_limit = c->params.wait_limit > 0 ? static_cast<uint32_t>(c->params.wait_limit) : 0u;
         a.no_publish = (c->params.debug_flags & MP_DEBUG_NO_PUBLISH) ? 1u : 0u;
+        a.ops = b->ops.p;
+        a.mat = c->d_mat.p;
         const uint32_t nitems = wv.iend - wv.ibegin;
         if (per_launch > 0) {
             // plain form: one kernel launch per group of pairs
@@ -1793,6 +1801,7 @@ extern "C" void mp_dp_destroy(mp_dp_ctx *c)
     c->codes.release();
     c->staging.release();
     c->exbuf.release();
+    c->d_mat.release();
     if (c->stream2) cudaStreamSynchronize(c->stream2);
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->stream2) cudaStreamDestroy(c->stream2);
