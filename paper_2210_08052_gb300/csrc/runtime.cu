@@ -490,9 +490,13 @@ static uint64_t shape_key_of(const mp_dp_batch &b)
 static mp_dp_tuning default_tuning()
 {
     mp_dp_tuning t{};
+    t.dp16_variant = 1;
     t.overlap_waves = 1;
     t.item_order = 1;
-    return t;     // int16 kernel for 3 CTAs/SM, all CTAs that fit, int16 first for wide pairs, overlapped waves
+    // int16 kernel built for 2 CTAs/SM (no spill; with the tracebacks in the
+    // kernel it is the faster build on the 4,096-pair workload), all CTAs that
+    // fit, int16 first for wide pairs, overlapped waves, interleaved items
+    return t;
 }
 
 static mp_dp_tuning tuning_for(const mp_dp_ctx *c, const mp_dp_batch *b)
