@@ -253,6 +253,8 @@ struct mp_dp_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;     // second stream: odd waves of an overlapped batch
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_staging = nullptr;   // recorded after the last copy out of the staging buffer
+    bool staging_busy = false;          // ev_staging is pending
     mp_dp_params params{};
     ScoreParams sp{};
     uint64_t budget = 0;
@@ -370,7 +372,8 @@ int mp_dp_init(mp_dp_ctx **out, const mp_dp_params *p, int device)
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return MP_ECUDA; }
     if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_staging, cudaEventDisableTiming) != cudaSuccess) {
         mp_dp_destroy(c);
         return MP_ECUDA;
     }
@@ -713,6 +716,14 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t)
 
 // (Re)fill batch b with n pairs: plan strips, waves and offsets on the host,
 // grow the device buffers when needed, and copy the inputs to the device.
+// Wait until the last copy out of the staging buffer has left it.
+static cudaError_t staging_wait(mp_dp_ctx *c)
+{
+    if (!c->staging_busy) return cudaSuccess;
+    c->staging_busy = false;
+    return cudaEventSynchronize(c->ev_staging);
+}
+
 // ascii_on_device: the caller writes the batch's ASCII into b->ascii on the
 // context's stream itself (the pairs' nt pointers are unused and may be null;
 // the protein pointers still serve the score bound).
@@ -801,38 +812,55 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
     cudaStream_t st = c->stream;
-    if (ascii_on_device) {
-        b->needs_waves = plan_code_bytes(c, b) > c->budget;
-        b->shape_key = shape_key_of(*b);
-        b->planned = -1;
-        return plan_waves(c, b, tuning_for(c, b));
+    // ---- the batch's shape class and the wave plan its configuration asks
+    // for, first: its pageable descriptor copies then find no sequence copy
+    // in flight on the stream
+    b->needs_waves = plan_code_bytes(c, b) > c->budget;
+    b->shape_key = shape_key_of(*b);
+    b->planned = -1;
+    {
+        const int rc = plan_waves(c, b, tuning_for(c, b));
+        if (rc != MP_OK || ascii_on_device) return rc;
     }
-    // ---- host -> device
+    // ---- host -> device: the sequences are gathered into the pinned staging
+    // buffer and sent in ranges of about 2 MB as they are gathered (on
+    // several threads for large batches); nothing waits for the copies here:
+    // the pipeline follows them on the stream, and the next user of the
+    // staging buffer waits for ev_staging
+    CK(staging_wait(c));
     if (c->staging.reserve(asc + 16) != cudaSuccess) return MP_ENOMEM;
-    auto gather = [&](size_t k0, size_t k1) {
+    std::atomic<int> copy_err{0};
+    auto gather_send = [&](size_t k0, size_t k1) {
+        size_t from = k0;
+        uint64_t acc = 0;
         for (size_t k = k0; k < k1; ++k) {
             const mp_pair &q = pairs[k];
             if (q.prot_len) memcpy(c->staging.p + b->desc[k].asc_prot_off, q.prot, q.prot_len);
             if (q.nt_len) memcpy(c->staging.p + b->desc[k].asc_nt_off, q.nt, q.nt_len);
+            acc += q.prot_len + q.nt_len;
+            if (acc >= (2u << 20) || k + 1 == k1) {
+                const uint64_t lo = b->desc[from].asc_prot_off;
+                const uint64_t hi = k + 1 < n ? b->desc[k + 1].asc_prot_off : asc;
+                if (hi > lo && cudaMemcpyAsync(b->ascii.p + lo, c->staging.p + lo, hi - lo, cudaMemcpyHostToDevice,
+                                               st) != cudaSuccess)
+                    copy_err = 1;
+                from = k + 1;
+                acc = 0;
+            }
         }
     };
-    // large batches: gather the sequences into the pinned buffer on several threads
     const unsigned nthr = asc > (16u << 20) ? std::min(8u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
     if (nthr > 1) {
         std::vector<std::thread> th;
-        for (unsigned t = 0; t < nthr; ++t) th.emplace_back(gather, n * t / nthr, n * (t + 1) / nthr);
+        for (unsigned t = 0; t < nthr; ++t) th.emplace_back(gather_send, n * t / nthr, n * (t + 1) / nthr);
         for (auto &x : th) x.join();
     } else {
-        gather(0, n);
+        gather_send(0, n);
     }
-    // the sequences travel while the host plans the waves (plan_waves waits
-    // for the stream before it returns, so the staging buffer is free again)
-    CK(cudaMemcpyAsync(b->ascii.p, c->staging.p, asc, cudaMemcpyHostToDevice, st));
-    // ---- the batch's shape class and the wave plan its configuration asks for
-    b->needs_waves = plan_code_bytes(c, b) > c->budget;
-    b->shape_key = shape_key_of(*b);
-    b->planned = -1;
-    return plan_waves(c, b, tuning_for(c, b));
+    if (copy_err) return MP_ECUDA;
+    CK(cudaEventRecord(c->ev_staging, st));
+    c->staging_busy = true;
+    return MP_OK;
 }
 
 int mp_dp_batch_upload(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_dp_batch **out)
@@ -1493,6 +1521,7 @@ static int exon_rescore_impl(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_re
         asc_bytes = asc;
     }
     const size_t total = jobs_bytes + ops_bytes + asc_bytes;
+    CK(staging_wait(c));
     if (c->staging.reserve(total + 16) != cudaSuccess || c->exbuf.reserve(total + 16) != cudaSuccess)
         return MP_ENOMEM;
     char *h = c->staging.p;
@@ -1807,6 +1836,7 @@ extern "C" void mp_dp_destroy(mp_dp_ctx *c)
     c->exbuf.release();
     c->d_mat.release();
     if (c->stream2) cudaStreamSynchronize(c->stream2);
+    if (c->ev_staging) cudaEventDestroy(c->ev_staging);
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->stream2) cudaStreamDestroy(c->stream2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
