@@ -260,6 +260,7 @@ struct mp_dp_ctx {
     uint64_t budget = 0;
     DevBuf<uint8_t> codes;      // traceback arena (shared by the waves of a batch)
     HostBuf<char> staging;
+    HostBuf<char> pstaging;        // a plan's descriptors, order, items and wave counts on their way to the device
     bool timing = false;
     mp_dp_stats stats{};
     mp_dp_batch *last = nullptr;   // batch of the last run (for its counters)
@@ -516,7 +517,7 @@ static int plan_key(const mp_dp_batch *b, const mp_dp_tuning &t)
     return (b->needs_waves && t.overlap_waves ? 1 : 0) | (t.item_order ? 2 : 0);
 }
 
-static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t);
+static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool stream_idle = false);
 
 // Re-plan the batch if its plan was made for another configuration.
 static int ensure_plan(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t)
@@ -581,7 +582,9 @@ static void interleave_items(const mp_dp_ctx *c, mp_dp_batch *b)
 // wave policy `overlap`, grow the buffers that depend on the plan, and copy
 // the plan to the device.  Called by the upload, and again when a
 // configuration with the other policy runs the batch.
-static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t)
+// stream_idle: the caller has synchronized the stream since the batch's
+// buffers were last used (copies the caller enqueued since then are fine)
+static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool stream_idle)
 {
     const bool overlap = t.overlap_waves != 0;
     const size_t n = b->n;
@@ -703,14 +706,26 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t)
         (e = c->codes.reserve(b->overlap ? 2 * b->arena_half : std::max<uint64_t>(maxw, 256))) != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     cudaStream_t st = c->stream;
-    CK(cudaStreamSynchronize(st));      // no run of an earlier plan still reads these buffers
-    CK(cudaMemcpyAsync(b->d_desc.p, b->desc.data(), n * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(b->work.p, b->order.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(b->items.p, b->h_items.data(), b->h_items.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
-    std::vector<uint32_t> nw(b->waves.size());
-    for (size_t w = 0; w < nw.size(); ++w) nw[w] = b->waves[w].nwide_items;
-    CK(cudaMemcpyAsync(b->wave_nwide.p, nw.data(), nw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
+    // no run of an earlier plan still reads these buffers, and the pinned
+    // plan staging buffer is free again
+    if (!stream_idle) CK(cudaStreamSynchronize(st));
+    // descriptors, order, items and wave counts go out of pinned memory, so
+    // the copies do not wait for sequence copies already on the stream
+    const size_t o_desc = 0, o_work = div_up(n * sizeof(PairDesc), 16) * 16;
+    const size_t o_items = o_work + div_up(n * sizeof(uint32_t), 16) * 16;
+    const size_t o_nw = o_items + div_up(b->h_items.size() * sizeof(uint2), 16) * 16;
+    const size_t total = o_nw + b->waves.size() * sizeof(uint32_t);
+    if (c->pstaging.reserve(total + 16) != cudaSuccess) return MP_ENOMEM;
+    char *h = c->pstaging.p;
+    memcpy(h + o_desc, b->desc.data(), n * sizeof(PairDesc));
+    memcpy(h + o_work, b->order.data(), n * sizeof(uint32_t));
+    memcpy(h + o_items, b->h_items.data(), b->h_items.size() * sizeof(uint2));
+    uint32_t *nw = reinterpret_cast<uint32_t *>(h + o_nw);
+    for (size_t w = 0; w < b->waves.size(); ++w) nw[w] = b->waves[w].nwide_items;
+    CK(cudaMemcpyAsync(b->d_desc.p, h + o_desc, n * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->work.p, h + o_work, n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->items.p, h + o_items, b->h_items.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->wave_nwide.p, nw, b->waves.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     return MP_OK;
 }
 
@@ -812,22 +827,19 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
     cudaStream_t st = c->stream;
-    // ---- the batch's shape class and the wave plan its configuration asks
-    // for, first: its pageable descriptor copies then find no sequence copy
-    // in flight on the stream
+    // no earlier run still uses this batch's buffers or the context's
+    // arenas, and the staging buffers are free
+    CK(cudaStreamSynchronize(st));
+    c->staging_busy = false;
     b->needs_waves = plan_code_bytes(c, b) > c->budget;
     b->shape_key = shape_key_of(*b);
     b->planned = -1;
-    {
-        const int rc = plan_waves(c, b, tuning_for(c, b));
-        if (rc != MP_OK || ascii_on_device) return rc;
-    }
-    // ---- host -> device: the sequences are gathered into the pinned staging
-    // buffer and sent in ranges of about 2 MB as they are gathered (on
-    // several threads for large batches); nothing waits for the copies here:
-    // the pipeline follows them on the stream, and the next user of the
-    // staging buffer waits for ev_staging
-    CK(staging_wait(c));
+    if (ascii_on_device) return plan_waves(c, b, tuning_for(c, b), true);
+    // ---- host -> device: worker threads gather the sequences into the
+    // pinned staging buffer and send each ~2 MB range as soon as it is
+    // gathered, while this thread plans the waves; nothing waits for the
+    // copies here: the pipeline follows them on the stream, and the next
+    // user of the staging buffer waits for ev_staging
     if (c->staging.reserve(asc + 16) != cudaSuccess) return MP_ENOMEM;
     std::atomic<int> copy_err{0};
     auto gather_send = [&](size_t k0, size_t k1) {
@@ -849,14 +861,15 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
             }
         }
     };
-    const unsigned nthr = asc > (16u << 20) ? std::min(8u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
-    if (nthr > 1) {
-        std::vector<std::thread> th;
-        for (unsigned t = 0; t < nthr; ++t) th.emplace_back(gather_send, n * t / nthr, n * (t + 1) / nthr);
-        for (auto &x : th) x.join();
-    } else {
-        gather_send(0, n);
-    }
+    const unsigned nthr = asc > (16u << 20) ? std::min(16u, std::max(1u, std::thread::hardware_concurrency())) : 0u;
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nthr; ++t) th.emplace_back(gather_send, n * t / nthr, n * (t + 1) / nthr);
+    // the plan reads the layout fields of the descriptors the workers read
+    // and writes others (code offsets), and copies out of its own buffer
+    const int rc = plan_waves(c, b, tuning_for(c, b), true);
+    if (nthr == 0) gather_send(0, n);
+    for (auto &x : th) x.join();
+    if (rc != MP_OK) return rc;
     if (copy_err) return MP_ECUDA;
     CK(cudaEventRecord(c->ev_staging, st));
     c->staging_busy = true;
@@ -1833,6 +1846,7 @@ extern "C" void mp_dp_destroy(mp_dp_ctx *c)
     c->own = nullptr;
     c->codes.release();
     c->staging.release();
+    c->pstaging.release();
     c->exbuf.release();
     c->d_mat.release();
     if (c->stream2) cudaStreamSynchronize(c->stream2);
