@@ -11,7 +11,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -247,6 +249,66 @@ struct Done {
 
 struct Slot;
 
+// A few host threads kept for the life of a context, so that gathering a
+// large batch's sequences does not start threads on every call.  run()
+// hands out job indices 0..n-1 to the workers and returns at once; wait()
+// returns when every job has finished.
+struct WorkerPool {
+    std::vector<std::thread> th;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::function<void(unsigned)> job;
+    unsigned njobs = 0, next = 0, finished = 0;
+    uint64_t gen = 0;
+    bool stop = false;
+
+    void start(unsigned n)
+    {
+        for (unsigned k = 0; k < n; ++k) th.emplace_back([this] { loop(); });
+    }
+    void loop()
+    {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait(lk, [&] { return stop || gen != seen; });
+            if (stop) return;
+            seen = gen;
+            while (next < njobs) {
+                const unsigned i = next++;
+                lk.unlock();
+                job(i);
+                lk.lock();
+                if (++finished == njobs) done_cv.notify_all();
+            }
+        }
+    }
+    void run(unsigned n, std::function<void(unsigned)> f)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        job = std::move(f);
+        njobs = n;
+        next = 0;
+        finished = 0;
+        ++gen;
+        cv.notify_all();
+    }
+    void wait()
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        done_cv.wait(lk, [&] { return finished == njobs; });
+    }
+    ~WorkerPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto &t : th) t.join();
+    }
+};
+
 struct mp_dp_ctx {
     int device = 0;
     int num_sms = 0;
@@ -261,6 +323,7 @@ struct mp_dp_ctx {
     DevBuf<uint8_t> codes;      // traceback arena (shared by the waves of a batch)
     HostBuf<char> staging;
     HostBuf<char> pstaging;        // a plan's descriptors, order, items and wave counts on their way to the device
+    std::unique_ptr<WorkerPool> pool;  // gather threads (started by the first large upload)
     bool timing = false;
     mp_dp_stats stats{};
     mp_dp_batch *last = nullptr;   // batch of the last run (for its counters)
@@ -862,13 +925,20 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         }
     };
     const unsigned nthr = asc > (16u << 20) ? std::min(16u, std::max(1u, std::thread::hardware_concurrency())) : 0u;
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nthr; ++t) th.emplace_back(gather_send, n * t / nthr, n * (t + 1) / nthr);
+    if (nthr && !c->pool) {
+        c->pool.reset(new (std::nothrow) WorkerPool());
+        if (c->pool) c->pool->start(nthr);
+    }
+    const bool pooled = nthr && c->pool;
+    if (pooled) {
+        const unsigned nj = static_cast<unsigned>(c->pool->th.size());
+        c->pool->run(nj, [&, nj](unsigned t) { gather_send(n * t / nj, n * (t + 1) / nj); });
+    }
     // the plan reads the layout fields of the descriptors the workers read
     // and writes others (code offsets), and copies out of its own buffer
     const int rc = plan_waves(c, b, tuning_for(c, b), true);
-    if (nthr == 0) gather_send(0, n);
-    for (auto &x : th) x.join();
+    if (pooled) c->pool->wait();
+    else gather_send(0, n);
     if (rc != MP_OK) return rc;
     if (copy_err) return MP_ECUDA;
     CK(cudaEventRecord(c->ev_staging, st));
