@@ -35,7 +35,7 @@ WORKLOAD_C5 = ("genome-scale: 500 Mb genome (40% GC) with 20000 planted genes; 2
                "every candidate region aligned with traceback; seed 5 (+1000 per rank)")
 # algorithmic integer ops per cell of the DP pass: the 27 max/add of Eq. 7 (I 3, D 3, A/B/C 2 each,
 # H 15) and one running maximum for the best cell.  Traceback decisions are re-derived from the
-# stored H values along the path only, in the traceback kernel.
+# stored H values along the path only (by the warp that finishes a pair's last strip).
 OPS_PER_CELL = 28
 
 
