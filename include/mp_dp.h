@@ -103,7 +103,10 @@ typedef struct {
                                   and of the aligned strand (strand -1: the input's end); in global
                                   mode every pair keeps its traceback (MP_PAIR_SCORE_ONLY is
                                   ignored) since the score is read at the end cell.  A pair
-                                  with an empty protein or region scores 0 in every mode */
+                                  with an empty protein or region scores 0 in every mode.  In the
+                                  anchored modes H can be as low as -(2q + f + e(|P| + |T|/3 + 2));
+                                  a batch holding a pair for which that reaches 2^27 is refused
+                                  with MP_EINVAL (the DP represents -inf by -2^28) */
     uint64_t tb_budget_bytes;  /* device bytes for traceback codes (default 40 GiB, capped
                                   by free device memory at init) */
     int32_t force_int32;       /* 1: skip the packed int16 pass and run every pair in int32 */

@@ -864,9 +864,14 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         // column (I run, D run, a frameshift) bounds it from below.  Pairs whose
         // bound leaves the int16 range safely run in int32 (PF_WIDE pairs of
         // these modes skip the int16 pass).
-        if (anchored && 2 * static_cast<int64_t>(c->params.q) + c->params.f +
-                                static_cast<int64_t>(c->params.e) * (q.prot_len + q.nt_len / 3 + 2) >= 12000)
-            d.flags |= PF_WIDE;
+        if (anchored) {
+            const int64_t lower = 2 * static_cast<int64_t>(c->params.q) + c->params.f +
+                                  static_cast<int64_t>(c->params.e) * (q.prot_len + q.nt_len / 3 + 2);
+            if (lower >= 12000) d.flags |= PF_WIDE;
+            // the int32 path represents -inf by -2^28; with half of that as
+            // margin, a pair whose H could fall lower is refused
+            if (lower >= (int64_t{1} << 27)) return MP_EINVAL;
+        }
         b->nt_len[k] = q.nt_len;
         b->strand[k] = q.strand;
         b->cells += static_cast<double>(q.prot_len) * q.nt_len;

@@ -609,6 +609,28 @@ def test_anchored_serving(mp, orc):
     _compare(orc, pairs[:8], ref[:8], op)
 
 
+def test_anchored_lower_bound_refused(mp):
+    """An anchored pair whose H could fall below -2^27 (large gap extension
+    and a long protein) is refused as a whole batch; the same pair in local
+    mode (H never below 0) is accepted and scored."""
+    rng = np.random.default_rng(172)
+    prot = synth.random_protein(rng, 140_000)
+    pair = synth.Pair(prot, "ATGGCCAAGTGG", 1)
+    for mode in (1, 2):
+        c = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode, q=1000, e=1000, f=5, r=10, stop=5), 0)
+        try:
+            with pytest.raises(mp.MPError):
+                mp.mp_dp_align_batch(c, [pair])
+        finally:
+            mp.mp_dp_destroy(c)
+    c = mp.mp_dp_init(mp.mp_dp_default_params(q=1000, e=1000, f=5, r=10, stop=5), 0)
+    try:
+        got = mp.mp_dp_align_batch(c, [pair])
+        assert got[0]["status"] & 0xF0 == 0
+    finally:
+        mp.mp_dp_destroy(c)
+
+
 def test_anchored_int32_pairs(mp, orc):
     """Anchored pairs whose lower bound leaves the int16 range run in int32
     at once (here by a large gap extension e), against the oracle."""
