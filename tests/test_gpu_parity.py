@@ -617,13 +617,13 @@ def test_anchored_lower_bound_refused(mp):
     prot = synth.random_protein(rng, 140_000)
     pair = synth.Pair(prot, "ATGGCCAAGTGG", 1)
     for mode in (1, 2):
-        c = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode, q=1000, e=1000, f=5, r=10, stop=5), 0)
+        c = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode, q=0, e=1000, f=5, r=10, stop=5), 0)
         try:
             with pytest.raises(mp.MPError):
                 mp.mp_dp_align_batch(c, [pair])
         finally:
             mp.mp_dp_destroy(c)
-    c = mp.mp_dp_init(mp.mp_dp_default_params(q=1000, e=1000, f=5, r=10, stop=5), 0)
+    c = mp.mp_dp_init(mp.mp_dp_default_params(q=0, e=1000, f=5, r=10, stop=5), 0)
     try:
         got = mp.mp_dp_align_batch(c, [pair])
         assert got[0]["status"] & 0xF0 == 0
