@@ -911,6 +911,8 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     if (c->staging.reserve(asc + 16) != cudaSuccess) return MP_ENOMEM;
     std::atomic<int> copy_err{0};
     auto gather_send = [&](size_t k0, size_t k1) {
+        // (a worker thread issues copies on the context's stream: its device first)
+        if (cudaSetDevice(c->device) != cudaSuccess) copy_err = 1;
         size_t from = k0;
         uint64_t acc = 0;
         for (size_t k = k0; k < k1; ++k) {
