@@ -855,9 +855,25 @@ int dp32_blocks_per_sm() { return kernel_blocks_per_sm<Ops32, 2>(dp32_smem_bytes
 
 namespace {
 // Per-nt records of every pair (see make_record), positions -kChunk upwards.
+// The genetic code and the splice terms are looked up in shared tables
+// (lanes index them at different positions: from constant memory such
+// reads serialise), the splice terms by three 5-symbol codes (four bases and
+// "outside the region"), filled from the splice model's own functions.
 __global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const uint32_t *nt2, const ScoreParams sp,
                                uint4 *recs)
 {
+    __shared__ int8_t s_code[64];
+    __shared__ int16_t s_don[125], s_acc[125];
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) s_code[k] = c_code.v[k];
+    for (int k = threadIdx.x; k < 125; k += blockDim.x) {
+        const int c1 = k / 25, c2 = (k / 5) % 5, c3 = k % 5;
+        const bool v1 = c1 != 4, v2 = c2 != 4, v3 = c3 != 4;
+        const int b1 = v1 ? c1 : 0, b2 = v2 ? c2 : 0, b3 = v3 ? c3 : 0;
+        s_don[k] = static_cast<int16_t>(splice_donor(sp, b1, b2, b3, v1, v2, v3));
+        s_acc[k] = static_cast<int16_t>(splice_acceptor(sp, b1, b2, b3, v1, v2, v3));
+    }
+    __syncthreads();
+    const uint32_t r = static_cast<uint32_t>(sp.r);
     for (uint32_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
         const PairDesc pd = pairs[p];
         if (pd.flags & PF_SKIP) continue;
@@ -865,7 +881,25 @@ __global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const ui
         const int cnt = static_cast<int>(records_of(pd.nt_len));
         const uint32_t *g = nt2 + pd.nt_word_off;
         uint4 *out = recs + pd.rec_off;
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) out[k] = make_record(g, n, k - kChunk, sp);
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            // the same record as make_record: window T0[ii-3 .. ii+4]
+            const int ii = k - kChunk;
+            const int s0 = ii - 3;
+            const int w = s0 >> 4;
+            const uint64_t pair64 = (static_cast<uint64_t>(g[w + 1]) << 32) | g[w];
+            const uint32_t win = static_cast<uint32_t>(pair64 >> ((s0 & 15) * 2));
+            int c[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                c[q] = static_cast<unsigned>(s0 + q) < static_cast<unsigned>(n) ? static_cast<int>((win >> (2 * q)) & 3)
+                                                                               : 4;
+            const int aa = (c[1] != 4 && c[3] != 4) ? s_code[c[1] * 16 + c[2] * 4 + c[3]] : 21;
+            const uint32_t dC = static_cast<uint32_t>(s_don[(c[5] * 5 + c[6]) * 5 + c[7]]);   // d(i+1)
+            const uint32_t dB = static_cast<uint32_t>(s_don[(c[4] * 5 + c[5]) * 5 + c[6]]);   // d(i)
+            const uint32_t aA = static_cast<uint32_t>(s_acc[(c[1] * 5 + c[2]) * 5 + c[3]]);   // a(i)
+            const uint32_t aC = static_cast<uint32_t>(s_acc[(c[0] * 5 + c[1]) * 5 + c[2]]);   // a(i-1)
+            out[k] = make_uint4((r + dC) | ((r + dB) << 16), aA | (aC << 16), static_cast<uint32_t>(aa) * 128u, 0u);
+        }
     }
 }
 }  // namespace
