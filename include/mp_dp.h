@@ -6,13 +6,14 @@
  * Eq. 7 (Methods, "DP for protein-to-genome alignment"): affine gaps (I, D),
  * frameshifts (the four f terms) and phase-0/1/2 introns (A, B, C) scored
  * together, with the final splice model d(i), a(i) of the "Splice models"
- * section.  The problem statement it serves is the paper's: take a protein
- * and a nucleotide sequence and return the spliced alignment between them
- * (Introduction).
+ * section.  It serves the problem the Introduction sets out: given a
+ * protein and a nucleotide sequence, find their spliced alignment.
  *
  * Conventions used by every call:
- *   - Alignment is local: H restarts at 0 and the best cell is the largest
- *     H, ties to the smallest genome position and then the smallest residue.
+ *   - Alignment is local unless mp_dp_params.mode says otherwise: H restarts
+ *     at 0 and the best cell is the largest H, ties to the smallest genome
+ *     position and then the smallest residue (the extension mode uses the
+ *     same best-cell rule; global mode ends at the last cell).
  *   - Ties inside each max of Eq. 7 go to the earliest printed term (open
  *     before extend; M, I, D, F1, F2, G1, G2, A, B, C for H); a restart at 0
  *     wins a tie at 0.
@@ -93,7 +94,8 @@ extern "C" {
  * protein letters outside the 20 amino acids and '*' map to X.
  * mp_dp_init rejects sets under which an intron of length <= 0 could beat
  * a frameshift or a match: it requires r > f, r > stop and r > -min(mat),
- * all penalties >= 0 and e >= 1. */
+ * all penalties >= 0 and e >= 1; and, for the packed int16 arithmetic,
+ * q + e <= 1000, f <= 1000, r <= 1000, stop <= 512 and splice_p <= 1000. */
 typedef struct {
     int32_t q, e, f, r, stop;  /* gap open, gap extend, frameshift, intron, stop codon */
     int8_t mat[22][22];
@@ -108,7 +110,7 @@ typedef struct {
                                   a batch holding a pair for which that reaches 2^27 is refused
                                   with MP_EINVAL (the DP represents -inf by -2^28) */
     uint64_t tb_budget_bytes;  /* device bytes for traceback codes (default 40 GiB, capped
-                                  by free device memory at init) */
+                                  at 60% of the device memory free at init) */
     int32_t force_int32;       /* 1: skip the packed int16 pass and run every pair in int32 */
     int32_t max_pairs_per_launch; /* 0: no limit; 1: one pair per kernel launch (plain form) */
     int32_t wait_limit;        /* polls (~0.25 us each) before a warp waiting on the previous
@@ -166,9 +168,10 @@ int mp_dp_init(mp_dp_ctx **ctx, const mp_dp_params *p, int device);
 
 /* Align n pairs end to end: host -> device copy, the DP, traceback, and
  * device -> host copy of results.  out[k] corresponds to pairs[k].  Blocks
- * until done.  Returns MP_EINVAL for a NULL or zero-length sequence pointer
- * with nonzero length, or strand not +-1; per-pair sequence errors go to
- * out[k].status. */
+ * until done.  Returns MP_EINVAL for a NULL sequence pointer with nonzero
+ * length, strand not +-1, a length beyond 1,047,551 nt or 1,048,575
+ * residues, or (anchored modes) a pair beyond the lower-bound limit given at
+ * mp_dp_params.mode; per-pair sequence errors go to out[k].status. */
 int mp_dp_align_batch(mp_dp_ctx *ctx, const mp_pair *pairs, size_t n, mp_result *out);
 
 /* Staged form of mp_dp_align_batch, for callers that keep a batch resident
