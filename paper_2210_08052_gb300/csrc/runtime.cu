@@ -16,6 +16,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <set>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -654,13 +655,14 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool 
     const uint64_t strips = b->strips_total;
     b->waves.clear();
     b->code_bytes_total = 0;
-    // ---- pair order: largest first (longest-processing-time first)
+    // ---- pair order: largest first (longest-processing-time first), ties
+    // in input order
+    std::vector<uint64_t> pcells(n);
+    for (size_t k = 0; k < n; ++k) pcells[k] = static_cast<uint64_t>(b->desc[k].prot_len) * b->desc[k].nt_len;
     b->order.resize(n);
     for (size_t k = 0; k < n; ++k) b->order[k] = static_cast<uint32_t>(k);
-    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
-        const uint64_t cx = static_cast<uint64_t>(b->desc[x].prot_len) * b->desc[x].nt_len;
-        const uint64_t cy = static_cast<uint64_t>(b->desc[y].prot_len) * b->desc[y].nt_len;
-        return cx > cy;
+    std::sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
+        return pcells[x] != pcells[y] ? pcells[x] > pcells[y] : x < y;
     });
     // ---- waves under the traceback budget
     // Every wave gets a share of large and small pairs: pairs are taken
@@ -695,28 +697,42 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool 
     const size_t nw0 = static_cast<size_t>(std::max<uint64_t>(1, div_up(total_bytes, wcap)));
     wbytes.assign(nw0, 0);
     wcells.assign(nw0, 0);
+    // waves by (work, index): the first one with room is the least-loaded
+    // wave that fits, the lowest index among equals
+    std::set<std::pair<uint64_t, uint32_t>> by_load;
+    for (uint32_t w = 0; w < nw0; ++w) by_load.insert({0, w});
     for (uint32_t k = 0; k < n; ++k) {
         const uint32_t p = b->order[k];
-        const uint64_t cells = static_cast<uint64_t>(b->desc[p].prot_len) * b->desc[p].nt_len;
-        size_t best = SIZE_MAX;
-        for (size_t w = 0; w < wbytes.size(); ++w)
-            if (wbytes[w] + cbytes[p] <= wcap && (best == SIZE_MAX || wcells[w] < wcells[best])) best = w;
-        if (best == SIZE_MAX) {
-            best = wbytes.size();
+        uint32_t best = UINT32_MAX;
+        for (auto it = by_load.begin(); it != by_load.end(); ++it) {
+            if (wbytes[it->second] + cbytes[p] <= wcap) {
+                best = it->second;
+                by_load.erase(it);
+                break;
+            }
+        }
+        if (best == UINT32_MAX) {
+            best = static_cast<uint32_t>(wbytes.size());
             wbytes.push_back(0);
             wcells.push_back(0);
         }
-        wave_of[p] = static_cast<uint32_t>(best);
+        wave_of[p] = best;
         wbytes[best] += cbytes[p];
-        wcells[best] += cells;
+        wcells[best] += pcells[p];
+        by_load.insert({wcells[best], best});
     }
     // group the largest-first order by wave, PF_WIDE pairs first within a wave
     // (so that their items form a prefix the int32 kernel can take directly),
     // otherwise still largest first
     auto wide = [&](uint32_t x) { return (b->desc[x].flags & PF_WIDE) && !(b->desc[x].flags & PF_SKIP) ? 0 : 1; };
-    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
-        return wave_of[x] != wave_of[y] ? wave_of[x] < wave_of[y] : wide(x) < wide(y);
-    });
+    {
+        // stable counting sort by key = 2 * wave + (not wide)
+        std::vector<uint32_t> start(2 * wbytes.size() + 1, 0), sorted(n);
+        for (uint32_t x : b->order) ++start[2 * wave_of[x] + wide(x) + 1];
+        for (size_t v = 1; v < start.size(); ++v) start[v] += start[v - 1];
+        for (uint32_t x : b->order) sorted[start[2 * wave_of[x] + wide(x)]++] = x;
+        b->order.swap(sorted);
+    }
     // strip items in pair order; each wave is a contiguous range
     uint64_t cur = 0, maxw = 0;
     uint32_t wbeg = 0, ibeg = 0, wcur = 0, nwide = 0;
