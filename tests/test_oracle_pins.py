@@ -136,6 +136,22 @@ def test_exhaustive_enumeration_equals_oracle(orc):
         assert got == want, (prot, nt, params)
 
 
+def test_exhaustive_enumeration_larger_cases(orc):
+    """Every path enumerated one by one at the largest sizes the CPU suite
+    affords (7 nt x 3 aa: 1.9 M paths; 9 nt x 2 aa: 4.5 M paths), with a
+    planted coding copy so that multi-op positive paths exist: the oracle's
+    score is the best enumerated op-sum."""
+    rng = random.Random(17)
+    for n, m in ((7, 3), (9, 2)):
+        prot = _rand_prot(rng, m)
+        nt = (_cds(rng, prot) + "".join(rng.choice("ACGT") for _ in range(n)))[:n]
+        params = dict(q=2, e=1, f=3, stop=4, r=7)
+        paths = bf.all_paths(bf.Problem(prot, nt, **params), limit=6_000_000)
+        want = bf.best_by_enumeration(paths)
+        got = orc.align(prot, nt, 1, orc.make_params(**params))["score"]
+        assert got == want, (prot, nt, len(paths))
+
+
 def test_segment_recursion_equals_oracle(orc):
     rng = random.Random(12)
     for _ in range(150):
