@@ -840,6 +840,31 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     b->waves.clear();
     b->cells = 0;
     b->code_bytes_total = 0;
+    // ---- shared host ranges: when every pair's region lies in one host
+    // range no longer than the regions' total length (windows of one genome),
+    // and the same holds for the proteins (one protein, several regions),
+    // the two ranges are sent once and the pairs point into them
+    uintptr_t nlo = UINTPTR_MAX, nhi = 0, plo = UINTPTR_MAX, phi = 0;
+    uint64_t nsum = 0, psum = 0;
+    for (size_t k = 0; k < n; ++k) {
+        const mp_pair &q = pairs[k];
+        if (q.nt_len) {
+            const uintptr_t x = reinterpret_cast<uintptr_t>(q.nt);
+            nlo = std::min(nlo, x);
+            nhi = std::max(nhi, x + q.nt_len);
+            nsum += q.nt_len;
+        }
+        if (q.prot_len) {
+            const uintptr_t x = reinterpret_cast<uintptr_t>(q.prot);
+            plo = std::min(plo, x);
+            phi = std::max(phi, x + q.prot_len);
+            psum += q.prot_len;
+        }
+    }
+    const uint64_t nspan = nsum ? nhi - nlo : 0, pspan = psum ? phi - plo : 0;
+    const uint64_t prot_base = div_up(nspan, 16) * 16;
+    const bool span = !ascii_on_device && nsum && psum && nspan <= nsum && pspan <= psum &&
+                      nspan + psum > 0 && prot_base + pspan < (uint64_t{1} << 32) && nspan + pspan < nsum + psum;
     // ---- layout
     const BoundTable bt(c->sp);
     uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0, nrec = 0, nc0 = 0;
@@ -850,11 +875,17 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         d.prot_len = q.prot_len;
         d.nt_len = q.nt_len;
         d.strand = q.strand;
-        d.asc_prot_off = static_cast<uint32_t>(asc);
-        asc += q.prot_len;
-        d.asc_nt_off = asc;
-        asc += q.nt_len;
-        asc = div_up(asc, 16) * 16;
+        if (span) {
+            d.asc_prot_off = static_cast<uint32_t>(
+                prot_base + (q.prot_len ? reinterpret_cast<uintptr_t>(q.prot) - plo : 0));
+            d.asc_nt_off = q.nt_len ? reinterpret_cast<uintptr_t>(q.nt) - nlo : 0;
+        } else {
+            d.asc_prot_off = static_cast<uint32_t>(asc);
+            asc += q.prot_len;
+            d.asc_nt_off = asc;
+            asc += q.nt_len;
+            asc = div_up(asc, 16) * 16;
+        }
         d.prot_off = static_cast<uint32_t>(pro);
         pro += q.prot_len;
         d.nt_word_off = static_cast<uint32_t>(ntw + kNtPadWords);
@@ -892,6 +923,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         b->strand[k] = q.strand;
         b->cells += static_cast<double>(q.prot_len) * q.nt_len;
     }
+    if (span) asc = prot_base + pspan;
     if (asc > 0xffffffffull || pro > 0xffffffffull || ntw > 0xffffffffull || strips > 0xffffffffull)
         return MP_EINVAL;
     b->ascii_bytes = asc; b->prot_total = pro; b->nt_words = ntw; b->bnd_total = bnd; b->ops_total = ops;
@@ -947,6 +979,21 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
             }
         }
     };
+    // shared ranges: staging [0, nspan) is the regions' host range,
+    // [prot_base, prot_base + pspan) the proteins'; sent in ~2 MB pieces
+    auto span_send = [&](uint64_t lo, uint64_t hi) {
+        if (cudaSetDevice(c->device) != cudaSuccess) copy_err = 1;
+        for (uint64_t a = lo; a < hi;) {
+            const uint64_t e = std::min<uint64_t>(hi, a + (2u << 20));
+            const uint64_t n0 = a, n1 = std::min(e, nspan);
+            if (n1 > n0) memcpy(c->staging.p + n0, reinterpret_cast<const char *>(nlo) + n0, n1 - n0);
+            const uint64_t p0 = std::max(a, prot_base), p1 = std::min(e, prot_base + pspan);
+            if (p1 > p0) memcpy(c->staging.p + p0, reinterpret_cast<const char *>(plo) + (p0 - prot_base), p1 - p0);
+            if (cudaMemcpyAsync(b->ascii.p + a, c->staging.p + a, e - a, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                copy_err = 1;
+            a = e;
+        }
+    };
     const unsigned nthr = asc > (16u << 20) ? std::min(16u, std::max(1u, std::thread::hardware_concurrency())) : 0u;
     if (nthr && !c->pool) {
         c->pool.reset(new (std::nothrow) WorkerPool());
@@ -955,12 +1002,16 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     const bool pooled = nthr && c->pool;
     if (pooled) {
         const unsigned nj = static_cast<unsigned>(c->pool->th.size());
-        c->pool->run(nj, [&, nj](unsigned t) { gather_send(n * t / nj, n * (t + 1) / nj); });
+        if (span)
+            c->pool->run(nj, [&, nj](unsigned t) { span_send(asc * t / nj, asc * (t + 1) / nj); });
+        else
+            c->pool->run(nj, [&, nj](unsigned t) { gather_send(n * t / nj, n * (t + 1) / nj); });
     }
     // the plan reads the layout fields of the descriptors the workers read
     // and writes others (code offsets), and copies out of its own buffer
     const int rc = plan_waves(c, b, tuning_for(c, b), true);
     if (pooled) c->pool->wait();
+    else if (span) span_send(0, asc);
     else gather_send(0, n);
     if (rc != MP_OK) return rc;
     if (copy_err) return MP_ECUDA;
