@@ -346,7 +346,16 @@ def main():
         po, pl, no, nl, st_ = gw.region_arrays()
         src = mp.RegionBatch(gw.prot_buf, po, pl, gw.genome, no, nl, st_)
         n_pairs, cells = gw.n_regions, gw.cells()
+        # the library sends a genome range and a protein range once when the
+        # regions (proteins) share them and the ranges are shorter than the
+        # records' total length
         ascii_bytes = int(pl.sum() + nl.sum())
+        nz, pz = nl > 0, pl > 0
+        if nz.any() and pz.any():
+            nspan = int((no[nz] + nl[nz]).max() - no[nz].min())
+            pspan = int((po[pz] + pl[pz]).max() - po[pz].min())
+            if nspan <= int(nl.sum()) and pspan <= int(pl.sum()) and nspan + pspan < ascii_bytes:
+                ascii_bytes = nspan + pspan
         get_pair = gw.pair
         workload = WORKLOAD_C5 if args.c5_scale == 1.0 else WORKLOAD_C5 + f" (scaled by {args.c5_scale})"
     else:
