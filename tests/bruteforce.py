@@ -155,6 +155,24 @@ def all_paths(pb: Problem, limit: int = 2_000_000):
     return out
 
 
+def anchored_paths(pb: Problem, limit: int = 5_000_000):
+    """Every path from cell (0, 0), by exhaustive depth-first walk:
+    (ops, end i, end j, score)."""
+    out = []
+
+    def walk(i, j, ops, sc):
+        out.append((tuple(ops), i, j, sc))
+        if len(out) > limit:
+            raise RuntimeError("too many paths")
+        for name, L, di, dj, c in pb.ops_from(i, j):
+            ops.append((name, L))
+            walk(i + di, j + dj, ops, sc + c)
+            ops.pop()
+
+    walk(0, 0, [], 0)
+    return out
+
+
 def best_by_enumeration(paths) -> int:
     return max(max(p[5] for p in paths), 0)
 

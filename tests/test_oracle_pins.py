@@ -445,6 +445,23 @@ def test_anchored_modes_against_enumeration(orc):
         assert orc.align(prot, nt, 1, orc.make_params(mode=2, **params))["score"] == x
 
 
+def test_anchored_modes_against_larger_enumeration(orc):
+    """Every path from cell (0, 0) enumerated one by one at 7 nt x 3 aa
+    (1.2 M paths) and 8 nt x 2 aa (0.8 M), with a planted coding copy: the
+    global score is the best path ending at (|T|, |P|), the extension score
+    the best path anywhere (the empty one included)."""
+    rng = random.Random(73)
+    for n, m in ((7, 3), (8, 2)):
+        prot = _rand_prot(rng, m)
+        nt = (_cds(rng, prot) + "".join(rng.choice("ACGT") for _ in range(n)))[:n]
+        params = dict(q=2, e=1, f=3, stop=4, r=7)
+        paths = bf.anchored_paths(bf.Problem(prot, nt, **params), limit=3_000_000)
+        g = max(p[3] for p in paths if (p[1], p[2]) == (n, m))
+        x = max(p[3] for p in paths)
+        assert orc.align(prot, nt, 1, orc.make_params(mode=1, **params))["score"] == g, (prot, nt)
+        assert orc.align(prot, nt, 1, orc.make_params(mode=2, **params))["score"] == x, (prot, nt)
+
+
 def test_anchored_paths_rescore_and_span(orc):
     """Anchored alignments start at (0, 0); global ones end at (|T|, |P|);
     their CIGARs rescore to the score (negative scores included), on both
