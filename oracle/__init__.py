@@ -144,6 +144,10 @@ def lib():
             L.orc_aa_code.restype = ctypes.c_int
             L.orc_nt_code.argtypes = [ctypes.c_int]
             L.orc_nt_code.restype = ctypes.c_int
+            L.orc_score_end.argtypes = [ctypes.POINTER(Params), ctypes.c_char_p, ctypes.c_int32,
+                                        ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(Result)]
+            L.orc_score_end.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -169,6 +173,22 @@ def align(prot: str, nt: str, strand: int = 1, params: Params | None = None):
     raw = [cig[k] for k in range(res.n_cigar)]
     return dict(score=res.score, status=res.status, prot_st=res.prot_st, prot_en=res.prot_en,
                 nt_st=res.nt_st, nt_en=res.nt_en, cigar=ops, cigar_raw=raw)
+
+
+def score_end(prot: str, nt: str, strand: int = 1, params: Params | None = None):
+    """Score and end cell of the best alignment with four rows of memory per
+    state (for pairs too large for the full matrices of ``align``).  Returns
+    a dict with score, prot_en and the genome end of the best cell: nt_en on
+    strand +1, nt_st on strand -1 (the other genome coordinate is None)."""
+    L = lib()
+    p = params if params is not None else make_params()
+    pb = prot.encode() if isinstance(prot, str) else bytes(prot)
+    tb = nt.encode() if isinstance(nt, str) else bytes(nt)
+    res = Result()
+    if L.orc_score_end(ctypes.byref(p), pb, len(pb), tb, len(tb), int(strand), ctypes.byref(res)) != 0:
+        raise ValueError("oracle rejected the input")
+    return dict(score=res.score, prot_en=res.prot_en,
+                nt_en=res.nt_en if strand > 0 else None, nt_st=res.nt_st if strand < 0 else None)
 
 
 def rescore(prot: str, nt: str, strand: int, prot_st: int, nt_st_aligned: int, cigar_raw,

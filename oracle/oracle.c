@@ -472,6 +472,106 @@ int32_t orc_score(const orc_params *p, const char *prot, int32_t plen, const cha
     return r.score;
 }
 
+/* Score and end cell only, for pairs whose six full matrices would not fit
+ * in memory: the same recurrence (Eq. 7), the same modes and the same
+ * best-cell rule as orc_align, with each state kept for the last four rows
+ * (the deepest look-back of Eq. 7 is H and D at i-3).  Every splice term
+ * and the codon of row i depend on i alone, so they are evaluated once per
+ * row.  Writes score, prot_en and the genome end of the best cell (nt_en on
+ * strand +1, nt_st on strand -1, both on the input's forward strand); the
+ * start coordinates are not computed (-1).  Returns 0, or -1 on bad input. */
+int orc_score_end(const orc_params *p, const char *prot, int32_t plen, const char *nt, int32_t tlen,
+                  int32_t strand, orc_result *res)
+{
+    memset(res, 0, sizeof(*res));
+    const int n = tlen, m = plen;
+    const int anchored = p->mode != 0;
+    int8_t *T = (int8_t *)malloc((size_t)n + 1);
+    int8_t *P = (int8_t *)malloc((size_t)m + 1);
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1) * 14);
+    if (!T || !P || !buf) { free(T); free(P); free(buf); res->status = 3; return -1; }
+    for (int i = 1; i <= n; ++i) {
+        int b = orc_nt_code(nt[strand < 0 ? n - i : i - 1]);
+        if (b < 0) { free(T); free(P); free(buf); res->status = 3; return -1; }
+        T[i] = (int8_t)(strand < 0 ? 3 - b : b);
+    }
+    for (int j = 1; j <= m; ++j) P[j] = (int8_t)orc_aa_code(prot[j - 1]);
+    /* rows i mod 4 of H and D; rows i mod 2 of A, B, C */
+    int32_t *Hr[4], *Dr[4], *Ar[2], *Br[2], *Cr[2];
+    for (int k = 0; k < 4; ++k) { Hr[k] = buf + (size_t)k * (m + 1); Dr[k] = buf + (size_t)(4 + k) * (m + 1); }
+    for (int k = 0; k < 2; ++k) {
+        Ar[k] = buf + (size_t)(8 + k) * (m + 1);
+        Br[k] = buf + (size_t)(10 + k) * (m + 1);
+        Cr[k] = buf + (size_t)(12 + k) * (m + 1);
+    }
+    int32_t best = 0;
+    int bi = 0, bj = 0;
+    for (int i = 0; i <= n; ++i) {
+        int32_t *H = Hr[i & 3], *D = Dr[i & 3], *A = Ar[i & 1], *B = Br[i & 1], *C = Cr[i & 1];
+        /* rows above 0 are outside the matrix (-inf) */
+        const int32_t *H1 = i >= 1 ? Hr[(i - 1) & 3] : NULL, *H2 = i >= 2 ? Hr[(i - 2) & 3] : NULL;
+        const int32_t *H3 = i >= 3 ? Hr[(i - 3) & 3] : NULL, *D3 = i >= 3 ? Dr[(i - 3) & 3] : NULL;
+        const int32_t *A1 = i >= 1 ? Ar[(i - 1) & 1] : NULL, *B1 = i >= 1 ? Br[(i - 1) & 1] : NULL;
+        const int32_t *C1 = i >= 1 ? Cr[(i - 1) & 1] : NULL;
+        /* terms of row i that depend on i only */
+        const int32_t rd_im1 = p->r + splice_d(p, T, n, i - 1), rd_i = p->r + splice_d(p, T, n, i);
+        const int32_t rd_ip1 = p->r + splice_d(p, T, n, i + 1);
+        const int32_t a_i = splice_a(p, T, n, i), a_im2 = splice_a(p, T, n, i - 2), a_im1 = splice_a(p, T, n, i - 1);
+        int aa = -1;
+        if (i >= 3) aa = orc_translate(T[i - 2], T[i - 1], T[i]);
+        int32_t Ij = ORC_NEG_INF;                   /* I[i][j-1] */
+        for (int j = 0; j <= m; ++j) {
+            const int32_t h1j = H1 ? H1[j] : ORC_NEG_INF, h2j = H2 ? H2[j] : ORC_NEG_INF;
+            const int32_t h1jm = (H1 && j >= 1) ? H1[j - 1] : ORC_NEG_INF;
+            const int32_t h2jm = (H2 && j >= 1) ? H2[j - 1] : ORC_NEG_INF;
+            if (anchored ? (i == 0 && j == 0) : (i == 0 || j == 0)) {
+                /* local: row and column 0 hold H = 0; anchored: cell (0, 0) */
+                H[j] = 0;
+                D[j] = A[j] = B[j] = C[j] = ORC_NEG_INF;
+                Ij = ORC_NEG_INF;
+                continue;
+            }
+            const int32_t I = j >= 1 ? max2(H[j - 1] - p->q, Ij) - p->e : ORC_NEG_INF;
+            const int32_t Dv = max2((H3 ? H3[j] : ORC_NEG_INF) - p->q, D3 ? D3[j] : ORC_NEG_INF) - p->e;
+            const int32_t Av = max2(h1j - rd_im1, A1 ? A1[j] : ORC_NEG_INF);
+            const int32_t Bv = max2(h1jm - rd_i, B1 ? B1[j] : ORC_NEG_INF);
+            const int32_t Cv = max2(h1jm - rd_ip1, C1 ? C1[j] : ORC_NEG_INF);
+            int32_t h = ORC_NEG_INF;
+            if (i >= 3 && j >= 1)
+                h = H3[j - 1] + (aa == ORC_AA_STOP ? -p->stop : p->mat[aa][P[j]]);
+            h = max2(h, I);
+            h = max2(h, Dv);
+            h = max2(h, h1jm - p->f);
+            h = max2(h, h2jm - p->f);
+            h = max2(h, h1j - p->f);
+            h = max2(h, h2j - p->f);
+            h = max2(h, Av - a_i);
+            h = max2(h, Bv - a_im2);
+            h = max2(h, Cv - a_im1);
+            if (!anchored && h < 0) h = 0;
+            H[j] = h;
+            D[j] = Dv;
+            A[j] = Av;
+            B[j] = Bv;
+            C[j] = Cv;
+            Ij = I;
+            /* best cell: largest H, then smallest i, then smallest j (local:
+             * cells after a residue and a base; extension: every cell) */
+            if (p->mode != 1 && h > best && (anchored || (i >= 1 && j >= 1))) { best = h; bi = i; bj = j; }
+        }
+    }
+    if (p->mode == 1) { best = Hr[n & 3][m]; bi = n; bj = m; }
+    res->score = best;
+    res->prot_st = res->nt_st = res->nt_en = -1;
+    res->prot_en = bj;
+    if (strand < 0) res->nt_st = n - bi;
+    else res->nt_en = bi;
+    free(T);
+    free(P);
+    free(buf);
+    return 0;
+}
+
 /* Op-sum rescoring of a CIGAR (no DP): walks the ops from the aligned start
  * (prot_st, nt position in the aligned orientation) and adds each op's cost
  * as defined by the transitions of Eq. 7.  Returns the score and writes the

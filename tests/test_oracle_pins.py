@@ -586,3 +586,144 @@ def test_paper_worked_example(orc):
         assert r["score"] >= max(want, 0)
         sc2, pe2, te2 = orc.rescore(prot, nt, 1, r["prot_st"], r["nt_st"], r["cigar_raw"], params)
         assert (sc2, pe2, te2) == (r["score"], r["prot_en"], r["nt_en"])
+
+
+# ------------------------------------------- score and end cell in four rows
+def _best_cell(table, mode, n, m):
+    """(score, i, j) of the best cell of a table of per-cell best path
+    scores: the largest score, then the smallest i, then the smallest j
+    (local: cells after a residue and a base, score 0 at (0, 0) when none is
+    positive; extension: every cell; global: the cell (n, m))."""
+    if mode == "global":
+        return table[n][m], n, m
+    best, bi, bj = 0, 0, 0
+    for i in range(n + 1):
+        for j in range(m + 1):
+            if mode == "local" and (i == 0 or j == 0):
+                continue
+            if table[i][j] > best:
+                best, bi, bj = table[i][j], i, j
+    return best, bi, bj
+
+
+def _end_of(res, strand, n):
+    """The best cell's genome row in the aligned orientation."""
+    return res["nt_en"] if strand > 0 else n - res["nt_st"]
+
+
+def test_score_end_against_segment_recursion(orc):
+    """The four-row fill's score and end cell equal the best cell of the
+    Bellman recursion over whole operations (no DP states), in all three
+    modes, both splice models, valid and invalid penalty sets."""
+    rng = random.Random(91)
+    modes = {0: "local", 1: "global", 2: "extend"}
+    for k in range(60):
+        prot, nt, params = _random_case(rng, rng.randint(0, 20), rng.randint(0, 5), valid=rng.random() < 0.6)
+        sp = rng.randint(0, 9) if k % 3 == 0 else None
+        pb = bf.Problem(prot, nt, splice_p=sp, **params)
+        for mode in (0, 1, 2):
+            want = _best_cell(bf.best_table(pb, modes[mode]), modes[mode], len(nt), len(prot))
+            pp = orc.make_params(mode=mode, splice_model=0 if sp is None else 1,
+                                 splice_p=30 if sp is None else sp, **params)
+            got = orc.score_end(prot, nt, 1, pp)
+            assert (got["score"], _end_of(got, 1, len(nt)), got["prot_en"]) == want, (prot, nt, params, mode)
+
+
+def test_score_end_against_enumeration(orc):
+    """Score and end cell against every enumerated path on tiny inputs: the
+    best op-sum, ending at the smallest (i, j) among optimal paths."""
+    rng = random.Random(92)
+    for _ in range(40):
+        prot, nt, params = _random_case(rng, rng.randint(1, 6), rng.randint(1, 2), valid=True)
+        paths = bf.all_paths(bf.Problem(prot, nt, **params))
+        best = bf.best_by_enumeration(paths)
+        got = orc.score_end(prot, nt, 1, orc.make_params(**params))
+        assert got["score"] == best
+        if best > 0:
+            assert (_end_of(got, 1, len(nt)), got["prot_en"]) == min((p[3], p[4]) for p in paths if p[5] == best)
+
+
+def test_score_end_equals_full_oracle(orc):
+    """On larger pairs (planted spliced genes with flanks, random regions,
+    both strands) the four-row fill gives the full-matrix oracle's score and
+    end cell in every mode, with default, random and tie-rich penalties."""
+    rng = np.random.default_rng(93)
+    r2 = random.Random(93)
+    tie = np.sign(orc.blosum62_22()).astype(np.int32)
+    tie[np.arange(20), np.arange(20)] = 2
+    cases = []
+    for k in range(24):
+        m = int(rng.integers(5, 90))
+        prot = synth.random_protein(rng, m)
+        if k % 4 == 3:
+            nt = synth.random_dna(rng, int(rng.integers(10, 900)))
+        else:
+            introns = [int(x) for x in rng.integers(40, 300, size=int(rng.integers(0, 3)))]
+            nt, _ = synth.gen.plant_gene(rng, prot, 0.25, int(rng.integers(0, 3)), introns,
+                                         int(rng.integers(0, 80)), int(rng.integers(0, 80)), 0.4)
+        cases.append((prot, nt))
+    psets = [dict(), dict(q=3, e=2, f=5, r=9, stop=4), dict(q=1, e=1, f=2, r=4, stop=1, mat=tie)]
+    for k, (prot, nt) in enumerate(cases):
+        for mode in (0, 1, 2):
+            ps = psets[(k + mode) % 3]
+            pp = orc.make_params(mode=mode, splice_model=k % 2, splice_p=r2.randint(0, 20), **ps)
+            for strand, t in ((1, nt), (-1, orc.revcomp(nt))):
+                full = orc.align(prot, t, strand, pp)
+                got = orc.score_end(prot, t, strand, pp)
+                assert got["score"] == full["score"], (k, mode, strand)
+                if full["score"] > 0 or mode == 1:
+                    assert got["prot_en"] == full["prot_en"], (k, mode, strand)
+                    if strand > 0:
+                        assert got["nt_en"] == full["nt_en"], (k, mode, strand)
+                    else:
+                        assert got["nt_st"] == full["nt_st"], (k, mode, strand)
+
+
+# ------------------------------------- tie rule of the anchored tracebacks
+def test_anchored_tie_rule_against_path_order(orc):
+    """Global and extension modes: the oracle's path is the optimum the
+    stated tie rules select among every enumerated path from cell (0, 0):
+    the end cell (global: (|T|, |P|); extension: the smallest i, then j,
+    among optimal ends, the empty path at (0, 0) included), then, reading
+    the operations backwards, the earliest term of Eq. 7's printed order,
+    the shorter run first inside I, D and intron runs.  Small integer
+    penalties and a {-1, 0, 1, 2} matrix make ties common."""
+    rng = random.Random(94)
+    mat = np.sign(orc.blosum62_22()).astype(np.int32)
+    mat[np.arange(20), np.arange(20)] = 2
+
+    def key(p):
+        return tuple((bf.ORDER[name], L) for name, L in reversed(p[0]))
+
+    checked = {1: 0, 2: 0}
+    for _ in range(90):
+        n, m = rng.randint(2, 7), rng.randint(1, 2)
+        prot = _rand_prot(rng, m)
+        nt = "".join(rng.choice("ACGT") for _ in range(n))
+        if rng.random() < 0.6:
+            k = rng.randint(0, max(0, n - 3))
+            nt = (nt[:k] + _cds(rng, prot) + nt[k:])[:n]
+        params = dict(q=rng.randint(0, 2), e=1, f=rng.randint(1, 2), stop=1, r=3)
+        paths = bf.anchored_paths(bf.Problem(prot, nt, mat=mat, **params))
+        for mode in (1, 2):
+            res = orc.align(prot, nt, 1, orc.make_params(mat=mat, mode=mode, **params))
+            if mode == 1:
+                ends = [p for p in paths if (p[1], p[2]) == (n, m)]
+                best = max(p[3] for p in ends)
+                opt = [p for p in ends if p[3] == best]
+            else:
+                best = max(p[3] for p in paths)            # the empty path scores 0
+                if best == 0:
+                    assert res["score"] == 0 and res["cigar"] == [], (prot, nt, params)
+                    continue
+                opt = [p for p in paths if p[3] == best]
+                ei, ej = min((p[1], p[2]) for p in opt)
+                opt = [p for p in opt if (p[1], p[2]) == (ei, ej)]
+            choice = min(opt, key=key)
+            ops, ei, ej, sc = choice
+            assert res["score"] == sc, (prot, nt, params, mode)
+            assert (res["prot_st"], res["prot_en"], res["nt_st"], res["nt_en"]) == (0, ej, 0, ei), \
+                (prot, nt, params, mode)
+            assert res["cigar"] == bf.to_cigar(ops), (prot, nt, params, mode, ops)
+            checked[mode] += 1
+    assert checked[1] > 40 and checked[2] > 30, checked
