@@ -225,16 +225,20 @@ void mp_dp_destroy(mp_dp_ctx *ctx);
 
 /* Allocation-free scoring of one pair (no counterpart in the paper).
  *
- * For callers that cannot allocate device memory: code running inside a
- * CUDA stream capture, where cudaMalloc is forbidden or breaks the capture,
- * and services that fix their device memory at start-up and must not
- * allocate, free or synchronize the device afterwards.  The call runs the
+ * For callers that cannot allocate device memory: services that fix their
+ * device memory at start-up and must not allocate or free afterwards
+ * (cudaMalloc and cudaFree can synchronize the device, and an allocation can
+ * fail once other tenants hold the memory), and hosts that give plug-ins
+ * device memory only from their own pools.  The call runs the
  * same DP as mp_dp_align_batch (packed int16, exact int32 re-run on
  * saturation), score only, for one pair, and allocates nothing: its scratch
  * is a fixed array of about 820 KB inside this library, held by every GPU
  * that loads the library until the process exits.
  *
- *   params  scoring parameters (NULL: defaults), validated as by mp_dp_init
+ *   params  scoring parameters (NULL: defaults), validated as by mp_dp_init;
+ *           wait_limit bounds the waits between cooperating warps as in
+ *           the batch calls; max_pairs_per_launch, tb_budget_bytes, autotune
+ *           and exon_rescore have no effect here
  *   d_prot  device pointer to prot_len ASCII residues, prot_len <= 4096
  *   d_nt    device pointer to nt_len ASCII nucleotides, nt_len <= 32768
  *   strand  +1, or -1 to align to the reverse complement of d_nt

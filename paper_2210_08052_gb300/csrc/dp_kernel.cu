@@ -932,12 +932,11 @@ cudaError_t launch_dp32(const DPArgs &a, int grid, bool rerun_only, cudaStream_t
 // ===========================================================================
 // Allocation-free scoring of one pair.
 //
-// Some callers cannot call cudaMalloc: code that runs inside a CUDA stream
-// capture (an allocation there is either forbidden or breaks the capture),
-// and services that fix their device memory at start-up and may not
-// allocate or free afterwards (cudaMalloc/cudaFree also synchronize the
-// device, which such a service cannot afford in its serving path).  For
-// them mp_dp_score_pair_noalloc runs the same packed-int16 DP (with the
+// Some callers cannot call cudaMalloc: services that fix their device
+// memory at start-up and may not allocate or free afterwards (cudaMalloc and
+// cudaFree can synchronize the device, and an allocation can fail once other
+// tenants hold the memory), and hosts that hand device memory to plug-ins
+// only from their own pools.  For them mp_dp_score_pair_noalloc runs the same packed-int16 DP (with the
 // same int32 re-run on saturation) on one pair, score only, using a fixed
 // scratch array that lives in this library's module for the life of the
 // process.  Every GPU that loads the library holds this array until exit.
@@ -996,7 +995,7 @@ __device__ __forceinline__ int na_nt_code(unsigned char c)
 // {score, status, protein end, genome end on the forward strand} to out4.
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 1)
 dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_ascii, int n, int strand,
-                  int32_t *out4, NoAllocScratch *S)
+                  int32_t *out4, NoAllocScratch *S, uint32_t spin_limit)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int bad;
@@ -1018,6 +1017,8 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
         S->strips_done = S->rerun_count = S->head16 = S->head32 = 0;
         bad = 0;
     }
+    // the flag is cleared before any thread can set it while packing
+    __syncthreads();
     // every call starts from zeroed progress counters
     for (int k = threadIdx.x; k < kNAMaxStrips; k += blockDim.x) S->progress[k] = 0;
     for (int k = threadIdx.x; k < m; k += blockDim.x)
@@ -1055,6 +1056,7 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
         a.rerun_items = S->rerun_items;
         a.rerun_count = &S->rerun_count;
         a.sp = sp;
+        a.spin_limit = spin_limit;
         {
             auto &sm = reinterpret_cast<WarpSmem<Ops16::Bnd> *>(smem_raw)[warp];
             for (;;) {
@@ -1111,7 +1113,7 @@ extern "C" int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *
     if (p.q < 0 || p.e < 1 || p.f < 0 || p.r < 0 || p.stop < 0 || p.q + p.e > 1000 || p.f > 1000 ||
         p.r > 1000 || p.stop > 512 || !(p.r > p.f && p.r > p.stop && p.r > -mn) ||
         (p.splice_model != MP_SPLICE_FINAL && p.splice_model != MP_SPLICE_SIMPLE) || p.splice_p < 0 ||
-        p.splice_p > 1000 || p.mode != MP_MODE_LOCAL)
+        p.splice_p > 1000 || p.mode != MP_MODE_LOCAL || p.wait_limit < 0 || p.max_pairs_per_launch < 0)
         return MP_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return MP_ECUDA;
@@ -1141,6 +1143,6 @@ extern "C" int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *
         for (int y = 0; y < 22; ++y) sp.mat[x][y] = p.mat[x][y];
     dp_noalloc_kernel<<<1, kWarpsPerCta * 32, kNASmem, static_cast<cudaStream_t>(stream)>>>(
         sp, d_prot, static_cast<int>(prot_len), d_nt, static_cast<int>(nt_len), strand, d_out,
-        static_cast<NoAllocScratch *>(scratch_ptr[dev]));
+        static_cast<NoAllocScratch *>(scratch_ptr[dev]), p.wait_limit > 0 ? static_cast<uint32_t>(p.wait_limit) : 0u);
     return cudaGetLastError() == cudaSuccess ? MP_OK : MP_ECUDA;
 }
