@@ -6,6 +6,11 @@ Step = one pass of the whole device pipeline (pack, packed-int16 DP with
 int32 re-run, traceback, CIGAR compaction) over the 4,096-pair workload
 (protein log-normal median 350 aa; Poisson(3) introns; 1 kb flanks; half on
 the reverse strand), inputs resident in HBM.  Prints one JSON line.
+At N=1 the line also carries, each measured the same way with its own
+autotuned launch configuration: the 20,000-pair uneven-size workload
+("c3"), the genome-scale candidate regions ("c5"), the plain
+one-launch-per-pair form, the anchored modes, pseudogene-aware rescoring,
+serving at 2k, 10k and 50k pairs/s for 60 s each, and the CPU oracle.
 Under torchrun each rank aligns its own 4,096-pair batch (weak scaling, no
 collective on the data path).
 """
@@ -289,6 +294,161 @@ def serve_once(mp, pairs, rate: float, seconds: float, device: int):
             "batches": int(st["batches"]), "mean_batch_pairs": st["mean_batch_pairs"]}
 
 
+TUNING_KEYS = ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct", "overlap_waves", "item_order",
+               "strip_w")
+
+
+def load_pairs(mp, pairs):
+    """A list of pairs as the C ABI takes them (host memory)."""
+    src = mp.PairBatch(pairs)
+    return (src, len(pairs), float(sum(p.cells for p in pairs)), sum(len(p.prot) + len(p.nt) for p in pairs),
+            pairs.__getitem__)
+
+
+def load_c5(mp, rank, scale=1.0):
+    """Candidate regions of the genome-scale workload as zero-copy records
+    into the genome and protein buffers; the generation and the host seed +
+    chain step are input preparation, outside every timed region."""
+    import numpy as np
+
+    import synth
+
+    t_gen = time.perf_counter()
+    gw = synth.config5(seed=rank_seed(5, rank), scale=scale)
+    prep = {"genome_bp": len(gw.genome), "proteins": len(gw.prot_len), "regions": gw.n_regions,
+            "regions_per_protein": gw.n_regions / len(gw.prot_len),
+            "generate_and_seed_chain_s": time.perf_counter() - t_gen}
+    po, pl, no, nl, st_ = gw.region_arrays()
+    src = mp.RegionBatch(gw.prot_buf, po, pl, gw.genome, no, nl, st_)
+    # the library sends a genome range and a protein range once when the
+    # regions (proteins) share them and the ranges are shorter than the
+    # records' total length
+    ascii_bytes = int(pl.sum() + nl.sum())
+    nz, pz = nl > 0, pl > 0
+    if nz.any() and pz.any():
+        nspan = int((no[nz] + nl[nz]).max() - no[nz].min())
+        pspan = int((po[pz] + pl[pz]).max() - po[pz].min())
+        if nspan <= int(nl.sum()) and pspan <= int(pl.sum()) and nspan + pspan < ascii_bytes:
+            ascii_bytes = nspan + pspan
+    workload = WORKLOAD_C5 if scale == 1.0 else WORKLOAD_C5 + f" (scaled by {scale})"
+    return src, gw.n_regions, gw.cells(), ascii_bytes, gw.pair, workload, prep
+
+
+def measure(mp, torch, src, n_pairs, cells, ascii_bytes, steps, warmup, device, dist, flush, mode=0, fixed=None,
+            autotune=True, e2e_steps=3):
+    """Time the device-resident pipeline (inputs in HBM, L2 flushed before
+    each step, CUDA events per kernel inside the library, wall time between
+    barriers + device syncs) and the end-to-end call with host buffers, with
+    the launch configuration the library's autotuner picks for the batch."""
+    ctx = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode), device)
+    mp.mp_dp_set_timing(ctx, True)
+    batch = mp.mp_dp_batch_upload(ctx, src)
+    tuning = None
+    if fixed:
+        mp.mp_dp_set_tuning(ctx, fixed)
+        tuning = {"fixed": fixed}
+    elif autotune:
+        # chosen on this batch, outside the timed region; the timed runs use the choice
+        best, tried = mp.mp_dp_autotune(ctx, batch)
+        tuning = {"chosen": best, "candidates": tried}
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clk = Clocks(device).__enter__()         # sampler starts before the warm-up, outside the timed region
+    for _ in range(warmup):
+        mp.mp_dp_batch_run(ctx, batch)
+        mp.mp_dp_batch_sync(ctx)
+    dp_ms, rr_ms, tb_ms, tot_ms = [], [], [], []
+    clk.samples.clear()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        mp.mp_dp_batch_run(ctx, batch)
+        mp.mp_dp_batch_sync(ctx)
+        st = mp.mp_dp_get_stats(ctx)
+        dp_ms.append(st["dp_ms"]); rr_ms.append(st["rerun_ms"]); tb_ms.append(st["tb_ms"])
+        tot_ms.append(st["total_ms"])
+    barrier()
+    elapsed = time.perf_counter() - t0
+    clk.__exit__()
+    stats = mp.mp_dp_get_stats(ctx)
+    res = mp.mp_dp_batch_download(ctx, batch, raw=True)
+    mp.mp_dp_batch_free(ctx, batch)
+    all_cells, t_max = job_totals(cells, elapsed, dist, "cuda")
+    # ---- end to end through the C ABI with host buffers
+    mp.mp_dp_set_timing(ctx, False)
+    out = res
+    if e2e_steps:
+        mp.mp_dp_align_batch(ctx, src, raw=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        out = mp.mp_dp_align_batch(ctx, src, raw=True)
+    barrier()
+    e2e_t = max(time.perf_counter() - t0, 1e-9)
+    _, e2e_t = job_totals(cells, e2e_t, dist, "cuda")
+    mp.mp_dp_destroy(ctx)
+    h2d = ascii_bytes + n_pairs * (72 + 4)          # sequences + pair descriptors + work order
+    d2h = n_pairs * 32 + 4 + int(out["n_cigar"].sum()) * 4
+    e2e = {"value": all_cells / (e2e_t / e2e_steps) / 1e9 if e2e_steps else None, "unit": "GCUPS",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    return {"elapsed": elapsed, "t_max": t_max, "all_cells": all_cells, "steps": steps,
+            "kernel_ms": {"dp_int16": statistics.mean(dp_ms), "rerun_int32": statistics.mean(rr_ms),
+                          "traceback_compact": statistics.mean(tb_ms), "pipeline": statistics.mean(tot_ms)},
+            "dp_ms": dp_ms, "tot_ms": tot_ms, "waves": stats["n_waves"], "code_bytes": stats["code_bytes"],
+            "launches": stats["n_launches"], "n_rerun": int(((res["status"] & 1) != 0).sum()),
+            "clocks": clk.summary(), "tuning": tuning, "e2e": e2e,
+            "e2e_s": e2e_t / e2e_steps if e2e_steps else None}
+
+
+def roofline(m, cells, torch, device, peaks):
+    """Integer-issue roofline of the DP kernel: int16 lane-ops of Eq. 7 per
+    cell over the kernel's time (CUDA events; for a batch of several waves
+    the whole pipeline's time, since overlapped waves' DP intervals
+    overlap), against N_SM x 128 lanes x 2 int16 halves x f_SM."""
+    clocks = m["clocks"]
+    nsm = torch.cuda.get_device_properties(device).multi_processor_count
+    f_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = nsm * 128 * 2 * f_mhz * 1e6 / 1e12          # int16 lane-ops/s (Tops)
+    dp_avg_ms = statistics.mean(m["dp_ms"]) if m["dp_ms"] else None
+    time_basis = "DP kernel launch (CUDA events on its stream)"
+    if m["waves"] > 1:
+        dp_avg_ms = statistics.mean(m["tot_ms"]) if m["tot_ms"] else None
+        time_basis = "whole pipeline (several waves)"
+    achieved = cells * OPS_PER_CELL / (dp_avg_ms / 1000) / 1e12 if dp_avg_ms else None
+    ips = _profile_value("instructions_per_step")
+    return {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s (int16 lane-ops)",
+            "frac": (achieved / peak_ops) if achieved else None, "traffic": _profiled_traffic(cells),
+            "ops_per_cell": OPS_PER_CELL, "time_basis": time_basis,
+            "peak_basis": f"{nsm} SMs x 128 lanes x 2 int16 halves x {f_mhz:.0f} MHz (median SM clock under load)",
+            "hbm_write_gbs": m["code_bytes"] / (dp_avg_ms / 1000) / 1e9 if dp_avg_ms else None,
+            "issue_frac": (cells / 64 * ips / (dp_avg_ms / 1000) / (nsm * 4 * f_mhz * 1e6))
+            if (dp_avg_ms and ips) else None,
+            "issue_basis": "warp-instructions per 64-cell step from the committed ncu summary x steps/s "
+                           "over N_SM x 4 issue slots x f_SM",
+            "hbm_peak_gbs": peaks.get("hbm_gbs")}
+
+
+def leg(mp, torch, name, loader, device, flush, peaks, steps=3, warmup=3):
+    """A further workload measured like the main line (its own autotuned
+    configuration, device-resident value, end-to-end figure, roofline)."""
+    src, n_pairs, cells, ascii_bytes, get_pair, workload, prep = loader()
+    m = measure(mp, torch, src, n_pairs, cells, ascii_bytes, steps, warmup, device, None, flush, e2e_steps=2)
+    e2e = m["e2e"]
+    e2e["pairs_per_s"] = n_pairs / m["e2e_s"]
+    return {"workload": workload, "value": cells / (m["t_max"] / steps) / 1e9, "unit": "GCUPS",
+            "pairs_per_s": n_pairs / (m["t_max"] / steps), "ms_per_step": m["t_max"] * 1000 / steps,
+            "steps": steps, "warmup": warmup, "pairs": n_pairs, "cells": cells, "waves": m["waves"], **prep,
+            "kernel_ms": m["kernel_ms"], "n_rerun": m["n_rerun"], "roofline": roofline(m, cells, torch, device, peaks),
+            "clocks": m["clocks"], "tuning": m["tuning"], "e2e": e2e,
+            "gpu_launches": m["launches"] * steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,8 +456,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain/serving/cpu legs")
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
-    ap.add_argument("--serve-rates", default="10000")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rates", default="2000,10000,50000")
+    ap.add_argument("--legs", default="c3,c5", help="further workloads measured after the main line "
+                                                  "(c3: 20,000 uneven pairs; c5: genome-scale regions); '' for none")
     ap.add_argument("--pairs", type=int, default=4096, help="first N pairs of the workload (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: skip the end-to-end leg")
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration, no tuning runs")
@@ -333,31 +495,9 @@ def main():
         dist.barrier()
     mpbuild.build()
 
-    prep = {}
     if args.workload == "c5":
-        # candidate regions of the genome-scale workload, as zero-copy records
-        # into the genome and protein buffers (the host seed + chain step is
-        # input preparation, outside every timed region)
-        t_gen = time.perf_counter()
-        gw = synth.config5(seed=rank_seed(5, rank), scale=args.c5_scale)
-        prep = {"genome_bp": len(gw.genome), "proteins": len(gw.prot_len), "regions": gw.n_regions,
-                "regions_per_protein": gw.n_regions / len(gw.prot_len),
-                "generate_and_seed_chain_s": time.perf_counter() - t_gen}
-        po, pl, no, nl, st_ = gw.region_arrays()
-        src = mp.RegionBatch(gw.prot_buf, po, pl, gw.genome, no, nl, st_)
-        n_pairs, cells = gw.n_regions, gw.cells()
-        # the library sends a genome range and a protein range once when the
-        # regions (proteins) share them and the ranges are shorter than the
-        # records' total length
-        ascii_bytes = int(pl.sum() + nl.sum())
-        nz, pz = nl > 0, pl > 0
-        if nz.any() and pz.any():
-            nspan = int((no[nz] + nl[nz]).max() - no[nz].min())
-            pspan = int((po[pz] + pl[pz]).max() - po[pz].min())
-            if nspan <= int(nl.sum()) and pspan <= int(pl.sum()) and nspan + pspan < ascii_bytes:
-                ascii_bytes = nspan + pspan
-        get_pair = gw.pair
-        workload = WORKLOAD_C5 if args.c5_scale == 1.0 else WORKLOAD_C5 + f" (scaled by {args.c5_scale})"
+        src, n_pairs, cells, ascii_bytes, get_pair, workload, prep = load_c5(mp, rank, args.c5_scale)
+        pairs = None
     else:
         if args.workload == "c3":
             pairs = synth.config3(seed=rank_seed(3, rank))[: args.pairs if args.pairs != 4096 else None]
@@ -365,86 +505,29 @@ def main():
         else:
             pairs = synth.config2(seed=rank_seed(2, rank))[: args.pairs]
             workload = WORKLOAD
-        src = mp.PairBatch(pairs)             # the sequences in host memory as the C ABI takes them
-        n_pairs, cells = len(pairs), float(sum(p.cells for p in pairs))
-        ascii_bytes = sum(len(p.prot) + len(p.nt) for p in pairs)
-        get_pair = pairs.__getitem__
+        src, n_pairs, cells, ascii_bytes, get_pair = load_pairs(mp, pairs)
+        prep = {}
     mode = {"local": 0, "global": 1, "extension": 2}[args.mode]
-    ctx = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode), local)
-    mp.mp_dp_set_timing(ctx, True)
-    batch = mp.mp_dp_batch_upload(ctx, src)
-    tuning = None
-    if args.tuning:
-        # a fixed launch configuration: int16 build, CTAs/SM (int16, int32), wide pairs direct
-        v, c16, c32, wd, ov, io = (int(x) for x in (args.tuning + ",1,1").split(",")[:6])
-        fixed = {"dp16_variant": v, "dp16_ctas_per_sm": c16, "dp32_ctas_per_sm": c32, "wide_direct": wd,
-                 "overlap_waves": ov, "item_order": io}
-        mp.mp_dp_set_tuning(ctx, fixed)
-        tuning = {"fixed": fixed}
-    elif not args.no_autotune:
-        # the launch configuration is chosen by the library's autotuner on this
-        # batch (outside the timed region); the timed runs use the choice
-        best, tried = mp.mp_dp_autotune(ctx, batch)
-        tuning = {"chosen": best, "candidates": tried}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     flush.zero_()                            # first touch of the flush buffer stays outside the timed region
     torch.cuda.synchronize()
-
-    def barrier():
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    clk = Clocks(local).__enter__()          # sampler starts before the warm-up, outside the timed region
-    for _ in range(args.warmup):
-        mp.mp_dp_batch_run(ctx, batch)
-        mp.mp_dp_batch_sync(ctx)
-    dp_ms, rr_ms, tb_ms, tot_ms = [], [], [], []
-    clk.samples.clear()
-    barrier()
-    if True:
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            mp.mp_dp_batch_run(ctx, batch)
-            mp.mp_dp_batch_sync(ctx)
-            st = mp.mp_dp_get_stats(ctx)
-            dp_ms.append(st["dp_ms"]); rr_ms.append(st["rerun_ms"]); tb_ms.append(st["tb_ms"])
-            tot_ms.append(st["total_ms"])
-        barrier()
-        elapsed = time.perf_counter() - t0
-    clk.__exit__()
-    stats = mp.mp_dp_get_stats(ctx)
-    res = mp.mp_dp_batch_download(ctx, batch, raw=True)
-    n_rerun = int(((res["status"] & 1) != 0).sum())
-    mp.mp_dp_batch_free(ctx, batch)
-    all_cells, t_max = job_totals(cells, elapsed, dist, "cuda")
-    all_pairs, _ = job_totals(n_pairs, elapsed, dist, "cuda")
-    ms_per_step = t_max * 1000 / args.steps
-    gcups = all_cells / (t_max / args.steps) / 1e9
+    fixed = None
+    if args.tuning:
+        # a fixed launch configuration: int16 build, CTAs/SM (int16, int32), wide pairs direct, then
+        # optionally the wave policy, the item order and the strip width (defaults 1, 1, 0)
+        vals = [int(x) for x in args.tuning.split(",")]
+        vals += [1, 1, 0][max(0, len(vals) - 4):]
+        fixed = dict(zip(TUNING_KEYS, vals))
+    m = measure(mp, torch, src, n_pairs, cells, ascii_bytes, args.steps, args.warmup, local, dist, flush,
+                mode=mode, fixed=fixed, autotune=not args.no_autotune, e2e_steps=0 if args.skip_e2e else
+                max(2, min(args.steps, 3)))
+    all_pairs, _ = job_totals(n_pairs, m["elapsed"], dist, "cuda")
+    t_max = m["t_max"]
+    gcups = m["all_cells"] / (t_max / args.steps) / 1e9
     pairs_per_s = all_pairs / (t_max / args.steps)
-
-    # ---- end to end through the C ABI with host buffers
-    e2e_steps = 0 if args.skip_e2e else max(2, min(args.steps, 3))
-    mp.mp_dp_set_timing(ctx, False)
-    out = res
     host_batch = src
-    if e2e_steps:
-        mp.mp_dp_align_batch(ctx, host_batch, raw=True)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        out = mp.mp_dp_align_batch(ctx, host_batch, raw=True)
-    barrier()
-    e2e_t = max(time.perf_counter() - t0, 1e-9)
-    _, e2e_t = job_totals(cells, e2e_t, dist, "cuda")
-    h2d = ascii_bytes + n_pairs * (72 + 4)          # sequences + pair descriptors + work order
-    d2h = n_pairs * 32 + 4 + int(out["n_cigar"].sum()) * 4
-    e2e = {"value": all_cells / (e2e_t / e2e_steps) / 1e9 if e2e_steps else None, "unit": "GCUPS",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "pairs_per_s": all_pairs / (e2e_t / e2e_steps) if e2e_steps else None}
-    mp.mp_dp_destroy(ctx)
+    e2e = m["e2e"]
+    e2e["pairs_per_s"] = all_pairs / m["e2e_s"] if m["e2e_s"] else None
 
     if rank != 0:
         if dist:
@@ -452,51 +535,27 @@ def main():
         return
 
     peaks = _peaks()
-    clocks = clk.summary()
-    nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    f_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_ops = nsm * 128 * 2 * f_mhz * 1e6 / 1e12          # int16 lane-ops/s (Tops)
-    dp_avg_ms = statistics.mean(dp_ms) if dp_ms else None
-    time_basis = "DP kernel launch (CUDA events on its stream)"
-    if stats["n_waves"] > 1:
-        # with overlapped waves the per-wave DP intervals overlap: the whole
-        # pipeline's time bounds the DP time from above
-        dp_avg_ms = statistics.mean(tot_ms) if tot_ms else None
-        time_basis = "whole pipeline (several waves)"
-    achieved = cells * OPS_PER_CELL / (dp_avg_ms / 1000) / 1e12 if dp_avg_ms else None
-    traffic = _profiled_traffic(cells)
-    ips = _profile_value("instructions_per_step")
+    clocks = m["clocks"]
     line = {
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": t_max * 1000 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
         "config": {"workload": workload + ("" if mode == 0 else f" ({args.mode} mode)"), "pairs": n_pairs,
-                   "cells": cells, "waves": stats["n_waves"], **prep,
+                   "cells": cells, "waves": m["waves"], **prep,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps; each step also writes "
-                         f"{stats['code_bytes'] / 1e9:.1f} GB of traceback codes"},
+                         f"{m['code_bytes'] / 1e9:.1f} GB of traceback codes"},
         "pairs_per_s": pairs_per_s,
-        "kernel_ms": {"dp_int16": dp_avg_ms, "rerun_int32": statistics.mean(rr_ms),
-                      "traceback_compact": statistics.mean(tb_ms), "pipeline": statistics.mean(tot_ms)},
-        "n_rerun": n_rerun,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s (int16 lane-ops)",
-                     "frac": (achieved / peak_ops) if achieved else None, "traffic": traffic,
-                     "ops_per_cell": OPS_PER_CELL, "time_basis": time_basis,
-                     "peak_basis": f"{nsm} SMs x 128 lanes x 2 int16 halves x {f_mhz:.0f} MHz (median SM clock "
-                                   "under load)",
-                     "hbm_write_gbs": stats["code_bytes"] / (dp_avg_ms / 1000) / 1e9 if dp_avg_ms else None,
-                     "issue_frac": (cells / 64 * ips / (dp_avg_ms / 1000) / (nsm * 4 * f_mhz * 1e6))
-                     if (dp_avg_ms and ips) else None,
-                     "issue_basis": "warp-instructions per 64-cell step from the committed ncu summary x steps/s "
-                                    "over N_SM x 4 issue slots x f_SM",
-                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "kernel_ms": m["kernel_ms"],
+        "n_rerun": m["n_rerun"],
+        "roofline": roofline(m, cells, torch, local, peaks),
         "clocks": clocks,
-        "gpu_launches": stats["n_launches"] * args.steps,
-        "tuning": tuning,
+        "gpu_launches": m["launches"] * args.steps,
+        "tuning": m["tuning"],
         "e2e": e2e,
     }
-    if not args.no_extras:
-        # plain form: one pair per kernel launch, on a sample
+    if not args.no_extras and world == 1:
+        # plain form: one pair per kernel launch, on a sample, timed three times
         ctxp = mp.mp_dp_init(mp.mp_dp_default_params(max_pairs_per_launch=1), local)
         rng = np.random.default_rng(0)
         sample = [get_pair(int(k)) for k in rng.choice(n_pairs, 48, replace=False)]
@@ -505,13 +564,18 @@ def main():
         mp.mp_dp_batch_run(ctxp, bp)
         mp.mp_dp_batch_sync(ctxp)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mp.mp_dp_batch_run(ctxp, bp)
-        mp.mp_dp_batch_sync(ctxp)
-        tp = time.perf_counter() - t0
+        pc = sum(p.cells for p in sample)
+        plain_g = []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mp.mp_dp_batch_run(ctxp, bp)
+            mp.mp_dp_batch_sync(ctxp)
+            plain_g.append(pc / (time.perf_counter() - t0) / 1e9)
         mp.mp_dp_batch_free(ctxp, bp)
         mp.mp_dp_destroy(ctxp)
-        pc = sum(p.cells for p in sample)
+        plain = statistics.median(plain_g)
         # pseudogene-aware rescoring: the end-to-end call with params.exon_rescore
         ctxe = mp.mp_dp_init(mp.mp_dp_default_params(exon_rescore=1), local)
         mp.mp_dp_align_batch(ctxe, host_batch, raw=True)
@@ -523,7 +587,7 @@ def main():
         mp.mp_dp_destroy(ctxe)
         line["exon_rescore"] = {"value": cells / te / 1e9, "unit": "GCUPS (alignment cells; end to end)",
                                 "ms_per_call": te * 1000,
-                                "extra_ms_over_e2e": te * 1000 - (e2e_t / e2e_steps * 1000 if e2e_steps else 0.0)}
+                                "extra_ms_over_e2e": te * 1000 - (m["e2e_s"] * 1000 if m["e2e_s"] else 0.0)}
         # anchored modes on the same batch (gap closing between anchors, and
         # extension from an anchor): device-resident inputs, pipeline time by
         # CUDA events, the L2 flushed before each timed run
@@ -554,10 +618,21 @@ def main():
                               "int32_ms": statistics.mean(ars), "traceback_ms": statistics.mean(ats),
                               "pairs_with_error_status": int(((ra["status"] & 0xF0) != 0).sum())}
         line["anchored_modes"] = anchored
-        line["plain"] = {"value": pc / tp / 1e9, "unit": "GCUPS", "pairs_per_s": len(sample) / tp,
-                         "sample": f"{len(sample)} random pairs of the workload, one kernel launch per pair",
-                         "batched_over_plain": gcups / (pc / tp / 1e9)}
-        # serving
+        line["plain"] = {"value": plain, "unit": "GCUPS", "pairs_per_s": plain * 1e9 / (pc / len(sample)),
+                         "runs": plain_g, "spread": [min(plain_g), max(plain_g)],
+                         "sample": f"{len(sample)} random pairs of the workload ({pc / 1e9:.3f} G cells), one "
+                                   "kernel launch per pair; median of 3 timed runs, L2 flushed before each",
+                         "batched_over_plain": gcups / plain}
+        # the 20,000-pair uneven-size workload and the genome-scale workload,
+        # each measured like the main line with its own autotuned configuration
+        if args.workload == "c2" and args.legs:
+            if "c3" in args.legs:
+                line["c3"] = leg(mp, torch, "c3",
+                                 lambda: load_pairs(mp, synth.config3(seed=rank_seed(3, rank))) + (WORKLOAD_C3, {}),
+                                 local, flush, peaks)
+            if "c5" in args.legs:
+                line["c5"] = leg(mp, torch, "c5", lambda: load_c5(mp, rank, args.c5_scale), local, flush, peaks)
+        # serving: open-loop Poisson arrivals at each rate
         try:
             sp = synth.serving_pairs()
             line["serving"] = [serve_once(mp, sp, float(r), args.serve_seconds, local)
