@@ -67,7 +67,8 @@ class Params(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("e", ctypes.c_int32), ("f", ctypes.c_int32),
                 ("r", ctypes.c_int32), ("stop", ctypes.c_int32),
                 ("mat", (ctypes.c_int32 * 22) * 22),
-                ("splice_model", ctypes.c_int32), ("splice_p", ctypes.c_int32), ("mode", ctypes.c_int32)]
+                ("splice_model", ctypes.c_int32), ("splice_p", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("prof", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Result(ctypes.Structure):
@@ -81,12 +82,25 @@ class Result(ctypes.Structure):
 DEFAULTS = dict(q=11, e=1, f=23, r=29, stop=23)
 
 
+PROF_W = 23     # ints per position of a profile: 21 substitution scores, gap open, gap extension
+
+
 def make_params(q=None, e=None, f=None, r=None, stop=None, mat=None, splice_model=0, splice_p=30,
-                mode=0) -> Params:
+                mode=0, prof=None) -> Params:
     """Scoring parameters; splice_model 0 is the final model, 1 the simple
     GT-AG model with cost splice_p; mode 0 local, 1 global (cell (0, 0) to
-    (|T|, |P|)), 2 extension (from (0, 0), ending anywhere)."""
+    (|T|, |P|)), 2 extension (from (0, 0), ending anywhere).  prof: None, or
+    the position-specific costs of a profile query, an int array of shape
+    (|P| + 1, 23): row j (j >= 1) holds the score of each translated code
+    (ORC_AA order, 20 = stop codon) against residue position j, then the gap
+    open and extension costs of column j (row 0: codons before the first
+    residue)."""
     p = Params()
+    if prof is not None:
+        arr = np.ascontiguousarray(prof, dtype=np.int32)
+        assert arr.ndim == 2 and arr.shape[1] == PROF_W
+        p._prof_keep = arr                      # keeps the buffer alive with the struct
+        p.prof = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     p.splice_model, p.splice_p, p.mode = splice_model, splice_p, mode
     d = dict(DEFAULTS)
     for k, v in (("q", q), ("e", e), ("f", f), ("r", r), ("stop", stop)):
@@ -242,6 +256,23 @@ def exon_score(prot: str, nt: str, strand: int = 1, params: Params | None = None
     s2 = align(prot, exon_sequence(nt, strand, r), 1, p)["score"]
     single = not any(op in "NUV" for op, _ in r["cigar"])
     return s2 - (p.r if single else 0)
+
+
+def profile_of(prot: str, params: Params | None = None) -> np.ndarray:
+    """The profile that reproduces the position-independent scoring of
+    `params` for protein `prot`: row j holds mat[c][P[j]] (and -stop for the
+    stop codon) and the global q and e."""
+    p = params if params is not None else make_params()
+    m = len(prot)
+    out = np.zeros((m + 1, PROF_W), dtype=np.int32)
+    for j in range(1, m + 1):
+        pc = lib().orc_aa_code(ord(prot[j - 1]))
+        for c in range(20):
+            out[j, c] = p.mat[c][pc]
+        out[j, 20] = -p.stop
+    out[:, 21] = p.q
+    out[:, 22] = p.e
+    return out
 
 
 def encode_cigar(ops) -> list:

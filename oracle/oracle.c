@@ -22,6 +22,10 @@
  *     the restart to 0 wins a tie at 0.
  *   - Split codons of phase-1/2 introns are not scored (Methods, after
  *     Eq. 7).
+ *   - Profile queries (Discussion: position-specific substitution and gap
+ *     costs): with orc_params.prof set, s(i,j) is the profile's score of the
+ *     codon's translation at residue position j, and the I and D states of
+ *     column j use that column's gap open and extension costs.
  *
  * Everything is int32 with full (|T|+1) x (|P|+1) matrices for all six
  * states; the traceback re-evaluates the recurrence at each cell, so no
@@ -50,7 +54,18 @@ typedef struct {
     int32_t splice_p;           /* simple model: cost p of a donor without GT / acceptor without AG */
     int32_t mode;               /* 0 local; 1 global (from cell (0,0) to (|T|,|P|)); 2 extension
                                    (from (0,0), ending anywhere) */
+    const int32_t *prof;        /* NULL, or the position-specific costs of a profile query
+                                   (Discussion: position-specific substitution and gap costs):
+                                   for residue position j = 1..|P|, prof[ORC_PW*j + c] is the score
+                                   of a codon translating to c (ORC_AA order, 20 = stop codon)
+                                   against position j, in place of mat[c][P[j]] and -stop; for
+                                   j = 0..|P|, prof[ORC_PW*j + 21] and prof[ORC_PW*j + 22] are the
+                                   gap open and extension costs of column j: an I step consuming
+                                   residue j, a D step adding a codon after residue j (j = 0:
+                                   before the first residue) */
 } orc_params;
+
+#define ORC_PW 23               /* ints per position of a profile */
 
 typedef struct {
     int32_t score;
@@ -188,9 +203,15 @@ static int32_t subst(const dp_t *dp, int i, int j)
 {
     if (i < 3) return ORC_NEG_INF;
     int aa = orc_translate(dp->T[i - 2], dp->T[i - 1], dp->T[i]);
+    if (dp->p->prof) return dp->p->prof[ORC_PW * j + aa];
     if (aa == ORC_AA_STOP) return -dp->p->stop;
     return dp->p->mat[aa][dp->P[j]];
 }
+
+/* Gap open and extension costs of column j (Eq. 7's q and e, or the
+ * profile's costs of position j). */
+static int32_t gap_q(const orc_params *p, int j) { return p->prof ? p->prof[ORC_PW * j + 21] : p->q; }
+static int32_t gap_e(const orc_params *p, int j) { return p->prof ? p->prof[ORC_PW * j + 22] : p->e; }
 
 static int32_t dfun(const dp_t *dp, int x) { return splice_d(dp->p, dp->T, dp->n, x); }
 static int32_t afun(const dp_t *dp, int x) { return splice_a(dp->p, dp->T, dp->n, x); }
@@ -228,8 +249,9 @@ static void fill_anchored(dp_t *dp)
                 dp->I[c] = dp->D[c] = dp->A[c] = dp->B[c] = dp->C[c] = ORC_NEG_INF;
                 continue;
             }
-            dp->I[c] = j >= 1 ? max2(getH(dp, i, j - 1) - p->q, getS(dp, dp->I, i, j - 1)) - p->e : ORC_NEG_INF;
-            dp->D[c] = max2(getH(dp, i - 3, j) - p->q, getS(dp, dp->D, i - 3, j)) - p->e;
+            dp->I[c] = j >= 1 ? max2(getH(dp, i, j - 1) - gap_q(p, j), getS(dp, dp->I, i, j - 1)) - gap_e(p, j)
+                              : ORC_NEG_INF;
+            dp->D[c] = max2(getH(dp, i - 3, j) - gap_q(p, j), getS(dp, dp->D, i - 3, j)) - gap_e(p, j);
             dp->A[c] = max2(getH(dp, i - 1, j) - p->r - dfun(dp, i - 1), getS(dp, dp->A, i - 1, j));
             dp->B[c] = max2(getH(dp, i - 1, j - 1) - p->r - dfun(dp, i), getS(dp, dp->B, i - 1, j));
             dp->C[c] = max2(getH(dp, i - 1, j - 1) - p->r - dfun(dp, i + 1), getS(dp, dp->C, i - 1, j));
@@ -262,8 +284,8 @@ static void fill(dp_t *dp)
         dp->A[IDX(dp, i, 0)] = dp->B[IDX(dp, i, 0)] = dp->C[IDX(dp, i, 0)] = ORC_NEG_INF;
         for (int j = 1; j <= m; ++j) {
             size_t c = IDX(dp, i, j);
-            dp->I[c] = max2(getH(dp, i, j - 1) - p->q, getS(dp, dp->I, i, j - 1)) - p->e;
-            dp->D[c] = max2(getH(dp, i - 3, j) - p->q, getS(dp, dp->D, i - 3, j)) - p->e;
+            dp->I[c] = max2(getH(dp, i, j - 1) - gap_q(p, j), getS(dp, dp->I, i, j - 1)) - gap_e(p, j);
+            dp->D[c] = max2(getH(dp, i - 3, j) - gap_q(p, j), getS(dp, dp->D, i - 3, j)) - gap_e(p, j);
             dp->A[c] = max2(getH(dp, i - 1, j) - p->r - dfun(dp, i - 1), getS(dp, dp->A, i - 1, j));
             dp->B[c] = max2(getH(dp, i - 1, j - 1) - p->r - dfun(dp, i), getS(dp, dp->B, i - 1, j));
             dp->C[c] = max2(getH(dp, i - 1, j - 1) - p->r - dfun(dp, i + 1), getS(dp, dp->C, i - 1, j));
@@ -318,8 +340,8 @@ static int traceback(const dp_t *dp, int bi, int bj, oplist *L, int *si, int *sj
             int k = 0;
             for (;;) {
                 ++k;
-                int32_t open = getH(dp, i, j - 1) - p->q - p->e;
-                int32_t ext = getS(dp, dp->I, i, j - 1) - p->e;
+                int32_t open = getH(dp, i, j - 1) - gap_q(p, j) - gap_e(p, j);
+                int32_t ext = getS(dp, dp->I, i, j - 1) - gap_e(p, j);
                 j -= 1;
                 if (open >= ext) break;
             }
@@ -328,8 +350,8 @@ static int traceback(const dp_t *dp, int bi, int bj, oplist *L, int *si, int *sj
             int k = 0;
             for (;;) {
                 ++k;
-                int32_t open = getH(dp, i - 3, j) - p->q - p->e;
-                int32_t ext = getS(dp, dp->D, i - 3, j) - p->e;
+                int32_t open = getH(dp, i - 3, j) - gap_q(p, j) - gap_e(p, j);
+                int32_t ext = getS(dp, dp->D, i - 3, j) - gap_e(p, j);
                 i -= 3;
                 if (open >= ext) break;
             }
@@ -531,14 +553,15 @@ int orc_score_end(const orc_params *p, const char *prot, int32_t plen, const cha
                 Ij = ORC_NEG_INF;
                 continue;
             }
-            const int32_t I = j >= 1 ? max2(H[j - 1] - p->q, Ij) - p->e : ORC_NEG_INF;
-            const int32_t Dv = max2((H3 ? H3[j] : ORC_NEG_INF) - p->q, D3 ? D3[j] : ORC_NEG_INF) - p->e;
+            const int32_t qj = gap_q(p, j), ej = gap_e(p, j);
+            const int32_t I = j >= 1 ? max2(H[j - 1] - qj, Ij) - ej : ORC_NEG_INF;
+            const int32_t Dv = max2((H3 ? H3[j] : ORC_NEG_INF) - qj, D3 ? D3[j] : ORC_NEG_INF) - ej;
             const int32_t Av = max2(h1j - rd_im1, A1 ? A1[j] : ORC_NEG_INF);
             const int32_t Bv = max2(h1jm - rd_i, B1 ? B1[j] : ORC_NEG_INF);
             const int32_t Cv = max2(h1jm - rd_ip1, C1 ? C1[j] : ORC_NEG_INF);
             int32_t h = ORC_NEG_INF;
             if (i >= 3 && j >= 1)
-                h = H3[j - 1] + (aa == ORC_AA_STOP ? -p->stop : p->mat[aa][P[j]]);
+                h = H3[j - 1] + (p->prof ? p->prof[ORC_PW * j + aa] : aa == ORC_AA_STOP ? -p->stop : p->mat[aa][P[j]]);
             h = max2(h, I);
             h = max2(h, Dv);
             h = max2(h, h1jm - p->f);
@@ -597,12 +620,18 @@ int32_t orc_rescore(const orc_params *p, const char *prot, int32_t plen, const c
                 if (i + 3 > tlen || j + 1 > plen) { bad = 1; break; }
                 int aa = orc_translate(T[i + 1], T[i + 2], T[i + 3]);
                 int pc = orc_aa_code(prot[j]);
-                sc += (aa == ORC_AA_STOP) ? -p->stop : p->mat[aa][pc];
+                sc += p->prof ? p->prof[ORC_PW * (j + 1) + aa] : (aa == ORC_AA_STOP) ? -p->stop : p->mat[aa][pc];
                 i += 3; j += 1;
             }
             break;
-        case OP_I: sc -= p->q + (int64_t)p->e * len; j += len; break;
-        case OP_D: sc -= p->q + (int64_t)p->e * len; i += 3 * len; break;
+        case OP_I:
+            /* residues j+1 .. j+len: open at the first, extension at each */
+            if (j + len > plen) { bad = 1; break; }
+            sc -= gap_q(p, j + 1);
+            for (int c = 1; c <= len; ++c) sc -= gap_e(p, j + c);
+            j += len;
+            break;
+        case OP_D: sc -= gap_q(p, j) + (int64_t)gap_e(p, j) * len; i += 3 * len; break;
         case OP_F: sc -= p->f; i += len; j += 1; break;
         case OP_G: sc -= p->f; i += len; break;
         case OP_N: sc -= p->r + splice_d(p, T, tlen, i) + splice_a(p, T, tlen, i + len); i += len; break;

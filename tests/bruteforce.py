@@ -45,10 +45,17 @@ def _simple_a(nt: str, x: int, p: int) -> int:
 
 
 class Problem:
-    def __init__(self, prot: str, nt: str, q=11, e=1, f=23, r=29, stop=23, mat=None, splice_p=None):
+    def __init__(self, prot: str, nt: str, q=11, e=1, f=23, r=29, stop=23, mat=None, splice_p=None, prof=None):
         """splice_p None: the final splice model (the oracle's tables, pinned
         on their own); an integer: the simple GT-AG model with that cost,
-        written out here from its definition."""
+        written out here from its definition.  prof: position-specific costs
+        of a profile query, rows j = 0..|P| of [21 substitution scores (the
+        translated code's index, 20 = stop), gap open, gap extension]: a
+        codon against position j scores prof[j][code]; an I run over
+        residues j+1..j+k costs the open of j+1 and the extension of each;
+        a D run of k codons after residue j costs the open and k extensions
+        of position j."""
+        self.prof = prof
         self.P = [oracle.AA.index(c) if c in oracle.AA else 21 for c in prot]
         self.T = ["ACGT".index(c) for c in nt]
         self.nt = nt
@@ -72,9 +79,23 @@ class Problem:
     def s(self, i, j):
         """Codon T[i+1..i+3] against residue P[j+1] (0-based T, P lists)."""
         aa = oracle.AA.index(oracle.translate_codon(self.T[i], self.T[i + 1], self.T[i + 2]))
+        if self.prof is not None:
+            return int(self.prof[j + 1][aa])
         if aa == 20:
             return -self.stop
         return int(self.mat[aa][self.P[j]])
+
+    def gap_i(self, j, k):
+        """Cost of an I run over residues j+1 .. j+k."""
+        if self.prof is None:
+            return self.q + self.e * k
+        return int(self.prof[j + 1][21]) + sum(int(self.prof[t][22]) for t in range(j + 1, j + k + 1))
+
+    def gap_d(self, j, k):
+        """Cost of a D run of k codons after residue j."""
+        if self.prof is None:
+            return self.q + self.e * k
+        return int(self.prof[j][21]) + int(self.prof[j][22]) * k
 
     def ops_from(self, i, j):
         """Every operation that can follow cell (i, j): (name, len, di, dj, cost)."""
@@ -83,9 +104,9 @@ class Problem:
         if i + 3 <= n and j + 1 <= m:
             yield ("M", 1, 3, 1, self.s(i, j))
         for k in range(1, m - j + 1):
-            yield ("I", k, 0, k, -(q + e * k))
+            yield ("I", k, 0, k, -self.gap_i(j, k))
         for k in range(1, (n - i) // 3 + 1):
-            yield ("D", k, 3 * k, 0, -(q + e * k))
+            yield ("D", k, 3 * k, 0, -self.gap_d(j, k))
         for L in (1, 2):
             if i + L <= n and j + 1 <= m:
                 yield ("F%d" % L, L, L, 1, -f)

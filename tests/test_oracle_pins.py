@@ -727,3 +727,99 @@ def test_anchored_tie_rule_against_path_order(orc):
             assert res["cigar"] == bf.to_cigar(ops), (prot, nt, params, mode, ops)
             checked[mode] += 1
     assert checked[1] > 40 and checked[2] > 30, checked
+
+
+# ------------------------------------------ profile queries (Discussion)
+def _random_profile(rng, m, lo=-6, hi=6, qmax=4, emax=3):
+    """Position-specific costs: random scores per position and translated
+    code (stop included), random gap open and extension per column."""
+    prof = np.zeros((m + 1, 23), dtype=np.int32)
+    for j in range(m + 1):
+        prof[j, :21] = [rng.randint(lo, hi) for _ in range(21)]
+        prof[j, 21] = rng.randint(0, qmax)
+        prof[j, 22] = rng.randint(1, emax)
+    prof[0, :21] = 0
+    return prof
+
+
+def test_profile_reduces_to_the_position_independent_model(orc):
+    """A profile holding mat[c][P[j]], -stop and the global q, e at every
+    position gives exactly the results of the position-independent scoring,
+    in every mode and on both strands (the profile path's plumbing)."""
+    rng = np.random.default_rng(95)
+    for k in range(16):
+        m = int(rng.integers(1, 60))
+        prot = synth.random_protein(rng, m)
+        introns = [int(x) for x in rng.integers(40, 200, size=int(rng.integers(0, 3)))]
+        nt, _ = synth.gen.plant_gene(rng, prot, 0.25, int(rng.integers(0, 2)), introns,
+                                     int(rng.integers(0, 60)), int(rng.integers(0, 60)), 0.4)
+        for mode in (0, 1, 2):
+            ps = dict(q=int(rng.integers(0, 12)), e=int(rng.integers(1, 4)), f=17, r=29, stop=11)
+            base = orc.make_params(mode=mode, **ps)
+            prof = orc.profile_of(prot, base)
+            pp = orc.make_params(mode=mode, prof=prof, **ps)
+            for strand, t in ((1, nt), (-1, orc.revcomp(nt))):
+                a = orc.align(prot, t, strand, base)
+                b = orc.align(prot, t, strand, pp)
+                assert {x: a[x] for x in ("score", "prot_st", "prot_en", "nt_st", "nt_en", "cigar")} == \
+                       {x: b[x] for x in ("score", "prot_st", "prot_en", "nt_st", "nt_en", "cigar")}, (k, mode)
+                se = orc.score_end(prot, t, strand, pp)
+                assert (se["score"], se["prot_en"]) == (a["score"], a["prot_en"])
+
+
+def test_profile_against_segment_recursion(orc):
+    """With arbitrary position-specific scores and gap costs the oracle's
+    score, in every mode, and the four-row fill's end cell equal the best
+    path of the operation-level recursion that charges each operation the
+    profile's costs."""
+    rng = random.Random(96)
+    modes = {0: "local", 1: "global", 2: "extend"}
+    for k in range(50):
+        n, m = rng.randint(0, 18), rng.randint(0, 5)
+        prot = _rand_prot(rng, m)
+        nt = "".join(rng.choice("ACGT") for _ in range(n))
+        if rng.random() < 0.5 and m:
+            nt = (_cds(rng, prot) + nt)[:max(n, 3 * m)]
+        prof = _random_profile(rng, m)
+        ps = dict(q=3, e=1, f=rng.randint(2, 6), stop=3, r=rng.randint(7, 12))
+        pb = bf.Problem(prot, nt, prof=prof, **ps)
+        for mode in (0, 1, 2):
+            pp = orc.make_params(mode=mode, prof=prof, **ps)
+            want = _best_cell(bf.best_table(pb, modes[mode]), modes[mode], len(nt), len(prot))
+            got = orc.align(prot, nt, 1, pp)
+            assert got["score"] == want[0], (k, mode, prot, nt)
+            se = orc.score_end(prot, nt, 1, pp)
+            assert (se["score"], _end_of(se, 1, len(nt)), se["prot_en"]) == want, (k, mode)
+            if got["cigar"]:
+                st = got["nt_st"]
+                sc, pe, te = orc.rescore(prot, nt, 1, got["prot_st"], st, got["cigar_raw"], pp)
+                assert (sc, pe, te) == (got["score"], got["prot_en"], got["nt_en"]), (k, mode)
+
+
+def test_profile_tie_rule_against_path_order(orc):
+    """Local mode with a profile: the oracle's path is the optimum the
+    stated tie rules select among all enumerated paths (tie-rich scores in
+    {-1, 0, 1, 2})."""
+    rng = random.Random(97)
+    checked = 0
+    for _ in range(70):
+        n, m = rng.randint(3, 7), rng.randint(1, 2)
+        prot = _rand_prot(rng, m)
+        nt = "".join(rng.choice("ACGT") for _ in range(n))
+        if rng.random() < 0.6:
+            kk = rng.randint(0, n - 3)
+            nt = (nt[:kk] + _cds(rng, prot) + nt[kk:])[:n]
+        prof = _random_profile(rng, m, lo=-1, hi=2, qmax=2, emax=1)
+        ps = dict(q=1, e=1, f=rng.randint(1, 2), stop=1, r=3)
+        paths = bf.all_paths(bf.Problem(prot, nt, prof=prof, **ps))
+        choice = bf.tie_rule_choice(paths)
+        res = orc.align(prot, nt, 1, orc.make_params(prof=prof, **ps))
+        if choice is None:
+            assert res["score"] == 0 and res["cigar"] == []
+            continue
+        si, sj, ops, ei, ej, sc = choice
+        assert res["score"] == sc
+        assert (res["prot_st"], res["prot_en"], res["nt_st"], res["nt_en"]) == (sj, ej, si, ei)
+        assert res["cigar"] == bf.to_cigar(ops), (prot, nt, ops)
+        checked += 1
+    assert checked > 30
