@@ -126,6 +126,23 @@ typedef struct {
     int32_t reserved[1];
 } mp_dp_params;
 
+/* Position-specific costs of one residue position of a profile query (Li
+ * 2022, Discussion: a profile, e.g. HMMER's, as the query, aligned with
+ * position-specific substitution and gap costs).  With a profile, Eq. 7's
+ * s(i, j) is subst[c] of position j, c the amino acid the codon ending at
+ * i translates to (ARNDCQEGHILKMFPSTWYV order; 20 = stop codon), and the I
+ * and D states of column j take that column's gap costs:
+ *   I[i][j] = max(H[i][j-1] - gap_open_j, I[i][j-1]) - gap_ext_j
+ *   D[i][j] = max(H[i-3][j] - gap_open_j, D[i-3][j]) - gap_ext_j
+ * (an I step consumes residue j; a D step adds a codon after residue j).
+ * Frameshift and intron costs stay f, r and the splice model. */
+typedef struct {
+    int16_t subst[21];         /* -500 .. 500; r must exceed -min(subst) over the profile */
+    int16_t gap_open;          /* 0 .. 999 */
+    int16_t gap_ext;           /* 1 .. 1000 - gap_open */
+    int16_t reserved;
+} mp_profile_pos;
+
 /* One alignment request.  prot: ASCII amino acids; nt: ASCII A/C/G/T
  * (either case).  strand -1 aligns the protein to the reverse complement of
  * nt. */
@@ -136,6 +153,12 @@ typedef struct {
     uint32_t nt_len;
     int8_t strand;
     uint32_t flags;            /* MP_PAIR_* */
+    const mp_profile_pos *profile; /* NULL: score with params (mat, q, e, stop); else prot_len + 1
+                                  positions: entry j (1..prot_len) for residue j, entry 0 the
+                                  gap costs of the column before the first residue (its subst is
+                                  not used).  The residue letters still name the positions in the
+                                  result.  Borrowed for the duration of the call; a profile pair
+                                  with a value out of range makes the call return MP_EINVAL */
 } mp_pair;
 
 /* One result.  cigar points into library-owned memory: for
@@ -188,10 +211,14 @@ int mp_dp_batch_download(mp_dp_ctx *ctx, mp_dp_batch *batch, mp_result *out);
 void mp_dp_batch_free(mp_dp_ctx *ctx, mp_dp_batch *batch);
 
 /* Serving: submit one pair; never blocks.  *ticket identifies the result.
- * MP_EAGAIN if the request ring is full.  The first submit starts the
- * serving thread, which admits requests while the traceback bytes in
- * flight stay within the budget and launches mixed-size batches as
- * requests arrive (continuous batching). */
+ * MP_EAGAIN if the request ring is full; MP_EBUDGET if the pair's traceback
+ * alone exceeds tb_budget_bytes.  The first submit starts the serving
+ * thread, which keeps one traceback arena of tb_budget_bytes on the device
+ * and runs up to three micro-batches at once, each in its own range of
+ * that arena: requests are taken in arrival order into a micro-batch of up
+ * to a third of the budget (a larger request alone, up to the whole budget,
+ * once that much of the arena is free), and batches are launched as
+ * requests arrive and ranges free up (continuous batching). */
 int mp_dp_submit(mp_dp_ctx *ctx, const mp_pair *pair, uint64_t *ticket);
 
 /* Wait up to timeout_us (0: do not wait; negative: forever) for ticket's
@@ -315,7 +342,13 @@ typedef struct {
                                   taken about two chunks after strip s; 0: pairs' strips back to
                                   back (a strip's warp first waits for its predecessor) */
     float ms;                  /* set by mp_dp_autotune: device time of one run of the batch */
-    int32_t reserved[1];
+    int32_t strip_width;       /* 0: every pair in strips of 64 residues (two per lane of a warp);
+                                  1: int16 pairs in strips of 128 residues (four per lane: one
+                                  shuffle, record load and profile load serve four cells) where that
+                                  adds little padding (an even number of 64-residue strips, or 9 or
+                                  more) and where the pair's longer critical path in that form stays
+                                  within the batch's longest one in 64-residue strips; run by the
+                                  2-CTA build whatever dp16_variant says */
 } mp_dp_tuning;
 
 /* Time the candidate configurations on an uploaded batch (warm-up runs;

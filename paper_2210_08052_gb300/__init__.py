@@ -44,10 +44,29 @@ class mp_dp_params(ctypes.Structure):
                 ("splice_p", ctypes.c_int32), ("exon_rescore", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
+class mp_profile_pos(ctypes.Structure):
+    _fields_ = [("subst", ctypes.c_int16 * 21), ("gap_open", ctypes.c_int16), ("gap_ext", ctypes.c_int16),
+                ("reserved", ctypes.c_int16)]
+
+
 class mp_pair(ctypes.Structure):
     _fields_ = [("prot", ctypes.c_char_p), ("prot_len", ctypes.c_uint32),
                 ("nt", ctypes.c_char_p), ("nt_len", ctypes.c_uint32),
-                ("strand", ctypes.c_int8), ("flags", ctypes.c_uint32)]
+                ("strand", ctypes.c_int8), ("flags", ctypes.c_uint32),
+                ("profile", ctypes.POINTER(mp_profile_pos))]
+
+
+def profile_array(prof) -> np.ndarray:
+    """A profile query's positions as the C ABI takes them (mp_profile_pos
+    records): prof is an int array of shape (|P| + 1, 23), row j holding
+    the 21 substitution scores of position j (ARNDCQEGHILKMFPSTWYV, then
+    the stop codon), its gap open and its gap extension cost."""
+    prof = np.asarray(prof)
+    if prof.ndim != 2 or prof.shape[1] != 23:
+        raise ValueError("a profile is an array of shape (|P| + 1, 23)")
+    out = np.zeros((prof.shape[0], 24), dtype=np.int16)
+    out[:, :23] = prof
+    return out
 
 
 class mp_result(ctypes.Structure):
@@ -69,11 +88,11 @@ class mp_dp_tuning(ctypes.Structure):
     _fields_ = [("dp16_variant", ctypes.c_int32), ("dp16_ctas_per_sm", ctypes.c_int32),
                 ("dp32_ctas_per_sm", ctypes.c_int32), ("wide_direct", ctypes.c_int32),
                 ("overlap_waves", ctypes.c_int32), ("item_order", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("strip_width", ctypes.c_int32)]
 
 
 TUNING_KEYS = ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct", "overlap_waves", "item_order",
-               "ms")
+               "strip_width", "ms")
 
 
 class mp_dp_serve_stats(ctypes.Structure):
@@ -180,6 +199,13 @@ class _PairArray:
             self.arr[k].nt_len = len(nt)
             self.arr[k].strand = strand
             self.arr[k].flags = flags
+            prof = getattr(p, "profile", None)
+            if prof is not None:
+                pa = profile_array(prof)
+                if pa.shape[0] != len(prot) + 1:
+                    raise ValueError("a profile has |P| + 1 positions")
+                self.keep.append(pa)
+                self.arr[k].profile = pa.ctypes.data_as(ctypes.POINTER(mp_profile_pos))
         self.n = n
 
 
@@ -235,10 +261,11 @@ class RegionBatch(_PairArray):
         if n and (prot_off.min() < 0 or (prot_off + prot_len).max() > len(prot_buf) or nt_off.min() < 0 or
                   (nt_off + nt_len).max() > len(nt_buf) or prot_len.max() >= 1 << 32 or nt_len.max() >= 1 << 32):
             raise ValueError("a record lies outside its buffer")
-        dt = np.dtype({"names": ["prot", "prot_len", "nt", "nt_len", "strand", "flags"],
-                       "formats": [np.uint64, np.uint32, np.uint64, np.uint32, np.int8, np.uint32],
+        dt = np.dtype({"names": ["prot", "prot_len", "nt", "nt_len", "strand", "flags", "profile"],
+                       "formats": [np.uint64, np.uint32, np.uint64, np.uint32, np.int8, np.uint32, np.uint64],
                        "offsets": [mp_pair.prot.offset, mp_pair.prot_len.offset, mp_pair.nt.offset,
-                                   mp_pair.nt_len.offset, mp_pair.strand.offset, mp_pair.flags.offset],
+                                   mp_pair.nt_len.offset, mp_pair.strand.offset, mp_pair.flags.offset,
+                                   mp_pair.profile.offset],
                        "itemsize": ctypes.sizeof(mp_pair)})
         rec = np.zeros(max(n, 1), dtype=dt)
         rec["prot"][:n] = prot_buf.ctypes.data + prot_off

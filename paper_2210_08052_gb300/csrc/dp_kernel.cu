@@ -132,19 +132,52 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 
 // queue the records of positions [lo, lo + kChunk) into the ring
+// (recs[ii + kRecPre] is the record of position ii)
 template <typename BndT>
 __device__ __forceinline__ void fetch_records(WarpSmem<BndT> &sm, const uint4 *recs, int lo, int lane)
 {
     for (int ii = lo + lane; ii < lo + kChunk; ii += 32) {
         const int half = ii & 1, idx = (ii >> 1) & (kRing / 2 - 1);
-        cp_async16(&sm.ring[half][idx], recs + ii + kChunk);
-        if (idx < kRingPad / 2) cp_async16(&sm.ring[half][idx + kRing / 2], recs + ii + kChunk);
+        cp_async16(&sm.ring[half][idx], recs + ii + kRecPre);
+        if (idx < kRingPad / 2) cp_async16(&sm.ring[half][idx + kRing / 2], recs + ii + kRecPre);
+    }
+}
+
+// Shared memory of a warp running a 128-residue strip (four residues per
+// lane).  At a step lane l reads the record of position t - 4l: the ring is
+// split by position mod 4, so all lanes read one quarter at consecutive
+// indices (conflict-free 16-byte loads).  Each quarter holds kRing4 entries
+// (a chunk reads positions t0-124 .. t0+95 while the next chunk's 96 arrive)
+// plus kRing4Pad mirrored ones so that a 12-step body never wraps.
+constexpr int kRing4 = 96;
+constexpr int kRing4Pad = 2;
+struct WarpSmem4 {
+    uint4 ring[4][kRing4 + kRing4Pad];
+    // prof[aa][lane] = {[s(aa, P[4l]), s(aa, P[4l+1])], [s(aa, P[4l+2]), s(aa, P[4l+3])]}, each + 512
+    uint2 prof[kProfRows * 32];
+    alignas(16) uint32_t bin[kChunk];
+    alignas(16) uint32_t bout[kChunk];
+};
+
+// quarter index of position ii (ii >= -8 * kRing4)
+__device__ __forceinline__ int ring4_idx(int ii) { return ((ii + 8 * kRing4) >> 2) % kRing4; }
+
+__device__ __forceinline__ uint4 get_record4(const WarpSmem4 &sm, int ii) { return sm.ring[ii & 3][ring4_idx(ii)]; }
+
+__device__ __forceinline__ void fetch_records4(WarpSmem4 &sm, const uint4 *recs, int lo, int lane)
+{
+    for (int ii = lo + lane; ii < lo + kChunk; ii += 32) {
+        const int q = ii & 3, idx = ring4_idx(ii);
+        cp_async16(&sm.ring[q][idx], recs + ii + kRecPre);
+        if (idx < kRing4Pad) cp_async16(&sm.ring[q][idx + kRing4], recs + ii + kRecPre);
     }
 }
 
 // ================================================================ int16 ops
 struct Ops16 {
     using Bnd = uint32_t;                  // [H, I] biased 16-bit
+    using Smem = WarpSmem<Bnd>;
+    static constexpr int W = kStripW, CPL = 2;
     static constexpr uint32_t Z = 0x80008000u;      // biased 0 in both halves
     static constexpr uint32_t NEGV = 0x40004000u;   // biased -16384
     static constexpr uint32_t K = 0x80008000u;
@@ -184,6 +217,12 @@ struct Ops16 {
         return static_cast<uint32_t>(lo + 32768) | (static_cast<uint32_t>(hi + 32768) << 16);
     }
     static __device__ __forceinline__ void set_row0(Consts &c, int lo, int hi) { c.ROW0 = pack2(lo, hi); }
+    // profile queries: the gap costs of the lane's two columns (packed halves)
+    static __device__ __forceinline__ void set_gaps(Consts &c, int qlo, int elo, int qhi, int ehi)
+    {
+        c.QE = static_cast<uint32_t>(qlo + elo) | (static_cast<uint32_t>(qhi + ehi) << 16);
+        c.E = static_cast<uint32_t>(elo) | (static_cast<uint32_t>(ehi) << 16);
+    }
     // boundary entry of column 0 in the anchored modes: [H, I = -inf]
     static __device__ __forceinline__ Bnd col0_entry(int h)
     {
@@ -329,6 +368,12 @@ struct Ops16 {
         return *reinterpret_cast<const uint32_t *>(strip + static_cast<size_t>(t >> 2) * 512 + lane * 16 +
                                                    (t & 3) * 4);
     }
+    static __device__ __forceinline__ int cell_max(const ColMax &m, int k) { return word_h(m, k); }
+    // stored H of cell k of the lane at step t
+    static __device__ __forceinline__ int load_cell(const uint8_t *strip, int t, int lane, int k)
+    {
+        return word_h(load_word(strip, t, lane), k);
+    }
 };
 
 // ================================================================ int32 ops
@@ -349,11 +394,14 @@ struct Ops32 {
     struct Bnd {
         int32_t h, i;
     };
+    using Smem = WarpSmem<Bnd>;
+    static constexpr int W = kStripW, CPL = 2;
     static constexpr int32_t NEG = -(1 << 28);
     static constexpr Bnd kBnd0 = {0, NEG};
 
     struct Consts {
-        int32_t qe, e, f;
+        V2 qe, e;                           // q + e and e of the lane's two columns
+        int32_t f;
         int32_t floor;                      // local: 0 (the restart); anchored modes: NEG (none)
         int32_t row0lo, row0hi;             // H in row 0 of the lane's two columns
     };
@@ -367,11 +415,17 @@ struct Ops32 {
 
     static __device__ __forceinline__ Consts consts(const ScoreParams &sp)
     {
-        return Consts{sp.q + sp.e, sp.e, sp.f, sp.mode == MP_MODE_LOCAL ? 0 : NEG, 0, 0};
+        return Consts{V2{sp.q + sp.e, sp.q + sp.e}, V2{sp.e, sp.e}, sp.f, sp.mode == MP_MODE_LOCAL ? 0 : NEG, 0, 0};
     }
 
     static __device__ __forceinline__ V2 pack2(int lo, int hi) { return V2{lo, hi}; }
     static __device__ __forceinline__ void set_row0(Consts &c, int lo, int hi) { c.row0lo = lo; c.row0hi = hi; }
+    // profile queries: the gap costs of the lane's two columns
+    static __device__ __forceinline__ void set_gaps(Consts &c, int qlo, int elo, int qhi, int ehi)
+    {
+        c.qe = V2{qlo + elo, qhi + ehi};
+        c.e = V2{elo, ehi};
+    }
     static __device__ __forceinline__ Bnd col0_entry(int h) { return Bnd{h, NEG}; }
 
     static __device__ __forceinline__ uint32_t prof_entry(int slo, int shi)
@@ -409,9 +463,9 @@ struct Ops32 {
             reinterpret_cast<const char *>(prof_lane) + rec.z);
         const V2 S{static_cast<int32_t>(X0 << 16) >> 16, static_cast<int32_t>(s.X1) >> 16};
         const V2 M = add(s.L3, S);
-        const V2 Iopen = subc(s.L0, c.qe), Iext = subc(s.IL, c.e);
+        const V2 Iopen = sub(s.L0, c.qe), Iext = sub(s.IL, c.e);
         V2 I0 = mx(Iopen, Iext);
-        const V2 Dopen = subc(s.H3, c.qe), Dext = subc(s.D3, c.e);
+        const V2 Dopen = sub(s.H3, c.qe), Dext = sub(s.D3, c.e);
         V2 D0 = mx(Dopen, Dext);
         const V2 Aopen = sub(s.H1, s.VD2);
         V2 A0 = mx(Aopen, s.A1);
@@ -481,6 +535,262 @@ struct Ops32 {
     }
 };
 
+// ==================================================== int16, 128-residue strips
+// Four residues per lane: lane l holds residues 4l .. 4l+3 of the strip in
+// two packed registers, a = [4l, 4l+1] and b = [4l+2, 4l+3] (biased 16-bit
+// halves, as in Ops16).  At step t the cells of lane l lie at rows t-4l
+// (a lo), t-4l-1 (a hi), t-4l-2 (b lo) and t-4l-3 (b hi), so every cell's
+// left neighbour was computed one step earlier: a's lo cell takes it from
+// lane l-1 (that lane's b hi cell, one shuffle for four cells), the other
+// three from the lane's own registers.  b's rows are a's rows of two steps
+// before, so b reuses the records and profile words a read then.  Per cell
+// the arithmetic of Eq. 7 is that of Ops16; the shuffle, the record load,
+// the profile load and the stores serve four cells instead of two.
+struct Ops16x4 {
+    using Bnd = uint32_t;                  // [H, I] biased 16-bit
+    using Smem = WarpSmem4;
+    static constexpr int W = kStripWMax, CPL = 4;
+    static constexpr uint32_t Z = 0x80008000u;
+    static constexpr uint32_t NEGV = 0x40004000u;
+    static constexpr uint32_t SBIAS = 0x02000200u;
+    static constexpr Bnd kBnd0 = 0x40008000u;
+    static constexpr bool kChunkMaxBest = true;
+
+    struct Consts {
+        uint32_t QE, E, F;
+        uint32_t FLOOR;
+        uint32_t ROW0A, ROW0B;             // H in row 0 of the lane's four columns (biased)
+    };
+    struct Reg {
+        uint32_t H1, H2, H3, L0, L1, L2, L3, IL, D1, D2, D3, A1, B1, C1;
+    };
+    struct State {
+        Reg a, b;
+        uint32_t VD1, VD2, VD3, VD4;        // record x of a's lo row minus 1 .. 4
+        uint32_t VA1, VA2, VA3, VA4;        // record y of the same rows
+        uint32_t X1;                        // a's profile word of the previous step
+        uint32_t Y1, Y2, Y3;                // b's profile words of the last three steps
+        uint32_t cma, cmb;                  // this chunk's maxima (pairs with a stream)
+        uint32_t TC, k0, k1, k2, k3;        // best-cell keys (pairs without one)
+    };
+    using ColMax = uint2;                   // [cma, cmb]
+
+    static __device__ __forceinline__ Consts consts(const ScoreParams &sp)
+    {
+        Consts c;
+        const uint32_t qe = sp.q + sp.e;
+        c.QE = qe | (qe << 16);
+        c.E = static_cast<uint32_t>(sp.e) | (static_cast<uint32_t>(sp.e) << 16);
+        c.F = static_cast<uint32_t>(sp.f) | (static_cast<uint32_t>(sp.f) << 16);
+        c.FLOOR = sp.mode == MP_MODE_LOCAL ? Z : 0u;
+        c.ROW0A = c.ROW0B = Z;
+        return c;
+    }
+    template <typename Row0>
+    static __device__ __forceinline__ void set_row0(Consts &c, Row0 row0, int jcol)
+    {
+        c.ROW0A = Ops16::pack2(row0(jcol), row0(jcol + 1));
+        c.ROW0B = Ops16::pack2(row0(jcol + 2), row0(jcol + 3));
+    }
+    static __device__ __forceinline__ Bnd col0_entry(int h) { return Ops16::col0_entry(h); }
+
+    static __device__ __forceinline__ void build_profile(Smem &sm, const ScoreParams &sp, const uint8_t *P, int m,
+                                                         int s, int lane)
+    {
+        int pc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = s * W + 4 * lane + k;
+            pc[k] = j < m ? P[j] : 21;
+        }
+#pragma unroll 2
+        for (int aa = 0; aa < kProfRows; ++aa)
+            sm.prof[aa * 32 + lane] =
+                make_uint2(Ops16::prof_entry(subst_score(sp, aa, pc[0]), subst_score(sp, aa, pc[1])),
+                           Ops16::prof_entry(subst_score(sp, aa, pc[2]), subst_score(sp, aa, pc[3])));
+    }
+    // records of positions [-kRecPre, kChunk): the history of the first
+    // step reaches position -(4 * 31 + 4)
+    static __device__ __forceinline__ void fetch_first(Smem &sm, const uint4 *recs, int lane)
+    {
+        fetch_records4(sm, recs, -2 * kChunk, lane);
+        fetch_records4(sm, recs, -kChunk, lane);
+        fetch_records4(sm, recs, 0, lane);
+    }
+    static __device__ __forceinline__ void fetch(Smem &sm, const uint4 *recs, int lo, int lane)
+    {
+        fetch_records4(sm, recs, lo, lane);
+    }
+    static __device__ __forceinline__ uint2 prof_at(const Smem &sm, uint32_t z, int lane)
+    {
+        return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(&sm.prof[lane]) + z);
+    }
+
+    // State before step 0 (see Ops16::init): only lane 0's a register touches
+    // row 0 and the strip's left boundary there; b's rows are above row 0.
+    static __device__ __forceinline__ void init(State &s, const Smem &sm, int lane, Bnd w0, int h_self, int h_left)
+    {
+        const uint32_t hs = Ops16::pack2(h_self, -16384), hl = Ops16::pack2(h_left, -16384);
+        Reg &a = s.a;
+        a.H1 = (lane == 0) ? hs : NEGV; a.H2 = NEGV; a.H3 = NEGV;
+        a.L1 = (lane == 0) ? hl : NEGV; a.L2 = NEGV; a.L3 = NEGV;
+        a.L0 = (lane == 0) ? ((w0 & 0xffffu) | (hs << 16)) : NEGV;
+        a.IL = (lane == 0) ? ((w0 >> 16) | 0x40000000u) : NEGV;
+        a.D1 = a.D2 = a.D3 = NEGV;
+        a.A1 = a.B1 = a.C1 = NEGV;
+        Reg &b = s.b;
+        b.H1 = b.H2 = b.H3 = b.L0 = b.L1 = b.L2 = b.L3 = b.IL = NEGV;
+        b.D1 = b.D2 = b.D3 = b.A1 = b.B1 = b.C1 = NEGV;
+        const int ii0 = -4 * lane;
+        const uint4 r1 = get_record4(sm, ii0 - 1), r2 = get_record4(sm, ii0 - 2);
+        const uint4 r3 = get_record4(sm, ii0 - 3), r4 = get_record4(sm, ii0 - 4);
+        s.VD1 = r1.x; s.VD2 = r2.x; s.VD3 = r3.x; s.VD4 = r4.x;
+        s.VA1 = r1.y; s.VA2 = r2.y; s.VA3 = r3.y; s.VA4 = r4.y;
+        const uint2 p1 = prof_at(sm, r1.z, lane), p2 = prof_at(sm, r2.z, lane), p3 = prof_at(sm, r3.z, lane);
+        s.X1 = p1.x;
+        s.Y1 = p1.y; s.Y2 = p2.y; s.Y3 = p3.y;
+        s.cma = s.cmb = 0;
+        s.TC = 0xffffu; s.k0 = s.k1 = s.k2 = s.k3 = 0;
+    }
+
+    // The cells of one register at rows (lo, lo - 1): Eq. 7 as in Ops16::step.
+    // VD0..VD2 / VA0..VA2: records x / y of rows lo, lo-1, lo-2.  Leaves L0
+    // and IL for the caller (they come from the neighbours of this step).
+    template <bool MASKED>
+    static __device__ __forceinline__ void cells(Reg &r, const Consts &c, uint32_t S, uint32_t VD0, uint32_t VD1,
+                                                 uint32_t VD2, uint32_t VA0, uint32_t VA1, uint32_t VA2,
+                                                 uint32_t ROW0, int ii, int n, uint32_t &H0, uint32_t &I0,
+                                                 uint32_t &vmask)
+    {
+        const uint32_t M = r.L3 + S - SBIAS;
+        I0 = vmax(r.L0 - c.QE, r.IL - c.E);
+        uint32_t D0 = vmax(r.H3 - c.QE, r.D3 - c.E);
+        uint32_t A0 = vmax(r.H1 - VD2, r.A1);             // H[i-1][j] - r - d(i-1)
+        uint32_t B0 = vmax(r.L1 - VD1, r.B1);             // H[i-1][j-1] - r - d(i)
+        uint32_t C0 = vmax(r.L1 - VD0, r.C1);             // H[i-1][j-1] - r - d(i+1)
+        const uint32_t FG = vmax(vmax(r.L1, r.L2), vmax(r.H1, r.H2)) - c.F;
+        const uint32_t Ap = A0 - VA0, Bp = B0 - VA2, Cp = C0 - VA1;
+        H0 = vmax(vmax(vmax(M, I0), vmax(D0, FG)), vmax(vmax(Ap, Bp), vmax(Cp, c.FLOOR)));
+        vmask = 0xffffffffu;
+        if (MASKED) {
+            const uint32_t kill = (ii < 0 ? 0x0000ffffu : 0u) | (ii < 1 ? 0xffff0000u : 0u);
+            const uint32_t row0 = (ii == -1 ? 0x0000ffffu : 0u) | (ii == 0 ? 0xffff0000u : 0u);
+            const uint32_t hforce = (row0 & ROW0) | (~row0 & NEGV);
+            H0 = (H0 & ~kill) | (hforce & kill);
+            I0 = (I0 & ~kill) | (NEGV & kill);
+            D0 = (D0 & ~kill) | (NEGV & kill);
+            A0 = (A0 & ~kill) | (NEGV & kill);
+            B0 = (B0 & ~kill) | (NEGV & kill);
+            C0 = (C0 & ~kill) | (NEGV & kill);
+            vmask = ((ii >= 0 && ii < n) ? 0x0000ffffu : 0u) | ((ii >= 1 && ii <= n) ? 0xffff0000u : 0u);
+        }
+        r.L3 = r.L2; r.L2 = r.L1; r.L1 = r.L0;
+        r.H3 = r.H2; r.H2 = r.H1; r.H1 = H0;
+        r.D3 = r.D2; r.D2 = r.D1; r.D1 = D0;
+        r.A1 = A0; r.B1 = B0; r.C1 = C0;
+    }
+
+    // One anti-diagonal step: the four cells of the lane.  rec: record of
+    // a's lo row ii; xy: the profile words of that row's codon.
+    template <bool MASKED, bool KEYS>
+    static __device__ __forceinline__ void step(State &s, const Consts &c, const uint4 rec, const uint2 xy, Bnd bin,
+                                                Bnd &wout, int lane, int ii, int n, uint32_t &wa, uint32_t &wb)
+    {
+        const uint32_t Sa = (xy.x & 0x0000ffffu) | (s.X1 & 0xffff0000u);   // s(i, 4l), s(i-1, 4l+1)
+        const uint32_t Sb = (s.Y2 & 0x0000ffffu) | (s.Y3 & 0xffff0000u);   // s(i-2, 4l+2), s(i-3, 4l+3)
+        uint32_t Ha, Ia, ma, Hb, Ib, mb;
+        cells<MASKED>(s.a, c, Sa, rec.x, s.VD1, s.VD2, rec.y, s.VA1, s.VA2, c.ROW0A, ii, n, Ha, Ia, ma);
+        cells<MASKED>(s.b, c, Sb, s.VD2, s.VD3, s.VD4, s.VA2, s.VA3, s.VA4, c.ROW0B, ii - 2, n, Hb, Ib, mb);
+        // hand [H, I] of b's hi cell to the next lane; lane 0 takes the strip boundary
+        const uint32_t Wd = prmt<0x7632>(Hb, Ib);
+        uint32_t R = __shfl_up_sync(kFull, Wd, 1);
+        if (lane == 0) R = bin;
+        wout = Wd;
+        s.a.L0 = prmt<0x5410>(R, Ha);
+        s.a.IL = prmt<0x5432>(R, Ia);
+        s.b.L0 = prmt<0x5432>(Ha, Hb);
+        s.b.IL = prmt<0x5432>(Ia, Ib);
+        s.VD4 = s.VD3; s.VD3 = s.VD2; s.VD2 = s.VD1; s.VD1 = rec.x;
+        s.VA4 = s.VA3; s.VA3 = s.VA2; s.VA2 = s.VA1; s.VA1 = rec.y;
+        s.X1 = xy.x;
+        s.Y3 = s.Y2; s.Y2 = s.Y1; s.Y1 = xy.y;
+        const uint32_t ha = Ha & ma, hb = Hb & mb;
+        if (KEYS) {
+            s.k0 = max(s.k0, ha * 65536u + s.TC);
+            s.k1 = max(s.k1, (ha & 0xffff0000u) | s.TC);
+            s.k2 = max(s.k2, hb * 65536u + s.TC);
+            s.k3 = max(s.k3, (hb & 0xffff0000u) | s.TC);
+            s.TC -= 1;
+        } else {
+            s.cma = vmax(s.cma, ha);
+            s.cmb = vmax(s.cmb, hb);
+        }
+        wa = Ha;
+        wb = Hb;
+    }
+
+    template <bool MASKED, bool STORE>
+    static __device__ __forceinline__ void chunk(State &st, const Consts &c, Smem &sm, int lane, int t0, int n,
+                                                 uint8_t *code_strip)
+    {
+#pragma unroll 1
+        for (int bdy = 0; bdy < kChunk / kBody; ++bdy) {
+            const int tb = t0 + bdy * kBody;
+            // record of a's lo cell at step tb+k: position tb+k-4l, quarter k&3,
+            // index ridx + k/4 within it (tb is a multiple of 4)
+            const int ridx = ring4_idx(tb - 4 * lane);
+            const uint4 *rq = &sm.ring[0][ridx];
+            uint32_t cw[2 * kBody];
+            Bnd bin4[4], wout4[4];
+#pragma unroll
+            for (int k = 0; k < kBody; ++k) {
+                if ((k & 3) == 0) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) bin4[u] = sm.bin[bdy * kBody + k + u];
+                }
+                const uint4 rec = rq[(k & 3) * (kRing4 + kRing4Pad) + (k >> 2)];
+                const uint2 xy = prof_at(sm, rec.z, lane);
+                step<MASKED, !STORE>(st, c, rec, xy, bin4[k & 3], wout4[k & 3], lane, tb + k - 4 * lane, n,
+                                     cw[2 * k], cw[2 * k + 1]);
+                if ((k & 3) == 3 && lane == 31) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) sm.bout[bdy * kBody + k - 3 + u] = wout4[u];
+                }
+                if (STORE && (k & 1) == 1) {
+                    // two steps of one lane: one 16-byte store
+                    *reinterpret_cast<uint4 *>(code_strip + static_cast<size_t>(tb + k - 1) * (W * 2) + lane * 16) =
+                        make_uint4(cw[2 * k - 2], cw[2 * k - 1], cw[2 * k], cw[2 * k + 1]);
+                }
+            }
+        }
+    }
+
+    // (score, step) of cell k's best key (pairs without a stream)
+    static __device__ __forceinline__ void take_best(const State &s, int k, int t0, int &score, int &t)
+    {
+        const uint32_t key = k == 0 ? s.k0 : k == 1 ? s.k1 : k == 2 ? s.k2 : s.k3;
+        score = static_cast<int>(key >> 16) - 32768;
+        t = t0 + static_cast<int>(0xffffu - (key & 0xffffu));
+    }
+    static __device__ __forceinline__ void reset_best(State &s)
+    {
+        s.TC = 0xffffu; s.k0 = s.k1 = s.k2 = s.k3 = 0; s.cma = s.cmb = 0;
+    }
+    static __device__ __forceinline__ ColMax chunk_max(const State &s) { return make_uint2(s.cma, s.cmb); }
+    static __device__ __forceinline__ int cell_max(const ColMax &m, int k)
+    {
+        const uint32_t w = k < 2 ? m.x : m.y;
+        return static_cast<int>((k & 1) ? (w >> 16) : (w & 0xffffu)) - 32768;
+    }
+    // stored H of cell k of the lane at step t
+    static __device__ __forceinline__ int load_cell(const uint8_t *strip, int t, int lane, int k)
+    {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(strip + static_cast<size_t>(t >> 1) * 512 + lane * 16 +
+                                                               (t & 1) * 8 + (k >> 1) * 4);
+        return static_cast<int>((k & 1) ? (w >> 16) : (w & 0xffffu)) - 32768;
+    }
+};
+
 // ============================================================ strip driver
 struct Best {
     int score, ii, jj;
@@ -499,6 +809,8 @@ __device__ __noinline__ void trace_inline(const DPArgs &a, uint32_t p, int lane)
     t.ops = a.ops;
     t.col0 = a.col0;
     t.sp = a.sp;
+    t.prof = a.prof;
+    t.epre = a.epre;
     trace_pair<true>(t, a.mat, p, lane);
 }
 
@@ -575,34 +887,51 @@ __device__ __forceinline__ unsigned long long best_key(int score, int ii, int jj
            static_cast<unsigned long long>(0xfffffu - static_cast<uint32_t>(jj));
 }
 
-// One 64-residue strip s of pair p.  Strip s reads the boundary row (H and
-// I of residue 64s-1 at every genome position) that strip s-1 publishes
-// chunk by chunk, and publishes its own last residue for strip s+1.
+// One strip s of pair p (64 residues, two per lane, or 128, four per lane).
+// Strip s reads the boundary row (H and I of the last residue of strip s-1
+// at every genome position) that strip s-1 publishes chunk by chunk, and
+// publishes its own last residue for strip s+1.
 template <typename Ops>
-__device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint32_t p, int s, int lane,
+__device__ void run_strip(const DPArgs &a, typename Ops::Smem &sm, const PairDesc &pd, uint32_t p, int s, int lane,
                           bool rerun)
 {
     using Bnd = typename Ops::Bnd;
-    const PairDesc pd = a.pairs[p];
+    constexpr int W = Ops::W, CPL = Ops::CPL;
     const int n = static_cast<int>(pd.nt_len);
     const int m = static_cast<int>(pd.prot_len);
     const int nstrips = static_cast<int>(pd.n_strips);
     const bool store = !(pd.flags & PF_SCORE_ONLY);
-    const uint32_t *g = a.nt2 + pd.nt_word_off;
     const uint8_t *P = a.prot + pd.prot_off;
-    Bnd *bnd = reinterpret_cast<Bnd *>(a.bnd) + pd.bnd_off + kBndPad;   // bnd[ii], ii >= -64
+    Bnd *bnd = reinterpret_cast<Bnd *>(a.bnd) + pd.bnd_off + kBndPad;   // bnd[ii], ii >= -kBndPad
     typename Ops::Consts c = Ops::consts(a.sp);
     // anchored modes: row 0 holds H[0][j] = -(q + e j) (an I run from cell
     // (0, 0)) and column 0 the values of the column-0 array; local: both 0
     const bool anchored = a.sp.mode != MP_MODE_LOCAL;
     const int32_t *c0 = anchored ? a.col0 + pd.col0_off : nullptr;      // c0[i] = H[i][0]
-    const int jcol = s * kStripW + 2 * lane + 1;                         // 1-based column of the lo cell
-    auto row0 = [&](int j) { return (!anchored || j == 0) ? 0 : -(a.sp.q + a.sp.e * j); };
-    Ops::set_row0(c, row0(jcol), row0(jcol + 1));
-    const int nsteps = n + kStripW - 1;
+    const int jcol = s * W + CPL * lane + 1;                             // 1-based column of the lane's first cell
+    // profile queries (2-cell forms only): position-specific gap costs and
+    // substitution scores of positions 1..m at pf[1..m]
+    const ProfPos *pf = (pd.flags & PF_PROF) ? a.prof + pd.prof_off : nullptr;
+    const int32_t *ep = (pd.flags & PF_PROF) ? a.epre + pd.prof_off : nullptr;
+    auto row0 = [&](int j) {
+        if (!anchored || j == 0) return 0;
+        if (pf) return -(pf[1].q + __ldg(ep + (j < m ? j : m)) + (j > m ? a.sp.e * (j - m) : 0));
+        return -(a.sp.q + a.sp.e * j);
+    };
+    if constexpr (CPL == 4) {
+        Ops::set_row0(c, row0, jcol);
+    } else {
+        Ops::set_row0(c, row0(jcol), row0(jcol + 1));
+        if (pf) {
+            const int jl = jcol <= m ? jcol : 0, jh = jcol + 1 <= m ? jcol + 1 : 0;
+            Ops::set_gaps(c, jl ? pf[jl].q : a.sp.q, jl ? pf[jl].e : a.sp.e, jh ? pf[jh].q : a.sp.q,
+                          jh ? pf[jh].e : a.sp.e);
+        }
+    }
+    const int nsteps = n + W - 1;
     const int nchunks = (nsteps + kChunk - 1) / kChunk;
-    // 2 bytes per cell in the int16 path, 4 in the int32 path
-    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes * (sizeof(Bnd) / 4);
+    // 2 bytes per cell in the int16 paths, 4 in the int32 path
+    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * W * 2 * (sizeof(Bnd) / 4);
     const uint32_t *prev = a.progress + pd.strip_base + s - 1;   // valid for s > 0
     uint32_t *mine = a.progress + pd.strip_base + s;
     bool timed_out = false;
@@ -624,38 +953,58 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
         __syncwarp();
     };
 
-    // profile: prof[aa][lane] = [s(aa, P[2l]), s(aa, P[2l+1])]
-    const int jlo = s * kStripW + 2 * lane, jhi = jlo + 1;
-    const int plo = jlo < m ? P[jlo] : 21, phi = jhi < m ? P[jhi] : 21;
+    const uint4 *recs = a.recs + pd.rec_off;            // recs[ii + kRecPre] is position ii
+    if constexpr (CPL == 4) {
+        Ops::build_profile(sm, a.sp, P, m, s, lane);
+        Ops::fetch_first(sm, recs, lane);
+    } else {
+        // profile: prof[aa][lane] = [s(aa, P[2l]), s(aa, P[2l+1])]
+        const int jlo = s * W + 2 * lane, jhi = jlo + 1;
+        const int plo = jlo < m ? P[jlo] : 21, phi = jhi < m ? P[jhi] : 21;
+        if (pf) {
+            // a profile query: position-specific scores (no codon: -512 as subst_score)
 #pragma unroll 2
-    for (int aa = 0; aa < kProfRows; ++aa)
-        sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), subst_score(a.sp, aa, phi));
-    // records for ii in [-max(kChunk, kStripW), kChunk)
-    const uint4 *recs = a.recs + pd.rec_off;            // recs[ii + kChunk] is position ii
-    fetch_records(sm, recs, -kChunk, lane);
-    fetch_records(sm, recs, 0, lane);
+            for (int aa = 0; aa < kProfRows; ++aa)
+                sm.prof[aa * 32 + lane] =
+                    Ops::prof_entry(aa == 21 ? -512 : jlo < m ? pf[jlo + 1].s[aa] : subst_score(a.sp, aa, 21),
+                                    aa == 21 ? -512 : jhi < m ? pf[jhi + 1].s[aa] : subst_score(a.sp, aa, 21));
+        } else {
+#pragma unroll 2
+            for (int aa = 0; aa < kProfRows; ++aa)
+                sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), subst_score(a.sp, aa, phi));
+        }
+        // records for ii in [-kChunk, kChunk)
+        fetch_records(sm, recs, -kChunk, lane);
+        fetch_records(sm, recs, 0, lane);
+    }
     cp_async_wait_all();
     __syncwarp();
     // chunk c reads boundary entries c*kChunk+1 .. (c+1)*kChunk, which strip s-1
-    // writes kStripW-1 steps later: up to its chunk c + 1 + (kStripW-1)/kChunk
-    constexpr int kLag = 2 + (kStripW - 1) / kChunk;
+    // writes W-1 steps later: up to its chunk c + 1 + (W-1)/kChunk
+    constexpr int kLag = 2 + (W - 1) / kChunk;
     wait_for(nchunks < kLag ? nchunks : kLag);
     __syncwarp();
     typename Ops::State st;
     {
-        const int ii0 = -2 * lane;
-        const uint4 rm1 = get_record(sm, ii0 - 1);
-        const uint4 rm2 = get_record(sm, ii0 - 2);
-        const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
         const Bnd w0 = s > 0 ? ld_l2(bnd) : (anchored ? Ops::col0_entry(__ldg(c0 + 1)) : Ops::kBnd0);
-        Ops::init(st, lane, w0, rm1, rm2, xm1, row0(jcol), row0(jcol - 1));
+        if constexpr (CPL == 4) {
+            Ops::init(st, sm, lane, w0, row0(jcol), row0(jcol - 1));
+        } else {
+            const int ii0 = -2 * lane;
+            const uint4 rm1 = get_record(sm, ii0 - 1);
+            const uint4 rm2 = get_record(sm, ii0 - 2);
+            const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
+            Ops::init(st, lane, w0, rm1, rm2, xm1, row0(jcol), row0(jcol - 1));
+        }
     }
     uint8_t *code_strip = a.codes + pd.code_off + static_cast<size_t>(s) * strip_bytes;
     // per-chunk column maxima of H follow the strips' streams: [strip][chunk][lane]
     typename Ops::ColMax *colmax = reinterpret_cast<typename Ops::ColMax *>(
         a.codes + pd.code_off + static_cast<size_t>(nstrips) * strip_bytes) + static_cast<size_t>(s) * nchunks * 32;
     Best best{0, 0x7fffffff, 0x7fffffff};
-    int cbest[2] = {0, 0}, cchunk[2] = {0, 0};      // per cell: best chunk maximum and its chunk
+    int cbest[CPL], cchunk[CPL];                    // per cell: best chunk maximum and its chunk
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) cbest[k] = cchunk[k] = 0;
 
     for (int ch = 0; ch < nchunks; ++ch) {
         const int t0 = ch * kChunk;
@@ -673,65 +1022,85 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
         }
         __syncwarp();
         // next chunk's records land in ring slots this chunk does not read
-        if (ch + 1 < nchunks) fetch_records(sm, recs, t0 + kChunk, lane);
-        const bool masked = (t0 < kStripW) || (t0 + kChunk > n);
-        if (masked) {
-            if (store) run_chunk<Ops, true, true>(st, c, sm, lane, t0, n, code_strip);
-            else run_chunk<Ops, true, false>(st, c, sm, lane, t0, n, code_strip);
+        if (ch + 1 < nchunks) {
+            if constexpr (CPL == 4) Ops::fetch(sm, recs, t0 + kChunk, lane);
+            else fetch_records(sm, recs, t0 + kChunk, lane);
+        }
+        const bool masked = (t0 < W) || (t0 + kChunk > n);
+        if constexpr (CPL == 4) {
+            if (masked) {
+                if (store) Ops::template chunk<true, true>(st, c, sm, lane, t0, n, code_strip);
+                else Ops::template chunk<true, false>(st, c, sm, lane, t0, n, code_strip);
+            } else {
+                if (store) Ops::template chunk<false, true>(st, c, sm, lane, t0, n, code_strip);
+                else Ops::template chunk<false, false>(st, c, sm, lane, t0, n, code_strip);
+            }
         } else {
-            if (store) run_chunk<Ops, false, true>(st, c, sm, lane, t0, n, code_strip);
-            else run_chunk<Ops, false, false>(st, c, sm, lane, t0, n, code_strip);
+            if (masked) {
+                if (store) run_chunk<Ops, true, true>(st, c, sm, lane, t0, n, code_strip);
+                else run_chunk<Ops, true, false>(st, c, sm, lane, t0, n, code_strip);
+            } else {
+                if (store) run_chunk<Ops, false, true>(st, c, sm, lane, t0, n, code_strip);
+                else run_chunk<Ops, false, false>(st, c, sm, lane, t0, n, code_strip);
+            }
         }
         __syncwarp();
         if (s + 1 < nstrips && !a.no_publish) {
-            // publish residue 64s+63 for strip s+1
-            for (int k = lane; k < kChunk; k += 32) bnd[t0 + k - (kStripW - 1)] = sm.bout[k];
+            // publish residue W(s+1)-1 for strip s+1
+            for (int k = lane; k < kChunk; k += 32) bnd[t0 + k - (W - 1)] = sm.bout[k];
             // __syncwarp orders every lane's stores before lane 0's release
             // (release is cumulative), so one release store publishes the chunk
             __syncwarp();
             if (lane == 0) st_release(mine, static_cast<uint32_t>(ch + 1));
         }
         if (store) colmax[static_cast<size_t>(ch) * 32 + lane] = Ops::chunk_max(st);
-        if (Ops::kChunkMaxBest && store) {
-            // remember the first chunk holding each cell's maximum
-            const typename Ops::ColMax cmw = Ops::chunk_max(st);
+        bool folded = false;
+        if constexpr (Ops::kChunkMaxBest) {
+            if (store) {
+                // remember the first chunk holding each cell's maximum
+                const typename Ops::ColMax cmw = Ops::chunk_max(st);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int v = Ops::word_h(cmw, h);
-                if (v > cbest[h]) { cbest[h] = v; cchunk[h] = ch; }
+                for (int k = 0; k < CPL; ++k) {
+                    const int v = Ops::cell_max(cmw, k);
+                    if (v > cbest[k]) { cbest[k] = v; cchunk[k] = ch; }
+                }
+                folded = true;
             }
-        } else {
+        }
+        if (!folded) {
             // fold this chunk's best cells into the strip's best
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int k = 0; k < CPL; ++k) {
                 int sc, t;
-                Ops::take_best(st, h, t0, sc, t);
-                const int jj = s * kStripW + 2 * lane + h;
-                const int ii = t - 2 * lane - h;
+                Ops::take_best(st, k, t0, sc, t);
+                const int jj = s * W + CPL * lane + k;
+                const int ii = t - CPL * lane - k;
                 if (sc > 0 && jj < m && better(sc, ii, jj, best)) best = Best{sc, ii, jj};
             }
         }
         Ops::reset_best(st);
         __syncwarp();
     }
-    if (Ops::kChunkMaxBest && store) {
+    if constexpr (Ops::kChunkMaxBest) {
+      if (store) {
         // first step of the best chunk holding the maximum, read back from this
         // lane's own stored H values (valid cells only)
         __syncwarp();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int jj = s * kStripW + 2 * lane + h;
-            if (cbest[h] <= 0 || jj >= m) continue;
-            const int tb = cchunk[h] * kChunk;
+        for (int k = 0; k < CPL; ++k) {
+            const int jj = s * W + CPL * lane + k;
+            if (cbest[k] <= 0 || jj >= m) continue;
+            const int tb = cchunk[k] * kChunk;
             for (int t = tb; t < tb + kChunk; ++t) {
-                const int ii = t - 2 * lane - h;
+                const int ii = t - CPL * lane - k;
                 if (ii < 0 || ii >= n) continue;
-                if (Ops::word_h(Ops::load_word(code_strip, t, lane), h) == cbest[h]) {
-                    if (better(cbest[h], ii, jj, best)) best = Best{cbest[h], ii, jj};
+                if (Ops::load_cell(code_strip, t, lane, k) == cbest[k]) {
+                    if (better(cbest[k], ii, jj, best)) best = Best{cbest[k], ii, jj};
                     break;
                 }
             }
         }
+      }
     }
     // warp reduction of (score desc, ii asc, jj asc)
 #pragma unroll
@@ -791,14 +1160,17 @@ __device__ void run_strip(const DPArgs &a, WarpSmem<typename Ops::Bnd> &sm, uint
 }
 
 // MinB: CTAs per SM the build is made for (the register budget per thread
-// follows from it: 3 -> 80, 2 -> 128 for 256-thread CTAs).
-template <typename Ops, int MinB>
+// follows from it: 3 -> 80, 2 -> 128 for 256-thread CTAs).  Wide4: the
+// int16 build that also runs pairs in 128-residue strips (PF_W128), each
+// warp's shared memory sized for either strip form.
+template <typename Ops, int MinB, bool Wide4 = false>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, MinB) dp_kernel(const DPArgs a, int rerun_only)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using SM = WarpSmem<typename Ops::Bnd>;
+    using SM = typename Ops::Smem;
+    constexpr size_t kWarpBytes = Wide4 && sizeof(WarpSmem4) > sizeof(SM) ? sizeof(WarpSmem4) : sizeof(SM);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    SM &sm = reinterpret_cast<SM *>(smem_raw)[warp];
+    unsigned char *mine = smem_raw + static_cast<size_t>(warp) * kWarpBytes;
     // a fixed list (the wave's interleaved strip items, or the re-run list):
     // a strip's warp waits, bounded, for its predecessor's rows
     const uint2 *list = rerun_only ? a.rerun_items : a.items;
@@ -809,13 +1181,26 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinB) dp_kernel(const DPArg
         idx = __shfl_sync(kFull, idx, 0);
         if (idx >= count) break;
         const uint2 it = list[idx];
-        run_strip<Ops>(a, sm, it.x, static_cast<int>(it.y), lane, rerun_only != 0);
+        const PairDesc pd = a.pairs[it.x];
+        if constexpr (Wide4) {
+            if (pd.flags & PF_W128) {
+                run_strip<Ops16x4>(a, *reinterpret_cast<WarpSmem4 *>(mine), pd, it.x, static_cast<int>(it.y), lane,
+                                   rerun_only != 0);
+                continue;
+            }
+        }
+        run_strip<Ops>(a, *reinterpret_cast<SM *>(mine), pd, it.x, static_cast<int>(it.y), lane, rerun_only != 0);
     }
 }
 
 }  // namespace
 
 size_t dp16_smem_bytes() { return sizeof(WarpSmem<Ops16::Bnd>) * kWarpsPerCta; }
+size_t dp16w_smem_bytes()
+{
+    return (sizeof(WarpSmem4) > sizeof(WarpSmem<Ops16::Bnd>) ? sizeof(WarpSmem4) : sizeof(WarpSmem<Ops16::Bnd>)) *
+           kWarpsPerCta;
+}
 size_t dp32_smem_bytes() { return sizeof(WarpSmem<Ops32::Bnd>) * kWarpsPerCta; }
 
 static int blocks_per_sm(const void *fn, size_t smem)
@@ -828,7 +1213,7 @@ static int blocks_per_sm(const void *fn, size_t smem)
 
 // The shared-memory opt-in is a per-device function attribute: set it, and
 // read the occupancy, once per device and build.
-template <typename Ops, int MinB>
+template <typename Ops, int MinB, bool Wide4 = false>
 static int kernel_blocks_per_sm(size_t smem)
 {
     constexpr int kMaxDev = 64;
@@ -837,16 +1222,17 @@ static int kernel_blocks_per_sm(size_t smem)
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = 0;
     int v = nb[dev].load(std::memory_order_relaxed);
     if (v <= 0) {
-        cudaFuncSetAttribute(dp_kernel<Ops, MinB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(dp_kernel<Ops, MinB, Wide4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem));
-        v = blocks_per_sm(reinterpret_cast<const void *>(dp_kernel<Ops, MinB>), smem);
+        v = blocks_per_sm(reinterpret_cast<const void *>(dp_kernel<Ops, MinB, Wide4>), smem);
         nb[dev].store(v, std::memory_order_relaxed);
     }
     return v;
 }
 
-int dp16_blocks_per_sm(int variant)
+int dp16_blocks_per_sm(int variant, bool wide4)
 {
+    if (wide4) return kernel_blocks_per_sm<Ops16, 2, true>(dp16w_smem_bytes());
     return variant == 1 ? kernel_blocks_per_sm<Ops16, 2>(dp16_smem_bytes())
                         : kernel_blocks_per_sm<Ops16, 3>(dp16_smem_bytes());
 }
@@ -854,7 +1240,9 @@ int dp16_blocks_per_sm(int variant)
 int dp32_blocks_per_sm() { return kernel_blocks_per_sm<Ops32, 2>(dp32_smem_bytes()); }
 
 namespace {
-// Per-nt records of every pair (see make_record), positions -kChunk upwards.
+// Per-nt records of every pair (see make_record), positions -kRecPre upwards
+// (z, the profile row's byte offset, for the pair's strip form: rows of 32
+// lanes x 4 B, or x 8 B in 128-residue strips).
 // The genetic code and the splice terms are looked up in shared tables
 // (lanes index them at different positions: from constant memory such
 // reads serialise), the splice terms by three 5-symbol codes (four bases and
@@ -881,9 +1269,10 @@ __global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const ui
         const int cnt = static_cast<int>(records_of(pd.nt_len));
         const uint32_t *g = nt2 + pd.nt_word_off;
         uint4 *out = recs + pd.rec_off;
+        const uint32_t zrow = (pd.flags & PF_W128) ? 256u : 128u;
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             // the same record as make_record: window T0[ii-3 .. ii+4]
-            const int ii = k - kChunk;
+            const int ii = k - kRecPre;
             const int s0 = ii - 3;
             const int w = s0 >> 4;
             const uint64_t pair64 = (static_cast<uint64_t>(g[w + 1]) << 32) | g[w];
@@ -898,7 +1287,7 @@ __global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const ui
             const uint32_t dB = static_cast<uint32_t>(s_don[(c[4] * 5 + c[5]) * 5 + c[6]]);   // d(i)
             const uint32_t aA = static_cast<uint32_t>(s_acc[(c[1] * 5 + c[2]) * 5 + c[3]]);   // a(i)
             const uint32_t aC = static_cast<uint32_t>(s_acc[(c[0] * 5 + c[1]) * 5 + c[2]]);   // a(i-1)
-            out[k] = make_uint4((r + dC) | ((r + dB) << 16), aA | (aC << 16), static_cast<uint32_t>(aa) * 128u, 0u);
+            out[k] = make_uint4((r + dC) | ((r + dB) << 16), aA | (aC << 16), static_cast<uint32_t>(aa) * zrow, 0u);
         }
     }
 }
@@ -912,10 +1301,11 @@ cudaError_t launch_records(const PairDesc *pairs, uint32_t n, const uint32_t *nt
     return cudaGetLastError();
 }
 
-cudaError_t launch_dp16(const DPArgs &a, int grid, int variant, cudaStream_t st)
+cudaError_t launch_dp16(const DPArgs &a, int grid, int variant, bool wide4, cudaStream_t st)
 {
-    dp16_blocks_per_sm(variant);
-    if (variant == 1) dp_kernel<Ops16, 2><<<grid, kWarpsPerCta * 32, dp16_smem_bytes(), st>>>(a, 0);
+    dp16_blocks_per_sm(variant, wide4);
+    if (wide4) dp_kernel<Ops16, 2, true><<<grid, kWarpsPerCta * 32, dp16w_smem_bytes(), st>>>(a, 0);
+    else if (variant == 1) dp_kernel<Ops16, 2><<<grid, kWarpsPerCta * 32, dp16_smem_bytes(), st>>>(a, 0);
     else dp_kernel<Ops16, 3><<<grid, kWarpsPerCta * 32, dp16_smem_bytes(), st>>>(a, 0);
     return cudaGetLastError();
 }
@@ -1039,9 +1429,10 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
     __syncthreads();
     // per-nt records of the pair (positions -kChunk upwards)
     for (int k = threadIdx.x; k < static_cast<int>(records_of(static_cast<uint32_t>(n))); k += blockDim.x)
-        S->recs[k] = make_record(S->nt2 + kNtPadWords, n, k - kChunk, sp);
+        S->recs[k] = make_record(S->nt2 + kNtPadWords, n, k - kRecPre, sp);
     __syncthreads();
     if (!bad && m > 0 && n > 0) {
+        const PairDesc pd = S->desc;             // written by thread 0 before the barriers above
         DPArgs a{};
         a.pairs = &S->desc;
         a.recs = S->recs;
@@ -1064,7 +1455,7 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
                 if (lane == 0) s = atomicAdd(&S->head16, 1u);
                 s = __shfl_sync(kFull, s, 0);
                 if (s >= static_cast<uint32_t>(nstrips)) break;
-                run_strip<Ops16>(a, sm, 0, static_cast<int>(s), lane, false);
+                run_strip<Ops16>(a, sm, pd, 0, static_cast<int>(s), lane, false);
             }
         }
         __syncthreads();
@@ -1076,7 +1467,7 @@ dp_noalloc_kernel(ScoreParams sp, const char *prot_ascii, int m, const char *nt_
                 if (lane == 0) s = atomicAdd(&S->head32, 1u);
                 s = __shfl_sync(kFull, s, 0);
                 if (s >= nre) break;
-                run_strip<Ops32>(a, sm, 0, static_cast<int>(S->rerun_items[s].y), lane, true);
+                run_strip<Ops32>(a, sm, pd, 0, static_cast<int>(S->rerun_items[s].y), lane, true);
             }
         }
         __syncthreads();

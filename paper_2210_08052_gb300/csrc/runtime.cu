@@ -58,15 +58,28 @@ constexpr uint64_t kDefaultBudget = 40ull << 30;
 
 inline uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
-// Traceback bytes of one pair: strips x padded steps x 128 B plus 128 B of
-// column maxima per strip and chunk (x 2 when the pair may need the int32
-// re-run, whose stream holds 4 B per cell).
-inline uint64_t code_bytes(uint32_t m, uint32_t n, bool wide = false)
+// Traceback bytes of one pair: strips x padded steps x 2 B per cell plus the
+// column maxima (2 B per cell and chunk) of every strip and chunk (x 2 when
+// the pair may need the int32 re-run, whose stream holds 4 B per cell);
+// w128: 128-residue strips.
+inline uint64_t code_bytes(uint32_t m, uint32_t n, bool wide = false, bool w128 = false)
 {
-    const uint64_t nchunks = div_up(static_cast<uint64_t>(n) + kStripW - 1, kChunk);
-    const uint64_t strips = div_up(m, kStripW);
-    // H stream, then the per-chunk column maxima (one word per lane and chunk)
-    return strips * nchunks * (kChunk * kStepBytes + 32 * 4) * (wide ? 2 : 1);
+    const uint64_t W = w128 ? kStripWMax : kStripW;
+    const uint64_t nchunks = div_up(static_cast<uint64_t>(n) + W - 1, kChunk);
+    const uint64_t strips = div_up(m, W);
+    // H stream, then the per-chunk column maxima
+    return strips * nchunks * (kChunk * W * 2 + W * 2) * (wide ? 2 : 1);
+}
+
+// Whether a pair runs in 128-residue strips when the configuration asks for
+// them: only int16 pairs (never PF_WIDE), and only where the wider strips do
+// not add much padding (an odd number of 64-residue strips would pad one
+// more 64-residue half strip).
+inline bool use_w128(const PairDesc &d)
+{
+    if (d.flags & (PF_WIDE | PF_SKIP | PF_PROF)) return false;
+    const uint64_t k64 = div_up(d.prot_len, kStripW);
+    return k64 % 2 == 0 || k64 >= 9;
 }
 
 // Residue letter -> code (ARNDCQEGHILKMFPSTWYV 0..19, '*' 20, else X 21).
@@ -118,9 +131,10 @@ inline int64_t score_bound(const BoundTable &bt, const char *prot, uint32_t m, i
     return s;
 }
 
+// boundary entries of a pair (for either strip form)
 inline uint64_t bnd_entries(uint32_t n)
 {
-    const uint64_t nchunks = div_up(static_cast<uint64_t>(n) + kStripW - 1, kChunk);
+    const uint64_t nchunks = div_up(static_cast<uint64_t>(n) + kStripWMax - 1, kChunk);
     return nchunks * kChunk + 2 * kBndPad + 32;
 }
 
@@ -211,6 +225,10 @@ struct mp_dp_batch {
     DevBuf<uint2> items, rerun_items;   // strip items in processing order; re-run list
     DevBuf<uint4> recs;                 // per-nt records of every pair
     DevBuf<int32_t> col0;               // anchored modes: column 0 of every pair
+    DevBuf<ProfPos> prof;               // profile queries: positions 0..|P| of each
+    DevBuf<int32_t> epre;               // and their gap-extension prefix sums
+    std::vector<ProfPos> h_prof;
+    std::vector<int32_t> h_epre;
     DevBuf<uint64_t> bnd;
     // per-run state, zeroed by one memset: counters | strips_done | progress | best_key
     DevBuf<unsigned long long> state;
@@ -239,6 +257,7 @@ struct Request {
     std::string prot, nt;
     int8_t strand;
     uint32_t flags;
+    std::vector<mp_profile_pos> profile;    // a profile query's positions (empty otherwise)
     std::chrono::steady_clock::time_point t_submit;
 };
 
@@ -322,6 +341,10 @@ struct mp_dp_ctx {
     ScoreParams sp{};
     uint64_t budget = 0;
     DevBuf<uint8_t> codes;      // traceback arena (shared by the waves of a batch)
+    // serving slots: a range of the serving loop's shared arena used instead
+    // of `codes` (null: the context's own arena)
+    uint8_t *codes_ext = nullptr;
+    uint64_t codes_ext_cap = 0;
     HostBuf<char> staging;
     HostBuf<char> pstaging;        // a plan's descriptors, order, items and wave counts on their way to the device
     std::unique_ptr<WorkerPool> pool;  // gather threads (started by the first large upload)
@@ -477,12 +500,14 @@ int mp_dp_debug_h(mp_dp_ctx *c, mp_dp_batch *b, size_t k, int32_t *h)
     if (tmp.reserve(cells) != cudaSuccess) return MP_ENOMEM;
     TBArgs t{};
     t.pairs = b->d_desc.p;
-    t.codes = c->codes.p;
+    t.codes = c->codes_ext ? c->codes_ext : c->codes.p;
     t.prot = b->prot.p;
     t.nt2 = b->nt2.p;
     t.out = b->out.p;
     t.col0 = c->params.mode != MP_MODE_LOCAL ? b->col0.p : nullptr;
     t.sp = c->sp;
+    t.prof = b->prof.p;
+    t.epre = b->epre.p;
     cudaError_t e = launch_dump_h(t, static_cast<uint32_t>(k), cells, tmp.p, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h, tmp.p, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
@@ -514,6 +539,7 @@ static void free_batch_device(mp_dp_batch *b)
     b->ascii.release(); b->d_desc.release(); b->prot.release(); b->nt2.release(); b->out.release();
     b->ops.release(); b->cig.release(); b->work.release(); b->items.release(); b->rerun_items.release();
     b->bnd.release(); b->state.release(); b->recs.release(); b->wave_nwide.release(); b->col0.release();
+    b->prof.release(); b->epre.release();
 }
 
 void mp_dp_batch_free(mp_dp_ctx *c, mp_dp_batch *b)
@@ -578,7 +604,7 @@ static mp_dp_tuning tuning_for(const mp_dp_ctx *c, const mp_dp_batch *b)
 // batch that needs several waves) and the item order.
 static int plan_key(const mp_dp_batch *b, const mp_dp_tuning &t)
 {
-    return (b->needs_waves && t.overlap_waves ? 1 : 0) | (t.item_order ? 2 : 0);
+    return (b->needs_waves && t.overlap_waves ? 1 : 0) | (t.item_order ? 2 : 0) | (t.strip_width ? 4 : 0);
 }
 
 static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool stream_idle = false);
@@ -618,7 +644,10 @@ static void interleave_items(const mp_dp_ctx *c, mp_dp_batch *b)
         if (hi - lo < 2) return;
         double chunks = 0;
         for (uint32_t k = lo; k < hi; ++k)
-            chunks += static_cast<double>((b->desc[b->h_items[k].x].nt_len + kStripW - 1 + kChunk - 1) / kChunk);
+        {
+            const PairDesc &d = b->desc[b->h_items[k].x];
+            chunks += static_cast<double>((d.nt_len + strip_w_of(d.flags) - 1 + kChunk - 1) / kChunk);
+        }
         const uint32_t D = static_cast<uint32_t>(std::max(1.0, std::round(2.0 * warps / (chunks / (hi - lo)))));
         // key = rank of the pair + D * strip; a stable counting sort by key
         key.resize(hi - lo);
@@ -672,10 +701,30 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool 
     const uint64_t cap = c->budget;
     std::vector<uint64_t> cbytes(n, 0);
     uint64_t total_bytes = 0;
+    // strip form of each pair under this configuration.  A 128-residue strip
+    // takes about twice as long per step as a 64-residue one and lags its
+    // predecessor by three chunks instead of two, so a pair's critical path
+    // is longer in the wide form: pairs whose wide critical path would exceed
+    // the batch's longest one in 64-residue strips stay in 64-residue strips.
+    uint64_t crit64 = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        const PairDesc &d = b->desc[k];
+        if (d.flags & PF_SKIP) continue;
+        crit64 = std::max<uint64_t>(crit64, div_up(d.nt_len + kStripW - 1, kChunk) + 2 * div_up(d.prot_len, kStripW));
+    }
+    for (uint32_t k = 0; k < n; ++k) {
+        PairDesc &d = b->desc[k];
+        d.flags &= ~PF_W128;
+        const uint64_t crit128 =
+            div_up(d.nt_len + kStripWMax - 1, kChunk) + 3 * div_up(d.prot_len, kStripWMax);
+        if (t.strip_width && !c->params.force_int32 && use_w128(d) && 2 * crit128 <= crit64) d.flags |= PF_W128;
+        d.n_strips = static_cast<uint32_t>(div_up(d.prot_len, strip_w_of(d.flags)));
+    }
     for (uint32_t k = 0; k < n; ++k) {
         PairDesc &d = b->desc[k];
         if (d.flags & (PF_SKIP | PF_SCORE_ONLY)) continue;
-        uint64_t cb = div_up(code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0), 256) * 256;
+        uint64_t cb = div_up(code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0, (d.flags & PF_W128) != 0),
+                             256) * 256;
         if (cb > cap) {
             d.flags |= PF_BUDGET | PF_SCORE_ONLY;
             cb = 0;
@@ -755,7 +804,8 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool 
         if (d.flags & PF_SKIP) continue;
         d.code_off = cur;
         cur += cbytes[p];
-        if (cbytes[p]) b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0);
+        if (cbytes[p])
+            b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0, (d.flags & PF_W128) != 0);
         for (uint32_t s = 0; s < d.n_strips; ++s) b->h_items.push_back(make_uint2(p, s));
         if (wide(p) == 0) nwide += d.n_strips;
     }
@@ -780,9 +830,11 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool 
     b->runs = 0;
     b->planned = plan_key(b, t);
     cudaError_t e = cudaSuccess;
+    const uint64_t arena_need = b->overlap ? 2 * b->arena_half : std::max<uint64_t>(maxw, 256);
+    if (c->codes_ext && arena_need > c->codes_ext_cap) return MP_ENOMEM;
     if ((e = b->state.reserve(b->state_bytes / 8 + 1)) != cudaSuccess ||
         (e = b->wave_nwide.reserve(b->waves.size())) != cudaSuccess ||
-        (e = c->codes.reserve(b->overlap ? 2 * b->arena_half : std::max<uint64_t>(maxw, 256))) != cudaSuccess)
+        (!c->codes_ext && (e = c->codes.reserve(arena_need)) != cudaSuccess))
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     cudaStream_t st = c->stream;
     // no run of an earlier plan still reads these buffers, and the pinned
@@ -821,6 +873,34 @@ static cudaError_t staging_wait(mp_dp_ctx *c)
 // ascii_on_device: the caller writes the batch's ASCII into b->ascii on the
 // context's stream itself (the pairs' nt pointers are unused and may be null;
 // the protein pointers still serve the score bound).
+// A profile query's positions are within range and keep the degenerate
+// intron paths losing (r above every negated score, as mp_dp_init requires
+// of the matrix).
+static bool profile_valid(const mp_dp_ctx *c, const mp_profile_pos *pf, uint32_t m)
+{
+    for (uint32_t j = 0; j <= m; ++j) {
+        const mp_profile_pos &x = pf[j];
+        if (x.gap_open < 0 || x.gap_ext < 1 || x.gap_open + x.gap_ext > 1000) return false;
+        if (j == 0) continue;
+        for (int a = 0; a < 21; ++a)
+            if (x.subst[a] < -500 || x.subst[a] > 500 || !(c->params.r > -x.subst[a])) return false;
+    }
+    return true;
+}
+
+// An upper bound of a profile query's local score: the sum over positions
+// of their best score (at least 0).
+static int64_t profile_score_bound(const mp_profile_pos *pf, uint32_t m)
+{
+    int64_t s = 0;
+    for (uint32_t j = 1; j <= m; ++j) {
+        int b = 0;
+        for (int a = 0; a < 21; ++a) b = std::max<int>(b, pf[j].subst[a]);
+        s += b;
+    }
+    return s;
+}
+
 static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_t n, bool ascii_on_device = false)
 {
     for (size_t k = 0; k < n; ++k) {
@@ -867,11 +947,29 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
                       nspan + psum > 0 && prot_base + pspan < (uint64_t{1} << 32) && nspan + pspan < nsum + psum;
     // ---- layout
     const BoundTable bt(c->sp);
-    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0, nrec = 0, nc0 = 0;
+    uint64_t asc = 0, pro = 0, ntw = 0, bnd = 0, ops = 0, strips = 0, nrec = 0, nc0 = 0, npf = 0;
     const bool anchored = c->params.mode != MP_MODE_LOCAL;
+    b->h_prof.clear();
+    b->h_epre.clear();
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
         PairDesc &d = b->desc[k];
+        if (q.profile) {
+            // a profile query: its positions go to the device with the
+            // prefix sums of their gap extensions
+            if (!profile_valid(c, q.profile, q.prot_len)) return MP_EINVAL;
+            d.flags |= PF_PROF;
+            d.prof_off = npf;
+            npf += static_cast<uint64_t>(q.prot_len) + 1;
+            int32_t acc = 0;
+            for (uint32_t j = 0; j <= q.prot_len; ++j) {
+                ProfPos x;
+                memcpy(&x, &q.profile[j], sizeof(x));
+                b->h_prof.push_back(x);
+                if (j > 0) acc += q.profile[j].gap_ext;
+                b->h_epre.push_back(acc);
+            }
+        }
         d.prot_len = q.prot_len;
         d.nt_len = q.nt_len;
         d.strand = q.strand;
@@ -905,15 +1003,21 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         // global mode reads its score at the end cell from the traceback stream
         if ((q.flags & MP_PAIR_SCORE_ONLY) && c->params.mode != MP_MODE_GLOBAL) d.flags |= PF_SCORE_ONLY;
         if (q.prot_len == 0 || q.nt_len == 0) d.flags |= PF_SKIP;
-        if (c->params.force_int32 || (q.prot_len && score_bound(bt, q.prot, q.prot_len, kOverflowT) >= kOverflowT))
-            d.flags |= PF_WIDE;
+        const int64_t bound = q.profile ? profile_score_bound(q.profile, q.prot_len)
+                                        : score_bound(bt, q.prot, q.prot_len, kOverflowT);
+        if (c->params.force_int32 || (q.prot_len && bound >= kOverflowT)) d.flags |= PF_WIDE;
         // anchored modes: H may go negative; a path through row 0 and one
         // column (I run, D run, a frameshift) bounds it from below.  Pairs whose
         // bound leaves the int16 range safely run in int32 (PF_WIDE pairs of
         // these modes skip the int16 pass).
         if (anchored) {
-            const int64_t lower = 2 * static_cast<int64_t>(c->params.q) + c->params.f +
-                                  static_cast<int64_t>(c->params.e) * (q.prot_len + q.nt_len / 3 + 2);
+            int64_t gq = c->params.q, ge = c->params.e;
+            if (q.profile)
+                for (uint32_t j = 0; j <= q.prot_len; ++j) {
+                    gq = std::max<int64_t>(gq, q.profile[j].gap_open);
+                    ge = std::max<int64_t>(ge, q.profile[j].gap_ext);
+                }
+            const int64_t lower = 2 * gq + c->params.f + ge * (q.prot_len + q.nt_len / 3 + 2);
             if (lower >= 12000) d.flags |= PF_WIDE;
             // the int32 path represents -inf by -2^28; with half of that as
             // margin, a pair whose H could fall lower is refused
@@ -939,6 +1043,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
         (e = b->items.reserve(strips + 1)) != cudaSuccess ||
         (e = b->rerun_items.reserve(strips + 1)) != cudaSuccess || (e = b->bnd.reserve(bnd + 1)) != cudaSuccess ||
         (anchored && (e = b->col0.reserve(nc0 + 1)) != cudaSuccess) ||
+        (npf && (e = b->prof.reserve(npf)) != cudaSuccess) || (npf && (e = b->epre.reserve(npf)) != cudaSuccess) ||
         (e = b->recs.reserve(nrec + 1)) != cudaSuccess) {
         return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
     }
@@ -947,6 +1052,12 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     // arenas, and the staging buffers are free
     CK(cudaStreamSynchronize(st));
     c->staging_busy = false;
+    if (npf) {
+        // profile queries' positions (pageable host memory: the copies
+        // return once the data is staged)
+        CK(cudaMemcpyAsync(b->prof.p, b->h_prof.data(), npf * sizeof(ProfPos), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b->epre.p, b->h_epre.data(), npf * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
     b->needs_waves = plan_code_bytes(c, b) > c->budget;
     b->shape_key = shape_key_of(*b);
     b->planned = -1;
@@ -1058,12 +1169,13 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
     launches += 2;
     const bool anchored = c->params.mode != MP_MODE_LOCAL;
     if (anchored) {
-        CK(launch_col0(b->d_desc.p, n, b->nt2.p, c->sp, b->col0.p, st));
+        CK(launch_col0(b->d_desc.p, n, b->nt2.p, c->sp, b->prof.p, b->col0.p, st));
         ++launches;
     }
     CK(rec(1));
     const int variant = t.dp16_variant == 1 ? 1 : 0;
-    const int fit16 = dp16_blocks_per_sm(variant), fit32 = dp32_blocks_per_sm();
+    const bool wide4 = t.strip_width != 0 && !c->params.force_int32;
+    const int fit16 = dp16_blocks_per_sm(variant, wide4), fit32 = dp32_blocks_per_sm();
     const int g16 = c->num_sms * (t.dp16_ctas_per_sm > 0 ? std::min(t.dp16_ctas_per_sm, fit16) : fit16);
     const int g32 = c->num_sms * (t.dp32_ctas_per_sm > 0 ? std::min(t.dp32_ctas_per_sm, fit32) : fit32);
     // in the anchored modes PF_WIDE pairs never take the int16 pass
@@ -1081,7 +1193,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         // odd waves of an overlapped batch: second stream, second arena half
         // (this `st` shadows the main stream for the wave's launches)
         const cudaStream_t st = overlap && (w & 1) ? c->stream2 : main_st;
-        uint8_t *arena = c->codes.p + (overlap && (w & 1) ? b->arena_half : 0);
+        uint8_t *arena = (c->codes_ext ? c->codes_ext : c->codes.p) + (overlap && (w & 1) ? b->arena_half : 0);
         CK(rec_on(static_cast<int>(2 + EV_PER_WAVE * w), st));
         DPArgs a{};
         a.pairs = b->d_desc.p;
@@ -1102,6 +1214,8 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         a.no_publish = (c->params.debug_flags & MP_DEBUG_NO_PUBLISH) ? 1u : 0u;
         a.ops = b->ops.p;
         a.mat = c->d_mat.p;
+        a.prof = b->prof.p;
+        a.epre = b->epre.p;
         const uint32_t nitems = wv.iend - wv.ibegin;
         if (per_launch > 0) {
             // plain form: one kernel launch per group of pairs
@@ -1114,7 +1228,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
                 a1.head = counters + 8 * W + 8 + 4 * k;
                 const int grid = std::max(1, std::min<int>(c->num_sms, static_cast<int>((a1.n_items + kWarpsPerCta - 1) / kWarpsPerCta)));
                 if (c->params.force_int32) CK(launch_dp32(a1, grid, false, st));
-                else CK(launch_dp16(a1, grid, variant, st));
+                else CK(launch_dp16(a1, grid, variant, wide4, st));
                 ++launches;
                 ++dp_launches;
             }
@@ -1136,7 +1250,7 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
             const int grid16 = std::max(1, std::min<int>(g16, want));
             const int grid32 = std::max(1, std::min<int>(g32, want));
             if (c->params.force_int32) CK(launch_dp32(a, grid32, false, st));
-            else CK(launch_dp16(a, grid16, variant, st));
+            else CK(launch_dp16(a, grid16, variant, wide4, st));
             ++launches;
             ++dp_launches;
         }
@@ -1163,6 +1277,8 @@ static int enqueue_pipeline(mp_dp_ctx *c, mp_dp_batch *b, cudaStream_t st, bool 
         t.ops = b->ops.p;
         t.col0 = anchored ? b->col0.p : nullptr;
         t.sp = c->sp;
+        t.prof = b->prof.p;
+        t.epre = b->epre.p;
         const int tgrid = std::max(1, std::min<int>(c->num_sms * 8, static_cast<int>((t.n_work + 7) / 8)));
         CK(launch_tb(t, tgrid, st));
         ++launches;
@@ -1185,7 +1301,8 @@ static uint64_t tuning_sig(const mp_dp_tuning &t, bool timed)
 {
     return (static_cast<uint64_t>(t.dp16_variant & 0xff)) | (static_cast<uint64_t>(t.dp16_ctas_per_sm & 0xff) << 8) |
            (static_cast<uint64_t>(t.dp32_ctas_per_sm & 0xff) << 16) | (static_cast<uint64_t>(t.wide_direct & 1) << 24) |
-           (static_cast<uint64_t>(timed) << 25) | (static_cast<uint64_t>(t.overlap_waves & 1) << 26) | (static_cast<uint64_t>(t.item_order & 1) << 27) | (1ull << 28);
+           (static_cast<uint64_t>(timed) << 25) | (static_cast<uint64_t>(t.overlap_waves & 1) << 26) |
+           (static_cast<uint64_t>(t.item_order & 1) << 27) | (1ull << 28) | (static_cast<uint64_t>(t.strip_width & 1) << 29);
 }
 
 static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp_tuning *tried, int max_tried,
@@ -1275,9 +1392,22 @@ static std::vector<mp_dp_tuning> kernel_candidates(mp_dp_ctx *c, const mp_dp_bat
                 t.dp16_ctas_per_sm = k;
                 t.dp32_ctas_per_sm = fit32;
                 t.wide_direct = wd;
+                t.strip_width = 0;
                 v.push_back(t);
             }
     }
+    // 128-residue strips (the 2-CTA build that runs both strip forms)
+    const int fitw = dp16_blocks_per_sm(1, true);
+    for (int k = fitw; k >= std::max(1, fitw - 1); --k)
+        for (int wd = 0; wd <= (any_wide ? 1 : 0); ++wd) {
+            mp_dp_tuning t = default_tuning();
+            t.dp16_variant = 1;
+            t.dp16_ctas_per_sm = k;
+            t.dp32_ctas_per_sm = fit32;
+            t.wide_direct = wd;
+            t.strip_width = 1;
+            v.push_back(t);
+        }
     return v;
 }
 
@@ -1401,7 +1531,7 @@ int mp_dp_set_tuning(mp_dp_ctx *c, const mp_dp_tuning *t)
     }
     if (t->dp16_variant < 0 || t->dp16_variant >= kDp16Variants || t->dp16_ctas_per_sm < 0 ||
         t->dp32_ctas_per_sm < 0 || t->wide_direct < 0 || t->wide_direct > 1 || t->overlap_waves < 0 ||
-        t->overlap_waves > 1 || t->item_order < 0 || t->item_order > 1)
+        t->overlap_waves > 1 || t->item_order < 0 || t->item_order > 1 || t->strip_width < 0 || t->strip_width > 1)
         return MP_EINVAL;
     c->fixed = *t;
     c->has_fixed = true;
@@ -1420,12 +1550,12 @@ int mp_dp_tuning_save(mp_dp_ctx *c, const char *path)
     if (!c || !path) return MP_EINVAL;
     FILE *f = fopen(path, "w");
     if (!f) return MP_EINVAL;
-    bool ok = fprintf(f, "mp_dp_tuning 3 %s %d\n", c->dev_name.c_str(), c->num_sms) > 0;
+    bool ok = fprintf(f, "mp_dp_tuning 4 %s %d\n", c->dev_name.c_str(), c->num_sms) > 0;
     for (const auto &kv : c->tuned) {
         const mp_dp_tuning &t = kv.second;
-        ok = ok && fprintf(f, "%016llx %d %d %d %d %d %d %.4f\n", static_cast<unsigned long long>(kv.first),
+        ok = ok && fprintf(f, "%016llx %d %d %d %d %d %d %d %.4f\n", static_cast<unsigned long long>(kv.first),
                            t.dp16_variant, t.dp16_ctas_per_sm, t.dp32_ctas_per_sm, t.wide_direct, t.overlap_waves,
-                           t.item_order, static_cast<double>(t.ms)) > 0;
+                           t.item_order, t.strip_width, static_cast<double>(t.ms)) > 0;
     }
     ok = (fclose(f) == 0) && ok;
     return ok ? MP_OK : MP_EINVAL;
@@ -1439,7 +1569,7 @@ int mp_dp_tuning_load(mp_dp_ctx *c, const char *path)
     if (!f) return MP_EINVAL;
     char name[256] = {0};
     int version = 0, sms = 0;
-    if (fscanf(f, "mp_dp_tuning %d %255s %d", &version, name, &sms) != 3 || version != 3 ||
+    if (fscanf(f, "mp_dp_tuning %d %255s %d", &version, name, &sms) != 3 || version != 4 ||
         c->dev_name != name || sms != c->num_sms) {
         fclose(f);
         return MP_EINVAL;
@@ -1449,12 +1579,12 @@ int mp_dp_tuning_load(mp_dp_ctx *c, const char *path)
         unsigned long long key = 0;
         mp_dp_tuning t{};
         double ms = 0;
-        const int k = fscanf(f, "%llx %d %d %d %d %d %d %lf", &key, &t.dp16_variant, &t.dp16_ctas_per_sm,
-                             &t.dp32_ctas_per_sm, &t.wide_direct, &t.overlap_waves, &t.item_order, &ms);
+        const int k = fscanf(f, "%llx %d %d %d %d %d %d %d %lf", &key, &t.dp16_variant, &t.dp16_ctas_per_sm,
+                             &t.dp32_ctas_per_sm, &t.wide_direct, &t.overlap_waves, &t.item_order, &t.strip_width, &ms);
         if (k == EOF) break;
-        if (k != 8 || t.item_order < 0 || t.item_order > 1 || t.dp16_variant < 0 || t.dp16_variant >= kDp16Variants || t.dp16_ctas_per_sm < 0 ||
-            t.dp32_ctas_per_sm < 0 || t.wide_direct < 0 || t.wide_direct > 1 || t.overlap_waves < 0 ||
-            t.overlap_waves > 1) {
+        if (k != 9 || t.item_order < 0 || t.item_order > 1 || t.dp16_variant < 0 || t.dp16_variant >= kDp16Variants ||
+            t.dp16_ctas_per_sm < 0 || t.dp32_ctas_per_sm < 0 || t.wide_direct < 0 || t.wide_direct > 1 ||
+            t.overlap_waves < 0 || t.overlap_waves > 1 || t.strip_width < 0 || t.strip_width > 1) {
             fclose(f);
             return MP_EINVAL;
         }
@@ -1632,7 +1762,8 @@ static int exon_rescore_impl(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_re
         j.strand = q.strand;
         j.i0 = static_cast<int32_t>(i0);
         jobs.push_back(j);
-        sub.push_back(mp_pair{q.prot, q.prot_len, nullptr, static_cast<uint32_t>(len), 1, MP_PAIR_SCORE_ONLY});
+        sub.push_back(mp_pair{q.prot, q.prot_len, nullptr, static_cast<uint32_t>(len), 1, MP_PAIR_SCORE_ONLY,
+                              q.profile});
         idx.push_back(k);
         intron.push_back(has_intron ? 1 : 0);
     }
@@ -1724,11 +1855,15 @@ int mp_dp_exon_rescore(mp_dp_ctx *c, const mp_pair *pairs, size_t n, mp_result *
 
 // ================================================================ serving
 // A serving thread turns submitted requests into micro-batches.  Each of
-// n_slots slots owns a private context (stream, arenas) with an equal share
-// of the traceback budget; a request is admitted into the next free slot
-// while the slot's traceback bytes stay within its share, and the slot's
-// pipeline is enqueued at once, so batches formed while others are still on
-// the device run concurrently with them (continuous batching).
+// n_slots slots owns a private context (stream, batch buffers) and, while
+// busy, a range of one traceback arena of the whole budget: requests are
+// admitted in arrival order into the next free slot, up to a slot's share
+// of the budget (a larger request alone, once a range that large is free),
+// and the slot's pipeline is enqueued at once, so batches formed while
+// others are still on the device run concurrently with them (continuous
+// batching).  The request queue is host memory: admission is a host
+// decision taken as ranges free up, and everything a batch runs on (its
+// arena range, sequences, plan and results) is on the device.
 struct Slot {
     mp_dp_ctx *ctx = nullptr;
     mp_dp_batch *batch = nullptr;
@@ -1736,7 +1871,50 @@ struct Slot {
     std::vector<std::chrono::steady_clock::time_point> t_submit;
     std::vector<mp_result> res;
     bool busy = false;
+    uint64_t off = 0, len = 0;          // the slot's range of the shared traceback arena while busy
 };
+
+// Traceback bytes a request may need, whichever strip form its run takes
+// (0 for score-only requests).
+static uint64_t request_bytes(const BoundTable &bt, const Request &r)
+{
+    if (r.flags & MP_PAIR_SCORE_ONLY) return 0;
+    const uint32_t m = static_cast<uint32_t>(r.prot.size()), n = static_cast<uint32_t>(r.nt.size());
+    const bool wide = (r.profile.empty() ? score_bound(bt, r.prot.data(), m, kOverflowT)
+                                         : profile_score_bound(r.profile.data(), m)) >= kOverflowT;
+    return div_up(std::max(code_bytes(m, n, wide, false), code_bytes(m, n, wide, !wide)), 256) * 256;
+}
+
+// Lowest offset of a free range of `len` bytes in [0, cap) beside the busy
+// slots' ranges, or UINT64_MAX.
+static uint64_t arena_fit(const std::vector<Slot> &slots, uint64_t cap, uint64_t len)
+{
+    std::vector<std::pair<uint64_t, uint64_t>> used;
+    for (const Slot &s : slots)
+        if (s.busy && s.len) used.push_back({s.off, s.off + s.len});
+    std::sort(used.begin(), used.end());
+    uint64_t at = 0;
+    for (const auto &u : used) {
+        if (u.first >= at + len) return at;
+        at = std::max(at, u.second);
+    }
+    return at + len <= cap ? at : UINT64_MAX;
+}
+
+// Largest free range beside the busy slots' ranges.
+static uint64_t arena_largest_gap(const std::vector<Slot> &slots, uint64_t cap)
+{
+    std::vector<std::pair<uint64_t, uint64_t>> used;
+    for (const Slot &s : slots)
+        if (s.busy && s.len) used.push_back({s.off, s.off + s.len});
+    std::sort(used.begin(), used.end());
+    uint64_t at = 0, best = 0;
+    for (const auto &u : used) {
+        if (u.first > at) best = std::max(best, u.first - at);
+        at = std::max(at, u.second);
+    }
+    return std::max(best, cap > at ? cap - at : 0);
+}
 
 static void finish_slot(mp_dp_ctx *c, Slot &s, bool ok)
 {
@@ -1764,6 +1942,7 @@ static void finish_slot(mp_dp_ctx *c, Slot &s, bool ok)
     }
     c->cv_done.notify_all();
     s.busy = false;
+    s.len = 0;
     s.tickets.clear();
 }
 
@@ -1774,7 +1953,7 @@ static void serve_loop(mp_dp_ctx *c)
     bool init_ok = true;
     for (auto &s : slots) {
         mp_dp_params p = c->params;
-        p.tb_budget_bytes = c->slot_budget;
+        p.tb_budget_bytes = c->budget;
         p.max_pairs_per_launch = 0;
         p.autotune = 0;
         if (mp_dp_init(&s.ctx, &p, c->device) != MP_OK) {
@@ -1785,6 +1964,12 @@ static void serve_loop(mp_dp_ctx *c)
         s.ctx->fixed = c->fixed;
         s.ctx->tuned = c->tuned;
     }
+    // One traceback arena of the whole budget shared by the slots: a
+    // micro-batch is admitted into a free range of it, so the slots' batches
+    // together never hold more than the budget, and one request may take up
+    // to all of it (it then waits until the other slots have drained).
+    DevBuf<uint8_t> arena;
+    if (init_ok && arena.reserve(std::max<uint64_t>(c->budget, 256)) != cudaSuccess) init_ok = false;
     std::vector<Request> take;
     for (;;) {
         bool progressed = false;
@@ -1798,24 +1983,29 @@ static void serve_loop(mp_dp_ctx *c)
         // admit queued requests into free slots
         const BoundTable bt(c->sp);
         for (auto &s : slots) {
-            if (s.busy || !init_ok) continue;
+            if (s.busy) continue;
             take.clear();
+            uint64_t bytes = 0;
             {
                 std::lock_guard<std::mutex> lk(c->mu);
-                uint64_t bytes = 0;
+                // requests in arrival order, up to a slot's share of the budget
+                // (or the first request alone, if larger), within the largest
+                // free range of the arena; the head of the queue waits while
+                // it does not fit
+                const uint64_t room = arena_largest_gap(slots, c->budget);
                 while (!c->queue.empty()) {
                     const Request &r = c->queue.front();
-                    const uint64_t cb = (r.flags & MP_PAIR_SCORE_ONLY)
-                                            ? 0
-                                            : code_bytes(r.prot.size(), r.nt.size(),
-                                                         score_bound(bt, r.prot.data(), r.prot.size(), kOverflowT) >= kOverflowT);
-                    if (!take.empty() && bytes + cb > c->slot_budget) break;
+                    const uint64_t cb = request_bytes(bt, r);
+                    const uint64_t cap = std::min(room, take.empty() ? std::max(cb, c->slot_budget) : c->slot_budget);
+                    if (bytes + cb > cap) break;
                     bytes += cb;
                     take.push_back(std::move(c->queue.front()));
                     c->queue.pop_front();
                 }
             }
             if (take.empty()) break;
+            s.len = std::max<uint64_t>(bytes, 256);
+            s.off = arena_fit(slots, c->budget, s.len);
             std::vector<mp_pair> pairs(take.size());
             for (size_t k = 0; k < take.size(); ++k) {
                 pairs[k].prot = take[k].prot.data();
@@ -1824,6 +2014,7 @@ static void serve_loop(mp_dp_ctx *c)
                 pairs[k].nt_len = static_cast<uint32_t>(take[k].nt.size());
                 pairs[k].strand = take[k].strand;
                 pairs[k].flags = take[k].flags;
+                pairs[k].profile = take[k].profile.empty() ? nullptr : take[k].profile.data();
             }
             s.tickets.clear();
             s.t_submit.clear();
@@ -1834,7 +2025,13 @@ static void serve_loop(mp_dp_ctx *c)
             s.res.assign(take.size(), mp_result{});
             // the slot's batch keeps its device buffers from one micro-batch to the next
             if (!s.batch) s.batch = new (std::nothrow) mp_dp_batch();
-            bool ok = s.batch && upload_impl(s.ctx, s.batch, pairs.data(), pairs.size()) == MP_OK;
+            bool ok = init_ok && s.off != UINT64_MAX;
+            if (ok) {
+                s.ctx->codes_ext = arena.p + s.off;
+                s.ctx->codes_ext_cap = s.len;
+                s.ctx->budget = s.len;
+            }
+            ok = ok && s.batch && upload_impl(s.ctx, s.batch, pairs.data(), pairs.size()) == MP_OK;
             if (ok) ok = mp_dp_batch_run(s.ctx, s.batch) == MP_OK;
             s.busy = true;
             if (!ok) finish_slot(c, s, false);
@@ -1858,6 +2055,7 @@ static void serve_loop(mp_dp_ctx *c)
         if (s.batch) mp_dp_batch_free(s.ctx, s.batch);
         if (s.ctx) mp_dp_destroy(s.ctx);
     }
+    arena.release();
 }
 
 extern "C" int mp_dp_submit(mp_dp_ctx *c, const mp_pair *q, uint64_t *ticket)
@@ -1868,18 +2066,17 @@ extern "C" int mp_dp_submit(mp_dp_ctx *c, const mp_pair *q, uint64_t *ticket)
     std::unique_lock<std::mutex> lk(c->mu);
     if (c->slot_budget == 0) c->slot_budget = c->budget / static_cast<uint64_t>(c->n_slots);
     const BoundTable bt(c->sp);
-    if (!(q->flags & MP_PAIR_SCORE_ONLY) &&
-        code_bytes(q->prot_len, q->nt_len, score_bound(bt, q->prot, q->prot_len, kOverflowT) >= kOverflowT) >
-            c->slot_budget)
-        return MP_EBUDGET;
-    if (c->stopping) return MP_ESTATE;
-    if (c->queue.size() >= c->ring_cap) return MP_EAGAIN;
     Request r;
-    r.ticket = c->next_ticket++;
     r.prot.assign(q->prot, q->prot_len);
     r.nt.assign(q->nt, q->nt_len);
-    r.strand = q->strand;
     r.flags = q->flags;
+    if (q->profile) r.profile.assign(q->profile, q->profile + q->prot_len + 1);
+    // a request is served if its traceback fits the whole budget
+    if (request_bytes(bt, r) > c->budget) return MP_EBUDGET;
+    if (c->stopping) return MP_ESTATE;
+    if (c->queue.size() >= c->ring_cap) return MP_EAGAIN;
+    r.ticket = c->next_ticket++;
+    r.strand = q->strand;
     r.t_submit = std::chrono::steady_clock::now();
     *ticket = r.ticket;
     c->inflight.insert(r.ticket);

@@ -280,7 +280,7 @@ __device__ __forceinline__ void col0_row(T *v, const Col0Ctx &c, int rd, int aa)
 
 __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *pairs, uint32_t n_pairs,
                                                                  const uint32_t *nt2, const ScoreParams sp,
-                                                                 int32_t *col0)
+                                                                 const ProfPos *prof, int32_t *col0)
 {
     __shared__ int16_t s_don[125], s_acc[125];
     for (int k = threadIdx.x; k < 125; k += blockDim.x) {
@@ -297,7 +297,10 @@ __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *p
         const PairDesc pd = pairs[p];
         if (pd.flags & PF_SKIP) continue;
         const int n = static_cast<int>(pd.nt_len);
-        const Col0Ctx c{nt2 + pd.nt_word_off, n, sp.q + sp.e, sp.e, sp.f, sp.r};
+        // column 0's D runs take the gap costs of column 0 (a profile's position 0)
+        const bool pq = (pd.flags & PF_PROF) != 0;
+        const int q0 = pq ? prof[pd.prof_off].q : sp.q, e0 = pq ? prof[pd.prof_off].e : sp.e;
+        const Col0Ctx c{nt2 + pd.nt_word_off, n, q0 + e0, e0, sp.f, sp.r};
         int32_t *h = col0 + pd.col0_off;
         const int L = (n + 31) / 32;
         const int r0 = lane * L + 1, r1 = min(n, (lane + 1) * L);     // this lane's rows (none if r0 > r1)
@@ -374,12 +377,12 @@ __global__ void __launch_bounds__(kCol0Warps * 32) col0_kernel(const PairDesc *p
 }
 }  // namespace
 
-cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, const ScoreParams &sp, int32_t *col0,
-                        cudaStream_t st)
+cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, const ScoreParams &sp,
+                        const ProfPos *prof, int32_t *col0, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
     const uint32_t blocks = (n + kCol0Warps - 1) / kCol0Warps;
-    col0_kernel<<<blocks < 4096 ? blocks : 4096, kCol0Warps * 32, 0, st>>>(pairs, n, nt2, sp, col0);
+    col0_kernel<<<blocks < 4096 ? blocks : 4096, kCol0Warps * 32, 0, st>>>(pairs, n, nt2, sp, prof, col0);
     return cudaGetLastError();
 }
 

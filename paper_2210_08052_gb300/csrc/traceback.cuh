@@ -30,26 +30,51 @@ struct PairView {
     const uint8_t *base;
     size_t strip_bytes;
     bool wide;               // int32 stream (4 B per cell)
-    const uint8_t *colmax;   // per strip, chunk and lane: the chunk's maximum H of the lane's two cells
+    const uint8_t *colmax;   // per strip, chunk and lane: the chunk's maximum H of the lane's cells
     int nchunks;
+    bool w128;               // 128-residue strips (four cells per lane) instead of 64 (two)
     const uint32_t *g;       // packed genome
     const uint8_t *P;        // residue codes
     int n, m;
     const ScoreParams *sp;
     const int8_t *mat;       // shared-memory copy of sp->mat
     const int32_t *c0;       // anchored modes: column 0 (H[i][0]); null in local mode
+    const ProfPos *pf;       // profile queries: positions 0..m; null otherwise
+    const int32_t *ep;       // profile queries: gap-extension prefix sums per position
+
+    // cost of an I run over residues j-k+1 .. j (open at the first, extension at each)
+    __device__ __forceinline__ int gap_i(int j, int k) const
+    {
+        if (pf) return pf[j - k + 1].q + (__ldg(ep + j) - __ldg(ep + j - k));
+        return sp->q + sp->e * k;
+    }
+    // cost of a D run of k codons in column j
+    __device__ __forceinline__ int gap_d(int j, int k) const
+    {
+        if (pf) return pf[j].q + pf[j].e * k;
+        return sp->q + sp->e * k;
+    }
 
     __device__ __forceinline__ int H(int i, int j) const
     {
         if (i < 0 || j < 0) return kNeg;
         if (c0) {
             // anchored modes: row 0 is an I run from (0, 0); column 0 precomputed
-            if (i == 0) return j == 0 ? 0 : -(sp->q + sp->e * j);
+            if (i == 0) return j == 0 ? 0 : -gap_i(j, j);
             if (j == 0) return __ldg(c0 + i);
         } else if (i == 0 || j == 0) {
             return 0;
         }
         const int ii = i - 1, jj = j - 1;
+        if (w128) {
+            // lane r/4 stores 16 B every two steps: [a(t), b(t), a(t+1), b(t+1)],
+            // a = residues 4l, 4l+1 and b = 4l+2, 4l+3 as biased 16-bit halves
+            const int s = jj >> 7, r = jj & 127, t = ii + r;
+            const uint32_t w = ld_tb<Coherent>(reinterpret_cast<const uint32_t *>(
+                base + static_cast<size_t>(s) * strip_bytes + static_cast<size_t>(t >> 1) * 512 + (r >> 2) * 16 +
+                (t & 1) * 8 + ((r >> 1) & 1) * 4));
+            return static_cast<int>((r & 1) ? (w >> 16) : (w & 0xffffu)) - 32768;
+        }
         const int s = jj >> 6, r = jj & 63, t = ii + r;
         if (wide) {
             return ld_tb<Coherent>(reinterpret_cast<const int *>(base + static_cast<size_t>(s) * strip_bytes +
@@ -64,6 +89,13 @@ struct PairView {
     // maximum H over chunk c of residue j (steps c*kChunk .. c*kChunk+kChunk-1)
     __device__ __forceinline__ int cmax(int c, int j) const
     {
+        if (w128) {
+            // one [a, b] pair of words per strip, chunk and lane
+            const int jj = j - 1, s = jj >> 7, r = jj & 127;
+            const size_t e = (static_cast<size_t>(s) * nchunks + c) * 32 + (r >> 2);
+            const uint32_t w = ld_tb<Coherent>(reinterpret_cast<const uint32_t *>(colmax) + 2 * e + ((r >> 1) & 1));
+            return static_cast<int>((r & 1) ? (w >> 16) : (w & 0xffffu)) - 32768;
+        }
         const int jj = j - 1, s = jj >> 6, r = jj & 63;
         const size_t e = (static_cast<size_t>(s) * nchunks + c) * 32 + (r >> 1);
         if (wide) return ld_tb<Coherent>(reinterpret_cast<const int *>(colmax) + 2 * e + (r & 1));
@@ -92,6 +124,7 @@ struct PairView {
     {
         if (i < 3 || i > n) return kNeg;
         const int aa = c_code.v[b(i - 2) * 16 + b(i - 1) * 4 + b(i)];
+        if (pf) return pf[j].s[aa];
         if (aa == 20) return -sp->stop;
         return mat[aa * 22 + P[j - 1]];
     }
@@ -143,7 +176,7 @@ template <bool Coherent, typename Pred>
 __device__ __forceinline__ int scan_column(const PairView<Coherent> &v, int jc, int xhi, int thr, int lane, Pred pred)
 {
     if (xhi < 1 || jc < 1) return 0;
-    const int r = (jc - 1) & 63;
+    const int r = (jc - 1) & (v.w128 ? 127 : 63);
     const int c_lo = r / kChunk, c_hi = (xhi - 1 + r) / kChunk;
     for (int cb = c_hi; cb >= c_lo; cb -= 32) {
         const int c = cb - lane;
@@ -177,14 +210,18 @@ __device__ __forceinline__ PairView<Coherent> make_view(const TBArgs &a, const P
                                               const int8_t *mat_s)
 {
     const int n = static_cast<int>(pd.nt_len);
-    const int nchunks = (n + kStripW - 1 + kChunk - 1) / kChunk;
+    const int W = strip_w_of(pd.flags);
+    const int nchunks = (n + W - 1 + kChunk - 1) / kChunk;
     const bool wide = (o.status & kStInt32Stream) != 0;
-    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * kStepBytes * (wide ? 2 : 1);
+    // 2 bytes per cell (4 for the int32 stream), W cells per step
+    const size_t strip_bytes = static_cast<size_t>(nchunks) * kChunk * W * 2 * (wide ? 2 : 1);
     const bool anchored = a.sp.mode != MP_MODE_LOCAL;
     return PairView<Coherent>{a.codes + pd.code_off, strip_bytes, wide,
-                    a.codes + pd.code_off + static_cast<size_t>(pd.n_strips) * strip_bytes, nchunks,
+                    a.codes + pd.code_off + static_cast<size_t>(pd.n_strips) * strip_bytes, nchunks, W == kStripWMax,
                     a.nt2 + pd.nt_word_off, a.prot + pd.prot_off, n, static_cast<int>(pd.prot_len),
-                    &a.sp, mat_s, anchored ? a.col0 + pd.col0_off : nullptr};
+                    &a.sp, mat_s, anchored ? a.col0 + pd.col0_off : nullptr,
+                    (pd.flags & PF_PROF) ? a.prof + pd.prof_off : nullptr,
+                    (pd.flags & PF_PROF) ? a.epre + pd.prof_off : nullptr};
 }
 
 template <bool Coherent>
@@ -260,16 +297,19 @@ __device__ void trace_pair(const TBArgs &a, const int8_t *mat_s, uint32_t p, int
         } else if (i <= 0 || j <= 0 || h <= 0) {
             break;                                           // restart wins a tie at 0
         }
-        // I: residues against no genome
-        const int kgap = (hmax - q - h) / e;
+        // I: residues against no genome (runs longer than kgap cannot reach
+        // h from an H of at most hmax: every step costs at least e, or 1 in a
+        // profile)
+        const int kgap = v.pf ? hmax - h : (hmax - q - h) / e;
         int k = kgap >= 1 ? first_hit(j < kgap ? j : kgap, lane,
-                                      [&](int kk) { return v.H(i, j - kk) - q - e * kk == h; })
+                                      [&](int kk) { return v.H(i, j - kk) - v.gap_i(j, kk) == h; })
                           : 0;
         if (k) { if (lane == 0) w.push(MP_OP_I, k); j -= k; continue; }
         // D: codons against no residue
-        k = kgap >= 1 ? first_hit(i / 3 < kgap ? i / 3 : kgap, lane,
-                                  [&](int kk) { return v.H(i - 3 * kk, j) - q - e * kk == h; })
-                      : 0;
+        const int kgd = v.pf ? (hmax - v.pf[j].q - h) / v.pf[j].e : kgap;
+        k = kgd >= 1 ? first_hit(i / 3 < kgd ? i / 3 : kgd, lane,
+                                 [&](int kk) { return v.H(i - 3 * kk, j) - v.gap_d(j, kk) == h; })
+                     : 0;
         if (k) { if (lane == 0) w.push(MP_OP_D, k); i -= 3 * k; continue; }
         // frameshifts
         if (v.H(i - 1, j - 1) - f == h) { if (lane == 0) w.push(MP_OP_F, 1); i -= 1; j -= 1; continue; }

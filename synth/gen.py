@@ -50,6 +50,7 @@ class Pair:
     strand: int = 1         # +1, or -1: the gene lies on the reverse complement of nt
     score_only: bool = False
     truth: dict = field(default_factory=dict)
+    profile: object = None  # optional position-specific costs of a profile query: (|P| + 1) x 23 ints
 
     @property
     def cells(self) -> int:

@@ -53,10 +53,11 @@ def test_struct_layout_matches_header(mp, tmp_path):
     src.write_text("""#include <stdio.h>
 #include <stddef.h>
 #include "mp_dp.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mp_result), sizeof(mp_pair),
- sizeof(mp_dp_params), sizeof(mp_dp_stats), offsetof(mp_result, cigar), offsetof(mp_pair, strand),
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mp_result),
+ sizeof(mp_pair), sizeof(mp_dp_params), sizeof(mp_dp_stats), offsetof(mp_result, cigar), offsetof(mp_pair, strand),
  offsetof(mp_dp_params, tb_budget_bytes), offsetof(mp_dp_params, autotune), sizeof(mp_dp_tuning),
- offsetof(mp_dp_tuning, ms)); return 0;}""")
+ offsetof(mp_dp_tuning, ms), offsetof(mp_dp_tuning, strip_width), offsetof(mp_pair, profile),
+ sizeof(mp_profile_pos), offsetof(mp_profile_pos, gap_ext)); return 0;}""")
     exe = tmp_path / "sz"
     import subprocess
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
@@ -64,7 +65,8 @@ int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mp_re
     want = [ctypes.sizeof(mp.mp_result), ctypes.sizeof(mp.mp_pair), ctypes.sizeof(mp.mp_dp_params),
             ctypes.sizeof(mp.mp_dp_stats), mp.mp_result.cigar.offset, mp.mp_pair.strand.offset,
             mp.mp_dp_params.tb_budget_bytes.offset, mp.mp_dp_params.autotune.offset,
-            ctypes.sizeof(mp.mp_dp_tuning), mp.mp_dp_tuning.ms.offset]
+            ctypes.sizeof(mp.mp_dp_tuning), mp.mp_dp_tuning.ms.offset, mp.mp_dp_tuning.strip_width.offset,
+            mp.mp_pair.profile.offset, ctypes.sizeof(mp.mp_profile_pos), mp.mp_profile_pos.gap_ext.offset]
     assert got == want
 
 

@@ -142,6 +142,44 @@ def test_sizes_across_strips_and_chunks(mp, ctx, ctx32, orc):
     assert [{k: g[k] for k in KEYS} for g in got32] == [{k: g[k] for k in KEYS} for g in got]
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_wide_strips_match_oracle(mp, orc, mode):
+    """Pairs run in 128-residue strips (four residues per lane) give the
+    oracle's score, coordinates and CIGAR in every mode: proteins of 1 to
+    1,200 residues (one to ten 128-residue strips, ragged last strips, and
+    the lengths that stay in 64-residue strips), regions spanning many
+    chunks, both strands, score-only pairs among them."""
+    rng = np.random.default_rng(160 + mode)
+    pairs = []
+    for m in list(rng.integers(1, 1200, size=40)) + [64, 65, 128, 129, 256, 257, 1152]:
+        prot = synth.random_protein(rng, int(m))
+        lens = [int(rng.integers(40, 700)) for _ in range(int(rng.integers(0, 3)))]
+        flank = 30 if mode else 400
+        region, _ = synth.gen.plant_gene(rng, prot, float(rng.uniform(0.05, 0.35)), int(rng.integers(0, 3)), lens,
+                                         int(rng.integers(0, flank)), int(rng.integers(0, flank)), 0.45)
+        strand = 1
+        if rng.random() < 0.5:
+            region, strand = synth.revcomp(region), -1
+        pairs.append(synth.Pair(prot, region, strand, score_only=bool(rng.random() < 0.1)))
+    params = mp.mp_dp_default_params(mode=mode)
+    op = _orc_params(orc, params)
+    op.mode = mode
+    c = mp.mp_dp_init(params, 0)
+    try:
+        mp.mp_dp_set_tuning(c, dict(dp16_variant=1, overlap_waves=1, item_order=1, strip_width=1))
+        for _ in range(2):                                # direct, then graph replay
+            got = mp.mp_dp_align_batch(c, pairs)
+            bad = []
+            for k, (p, g) in enumerate(zip(pairs, got)):
+                w = orc.align(p.prot, p.nt, p.strand, op)
+                keys = ("score", "prot_en") if p.score_only and mode != 1 else KEYS
+                if any(g[x] != w[x] for x in keys) or g["status"] & 0xF0:
+                    bad.append((k, len(p.prot), len(p.nt), [x for x in keys if g[x] != w[x]], g["status"]))
+            assert not bad, bad[:5]
+    finally:
+        mp.mp_dp_destroy(c)
+
+
 def test_boundary_lengths(mp, ctx, orc):
     """Protein lengths at strip edges and regions at chunk edges."""
     rng = np.random.default_rng(3)
@@ -438,18 +476,20 @@ def _anchored_pairs(seed, count, mmax):
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("force_int32", [0, 1])
-def test_stored_h_matches_oracle(mp, orc, mode, force_int32):
+@pytest.mark.parametrize("kernel", ["int16", "int16-w128", "int32"])
+def test_stored_h_matches_oracle(mp, orc, mode, kernel):
     """Every stored H value of Eq. 7 (read back from the traceback stream,
     with the mode's row 0 and column 0) equals the oracle's H matrix, cell
     by cell, for pairs spanning several strips and chunks, both strands,
-    in the int16 and int32 kernels."""
-    pairs = _anchored_pairs(140 + mode, 6, 150)
-    params = mp.mp_dp_default_params(mode=mode, force_int32=force_int32)
+    in the int16 kernel (64- and 128-residue strips) and the int32 kernel."""
+    pairs = _anchored_pairs(140 + mode, 6, 300 if kernel == "int16-w128" else 150)
+    params = mp.mp_dp_default_params(mode=mode, force_int32=1 if kernel == "int32" else 0)
     op = _orc_params(orc, params)
     op.mode = mode
     c = mp.mp_dp_init(params, 0)
     try:
+        if kernel == "int16-w128":
+            mp.mp_dp_set_tuning(c, dict(dp16_variant=1, overlap_waves=1, item_order=1, strip_width=1))
         b = mp.mp_dp_batch_upload(c, pairs)
         mp.mp_dp_batch_run(c, b)
         mp.mp_dp_batch_sync(c)
@@ -654,6 +694,48 @@ def test_serving_alone_and_in_mix(mp, ctx):
         mp.mp_dp_destroy(c)
 
 
+def test_serving_admits_requests_up_to_the_whole_budget(mp, orc):
+    """A request whose traceback exceeds a third of the budget (a slot's
+    share) but fits the whole budget is served, alone and among small
+    requests, with the batch call's result; one beyond the budget is
+    refused with MP_EBUDGET."""
+    rng = np.random.default_rng(77)
+    prot = synth.random_protein(rng, 900)
+    big, _ = synth.gen.plant_gene(rng, prot, 0.2, 1, [700, 2500], 3000, 3000, 0.4)
+    big_pair = synth.Pair(prot, big, 1)
+    # traceback bytes of the big pair: about 2 bytes per cell (here ~ 28 MB)
+    budget = int(2.6 * big_pair.cells) + (4 << 20)
+    assert 2 * big_pair.cells > budget / 3
+    small = _gene_pairs(91, 30, 120, 300)
+    params = mp.mp_dp_default_params(tb_budget_bytes=budget)
+    c = mp.mp_dp_init(params, 0)
+    try:
+        want = mp.mp_dp_align_batch(c, [big_pair] + small)
+        t = mp.mp_dp_submit(c, big_pair)
+        r = mp.mp_dp_poll(c, t, 60_000_000)
+        assert r is not None and {x: r[x] for x in KEYS} == {x: want[0][x] for x in KEYS}
+        assert r["status"] & 0xF0 == 0
+        tickets = [mp.mp_dp_submit(c, p) for p in small[:10]] + [mp.mp_dp_submit(c, big_pair)] + \
+                  [mp.mp_dp_submit(c, p) for p in small[10:]]
+        got = {}
+        while len(got) < len(tickets):
+            x = mp.mp_dp_wait_any(c, 30_000_000)
+            assert x is not None
+            got[x[0]] = x[1]
+        order = small[:10] + [big_pair] + small[10:]
+        refs = want[1:11] + [want[0]] + want[11:]
+        for tk, r in zip(tickets, refs):
+            assert {x: got[tk][x] for x in KEYS} == {x: r[x] for x in KEYS}
+        w = orc.align(big_pair.prot, big_pair.nt, 1)
+        assert {x: want[0][x] for x in KEYS} == {x: w[x] for x in KEYS}
+        huge = synth.Pair(prot + prot, big + big, 1)
+        with pytest.raises(mp.MPError):
+            mp.mp_dp_submit(c, huge)
+        assert len(order) == len(tickets)
+    finally:
+        mp.mp_dp_destroy(c)
+
+
 def test_cooperating_wait_runs_out_without_fault(mp, ctx, orc):
     """Failure detection without a GPU fault: with every boundary row
     withheld, each warp waiting on the previous strip of its pair gives up
@@ -672,5 +754,94 @@ def test_cooperating_wait_runs_out_without_fault(mp, ctx, orc):
         again = mp.mp_dp_align_batch(ctx, pairs)
         _compare(orc, pairs[:6], again[:6])
         assert any(len(p.prot) > 64 for p in pairs) and any(len(p.prot) <= 64 for p in pairs)
+    finally:
+        mp.mp_dp_destroy(c)
+
+
+def _profile_for(orc, rng, prot, diag=None, jitter=2):
+    """A profile query for `prot`: BLOSUM62's row of each residue perturbed
+    per position (diag: the residue's own score replaced by that value), a
+    stop-codon score, and random gap costs per column."""
+    B = orc.blosum62_22()
+    m = len(prot)
+    prof = np.zeros((m + 1, 23), dtype=np.int32)
+    for j in range(1, m + 1):
+        pc = orc.AA.index(prot[j - 1]) if prot[j - 1] in orc.AA else 21
+        prof[j, :20] = B[:20, pc] + rng.integers(-jitter, jitter + 1, size=20)
+        if diag is not None and pc < 20:
+            prof[j, pc] = diag
+        prof[j, 20] = -int(rng.integers(10, 25))
+    prof[:, 21] = rng.integers(4, 16, size=m + 1)
+    prof[:, 22] = rng.integers(1, 4, size=m + 1)
+    return prof
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_profile_queries_match_oracle(mp, orc, mode):
+    """Profile queries (position-specific substitution scores and gap costs)
+    give the oracle's score, coordinates and CIGAR in every mode, in the
+    int16 kernel and the int32 kernel, with pseudogene-aware rescoring in
+    local mode; a profile holding the default scoring reproduces the
+    unprofiled results; a pair whose profile can pass the int16 range is
+    re-run exactly; a profile whose scores break the intron rule is
+    refused."""
+    rng = np.random.default_rng(180 + mode)
+    pairs = []
+    for k in range(36):
+        m = int(rng.integers(1, 320))
+        prot = synth.random_protein(rng, m)
+        lens = [int(rng.integers(40, 600)) for _ in range(int(rng.integers(0, 3)))]
+        flank = 30 if mode else 300
+        region, _ = synth.gen.plant_gene(rng, prot, float(rng.uniform(0.05, 0.35)), int(rng.integers(0, 3)), lens,
+                                         int(rng.integers(0, flank)), int(rng.integers(0, flank)), 0.45)
+        strand = 1
+        if rng.random() < 0.5:
+            region, strand = synth.revcomp(region), -1
+        pairs.append(synth.Pair(prot, region, strand, profile=_profile_for(orc, rng, prot)))
+    # a profile whose scores can pass the int16 range (re-run in int32)
+    prot = synth.random_protein(rng, 420)
+    region, _ = synth.gen.plant_gene(rng, prot, 0.0, 0, [300], 50, 50, 0.45)
+    pairs.append(synth.Pair(prot, region, 1, profile=_profile_for(orc, rng, prot, diag=80)))
+    # the default scoring as a profile
+    plain = _gene_pairs(181, 8, 200, 500)
+    base = mp.mp_dp_default_params(mode=mode)
+    op = _orc_params(orc, base)
+    op.mode = mode
+    for p in plain:
+        pairs.append(synth.Pair(p.prot, p.nt, p.strand, profile=orc.profile_of(p.prot, op)))
+    for force in (0, 1):
+        params = mp.mp_dp_default_params(mode=mode, force_int32=force, exon_rescore=1 if mode == 0 else 0)
+        c = mp.mp_dp_init(params, 0)
+        try:
+            got = mp.mp_dp_align_batch(c, pairs)
+            ref_plain = mp.mp_dp_align_batch(c, plain)
+        finally:
+            mp.mp_dp_destroy(c)
+        bad = []
+        for k, (p, g) in enumerate(zip(pairs, got)):
+            pp = orc.make_params(mode=mode, prof=p.profile)
+            w = orc.align(p.prot, p.nt, p.strand, pp)
+            if any(g[x] != w[x] for x in KEYS) or g["status"] & 0xF0:
+                bad.append((k, len(p.prot), [x for x in KEYS if g[x] != w[x]], g["status"]))
+            elif mode == 0 and g["exon_score"] != orc.exon_score(p.prot, p.nt, p.strand, pp, w):
+                bad.append((k, "exon_score", g["exon_score"]))
+        assert not bad, (force, bad[:5])
+        for g, r in zip(got[-len(plain):], ref_plain):
+            assert {x: g[x] for x in KEYS} == {x: r[x] for x in KEYS}
+        if not force and mode == 0:
+            # local mode runs it in int16 first (the anchored modes send it to int32 at once)
+            assert got[-len(plain) - 1]["status"] & mp.MP_ST_RERUN
+    # serving takes the profile with the request
+    c = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode), 0)
+    try:
+        for p in pairs[:3]:
+            t = mp.mp_dp_submit(c, p)
+            r = mp.mp_dp_poll(c, t, 30_000_000)
+            w = orc.align(p.prot, p.nt, p.strand, orc.make_params(mode=mode, prof=p.profile))
+            assert {x: r[x] for x in KEYS} == {x: w[x] for x in KEYS}
+        bad_prof = pairs[0].profile.copy()
+        bad_prof[1, 3] = -40                       # r = 29 must exceed every negated score
+        with pytest.raises(mp.MPError):
+            mp.mp_dp_align_batch(c, [synth.Pair(pairs[0].prot, pairs[0].nt, pairs[0].strand, profile=bad_prof)])
     finally:
         mp.mp_dp_destroy(c)

@@ -2,7 +2,8 @@
 
 Every configuration the tuner may pick (both int16 kernel builds, each CTA
 count per SM it tries, int16-first or int32-at-once for pairs whose score
-bound reaches the int16 limit, both item orders; the wave policies are
+bound reaches the int16 limit, both item orders, 64- or 128-residue strips
+for int16 pairs; the wave policies are
 covered by the parity tests) must give the oracle's results bit-exactly;
 the tuner must pick one of its timed candidates and keep it per shape class,
 and its table must survive a save/load round trip.
@@ -69,12 +70,13 @@ def _same(got, want):
 @pytest.mark.parametrize("ctas", [0, 1, 2])
 @pytest.mark.parametrize("wide_direct", [0, 1])
 @pytest.mark.parametrize("item_order", [0, 1])
-def test_every_configuration_matches_oracle(mp, mixed, variant, ctas, wide_direct, item_order):
+@pytest.mark.parametrize("strip_width", [0, 1])
+def test_every_configuration_matches_oracle(mp, mixed, variant, ctas, wide_direct, item_order, strip_width):
     pairs, want = mixed
     ctx = mp.mp_dp_init(None, 0)
     try:
         mp.mp_dp_set_tuning(ctx, dict(dp16_variant=variant, dp16_ctas_per_sm=ctas, dp32_ctas_per_sm=ctas,
-                                      wide_direct=wide_direct, item_order=item_order))
+                                      wide_direct=wide_direct, item_order=item_order, strip_width=strip_width))
         for _ in range(3):                          # direct, then graph capture and replay
             got = mp.mp_dp_align_batch(ctx, pairs)
             _same(got, want)
@@ -96,7 +98,8 @@ def test_autotune_picks_a_timed_candidate_and_keeps_results(mp, mixed, tmp_path)
         assert len(tried) >= 4 and all(t["ms"] > 0 for t in tried)
         assert best["ms"] == min(t["ms"] for t in tried)
         strip = lambda t: {k: t[k] for k in ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct",
-                                             "overlap_waves", "item_order")}
+                                             "overlap_waves", "item_order", "strip_width")}
+        assert {t["strip_width"] for t in tried} == {0, 1}
         assert strip(best) in [strip(t) for t in tried]
         assert {t["wide_direct"] for t in tried} == {0, 1}         # the batch has wide pairs
         # the batch holds the results of the tuning runs
@@ -143,7 +146,8 @@ def test_tuning_arguments_checked(mp, tmp_path):
     L = mp.lib()
     try:
         for bad in (dict(dp16_variant=2), dict(dp16_variant=-1), dict(wide_direct=2), dict(dp16_ctas_per_sm=-1),
-                    dict(dp32_ctas_per_sm=-3), dict(overlap_waves=2), dict(item_order=-1)):
+                    dict(dp32_ctas_per_sm=-3), dict(overlap_waves=2), dict(item_order=-1), dict(strip_width=2),
+                    dict(strip_width=-1)):
             with pytest.raises(mp.MPError):
                 mp.mp_dp_set_tuning(ctx, bad)
         mp.mp_dp_set_tuning(ctx, dict(dp16_ctas_per_sm=99))       # clamped at launch
@@ -152,7 +156,7 @@ def test_tuning_arguments_checked(mp, tmp_path):
         assert all(g["status"] & 0xF0 == 0 for g in got)
         mp.mp_dp_set_tuning(ctx, None)
         bad_file = tmp_path / "other.txt"
-        bad_file.write_text("mp_dp_tuning 3 Some_Other_GPU 7\n0000000000000001 0 3 2 0 1 1 1.0\n")
+        bad_file.write_text("mp_dp_tuning 4 Some_Other_GPU 7\n0000000000000001 0 3 2 0 1 1 0 1.0\n")
         assert L.mp_dp_tuning_load(ctx, str(bad_file).encode()) == mp.MP_EINVAL
         assert L.mp_dp_tuning_load(ctx, str(tmp_path / "missing.txt").encode()) == mp.MP_EINVAL
     finally:
