@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "chain.c")]
 
 AA = "ARNDCQEGHILKMFPSTWYV*X"
 OP_NAMES = "MIDFGNUV"
@@ -121,9 +122,9 @@ _lib = None
 def build_oracle(force: bool = False) -> str:
     """Compile oracle.c into a shared library (plain gcc, -O2)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -330,3 +331,98 @@ def acceptor_simple(nt: str, x: int, p: int) -> int:
 
 def revcomp(s: str) -> str:
     return s.upper().translate(str.maketrans("ACGT", "TGCA"))[::-1]
+
+
+# ---------------------------------------------------------- seeding and chaining
+class Chain(ctypes.Structure):
+    _fields_ = [("strand", ctypes.c_int32), ("n_anchors", ctypes.c_int32), ("score", ctypes.c_int64),
+                ("x_first", ctypes.c_int64), ("x_last", ctypes.c_int64),
+                ("y_first", ctypes.c_int64), ("y_last", ctypes.c_int64)]
+
+
+CHAIN_K = 6
+CHAIN_SCALE = 65536
+
+
+def _chain_lib():
+    L = lib()
+    if not hasattr(L, "_chain_ready"):
+        L.orc_phi.argtypes = [ctypes.c_int]
+        L.orc_phi.restype = ctypes.c_int
+        L.orc_psi.argtypes = [ctypes.c_uint64, ctypes.c_int]
+        L.orc_psi.restype = ctypes.c_uint64
+        L.orc_index.argtypes = [ctypes.c_char_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_index.restype = ctypes.c_int64
+        L.orc_gap.argtypes = [ctypes.c_int64, ctypes.c_int64]
+        L.orc_gap.restype = ctypes.c_int64
+        L.orc_gap_penalty.argtypes = [ctypes.c_int64]
+        L.orc_gap_penalty.restype = ctypes.c_int64
+        L.orc_anchors.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.c_int64]
+        L.orc_anchors.restype = ctypes.c_int64
+        L.orc_chain_anchors.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(Chain), ctypes.c_void_p]
+        L.orc_chain_anchors.restype = ctypes.c_int
+        L._chain_ready = True
+    return L
+
+
+def phi(ch: str) -> int:
+    """Reduced-alphabet code of an amino-acid letter (Methods, "Reduced alphabet")."""
+    return _chain_lib().orc_phi(ord(ch))
+
+
+def psi(key: int, bits: int) -> int:
+    """The invertible k-mer hash over [0, 2^bits)."""
+    return _chain_lib().orc_psi(key, bits)
+
+
+def build_index(genome, k: int = CHAIN_K):
+    """The k-mer index of a genome (ASCII str or bytes): (offsets, positions)
+    as a CSR table over all 2^(4k) hash values; each position is
+    strand << 31 | bin (bin = floor(x / 256), x on the strand's own
+    coordinates)."""
+    L = _chain_lib()
+    g = genome.encode() if isinstance(genome, str) else bytes(genome)
+    n = L.orc_index(g, len(g), k, None, None)
+    if n < 0:
+        raise MemoryError("oracle index")
+    offsets = np.zeros((1 << (4 * k)) + 1, dtype=np.uint64)
+    positions = np.zeros(max(n, 1), dtype=np.uint32)
+    L.orc_index(g, len(g), k, offsets.ctypes.data, positions.ctypes.data)
+    return offsets, positions[:n]
+
+
+def anchors(offsets, positions, prot: str, k: int = CHAIN_K) -> np.ndarray:
+    """The anchors (strand, x bin, y residue) of a protein against an index."""
+    L = _chain_lib()
+    pb = prot.encode() if isinstance(prot, str) else bytes(prot)
+    n = L.orc_anchors(offsets.ctypes.data, positions.ctypes.data, k, pb, len(pb), None, 0)
+    out = np.zeros((max(n, 1), 3), dtype=np.int64)
+    L.orc_anchors(offsets.ctypes.data, positions.ctypes.data, k, pb, len(pb), out.ctypes.data, n)
+    return out[:n]
+
+
+def chain(anc, top: int, k: int = CHAIN_K):
+    """Chain a protein's anchors (Eqs. 1-3 of "Chaining"): (chains, f) with
+    the first `top` chains of at least two anchors as dicts (scores in
+    units of 2^-16) and every anchor's chaining score in sorted order."""
+    L = _chain_lib()
+    anc = np.ascontiguousarray(anc, dtype=np.int64).reshape(-1, 3)
+    n = len(anc)
+    f = np.zeros(max(n, 1), dtype=np.int64)
+    buf = (Chain * max(top, 1))()
+    nc = L.orc_chain_anchors(anc.ctypes.data, n, k, top, buf, f.ctypes.data)
+    if nc < 0:
+        raise MemoryError("oracle chaining")
+    keys = ("strand", "n_anchors", "score", "x_first", "x_last", "y_first", "y_last")
+    return [{x: getattr(buf[t], x) for x in keys} for t in range(nc)], f[:n]
+
+
+def gap(dx: int, dy: int) -> int:
+    return _chain_lib().orc_gap(dx, dy)
+
+
+def gap_penalty(g: int) -> int:
+    """Eq. 3 in units of 2^-16, -1 for an infinite penalty."""
+    return _chain_lib().orc_gap_penalty(g)
