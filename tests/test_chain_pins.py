@@ -135,7 +135,7 @@ def test_gap_penalty_eq3(orc):
     S = 65536
     assert orc.gap_penalty(0) == 0
     assert orc.gap_penalty(200000) == -1 and orc.gap_penalty(-200000) == -1
-    for g in (1, 2, 3, 7, 100, 1023, 1024, 4097, 65535, 199999):
+    for g in (1, 2, 3, 7, 15, 100, 1023, 1024, 4097, 65535, 131071, 199999):
         lin = (g * S) // 3
         lg = int(mpmath.floor(mpmath.mpf(S) * mpmath.mpf("0.75") * mpmath.log(g + 1, 2)))
         assert orc.gap_penalty(g) == lin + lg, g
