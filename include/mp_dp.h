@@ -288,6 +288,55 @@ int mp_dp_score_pair_noalloc(const mp_dp_params *params, const char *d_prot, uin
                              const char *d_nt, uint32_t nt_len, int8_t strand, int32_t *d_out,
                              void *stream);
 
+/* ------------------------------------------------ seeding and chaining
+ * The stage before the DP (Li 2022, Methods: "Reduced alphabet", "Indexing
+ * the genome", "Chaining"), on the GPU.  The index holds, for both strands
+ * of the genome as independent sequences and all three reading frames,
+ * every 6-mer of the reduced amino-acid alphabet inside an open reading
+ * frame (a maximal run of codons without a stop codon) of at least 30
+ * amino acids whose hash (an invertible integer hash of its 24-bit code)
+ * has lowest bit 0, as strand << 31 | floor(x / 256), x the k-mer's first
+ * base on its strand.  A protein's 6-mers looked up there are its anchors
+ * (strand, x = bin, y = residue); they are chained per strand by Eqs. 1-3
+ * (binned gap, gap penalty with G = 200,000 bp and beta = 0.75, alpha =
+ * min(dy, 6), f at least 6), in fixed point with 16 fractional bits (each
+ * penalty term floored to a multiple of 2^-16).  Chains are taken in order
+ * of decreasing score of their last anchor (ties: the earlier anchor in
+ * (strand, x, y) order), each by following predecessors (the first of equal
+ * best ones) until an anchor already taken, scored f(last) minus f of that
+ * anchor; chains of one anchor are dropped. */
+typedef struct mp_index mp_index;
+
+typedef struct {
+    int32_t strand;            /* 0: the genome as given; 1: its reverse complement */
+    int32_t n_anchors;
+    int64_t score;             /* chaining score in units of 2^-16 */
+    int64_t x_first, x_last;   /* bins (256 bp) of the first and last anchor on the chain's strand */
+    int64_t y_first, y_last;   /* residue positions of their 6-mers' first residues */
+} mp_chain;
+
+/* Build the index of a genome (host ASCII, len bases; letters other than
+ * ACGT translate to no amino acid and break no reading frame's k-mers
+ * other than their own codons' ones) on the context's device.  *out is
+ * owned by the caller until mp_index_free.  MP_ENOMEM if the device cannot
+ * hold it (about 2 bytes per base while building, 0.4 after). */
+int mp_index_build(mp_dp_ctx *ctx, const char *genome, uint64_t len, mp_index **out);
+
+/* Chain n_prot proteins (host ASCII; protein k at prot + prot_off[k],
+ * prot_len[k] residues) against the index: chains (caller-owned, n_prot x
+ * top) receives up to `top` chains per protein in extraction order,
+ * n_chains[k] how many.  Blocking. */
+int mp_index_chain(mp_dp_ctx *ctx, const mp_index *idx, const char *prot, const uint64_t *prot_off,
+                   const uint32_t *prot_len, uint32_t n_prot, int32_t top, mp_chain *chains, uint32_t *n_chains);
+
+/* Test hook: the index as CSR over all 2^24 hash values.  With offsets and
+ * entries NULL only *n_entries is set; else offsets receives 2^24 + 1
+ * values and entries *n_entries. */
+int mp_index_download(mp_dp_ctx *ctx, const mp_index *idx, uint64_t *offsets, uint32_t *entries,
+                      uint64_t *n_entries);
+
+void mp_index_free(mp_index *idx);
+
 /* Static string for a return code. */
 const char *mp_dp_strerror(int code);
 
@@ -347,8 +396,9 @@ typedef struct {
                                   shuffle, record load and profile load serve four cells) where that
                                   adds little padding (an even number of 64-residue strips, or 9 or
                                   more) and where the pair's longer critical path in that form stays
-                                  within the batch's longest one in 64-residue strips; run by the
-                                  2-CTA build whatever dp16_variant says */
+                                  within half the batch's longest one in 64-residue strips; 2: every
+                                  such pair, whatever its critical path.  1 and 2 run the 2-CTA
+                                  build whatever dp16_variant says */
 } mp_dp_tuning;
 
 /* Time the candidate configurations on an uploaded batch (warm-up runs;

@@ -141,6 +141,10 @@ def lib():
             "mp_dp_exon_rescore": (ctypes.c_int, [vp, P(mp_pair), ctypes.c_size_t, P(mp_result)]),
             "mp_dp_tuning_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
             "mp_dp_debug_h": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
+            "mp_index_build": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_uint64, P(vp)]),
+            "mp_index_chain": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_int32, vp, vp]),
+            "mp_index_download": (ctypes.c_int, [vp, vp, vp, vp, P(ctypes.c_uint64)]),
+            "mp_index_free": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -484,3 +488,53 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------- seeding and chaining
+class mp_chain(ctypes.Structure):
+    _fields_ = [("strand", ctypes.c_int32), ("n_anchors", ctypes.c_int32), ("score", ctypes.c_int64),
+                ("x_first", ctypes.c_int64), ("x_last", ctypes.c_int64),
+                ("y_first", ctypes.c_int64), ("y_last", ctypes.c_int64)]
+
+
+CHAIN_DTYPE = np.dtype([("strand", "<i4"), ("n_anchors", "<i4"), ("score", "<i8"), ("x_first", "<i8"),
+                        ("x_last", "<i8"), ("y_first", "<i8"), ("y_last", "<i8")])
+
+
+def mp_index_build(ctx, genome):
+    """Index a genome (ASCII bytes, str or uint8 array) on the context's
+    device; returns the index handle."""
+    g = np.ascontiguousarray(np.frombuffer(genome.encode() if isinstance(genome, str) else genome, dtype=np.uint8))
+    idx = ctypes.c_void_p()
+    _check(lib().mp_index_build(ctx, g.ctypes.data_as(ctypes.c_char_p), len(g), ctypes.byref(idx)),
+           "mp_index_build")
+    return idx
+
+
+def mp_index_download(ctx, idx):
+    """(offsets uint64[2^24 + 1], entries uint32[]) of an index (test hook)."""
+    n = ctypes.c_uint64()
+    _check(lib().mp_index_download(ctx, idx, None, None, ctypes.byref(n)), "mp_index_download")
+    off = np.zeros((1 << 24) + 1, dtype=np.uint64)
+    ent = np.zeros(max(1, n.value), dtype=np.uint32)
+    _check(lib().mp_index_download(ctx, idx, off.ctypes.data, ent.ctypes.data, ctypes.byref(n)), "mp_index_download")
+    return off, ent[:n.value]
+
+
+def mp_index_chain(ctx, idx, prot_buf, prot_off, prot_len, top: int):
+    """Chains of every protein (proteins in one ASCII buffer at prot_off,
+    prot_len): (chains structured array [n_prot, top], n_chains uint32[n_prot])."""
+    pb = np.ascontiguousarray(np.frombuffer(prot_buf.encode() if isinstance(prot_buf, str) else prot_buf,
+                                            dtype=np.uint8))
+    po = np.ascontiguousarray(prot_off, dtype=np.uint64)
+    pl = np.ascontiguousarray(prot_len, dtype=np.uint32)
+    n = len(po)
+    ch = np.zeros((max(n, 1), top), dtype=CHAIN_DTYPE)
+    nch = np.zeros(max(n, 1), dtype=np.uint32)
+    _check(lib().mp_index_chain(ctx, idx, pb.ctypes.data, po.ctypes.data, pl.ctypes.data, n, top, ch.ctypes.data,
+                                nch.ctypes.data), "mp_index_chain")
+    return ch[:n], nch[:n]
+
+
+def mp_index_free(idx) -> None:
+    lib().mp_index_free(idx)

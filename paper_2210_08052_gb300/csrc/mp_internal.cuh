@@ -190,6 +190,10 @@ cudaError_t launch_col0(const PairDesc *pairs, uint32_t n, const uint32_t *nt2, 
 cudaError_t launch_compact(const PairDesc *pairs, PairOut *out, uint32_t n, const uint32_t *ops,
                            uint32_t *cig, uint32_t *total, cudaStream_t st);
 int dp16_blocks_per_sm(int variant, bool wide4 = false);
+
+// the device and stream of a context (for the seeding and chaining calls)
+int ctx_device(const mp_dp_ctx *c);
+cudaStream_t ctx_stream(const mp_dp_ctx *c);
 int dp32_blocks_per_sm();
 size_t dp16_smem_bytes();
 size_t dp32_smem_bytes();

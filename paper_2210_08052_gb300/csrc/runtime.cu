@@ -379,6 +379,11 @@ struct mp_dp_ctx {
     std::vector<float> latencies_ms;      // submit -> result available, per completed request
 };
 
+namespace mpdp {
+int ctx_device(const mp_dp_ctx *c) { return c->device; }
+cudaStream_t ctx_stream(const mp_dp_ctx *c) { return c->stream; }
+}  // namespace mpdp
+
 // ====================================================================== API
 extern "C" {
 
@@ -604,7 +609,7 @@ static mp_dp_tuning tuning_for(const mp_dp_ctx *c, const mp_dp_batch *b)
 // batch that needs several waves) and the item order.
 static int plan_key(const mp_dp_batch *b, const mp_dp_tuning &t)
 {
-    return (b->needs_waves && t.overlap_waves ? 1 : 0) | (t.item_order ? 2 : 0) | (t.strip_width ? 4 : 0);
+    return (b->needs_waves && t.overlap_waves ? 1 : 0) | (t.item_order ? 2 : 0) | (t.strip_width << 2);
 }
 
 static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool stream_idle = false);
@@ -717,7 +722,8 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool 
         d.flags &= ~PF_W128;
         const uint64_t crit128 =
             div_up(d.nt_len + kStripWMax - 1, kChunk) + 3 * div_up(d.prot_len, kStripWMax);
-        if (t.strip_width && !c->params.force_int32 && use_w128(d) && 2 * crit128 <= crit64) d.flags |= PF_W128;
+        if (t.strip_width && !c->params.force_int32 && use_w128(d) && (t.strip_width == 2 || 2 * crit128 <= crit64))
+            d.flags |= PF_W128;
         d.n_strips = static_cast<uint32_t>(div_up(d.prot_len, strip_w_of(d.flags)));
     }
     for (uint32_t k = 0; k < n; ++k) {
@@ -1302,7 +1308,7 @@ static uint64_t tuning_sig(const mp_dp_tuning &t, bool timed)
     return (static_cast<uint64_t>(t.dp16_variant & 0xff)) | (static_cast<uint64_t>(t.dp16_ctas_per_sm & 0xff) << 8) |
            (static_cast<uint64_t>(t.dp32_ctas_per_sm & 0xff) << 16) | (static_cast<uint64_t>(t.wide_direct & 1) << 24) |
            (static_cast<uint64_t>(timed) << 25) | (static_cast<uint64_t>(t.overlap_waves & 1) << 26) |
-           (static_cast<uint64_t>(t.item_order & 1) << 27) | (1ull << 28) | (static_cast<uint64_t>(t.strip_width & 1) << 29);
+           (static_cast<uint64_t>(t.item_order & 1) << 27) | (1ull << 28) | (static_cast<uint64_t>(t.strip_width & 3) << 29);
 }
 
 static int autotune_impl(mp_dp_ctx *c, mp_dp_batch *b, mp_dp_tuning *best, mp_dp_tuning *tried, int max_tried,
@@ -1396,16 +1402,17 @@ static std::vector<mp_dp_tuning> kernel_candidates(mp_dp_ctx *c, const mp_dp_bat
                 v.push_back(t);
             }
     }
-    // 128-residue strips (the 2-CTA build that runs both strip forms)
+    // 128-residue strips (the 2-CTA build that runs both strip forms), for
+    // the pairs whose critical path allows it or for every eligible pair
     const int fitw = dp16_blocks_per_sm(1, true);
-    for (int k = fitw; k >= std::max(1, fitw - 1); --k)
+    for (int sw = 1; sw <= 2; ++sw)
         for (int wd = 0; wd <= (any_wide ? 1 : 0); ++wd) {
             mp_dp_tuning t = default_tuning();
             t.dp16_variant = 1;
-            t.dp16_ctas_per_sm = k;
+            t.dp16_ctas_per_sm = fitw;
             t.dp32_ctas_per_sm = fit32;
             t.wide_direct = wd;
-            t.strip_width = 1;
+            t.strip_width = sw;
             v.push_back(t);
         }
     return v;
@@ -1531,7 +1538,7 @@ int mp_dp_set_tuning(mp_dp_ctx *c, const mp_dp_tuning *t)
     }
     if (t->dp16_variant < 0 || t->dp16_variant >= kDp16Variants || t->dp16_ctas_per_sm < 0 ||
         t->dp32_ctas_per_sm < 0 || t->wide_direct < 0 || t->wide_direct > 1 || t->overlap_waves < 0 ||
-        t->overlap_waves > 1 || t->item_order < 0 || t->item_order > 1 || t->strip_width < 0 || t->strip_width > 1)
+        t->overlap_waves > 1 || t->item_order < 0 || t->item_order > 1 || t->strip_width < 0 || t->strip_width > 2)
         return MP_EINVAL;
     c->fixed = *t;
     c->has_fixed = true;
@@ -1584,7 +1591,7 @@ int mp_dp_tuning_load(mp_dp_ctx *c, const char *path)
         if (k == EOF) break;
         if (k != 9 || t.item_order < 0 || t.item_order > 1 || t.dp16_variant < 0 || t.dp16_variant >= kDp16Variants ||
             t.dp16_ctas_per_sm < 0 || t.dp32_ctas_per_sm < 0 || t.wide_direct < 0 || t.wide_direct > 1 ||
-            t.overlap_waves < 0 || t.overlap_waves > 1 || t.strip_width < 0 || t.strip_width > 1) {
+            t.overlap_waves < 0 || t.overlap_waves > 1 || t.strip_width < 0 || t.strip_width > 2) {
             fclose(f);
             return MP_EINVAL;
         }

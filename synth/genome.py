@@ -125,7 +125,10 @@ def _paralog(rng, src: np.ndarray, identity: float) -> np.ndarray:
 
 
 def make_workload(seed: int = 5, genome_len: int = 500_000_000, n_genes: int = 20_000,
-                  n_proteins: int = 200_000, gc: float = 0.4) -> GenomeWorkload:
+                  n_proteins: int = 200_000, gc: float = 0.4, host_seeding: bool = True) -> GenomeWorkload:
+    """The genome, planted genes and proteins; with host_seeding the
+    candidate regions of the host stand-in below, otherwise none (to be set
+    from the library's seeding and chaining with regions_from_chains)."""
     rng = np.random.default_rng(seed)
     genome = _random_genome(rng, genome_len, gc)
     # ---- planted genes, one per slot of the genome
@@ -169,7 +172,11 @@ def make_workload(seed: int = 5, genome_len: int = 500_000_000, n_genes: int = 2
     prot_len = np.array([len(p) for p in prots], dtype=np.int64)
     prot_off = np.concatenate([[0], np.cumsum(prot_len)[:-1]]).astype(np.int64)
     prot_buf = np.concatenate(prots) if prots else np.zeros(0, np.uint8)
-    reg = seed_and_chain(genome, prot_buf, prot_off, prot_len)
+    if host_seeding:
+        reg = seed_and_chain(genome, prot_buf, prot_off, prot_len)
+    else:
+        reg = (np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0, np.int8),
+               np.zeros(0, np.int64))
     return GenomeWorkload(genome, prot_buf, prot_off, prot_len, kind, gene_of, np.asarray(gs, np.int64),
                           np.asarray(ge, np.int64), np.asarray(gstr, np.int8), *reg)
 
@@ -318,8 +325,34 @@ def seed_and_chain(genome: np.ndarray, prot_buf: np.ndarray, prot_off: np.ndarra
             np.where(rev, -1, 1)[keep].astype(np.int8), c_n[pick][keep].astype(np.int64))
 
 
-def config5(seed: int = 5, scale: float = 1.0) -> GenomeWorkload:
+def config5(seed: int = 5, scale: float = 1.0, host_seeding: bool = True) -> GenomeWorkload:
     """The genome-scale workload; scale < 1 shrinks the genome, the gene
     count and the protein count together (tests)."""
     return make_workload(seed, genome_len=int(500_000_000 * scale), n_genes=max(1, int(20_000 * scale)),
-                         n_proteins=max(10, int(200_000 * scale)))
+                         n_proteins=max(10, int(200_000 * scale)), host_seeding=host_seeding)
+
+
+def regions_from_chains(w: GenomeWorkload, chains, n_chains) -> GenomeWorkload:
+    """Candidate regions from chains (the library's seeding and chaining:
+    per protein up to `top` chains of (strand, n_anchors, score, x_first,
+    x_last, y_first, y_last), x in 256-bp bins on the chain's strand, y
+    residues): each chain's span extended by 3 nt per residue the chain
+    leaves unaligned on either side and FLANK bp, clipped to the genome,
+    on the forward strand's coordinates (strand -1 for the reverse
+    complement).  Returns the workload with these regions."""
+    G = len(w.genome)
+    n_p, top = chains.shape
+    k = np.arange(top)[None, :] < np.asarray(n_chains)[:, None]
+    prot = np.broadcast_to(np.arange(n_p)[:, None], (n_p, top))[k].astype(np.int64)
+    c = chains[k]
+    m = w.prot_len[prot]
+    s = c["x_first"] * BIN - 3 * c["y_first"] - FLANK
+    e = (c["x_last"] + 1) * BIN + 3 * (m - c["y_last"]) + FLANK
+    s, e = np.clip(s, 0, G), np.clip(e, 0, G)
+    rev = c["strand"] == 1
+    fs, fe = np.where(rev, G - e, s), np.where(rev, G - s, e)
+    keep = fe > fs
+    w.reg_prot, w.reg_start, w.reg_end = prot[keep], fs[keep].astype(np.int64), fe[keep].astype(np.int64)
+    w.reg_strand = np.where(rev, -1, 1)[keep].astype(np.int8)
+    w.reg_anchors = c["n_anchors"][keep].astype(np.int64)
+    return w

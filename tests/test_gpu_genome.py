@@ -1,6 +1,7 @@
-"""Genome-scale workload on the GPU: candidate regions from the host seed +
-chain step, aligned through the C ABI from zero-copy pair records that point
-into the genome and protein buffers.  Every region's score and end cell
+"""Genome-scale workload on the GPU: candidate regions from the library's
+seeding and chaining (the first 3 chains of each protein, extended to
+candidate regions), aligned through the C ABI from zero-copy pair records
+that point into the genome and protein buffers.  Every region's score and end cell
 equal the oracle's four-row fill; every region up to 12 M cells matches the
 full-matrix oracle in score, coordinates and CIGAR; every returned CIGAR
 rescores to its score at the oracle's end cell.
@@ -27,8 +28,18 @@ def mp():
 
 
 def test_genome_regions_match_oracle(mp, orc):
-    w = synth.config5(scale=0.02)
-    assert w.n_regions > 8000
+    w = synth.config5(scale=0.02, host_seeding=False)
+    ctx = mp.mp_dp_init(None, 0)
+    try:
+        idx = mp.mp_index_build(ctx, w.genome)
+        try:
+            chains, nch = mp.mp_index_chain(ctx, idx, w.prot_buf, w.prot_off, w.prot_len, 3)
+        finally:
+            mp.mp_index_free(idx)
+    finally:
+        mp.mp_dp_destroy(ctx)
+    w = synth.regions_from_chains(w, chains, nch)
+    assert w.n_regions > 1000
     po, pl, no, nl, st = w.region_arrays()
     batch = mp.RegionBatch(w.prot_buf, po, pl, w.genome, no, nl, st)
     ctx = mp.mp_dp_init(None, 0)

@@ -166,7 +166,7 @@ def test_wide_strips_match_oracle(mp, orc, mode):
     op.mode = mode
     c = mp.mp_dp_init(params, 0)
     try:
-        mp.mp_dp_set_tuning(c, dict(dp16_variant=1, overlap_waves=1, item_order=1, strip_width=1))
+        mp.mp_dp_set_tuning(c, dict(dp16_variant=1, overlap_waves=1, item_order=1, strip_width=2))
         for _ in range(2):                                # direct, then graph replay
             got = mp.mp_dp_align_batch(c, pairs)
             bad = []
@@ -489,7 +489,7 @@ def test_stored_h_matches_oracle(mp, orc, mode, kernel):
     c = mp.mp_dp_init(params, 0)
     try:
         if kernel == "int16-w128":
-            mp.mp_dp_set_tuning(c, dict(dp16_variant=1, overlap_waves=1, item_order=1, strip_width=1))
+            mp.mp_dp_set_tuning(c, dict(dp16_variant=1, overlap_waves=1, item_order=1, strip_width=2))
         b = mp.mp_dp_batch_upload(c, pairs)
         mp.mp_dp_batch_run(c, b)
         mp.mp_dp_batch_sync(c)

@@ -70,7 +70,7 @@ def _same(got, want):
 @pytest.mark.parametrize("ctas", [0, 1, 2])
 @pytest.mark.parametrize("wide_direct", [0, 1])
 @pytest.mark.parametrize("item_order", [0, 1])
-@pytest.mark.parametrize("strip_width", [0, 1])
+@pytest.mark.parametrize("strip_width", [0, 1, 2])
 def test_every_configuration_matches_oracle(mp, mixed, variant, ctas, wide_direct, item_order, strip_width):
     pairs, want = mixed
     ctx = mp.mp_dp_init(None, 0)
@@ -99,7 +99,7 @@ def test_autotune_picks_a_timed_candidate_and_keeps_results(mp, mixed, tmp_path)
         assert best["ms"] == min(t["ms"] for t in tried)
         strip = lambda t: {k: t[k] for k in ("dp16_variant", "dp16_ctas_per_sm", "dp32_ctas_per_sm", "wide_direct",
                                              "overlap_waves", "item_order", "strip_width")}
-        assert {t["strip_width"] for t in tried} == {0, 1}
+        assert {t["strip_width"] for t in tried} == {0, 1, 2}
         assert strip(best) in [strip(t) for t in tried]
         assert {t["wide_direct"] for t in tried} == {0, 1}         # the batch has wide pairs
         # the batch holds the results of the tuning runs
@@ -146,7 +146,7 @@ def test_tuning_arguments_checked(mp, tmp_path):
     L = mp.lib()
     try:
         for bad in (dict(dp16_variant=2), dict(dp16_variant=-1), dict(wide_direct=2), dict(dp16_ctas_per_sm=-1),
-                    dict(dp32_ctas_per_sm=-3), dict(overlap_waves=2), dict(item_order=-1), dict(strip_width=2),
+                    dict(dp32_ctas_per_sm=-3), dict(overlap_waves=2), dict(item_order=-1), dict(strip_width=3),
                     dict(strip_width=-1)):
             with pytest.raises(mp.MPError):
                 mp.mp_dp_set_tuning(ctx, bad)
