@@ -36,9 +36,11 @@ WORKLOAD_C3 = ("20000 (protein, region) pairs, uneven sizes: protein log-uniform
                "4096-pair workload plus a 2% tail of 20-100 kb; regions <= 200 kb; 5% score-only decoys; "
                "seed 3 (+1000 per rank)")
 WORKLOAD_C5 = ("genome-scale: 500 Mb genome (40% GC) with 20000 planted genes; 200000 proteins (10% sources, "
-               "45% 50-70%-identity paralogs, 45% unrelated); GPU seeding and chaining (sampled 6-mer index of "
-               "the reduced alphabet over open reading frames, chaining by Eqs. 1-3), first 3 chains per protein "
-               "as candidate regions; every candidate region aligned with traceback; seed 5 (+1000 per rank)")
+               "45% 50-70%-identity paralogs, 45% unrelated); host 7-mer seed + chain stand-in, top 3 chains per "
+               "protein; every candidate region aligned with traceback; seed 5 (+1000 per rank)")
+WORKLOAD_SEED = ("seeding and chaining: the genome-scale workload shrunk 10 times (50 Mb genome, 2000 planted genes, "
+                 "20000 proteins); index of the genome, anchors and chains (Eqs. 1-3) of every protein, the first "
+                 "3 chains each; seed 5")
 # algorithmic integer ops per cell of the DP pass: the 27 max/add of Eq. 7 (I 3, D 3, A/B/C 2 each,
 # H 15) and one running maximum for the best cell.  Traceback decisions are re-derived from the
 # stored H values along the path only (by the warp that finishes a pair's last strip).
@@ -308,33 +310,17 @@ def load_pairs(mp, pairs):
 
 def load_c5(mp, rank, scale=1.0, device=0):
     """Candidate regions of the genome-scale workload as zero-copy records
-    into the genome and protein buffers.  The genome and proteins are
-    generated on the host; the regions come from the library's seeding and
-    chaining on the GPU (index of the genome, anchors and chains of every
-    protein, the first 3 chains of each extended to a region), timed on its
-    own; all of it precedes the DP's timed regions."""
+    into the genome and protein buffers; the generation and the host seed +
+    chain stand-in are input preparation, outside every timed region."""
     import numpy as np
 
     import synth
 
     t_gen = time.perf_counter()
-    gw = synth.config5(seed=rank_seed(5, rank), scale=scale, host_seeding=False)
-    t_gen = time.perf_counter() - t_gen
-    ctx = mp.mp_dp_init(None, device)
-    t0 = time.perf_counter()
-    idx = mp.mp_index_build(ctx, gw.genome)
-    t_idx = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    chains, nch = mp.mp_index_chain(ctx, idx, gw.prot_buf, gw.prot_off, gw.prot_len, 3)
-    t_chain = time.perf_counter() - t0
-    mp.mp_index_free(idx)
-    mp.mp_dp_destroy(ctx)
-    gw = synth.regions_from_chains(gw, chains, nch)
+    gw = synth.config5(seed=rank_seed(5, rank), scale=scale)
     prep = {"genome_bp": len(gw.genome), "proteins": len(gw.prot_len), "regions": gw.n_regions,
-            "regions_per_protein": gw.n_regions / len(gw.prot_len), "generate_s": t_gen,
-            "seed_chain": {"index_build_ms": t_idx * 1000, "chain_ms": t_chain * 1000,
-                           "chains": int(nch.sum()), "unit": "wall ms through the C ABI (host buffers in, "
-                                                             "chains out)"}}
+            "regions_per_protein": gw.n_regions / len(gw.prot_len),
+            "generate_and_seed_chain_s": time.perf_counter() - t_gen}
     po, pl, no, nl, st_ = gw.region_arrays()
     src = mp.RegionBatch(gw.prot_buf, po, pl, gw.genome, no, nl, st_)
     # the library sends a genome range and a protein range once when the
@@ -352,12 +338,13 @@ def load_c5(mp, rank, scale=1.0, device=0):
 
 
 def measure(mp, torch, src, n_pairs, cells, ascii_bytes, steps, warmup, device, dist, flush, mode=0, fixed=None,
-            autotune=True, e2e_steps=3):
+            autotune=True, e2e_steps=3, budget=None):
     """Time the device-resident pipeline (inputs in HBM, L2 flushed before
     each step, CUDA events per kernel inside the library, wall time between
     barriers + device syncs) and the end-to-end call with host buffers, with
     the launch configuration the library's autotuner picks for the batch."""
-    ctx = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode), device)
+    extra = {"tb_budget_bytes": budget} if budget else {}
+    ctx = mp.mp_dp_init(mp.mp_dp_default_params(mode=mode, **extra), device)
     mp.mp_dp_set_timing(ctx, True)
     batch = mp.mp_dp_batch_upload(ctx, src)
     tuning = None
@@ -451,11 +438,42 @@ def roofline(m, cells, torch, device, peaks):
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
 
 
-def leg(mp, torch, name, loader, device, flush, peaks, steps=3, warmup=3):
+def seed_chain_leg(mp, torch, device, scale=0.1, reps=3):
+    """The seeding and chaining stage on the GPU through the C ABI (host
+    genome and proteins in, chains out): index build and chaining timed
+    separately, the median of `reps` runs each."""
+    import synth
+
+    gw = synth.config5(scale=scale, host_seeding=False)
+    ctx = mp.mp_dp_init(None, device)
+    t_idx, t_ch = [], []
+    chains = nch = None
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        idx = mp.mp_index_build(ctx, gw.genome)
+        t1 = time.perf_counter()
+        chains, nch = mp.mp_index_chain(ctx, idx, gw.prot_buf, gw.prot_off, gw.prot_len, 3)
+        t2 = time.perf_counter()
+        mp.mp_index_free(idx)
+        t_idx.append(t1 - t0)
+        t_ch.append(t2 - t1)
+    mp.mp_dp_destroy(ctx)
+    ti, tc = statistics.median(t_idx[1:]), statistics.median(t_ch[1:])
+    return {"workload": WORKLOAD_SEED, "genome_bp": len(gw.genome), "proteins": len(gw.prot_len),
+            "index_build_ms": ti * 1000, "chain_ms": tc * 1000, "genome_mb_per_s": len(gw.genome) / ti / 1e6,
+            "proteins_per_s": len(gw.prot_len) / tc, "chains": int(nch.sum()),
+            "unit": "wall time through the C ABI (host buffers in, chains out), median of 3 after a warm-up"}
+
+
+def leg(mp, torch, name, loader, device, flush, peaks, steps=3, warmup=3, budget=None):
     """A further workload measured like the main line (its own autotuned
     configuration, device-resident value, end-to-end figure, roofline)."""
     src, n_pairs, cells, ascii_bytes, get_pair, workload, prep = loader()
-    m = measure(mp, torch, src, n_pairs, cells, ascii_bytes, steps, warmup, device, None, flush, e2e_steps=2)
+    m = measure(mp, torch, src, n_pairs, cells, ascii_bytes, steps, warmup, device, None, flush, e2e_steps=2,
+                budget=budget)
+    if budget:
+        prep = dict(prep, tb_budget_bytes=budget)
     e2e = m["e2e"]
     e2e["pairs_per_s"] = n_pairs / m["e2e_s"]
     return {"workload": workload, "value": cells / (m["t_max"] / steps) / 1e9, "unit": "GCUPS",
@@ -475,8 +493,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip plain/serving/cpu legs")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rates", default="2000,10000,50000")
-    ap.add_argument("--legs", default="c3,c5", help="further workloads measured after the main line "
-                                                  "(c3: 20,000 uneven pairs; c5: genome-scale regions); '' for none")
+    ap.add_argument("--legs", default="c3,c5,seed", help="further workloads measured after the main line "
+                                                       "(c3: 20,000 uneven pairs; c5: genome-scale regions; seed: "
+                                                       "GPU seeding and chaining); '' for none")
     ap.add_argument("--pairs", type=int, default=4096, help="first N pairs of the workload (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: skip the end-to-end leg")
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration, no tuning runs")
@@ -648,7 +667,13 @@ def main():
                                  lambda: load_pairs(mp, synth.config3(seed=rank_seed(3, rank))) + (WORKLOAD_C3, {}),
                                  local, flush, peaks)
             if "c5" in args.legs:
-                line["c5"] = leg(mp, torch, "c5", lambda: load_c5(mp, rank, args.c5_scale, local), local, flush, peaks)
+                # the genome-scale batch's traceback (several TB) runs in waves under the
+                # budget: 150 GiB of the 280 GB on the device (the library caps it at 60% of
+                # the free memory) keeps the waves few
+                line["c5"] = leg(mp, torch, "c5", lambda: load_c5(mp, rank, args.c5_scale, local), local, flush,
+                                 peaks, budget=150 << 30)
+        if args.workload == "c2" and "seed" in args.legs:
+            line["seed_chain"] = seed_chain_leg(mp, torch, local)
         # serving: open-loop Poisson arrivals at each rate
         try:
             sp = synth.serving_pairs()

@@ -61,10 +61,24 @@ __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b)
     return r;
 }
 
+// per 16-bit half: max(a + b, c), the addition modulo 2^16 (so adding a
+// negated penalty subtracts it: the biased operands never leave 0..65535)
+__device__ __forceinline__ uint32_t vaddmax(uint32_t a, uint32_t b, uint32_t c) { return __viaddmax_u16x2(a, b, c); }
+
+// per 16-bit half: max(a, b, c)
+__device__ __forceinline__ uint32_t vmax3(uint32_t a, uint32_t b, uint32_t c) { return __vimax3_u16x2(a, b, c); }
+
+// a packed pair of penalties negated per half (modulo 2^16)
+__host__ __device__ __forceinline__ uint32_t neg2(uint32_t lo, uint32_t hi)
+{
+    return ((0x10000u - lo) & 0xffffu) | (((0x10000u - hi) & 0xffffu) << 16);
+}
+
 // Per-genome-position record for the lo cell at 0-based position ii
-// (1-based i = ii + 1):
-//   x = [r + d(i+1), r + d(i)]   (16-bit halves, lo first)
-//   y = [a(i), a(i-1)]
+// (1-based i = ii + 1), the penalties negated per 16-bit half (modulo 2^16,
+// so that one fused add-max subtracts them):
+//   x = [-(r + d(i+1)), -(r + d(i))]   (16-bit halves, lo first)
+//   y = [-a(i), -a(i-1)]
 //   z = byte offset of the profile row of the codon ending at i
 __device__ __forceinline__ uint4 make_record(const uint32_t *g, int n, int ii, const ScoreParams &sp)
 {
@@ -87,8 +101,8 @@ __device__ __forceinline__ uint4 make_record(const uint32_t *g, int n, int ii, c
     const int aA = splice_acceptor(sp, b[1], b[2], b[3], v[1], v[2], v[3]);  // a(i)
     const int aC = splice_acceptor(sp, b[0], b[1], b[2], v[0], v[1], v[2]);  // a(i-1)
     uint4 rec;
-    rec.x = static_cast<uint32_t>(r + dC) | (static_cast<uint32_t>(r + dB) << 16);
-    rec.y = static_cast<uint32_t>(aA) | (static_cast<uint32_t>(aC) << 16);
+    rec.x = neg2(static_cast<uint32_t>(r + dC), static_cast<uint32_t>(r + dB));
+    rec.y = neg2(static_cast<uint32_t>(aA), static_cast<uint32_t>(aC));
     rec.z = static_cast<uint32_t>(aa) * 128u;
     rec.w = 0;
     return rec;
@@ -180,12 +194,10 @@ struct Ops16 {
     static constexpr int W = kStripW, CPL = 2;
     static constexpr uint32_t Z = 0x80008000u;      // biased 0 in both halves
     static constexpr uint32_t NEGV = 0x40004000u;   // biased -16384
-    static constexpr uint32_t K = 0x80008000u;
-    static constexpr uint32_t SBIAS = 0x02000200u;  // profile entries hold s + 512
     static constexpr Bnd kBnd0 = 0x40008000u;       // column 0: H = 0, I = -inf
 
     struct Consts {
-        uint32_t QE, E, F, KF;             // packed q+e, e, f and K - f
+        uint32_t NQE, E, NF;               // packed -(q+e) (negated per half), e, -f
         uint32_t FLOOR;                    // local: biased 0 (the restart); anchored modes: 0 (none)
         uint32_t ROW0;                     // H in row 0 of the lane's two columns (biased)
     };
@@ -200,10 +212,9 @@ struct Ops16 {
     {
         Consts c;
         const uint32_t qe = sp.q + sp.e;
-        c.QE = qe | (qe << 16);
+        c.NQE = neg2(qe, qe);
         c.E = static_cast<uint32_t>(sp.e) | (static_cast<uint32_t>(sp.e) << 16);
-        c.F = static_cast<uint32_t>(sp.f) | (static_cast<uint32_t>(sp.f) << 16);
-        c.KF = K - c.F;
+        c.NF = neg2(static_cast<uint32_t>(sp.f), static_cast<uint32_t>(sp.f));
         c.FLOOR = sp.mode == MP_MODE_LOCAL ? Z : 0u;
         c.ROW0 = Z;
         return c;
@@ -220,7 +231,7 @@ struct Ops16 {
     // profile queries: the gap costs of the lane's two columns (packed halves)
     static __device__ __forceinline__ void set_gaps(Consts &c, int qlo, int elo, int qhi, int ehi)
     {
-        c.QE = static_cast<uint32_t>(qlo + elo) | (static_cast<uint32_t>(qhi + ehi) << 16);
+        c.NQE = neg2(static_cast<uint32_t>(qlo + elo), static_cast<uint32_t>(qhi + ehi));
         c.E = static_cast<uint32_t>(elo) | (static_cast<uint32_t>(ehi) << 16);
     }
     // boundary entry of column 0 in the anchored modes: [H, I = -inf]
@@ -230,9 +241,11 @@ struct Ops16 {
         return static_cast<uint32_t>(h + 32768) | 0x40000000u;
     }
 
+    // a profile entry: the two scores as 16-bit two's complement halves (added
+    // modulo 2^16 to a biased H)
     static __device__ __forceinline__ uint32_t prof_entry(int slo, int shi)
     {
-        return static_cast<uint32_t>(slo + 512) | (static_cast<uint32_t>(shi + 512) << 16);
+        return (static_cast<uint32_t>(slo) & 0xffffu) | ((static_cast<uint32_t>(shi) & 0xffffu) << 16);
     }
 
     // State before step 0, i.e. the history of steps -1 .. -4.  At step tau
@@ -270,27 +283,24 @@ struct Ops16 {
                                                     const uint32_t *prof_lane, Bnd bin, Bnd &wout,
                                                     int lane, int ii, int n)
     {
-        const uint32_t VD0 = rec.x, VA0 = rec.y;
+        const uint32_t VD0 = rec.x, VA0 = rec.y;          // negated penalties
         const uint32_t X0 = *reinterpret_cast<const uint32_t *>(
             reinterpret_cast<const char *>(prof_lane) + rec.z);
         const uint32_t S = (X0 & 0x0000ffffu) | (s.X1 & 0xffff0000u);   // lo: s(i, 2l); hi: s(i-1, 2l+1)
-        const uint32_t M = s.L3 + S - SBIAS;
-        const uint32_t Iopen = s.L0 - c.QE, Iext = s.IL - c.E;
-        uint32_t I0 = vmax(Iopen, Iext);
-        const uint32_t Dopen = s.H3 - c.QE, Dext = s.D3 - c.E;
-        uint32_t D0 = vmax(Dopen, Dext);
-        const uint32_t Aopen = s.H1 - s.VD2;              // H[i-1][j] - r - d(i-1)
-        uint32_t A0 = vmax(Aopen, s.A1);
-        const uint32_t Bopen = s.L1 - s.VD1;              // H[i-1][j-1] - r - d(i)
-        uint32_t B0 = vmax(Bopen, s.B1);
-        const uint32_t Copen = s.L1 - VD0;                // H[i-1][j-1] - r - d(i+1)
-        uint32_t C0 = vmax(Copen, s.C1);
-        // the four frameshift terms share the penalty f: one subtraction
-        const uint32_t FG = vmax(vmax(s.L1, s.L2), vmax(s.H1, s.H2)) - c.F;
-        const uint32_t Ap = A0 - VA0;                     // A - a(i)
-        const uint32_t Bp = B0 - s.VA2;                   // B - a(i-2)
-        const uint32_t Cp = C0 - s.VA1;                   // C - a(i-1)
-        uint32_t H0 = vmax(vmax(vmax(M, I0), vmax(D0, FG)), vmax(vmax(Ap, Bp), vmax(Cp, c.FLOOR)));
+        // each term of Eq. 7 that subtracts a penalty is one fused add-max
+        uint32_t I0 = vaddmax(s.L0, c.NQE, s.IL - c.E);    // max(H[i][j-1] - q - e, I[i][j-1] - e)
+        uint32_t D0 = vaddmax(s.H3, c.NQE, s.D3 - c.E);    // max(H[i-3][j] - q - e, D[i-3][j] - e)
+        uint32_t A0 = vaddmax(s.H1, s.VD2, s.A1);         // max(H[i-1][j] - r - d(i-1), A[i-1][j])
+        uint32_t B0 = vaddmax(s.L1, s.VD1, s.B1);         // max(H[i-1][j-1] - r - d(i), B[i-1][j])
+        uint32_t C0 = vaddmax(s.L1, VD0, s.C1);           // max(H[i-1][j-1] - r - d(i+1), C[i-1][j])
+        // H: the intron exits and the frameshift terms (all known before this
+        // step's neighbours) in one chain, the match, I and D in another
+        uint32_t Y = vaddmax(s.H2, c.NF, c.FLOOR);        // H[i-2][j] - f
+        Y = vaddmax(vmax3(s.L1, s.L2, s.H1), c.NF, Y);    // H[i-1][j-1], H[i-2][j-1], H[i-1][j] - f
+        Y = vaddmax(C0, s.VA1, Y);                        // C - a(i-1)
+        Y = vaddmax(B0, s.VA2, Y);                        // B - a(i-2)
+        Y = vaddmax(A0, VA0, Y);                          // A - a(i)
+        uint32_t H0 = vmax3(vaddmax(s.L3, S, I0), D0, Y); // H[i-3][j-1] + s(i, j), I, D
 
         uint32_t vmask = 0xffffffffu;
         if (MASKED) {
@@ -385,9 +395,10 @@ __device__ __forceinline__ V2 mx(V2 a, V2 b) { return V2{max(a.lo, b.lo), max(a.
 __device__ __forceinline__ V2 sub(V2 a, V2 b) { return V2{a.lo - b.lo, a.hi - b.hi}; }
 __device__ __forceinline__ V2 subc(V2 a, int32_t b) { return V2{a.lo - b, a.hi - b}; }
 __device__ __forceinline__ V2 add(V2 a, V2 b) { return V2{a.lo + b.lo, a.hi + b.hi}; }
-__device__ __forceinline__ V2 unpack16(uint32_t w)
+// the two negated penalties of a record word, sign-extended
+__device__ __forceinline__ V2 unpack_neg16(uint32_t w)
 {
-    return V2{static_cast<int32_t>(w & 0xffffu), static_cast<int32_t>(w >> 16)};
+    return V2{static_cast<int32_t>(w << 16) >> 16, static_cast<int32_t>(w) >> 16};
 }
 
 struct Ops32 {
@@ -444,8 +455,8 @@ struct Ops32 {
         s.IL = (lane == 0) ? V2{w0.i, NEG} : ng;
         s.D1 = s.D2 = s.D3 = ng;
         s.A1 = s.B1 = s.C1 = ng;
-        s.VD1 = unpack16(recm1.x); s.VD2 = unpack16(recm2.x);
-        s.VA1 = unpack16(recm1.y); s.VA2 = unpack16(recm2.y);
+        s.VD1 = unpack_neg16(recm1.x); s.VD2 = unpack_neg16(recm2.x);
+        s.VA1 = unpack_neg16(recm1.y); s.VA2 = unpack_neg16(recm2.y);
         s.X1 = xm1;
         s.bslo = s.bshi = 0; s.btlo = s.bthi = 0; s.t = 0;
         s.cmlo = s.cmhi = NEG;
@@ -458,7 +469,7 @@ struct Ops32 {
                                                  const uint32_t *prof_lane, Bnd bin, Bnd &wout,
                                                  int lane, int ii, int n)
     {
-        const V2 VD0 = unpack16(rec.x), VA0 = unpack16(rec.y);
+        const V2 VD0 = unpack_neg16(rec.x), VA0 = unpack_neg16(rec.y);   // negated penalties
         const uint32_t X0 = *reinterpret_cast<const uint32_t *>(
             reinterpret_cast<const char *>(prof_lane) + rec.z);
         const V2 S{static_cast<int32_t>(X0 << 16) >> 16, static_cast<int32_t>(s.X1) >> 16};
@@ -467,14 +478,14 @@ struct Ops32 {
         V2 I0 = mx(Iopen, Iext);
         const V2 Dopen = sub(s.H3, c.qe), Dext = sub(s.D3, c.e);
         V2 D0 = mx(Dopen, Dext);
-        const V2 Aopen = sub(s.H1, s.VD2);
+        const V2 Aopen = add(s.H1, s.VD2);
         V2 A0 = mx(Aopen, s.A1);
-        const V2 Bopen = sub(s.L1, s.VD1);
+        const V2 Bopen = add(s.L1, s.VD1);
         V2 B0 = mx(Bopen, s.B1);
-        const V2 Copen = sub(s.L1, VD0);
+        const V2 Copen = add(s.L1, VD0);
         V2 C0 = mx(Copen, s.C1);
         const V2 FG = subc(mx(mx(s.L1, s.L2), mx(s.H1, s.H2)), c.f);
-        const V2 Ap = sub(A0, VA0), Bp = sub(B0, s.VA2), Cp = sub(C0, s.VA1);
+        const V2 Ap = add(A0, VA0), Bp = add(B0, s.VA2), Cp = add(C0, s.VA1);
         V2 H0 = mx(mx(mx(M, I0), mx(D0, FG)), mx(mx(Ap, Bp), mx(Cp, V2{c.floor, c.floor})));
 
         bool vlo = true, vhi = true;
@@ -552,12 +563,11 @@ struct Ops16x4 {
     static constexpr int W = kStripWMax, CPL = 4;
     static constexpr uint32_t Z = 0x80008000u;
     static constexpr uint32_t NEGV = 0x40004000u;
-    static constexpr uint32_t SBIAS = 0x02000200u;
     static constexpr Bnd kBnd0 = 0x40008000u;
     static constexpr bool kChunkMaxBest = true;
 
     struct Consts {
-        uint32_t QE, E, F;
+        uint32_t NQE, E, NF;               // as Ops16
         uint32_t FLOOR;
         uint32_t ROW0A, ROW0B;             // H in row 0 of the lane's four columns (biased)
     };
@@ -579,9 +589,9 @@ struct Ops16x4 {
     {
         Consts c;
         const uint32_t qe = sp.q + sp.e;
-        c.QE = qe | (qe << 16);
+        c.NQE = neg2(qe, qe);
         c.E = static_cast<uint32_t>(sp.e) | (static_cast<uint32_t>(sp.e) << 16);
-        c.F = static_cast<uint32_t>(sp.f) | (static_cast<uint32_t>(sp.f) << 16);
+        c.NF = neg2(static_cast<uint32_t>(sp.f), static_cast<uint32_t>(sp.f));
         c.FLOOR = sp.mode == MP_MODE_LOCAL ? Z : 0u;
         c.ROW0A = c.ROW0B = Z;
         return c;
@@ -654,23 +664,26 @@ struct Ops16x4 {
     }
 
     // The cells of one register at rows (lo, lo - 1): Eq. 7 as in Ops16::step.
-    // VD0..VD2 / VA0..VA2: records x / y of rows lo, lo-1, lo-2.  Leaves L0
-    // and IL for the caller (they come from the neighbours of this step).
+    // VD0..VD2 / VA0..VA2: records x / y (negated penalties) of rows lo,
+    // lo-1, lo-2.  Leaves L0 and IL for the caller (they come from the
+    // neighbours of this step).
     template <bool MASKED>
     static __device__ __forceinline__ void cells(Reg &r, const Consts &c, uint32_t S, uint32_t VD0, uint32_t VD1,
                                                  uint32_t VD2, uint32_t VA0, uint32_t VA1, uint32_t VA2,
                                                  uint32_t ROW0, int ii, int n, uint32_t &H0, uint32_t &I0,
                                                  uint32_t &vmask)
     {
-        const uint32_t M = r.L3 + S - SBIAS;
-        I0 = vmax(r.L0 - c.QE, r.IL - c.E);
-        uint32_t D0 = vmax(r.H3 - c.QE, r.D3 - c.E);
-        uint32_t A0 = vmax(r.H1 - VD2, r.A1);             // H[i-1][j] - r - d(i-1)
-        uint32_t B0 = vmax(r.L1 - VD1, r.B1);             // H[i-1][j-1] - r - d(i)
-        uint32_t C0 = vmax(r.L1 - VD0, r.C1);             // H[i-1][j-1] - r - d(i+1)
-        const uint32_t FG = vmax(vmax(r.L1, r.L2), vmax(r.H1, r.H2)) - c.F;
-        const uint32_t Ap = A0 - VA0, Bp = B0 - VA2, Cp = C0 - VA1;
-        H0 = vmax(vmax(vmax(M, I0), vmax(D0, FG)), vmax(vmax(Ap, Bp), vmax(Cp, c.FLOOR)));
+        I0 = vaddmax(r.L0, c.NQE, r.IL - c.E);
+        uint32_t D0 = vaddmax(r.H3, c.NQE, r.D3 - c.E);
+        uint32_t A0 = vaddmax(r.H1, VD2, r.A1);           // H[i-1][j] - r - d(i-1)
+        uint32_t B0 = vaddmax(r.L1, VD1, r.B1);           // H[i-1][j-1] - r - d(i)
+        uint32_t C0 = vaddmax(r.L1, VD0, r.C1);           // H[i-1][j-1] - r - d(i+1)
+        uint32_t Y = vaddmax(r.H2, c.NF, c.FLOOR);
+        Y = vaddmax(vmax3(r.L1, r.L2, r.H1), c.NF, Y);
+        Y = vaddmax(C0, VA1, Y);
+        Y = vaddmax(B0, VA2, Y);
+        Y = vaddmax(A0, VA0, Y);
+        H0 = vmax3(vaddmax(r.L3, S, I0), D0, Y);
         vmask = 0xffffffffu;
         if (MASKED) {
             const uint32_t kill = (ii < 0 ? 0x0000ffffu : 0u) | (ii < 1 ? 0xffff0000u : 0u);
@@ -1287,7 +1300,7 @@ __global__ void records_kernel(const PairDesc *pairs, uint32_t n_pairs, const ui
             const uint32_t dB = static_cast<uint32_t>(s_don[(c[4] * 5 + c[5]) * 5 + c[6]]);   // d(i)
             const uint32_t aA = static_cast<uint32_t>(s_acc[(c[1] * 5 + c[2]) * 5 + c[3]]);   // a(i)
             const uint32_t aC = static_cast<uint32_t>(s_acc[(c[0] * 5 + c[1]) * 5 + c[2]]);   // a(i-1)
-            out[k] = make_uint4((r + dC) | ((r + dB) << 16), aA | (aC << 16), static_cast<uint32_t>(aa) * zrow, 0u);
+            out[k] = make_uint4(neg2(r + dC, r + dB), neg2(aA, aC), static_cast<uint32_t>(aa) * zrow, 0u);
         }
     }
 }

@@ -20,8 +20,9 @@
 // Chaining, per protein (one warp each): its k-mers' hits as anchors
 // (strand, x = bin, y = residue), sorted; the recurrence of Eq. 2 with the
 // gap of Eq. 1 and the penalty of Eq. 3 (G = 200,000, beta = 0.75) in fixed
-// point with 16 fractional bits, predecessors evaluated 32 at a time; then
-// the chains in order of decreasing score of their last anchor.
+// point with 16 fractional bits (the log term from a table of every |g| < G),
+// predecessors evaluated 32 at a time; then the chains in order of
+// decreasing score of their last anchor.
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -370,21 +371,34 @@ __device__ __forceinline__ int64_t gap_eq1(int64_t dx, int64_t dy)
     return 0;
 }
 
+// floor(S beta log2(v)) for v = |g| + 1: an integer log2 for a power of two
+// (the device log2 need not be exact there), the double log2 otherwise
+// (each such value lies at least 6.8e-6 from an integer for |g| < G)
+__device__ __forceinline__ int64_t log_term(uint64_t v)
+{
+    return (v & (v - 1)) == 0
+               ? static_cast<int64_t>(63 - __clzll(static_cast<long long>(v))) * (3 * kScale / 4)
+               : static_cast<int64_t>(floor(0.75 * static_cast<double>(kScale) * log2(static_cast<double>(v))));
+}
+
+// the log term of every |g| < G, computed once per chaining call
+__global__ void log_table_kernel(int32_t *tab)
+{
+    for (int64_t a = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; a < kG;
+         a += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        tab[a] = static_cast<int32_t>(log_term(static_cast<uint64_t>(a + 1)));
+}
+
 // Eq. 3 in units of 2^-16: floor(S |g| / 3) and floor(S beta log2(|g| + 1))
-// (their sum for g > 0, the smaller for g < 0); -1 if |g| >= G
-__device__ __forceinline__ int64_t penalty_eq3(int64_t g)
+// (their sum for g > 0, the smaller for g < 0); -1 if |g| >= G.  lt: the
+// log terms of log_table_kernel.
+__device__ __forceinline__ int64_t penalty_eq3(int64_t g, const int32_t *lt)
 {
     if (g == 0) return 0;
     const int64_t a = g < 0 ? -g : g;
     if (a >= kG) return -1;
     const int64_t lin = (a * kScale) / 3;
-    // floor(S beta log2(|g| + 1)): an integer log2 for a power of two (the
-    // device log2 need not be exact there), the double log2 otherwise (each
-    // such value lies at least 6.8e-6 from an integer for |g| < G)
-    const uint64_t v = static_cast<uint64_t>(a + 1);
-    const int64_t lg = (v & (v - 1)) == 0
-                           ? static_cast<int64_t>(63 - __clzll(static_cast<long long>(v))) * (3 * kScale / 4)
-                           : static_cast<int64_t>(floor(0.75 * static_cast<double>(kScale) * log2(static_cast<double>(v))));
+    const int64_t lg = __ldg(lt + a);
     if (g > 0) return lin + lg;
     return lin < lg ? lin : lg;
 }
@@ -413,6 +427,7 @@ struct ChainArgs {
     int top;
     mp_chain *chains;             // n_prot * top
     uint32_t *n_chains;
+    const int32_t *log_tab;       // log terms of Eq. 3 for |g| < G
 };
 
 __global__ void anchor_count_kernel(ChainArgs a, uint64_t *count)
@@ -469,13 +484,13 @@ __global__ void anchor_fill_kernel(ChainArgs a)
 // bitonic network, in shared memory up to kSortMax anchors, otherwise over
 // a scratch range of the next power of two (its tail padded with the
 // largest key) in global memory.
-constexpr int kSortMax = 4096;
-constexpr int kSortThreads = 512;
+constexpr int kSortMax = 16384;           // 128 KB of shared memory
+constexpr int kSortThreads = 1024;
 
 __global__ void __launch_bounds__(kSortThreads) anchor_sort_kernel(ChainArgs a, uint64_t *scratch,
                                                                    const uint64_t *scratch_off)
 {
-    __shared__ uint64_t sh[kSortMax];
+    extern __shared__ uint64_t sh[];
     for (uint32_t p = blockIdx.x; p < a.n_prot; p += gridDim.x) {
         const uint64_t b0 = a.anc_off[p], n = a.anc_off[p + 1] - b0;
         if (n < 2) continue;
@@ -537,7 +552,7 @@ __global__ void chain_kernel(ChainArgs a)
                     const uint64_t vi = A[i];
                     const int64_t dy = yj - anc_y(vi);
                     if (anc_strand(vi) == sj && anc_x(vi) <= xj && dy > 0) {
-                        const int64_t pen = penalty_eq3(gap_eq1(xj - anc_x(vi), dy));
+                        const int64_t pen = penalty_eq3(gap_eq1(xj - anc_x(vi), dy), a.log_tab);
                         if (pen >= 0) cand = F[i] + (dy < kK ? dy : kK) * S - pen;
                     }
                 }
@@ -798,7 +813,13 @@ extern "C" int mp_index_chain(mp_dp_ctx *ctx, const mp_index *idx, const char *p
     SCK(cudaMemcpyAsync(d_prot.p, prot, span, cudaMemcpyHostToDevice, st));
     SCK(cudaMemcpyAsync(d_off.p, prot_off, n_prot * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
     SCK(cudaMemcpyAsync(d_len.p, prot_len, n_prot * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    Tmp<int32_t> d_log;
+    SCK(d_log.alloc(kG));
+    SCK(cudaFuncSetAttribute(anchor_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSortMax * sizeof(uint64_t))));
+    log_table_kernel<<<grid_for(kG, 256), 256, 0, st>>>(d_log.p);
     ChainArgs a{};
+    a.log_tab = d_log.p;
     a.prot = d_prot.p;
     a.prot_off = d_off.p;
     a.prot_len = d_len.p;
@@ -856,7 +877,8 @@ extern "C" int mp_index_chain(mp_dp_ctx *ctx, const mp_index *idx, const char *p
         b.chains = d_ch.p + static_cast<uint64_t>(p0) * top;
         b.n_chains = d_nch.p + p0;
         anchor_fill_kernel<<<grid_for(np * 32ull, 256), 256, 0, st>>>(b);
-        anchor_sort_kernel<<<np < 65535u * 4 ? np : 65535u * 4, kSortThreads, 0, st>>>(b, sc.p, d_soff.p);
+        anchor_sort_kernel<<<np < 65535u * 4 ? np : 65535u * 4, kSortThreads, kSortMax * sizeof(uint64_t), st>>>(
+            b, sc.p, d_soff.p);
         chain_kernel<<<grid_for(np * 32ull, 128), 128, 0, st>>>(b);
         SCK(cudaGetLastError());
         SCK(cudaStreamSynchronize(st));
