@@ -503,9 +503,11 @@ def main():
     ap.add_argument("--c5-scale", type=float, default=1.0, help="shrink the genome-scale workload (tests)")
     ap.add_argument("--mode", default="local", choices=["local", "global", "extension"],
                     help="DP mode of the main leg (profiling runs; the bench line reports local mode)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "seed"],
                     help="c2: the 4,096-pair batch (default); c3: the 20,000-pair uneven-size stress batch; "
-                         "c5: the candidate regions of the genome-scale workload")
+                         "c5: the candidate regions of the genome-scale workload; seed: only the GPU seeding and "
+                         "chaining of the genome-scale workload shrunk by --seed-scale (profiling runs)")
+    ap.add_argument("--seed-scale", type=float, default=0.1, help="size of the seeding and chaining workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -521,6 +523,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.workload == "seed":
+        mpbuild.build()
+        print(json.dumps({"metric": METRIC, "seed_chain": seed_chain_leg(mp, torch, local, args.seed_scale)}),
+              flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

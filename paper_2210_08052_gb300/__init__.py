@@ -30,7 +30,8 @@ EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_ba
             "mp_dp_submit", "mp_dp_poll", "mp_dp_wait_any", "mp_dp_destroy", "mp_dp_strerror",
             "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats",
             "mp_dp_score_pair_noalloc", "mp_dp_autotune", "mp_dp_set_tuning", "mp_dp_get_tuning",
-            "mp_dp_tuning_save", "mp_dp_tuning_load", "mp_dp_exon_rescore", "mp_dp_debug_h"]
+            "mp_dp_tuning_save", "mp_dp_tuning_load", "mp_dp_exon_rescore", "mp_dp_debug_h",
+            "mp_index_build", "mp_index_chain", "mp_index_download", "mp_index_free"]
 
 
 class mp_dp_params(ctypes.Structure):
