@@ -405,6 +405,7 @@ def measure(mp, torch, src, n_pairs, cells, ascii_bytes, steps, warmup, device, 
             "kernel_ms": {"dp_int16": statistics.mean(dp_ms), "rerun_int32": statistics.mean(rr_ms),
                           "traceback_compact": statistics.mean(tb_ms), "pipeline": statistics.mean(tot_ms)},
             "dp_ms": dp_ms, "tot_ms": tot_ms, "waves": stats["n_waves"], "code_bytes": stats["code_bytes"],
+            "moved": {k: stats[k] for k in ("record_bytes", "record_read_bytes", "boundary_bytes")},
             "launches": stats["n_launches"], "n_rerun": int(((res["status"] & 1) != 0).sum()),
             "clocks": clk.summary(), "tuning": tuning, "e2e": e2e,
             "e2e_s": e2e_t / e2e_steps if e2e_steps else None}
@@ -431,11 +432,45 @@ def roofline(m, cells, torch, device, peaks):
             "ops_per_cell": OPS_PER_CELL, "time_basis": time_basis,
             "peak_basis": f"{nsm} SMs x 128 lanes x 2 int16 halves x {f_mhz:.0f} MHz (median SM clock under load)",
             "hbm_write_gbs": m["code_bytes"] / (dp_avg_ms / 1000) / 1e9 if dp_avg_ms else None,
+            "bytes_by_construction": {
+                "stream_written": m["code_bytes"], "records_written": m["moved"]["record_bytes"],
+                "records_read_by_strips": m["moved"]["record_read_bytes"],
+                "boundary_rows": m["moved"]["boundary_bytes"],
+                "stream_per_cell": m["code_bytes"] / cells if cells else None,
+                "basis": "counted by the library's planner for this run, per pipeline run: the H stream "
+                         "(padding of the last strip and chunk and the column maxima included), the per-nt "
+                         "records (written once, read by every strip of the pair, mostly from L2), the "
+                         "boundary rows between strips (written and read once, mostly in L2); "
+                         "'traffic' is the DRAM count of the committed ncu capture, scaled by cells"},
             "issue_frac": (cells / 64 * ips / (dp_avg_ms / 1000) / (nsm * 4 * f_mhz * 1e6))
             if (dp_avg_ms and ips) else None,
             "issue_basis": "warp-instructions per 64-cell step from the committed ncu summary x steps/s "
                            "over N_SM x 4 issue slots x f_SM",
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
+
+
+def with_ceilings(roof, mp, m, cells, torch, device):
+    """Add the measured integer ceilings (mp_dp_op_rates): each packed
+    operation's rate alone and the int16 step's arithmetic alone at full
+    occupancy, and the DP kernel's fraction of the latter."""
+    try:
+        r = mp.mp_dp_op_rates(device if isinstance(device, int) else (device.index or 0))
+    except Exception as exc:                      # reported, not fatal: the main figures stand
+        roof["alu_ceilings"] = {"error": str(exc)}
+        return roof
+    nsm = torch.cuda.get_device_properties(device).multi_processor_count
+    f_mhz = m["clocks"].get("sm_mhz") or 2070.0
+    dp_ms = statistics.mean(m["tot_ms"] if m["waves"] > 1 else m["dp_ms"]) if m["dp_ms"] else None
+    step_cells_s = r["step_cells_per_clk_sm"] * nsm * f_mhz * 1e6
+    roof["alu_ceilings"] = {
+        **{k: round(v, 3) if isinstance(v, float) else v for k, v in r.items()},
+        "unit": "warp instructions per clock per SM (each operation alone); cells per clock per SM (step)",
+        "step_ceiling_gcups": step_cells_s / 1e9,
+        "frac_of_step_ceiling": (cells / (dp_ms / 1000) / step_cells_s) if dp_ms else None,
+        "basis": "SM clocks counted in the kernels; the step ceiling is the int16 step's arithmetic on "
+                 "register state at full occupancy, without records, profile loads, stream stores or waits",
+    }
+    return roof
 
 
 def seed_chain_leg(mp, torch, device, scale=0.1, reps=3):
@@ -591,7 +626,7 @@ def main():
         "pairs_per_s": pairs_per_s,
         "kernel_ms": m["kernel_ms"],
         "n_rerun": m["n_rerun"],
-        "roofline": roofline(m, cells, torch, local, peaks),
+        "roofline": with_ceilings(roofline(m, cells, torch, local, peaks), mp, m, cells, torch, local),
         "clocks": clocks,
         "gpu_launches": m["launches"] * args.steps,
         "tuning": m["tuning"],

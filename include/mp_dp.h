@@ -367,7 +367,14 @@ typedef struct {
     int32_t n_rerun;           /* pairs re-run in int32 */
     int32_t n_launches;        /* kernels launched by the last run */
     int32_t n_dp_launches;     /* DP kernel launches (int16 + int32) */
-    uint64_t code_bytes;       /* traceback bytes written (algorithmic) */
+    uint64_t code_bytes;       /* traceback stream written: H of every cell of every strip
+                                  (padding of the last strip and chunk included) and the
+                                  per-chunk column maxima */
+    uint64_t record_bytes;     /* per-nt records written by the precompute kernel */
+    uint64_t record_read_bytes;  /* records the strips queue into shared memory (every strip
+                                    reads its pair's records; mostly L2 hits after the first) */
+    uint64_t boundary_bytes;   /* boundary rows written between strips (each read once by
+                                  the next strip) */
 } mp_dp_stats;
 
 /* Launch configuration of the DP.  The paper's DP is a SIMD loop on CPU
@@ -436,6 +443,28 @@ int mp_dp_get_stats(mp_dp_ctx *ctx, mp_dp_stats *s);
 
 /* Number of streaming multiprocessors of the context's device. */
 int mp_dp_num_sms(mp_dp_ctx *ctx);
+
+/* Measured integer ceilings behind the DP kernel's roofline (no
+ * counterpart in the method: Eq. 7 is a max-plus scan on the integer ALU).
+ * Rates are counted in SM clocks, every warp slot occupied:
+ *   - max_u16x2 .. imad: warp instructions per clock per SM of one packed
+ *     16-bit operation alone (max, fused add-max, three-way max, byte
+ *     permute, three-input logic, integer multiply-add), eight independent
+ *     chains per thread, one plain add per eight operations;
+ *   - step_cells_per_clk_sm: cells per clock per SM of the int16 step's
+ *     arithmetic alone (the eleven fused add-max terms of Eq. 7, the
+ *     three-way maxima, the [H, I] hand-over by shuffle and byte permute,
+ *     the chunk maximum) on register state, warps_per_sm_step warps per SM.
+ * The call allocates a few MB on `device` and runs for well under a second;
+ * it needs no context.  MP_EINVAL: null out or no such device; MP_ENOMEM,
+ * MP_ECUDA as usual. */
+typedef struct {
+    double max_u16x2, viaddmax_u16x2, vimax3_u16x2, prmt, lop3, imad;
+    double step_cells_per_clk_sm;
+    int32_t warps_per_sm_step;
+    int32_t reserved;
+} mp_op_rates;
+int mp_dp_op_rates(int device, mp_op_rates *out);
 
 /* Test hook (no counterpart in the method): the H values of Eq. 7 the DP
  * stored for pair k of `batch`, read back through the traceback's view of

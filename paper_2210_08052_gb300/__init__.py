@@ -31,7 +31,7 @@ EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_ba
             "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats",
             "mp_dp_score_pair_noalloc", "mp_dp_autotune", "mp_dp_set_tuning", "mp_dp_get_tuning",
             "mp_dp_tuning_save", "mp_dp_tuning_load", "mp_dp_exon_rescore", "mp_dp_debug_h",
-            "mp_index_build", "mp_index_chain", "mp_index_download", "mp_index_free"]
+            "mp_index_build", "mp_index_chain", "mp_index_download", "mp_index_free", "mp_dp_op_rates"]
 
 
 class mp_dp_params(ctypes.Structure):
@@ -43,6 +43,13 @@ class mp_dp_params(ctypes.Structure):
                 ("max_pairs_per_launch", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
                 ("debug_flags", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("splice_p", ctypes.c_int32), ("exon_rescore", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+
+
+class mp_op_rates(ctypes.Structure):
+    _fields_ = [("max_u16x2", ctypes.c_double), ("viaddmax_u16x2", ctypes.c_double),
+                ("vimax3_u16x2", ctypes.c_double), ("prmt", ctypes.c_double), ("lop3", ctypes.c_double),
+                ("imad", ctypes.c_double), ("step_cells_per_clk_sm", ctypes.c_double),
+                ("warps_per_sm_step", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class mp_profile_pos(ctypes.Structure):
@@ -82,7 +89,9 @@ class mp_dp_stats(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_double), ("dp_ms", ctypes.c_double), ("rerun_ms", ctypes.c_double),
                 ("tb_ms", ctypes.c_double), ("pack_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
                 ("n_waves", ctypes.c_int32), ("n_rerun", ctypes.c_int32), ("n_launches", ctypes.c_int32),
-                ("n_dp_launches", ctypes.c_int32), ("code_bytes", ctypes.c_uint64)]
+                ("n_dp_launches", ctypes.c_int32), ("code_bytes", ctypes.c_uint64),
+                ("record_bytes", ctypes.c_uint64), ("record_read_bytes", ctypes.c_uint64),
+                ("boundary_bytes", ctypes.c_uint64)]
 
 
 class mp_dp_tuning(ctypes.Structure):
@@ -131,6 +140,7 @@ def lib():
             "mp_dp_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "mp_dp_get_stats": (ctypes.c_int, [vp, P(mp_dp_stats)]),
             "mp_dp_num_sms": (ctypes.c_int, [vp]),
+            "mp_dp_op_rates": (ctypes.c_int, [ctypes.c_int, P(mp_op_rates)]),
             "mp_dp_get_serve_stats": (ctypes.c_int, [vp, P(mp_dp_serve_stats), ctypes.c_int]),
             "mp_dp_score_pair_noalloc": (ctypes.c_int, [P(mp_dp_params), vp, ctypes.c_uint32, vp, ctypes.c_uint32,
                                                         ctypes.c_int8, vp, vp]),
@@ -438,6 +448,13 @@ def mp_dp_exon_rescore(ctx, pairs, results) -> list:
 
 def mp_dp_num_sms(ctx) -> int:
     return lib().mp_dp_num_sms(ctx)
+
+
+def mp_dp_op_rates(device: int = 0) -> dict:
+    """Measured integer ceilings of the device (see mp_dp_op_rates in mp_dp.h)."""
+    r = mp_op_rates()
+    _check(lib().mp_dp_op_rates(device, ctypes.byref(r)), "mp_dp_op_rates")
+    return {name: getattr(r, name) for name, _ in mp_op_rates._fields_ if name != "reserved"}
 
 
 def mp_dp_debug_h(ctx, batch, k: int, nt_len: int, prot_len: int) -> np.ndarray:

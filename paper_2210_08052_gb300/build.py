@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libmpdp.so")
-SOURCES = ["dp_kernel.cu", "tb_kernel.cu", "runtime.cu", "seed.cu"]
+SOURCES = ["dp_kernel.cu", "tb_kernel.cu", "runtime.cu", "seed.cu", "opbench.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

@@ -215,6 +215,9 @@ struct mp_dp_batch {
     uint64_t ascii_bytes = 0, prot_total = 0, nt_words = 0, bnd_total = 0, ops_total = 0;
     double cells = 0;
     uint64_t code_bytes_total = 0;
+    // bytes moved by construction (planned, per run): records written and
+    // read by the strips, boundary rows handed between strips
+    uint64_t record_bytes_total = 0, record_read_total = 0, bnd_bytes_total = 0;
     // device
     DevBuf<char> ascii;
     DevBuf<PairDesc> d_desc;
@@ -689,6 +692,7 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool 
     const uint64_t strips = b->strips_total;
     b->waves.clear();
     b->code_bytes_total = 0;
+    b->record_bytes_total = b->record_read_total = b->bnd_bytes_total = 0;
     // ---- pair order: largest first (longest-processing-time first), ties
     // in input order
     std::vector<uint64_t> pcells(n);
@@ -812,6 +816,15 @@ static int plan_waves(mp_dp_ctx *c, mp_dp_batch *b, const mp_dp_tuning &t, bool 
         cur += cbytes[p];
         if (cbytes[p])
             b->code_bytes_total += code_bytes(d.prot_len, d.nt_len, (d.flags & PF_WIDE) != 0, (d.flags & PF_W128) != 0);
+        {
+            const uint64_t W = (d.flags & PF_W128) ? kStripWMax : kStripW;
+            const uint64_t nch = div_up(static_cast<uint64_t>(d.nt_len) + W - 1, kChunk);
+            b->record_bytes_total += records_of(d.nt_len) * sizeof(uint4);
+            // each strip queues one chunk of records ahead of its first
+            b->record_read_total += static_cast<uint64_t>(d.n_strips) * (nch + 1) * kChunk * sizeof(uint4);
+            b->bnd_bytes_total += static_cast<uint64_t>(d.n_strips > 0 ? d.n_strips - 1 : 0) * nch * kChunk *
+                                  ((d.flags & PF_WIDE) ? 8 : 4);
+        }
         for (uint32_t s = 0; s < d.n_strips; ++s) b->h_items.push_back(make_uint2(p, s));
         if (wide(p) == 0) nwide += d.n_strips;
     }
@@ -926,6 +939,7 @@ static int upload_impl(mp_dp_ctx *c, mp_dp_batch *b, const mp_pair *pairs, size_
     b->waves.clear();
     b->cells = 0;
     b->code_bytes_total = 0;
+    b->record_bytes_total = b->record_read_total = b->bnd_bytes_total = 0;
     // ---- shared host ranges: when every pair's region lies in one host
     // range no longer than the regions' total length (windows of one genome),
     // and the same holds for the proteins (one protein, several regions),
@@ -1612,6 +1626,9 @@ static int collect_stats(mp_dp_ctx *c, mp_dp_batch *b)
     s.n_launches = b->n_launches;
     s.n_dp_launches = b->n_dp_launches;
     s.code_bytes = b->code_bytes_total;
+    s.record_bytes = b->record_bytes_total;
+    s.record_read_bytes = b->record_read_total;
+    s.boundary_bytes = b->bnd_bytes_total;
     if (c->timing && !b->events.empty()) {
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, b->events[0], b->events[1]));

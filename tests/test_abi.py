@@ -53,11 +53,12 @@ def test_struct_layout_matches_header(mp, tmp_path):
     src.write_text("""#include <stdio.h>
 #include <stddef.h>
 #include "mp_dp.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mp_result),
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mp_result),
  sizeof(mp_pair), sizeof(mp_dp_params), sizeof(mp_dp_stats), offsetof(mp_result, cigar), offsetof(mp_pair, strand),
  offsetof(mp_dp_params, tb_budget_bytes), offsetof(mp_dp_params, autotune), sizeof(mp_dp_tuning),
  offsetof(mp_dp_tuning, ms), offsetof(mp_dp_tuning, strip_width), offsetof(mp_pair, profile),
- sizeof(mp_profile_pos), offsetof(mp_profile_pos, gap_ext)); return 0;}""")
+ sizeof(mp_profile_pos), offsetof(mp_profile_pos, gap_ext), sizeof(mp_op_rates),
+ offsetof(mp_op_rates, warps_per_sm_step)); return 0;}""")
     exe = tmp_path / "sz"
     import subprocess
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
@@ -66,7 +67,8 @@ int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\
             ctypes.sizeof(mp.mp_dp_stats), mp.mp_result.cigar.offset, mp.mp_pair.strand.offset,
             mp.mp_dp_params.tb_budget_bytes.offset, mp.mp_dp_params.autotune.offset,
             ctypes.sizeof(mp.mp_dp_tuning), mp.mp_dp_tuning.ms.offset, mp.mp_dp_tuning.strip_width.offset,
-            mp.mp_pair.profile.offset, ctypes.sizeof(mp.mp_profile_pos), mp.mp_profile_pos.gap_ext.offset]
+            mp.mp_pair.profile.offset, ctypes.sizeof(mp.mp_profile_pos), mp.mp_profile_pos.gap_ext.offset,
+            ctypes.sizeof(mp.mp_op_rates), mp.mp_op_rates.warps_per_sm_step.offset]
     assert got == want
 
 
