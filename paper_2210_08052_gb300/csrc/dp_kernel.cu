@@ -115,7 +115,12 @@ struct WarpSmem {
     // step all lanes read records of one parity at consecutive indices, so the
     // 16-byte loads are free of bank conflicts
     uint4 ring[2][kRing / 2 + kRingPad / 2];
-    uint32_t prof[kProfRows * 32];
+    // substitution profile of the strip, as two tables: prof[aa][lane] holds
+    // s(aa, P[2l]) in its low half (high half 0) and prof[kProfRows + aa][lane]
+    // s(aa, P[2l+1]) in its high half (low half 0), so that one addition of
+    // this step's low word and the previous step's high word packs the two
+    // cells' scores (the hi cell is a row behind the lo cell)
+    uint32_t prof[2 * kProfRows * 32];
     alignas(16) BndT bin[kChunk];
     alignas(16) BndT bout[kChunk];
 };
@@ -198,6 +203,8 @@ struct Ops16 {
 
     struct Consts {
         uint32_t NQE, E, NF;               // packed -(q+e) (negated per half), e, -f
+        uint32_t EN;                       // e of the columns the lane's I values move to:
+                                           // [e(2l+1), e(2l+2)] (the same as E unless a profile)
         uint32_t FLOOR;                    // local: biased 0 (the restart); anchored modes: 0 (none)
         uint32_t ROW0;                     // H in row 0 of the lane's two columns (biased)
     };
@@ -215,6 +222,7 @@ struct Ops16 {
         c.NQE = neg2(qe, qe);
         c.E = static_cast<uint32_t>(sp.e) | (static_cast<uint32_t>(sp.e) << 16);
         c.NF = neg2(static_cast<uint32_t>(sp.f), static_cast<uint32_t>(sp.f));
+        c.EN = c.E;
         c.FLOOR = sp.mode == MP_MODE_LOCAL ? Z : 0u;
         c.ROW0 = Z;
         return c;
@@ -229,10 +237,12 @@ struct Ops16 {
     }
     static __device__ __forceinline__ void set_row0(Consts &c, int lo, int hi) { c.ROW0 = pack2(lo, hi); }
     // profile queries: the gap costs of the lane's two columns (packed halves)
-    static __device__ __forceinline__ void set_gaps(Consts &c, int qlo, int elo, int qhi, int ehi)
+    // enext: e of the column right of the lane's hi column
+    static __device__ __forceinline__ void set_gaps(Consts &c, int qlo, int elo, int qhi, int ehi, int enext)
     {
         c.NQE = neg2(static_cast<uint32_t>(qlo + elo), static_cast<uint32_t>(qhi + ehi));
         c.E = static_cast<uint32_t>(elo) | (static_cast<uint32_t>(ehi) << 16);
+        c.EN = static_cast<uint32_t>(ehi) | (static_cast<uint32_t>(enext) << 16);
     }
     // boundary entry of column 0 in the anchored modes: [H, I = -inf]
     static __device__ __forceinline__ Bnd col0_entry(int h)
@@ -286,21 +296,26 @@ struct Ops16 {
         const uint32_t VD0 = rec.x, VA0 = rec.y;          // negated penalties
         const uint32_t X0 = *reinterpret_cast<const uint32_t *>(
             reinterpret_cast<const char *>(prof_lane) + rec.z);
-        const uint32_t S = (X0 & 0x0000ffffu) | (s.X1 & 0xffff0000u);   // lo: s(i, 2l); hi: s(i-1, 2l+1)
-        // each term of Eq. 7 that subtracts a penalty is one fused add-max
-        uint32_t I0 = vaddmax(s.L0, c.NQE, s.IL - c.E);    // max(H[i][j-1] - q - e, I[i][j-1] - e)
+        const uint32_t X0h = *reinterpret_cast<const uint32_t *>(
+            reinterpret_cast<const char *>(prof_lane + kProfRows * 32) + rec.z);
+        const uint32_t S = X0 + s.X1;                     // lo: s(i, 2l); hi: s(i-1, 2l+1)
+        // each term of Eq. 7 that subtracts a penalty is one fused add-max;
+        // IL holds I[i][j-1] - e (the sender subtracted the extension)
+        uint32_t I0 = vaddmax(s.L0, c.NQE, s.IL);         // max(H[i][j-1] - q - e, I[i][j-1] - e)
         uint32_t D0 = vaddmax(s.H3, c.NQE, s.D3 - c.E);    // max(H[i-3][j] - q - e, D[i-3][j] - e)
         uint32_t A0 = vaddmax(s.H1, s.VD2, s.A1);         // max(H[i-1][j] - r - d(i-1), A[i-1][j])
         uint32_t B0 = vaddmax(s.L1, s.VD1, s.B1);         // max(H[i-1][j-1] - r - d(i), B[i-1][j])
         uint32_t C0 = vaddmax(s.L1, VD0, s.C1);           // max(H[i-1][j-1] - r - d(i+1), C[i-1][j])
-        // H: the intron exits and the frameshift terms (all known before this
-        // step's neighbours) in one chain, the match, I and D in another
+        // H: the intron exits and the frameshift terms in one chain, the terms
+        // known a step early (H two rows up, the B and C exits) first and
+        // those of the previous step's H last; the match and D in another;
+        // I, which depends on this step's neighbour, joins in the last max
         uint32_t Y = vaddmax(s.H2, c.NF, c.FLOOR);        // H[i-2][j] - f
-        Y = vaddmax(vmax3(s.L1, s.L2, s.H1), c.NF, Y);    // H[i-1][j-1], H[i-2][j-1], H[i-1][j] - f
         Y = vaddmax(C0, s.VA1, Y);                        // C - a(i-1)
         Y = vaddmax(B0, s.VA2, Y);                        // B - a(i-2)
+        Y = vaddmax(vmax3(s.L1, s.L2, s.H1), c.NF, Y);    // H[i-1][j-1], H[i-2][j-1], H[i-1][j] - f
         Y = vaddmax(A0, VA0, Y);                          // A - a(i)
-        uint32_t H0 = vmax3(vaddmax(s.L3, S, I0), D0, Y); // H[i-3][j-1] + s(i, j), I, D
+        uint32_t H0 = vmax3(vaddmax(s.L3, S, D0), I0, Y); // H[i-3][j-1] + s(i, j), D, I
 
         uint32_t vmask = 0xffffffffu;
         if (MASKED) {
@@ -317,20 +332,23 @@ struct Ops16 {
             vmask = ((ii >= 0 && ii < n) ? 0x0000ffffu : 0u) | ((ii >= 1 && ii <= n) ? 0xffff0000u : 0u);
         }
 
-        // hand [H, I] of the hi cell to the next lane; lane 0 takes the strip boundary
-        const uint32_t W = prmt<0x7632>(H0, I0);
+        // hand [H, I - e] of the hi cell to the next lane (the receiving
+        // column's extension, subtracted here, off the step's chain); lane 0
+        // takes the strip boundary, which holds the same form
+        const uint32_t I0mE = I0 - c.EN;
+        const uint32_t W = prmt<0x7632>(H0, I0mE);
         uint32_t R = __shfl_up_sync(kFull, W, 1);
         if (lane == 0) R = bin;
         wout = W;
         s.L3 = s.L2; s.L2 = s.L1; s.L1 = s.L0;
         s.L0 = prmt<0x5410>(R, H0);
-        s.IL = prmt<0x5432>(R, I0);
+        s.IL = prmt<0x5432>(R, I0mE);
         s.H3 = s.H2; s.H2 = s.H1; s.H1 = H0;
         s.D3 = s.D2; s.D2 = s.D1; s.D1 = D0;
         s.A1 = A0; s.B1 = B0; s.C1 = C0;
         s.VD2 = s.VD1; s.VD1 = VD0;
         s.VA2 = s.VA1; s.VA1 = VA0;
-        s.X1 = X0;
+        s.X1 = X0h;
 
         // best cell: key = H << 16 | (0xffff - step within chunk); the
         // largest key is the largest H at its first step
@@ -432,7 +450,7 @@ struct Ops32 {
     static __device__ __forceinline__ V2 pack2(int lo, int hi) { return V2{lo, hi}; }
     static __device__ __forceinline__ void set_row0(Consts &c, int lo, int hi) { c.row0lo = lo; c.row0hi = hi; }
     // profile queries: the gap costs of the lane's two columns
-    static __device__ __forceinline__ void set_gaps(Consts &c, int qlo, int elo, int qhi, int ehi)
+    static __device__ __forceinline__ void set_gaps(Consts &c, int qlo, int elo, int qhi, int ehi, int)
     {
         c.qe = V2{qlo + elo, qhi + ehi};
         c.e = V2{elo, ehi};
@@ -472,6 +490,8 @@ struct Ops32 {
         const V2 VD0 = unpack_neg16(rec.x), VA0 = unpack_neg16(rec.y);   // negated penalties
         const uint32_t X0 = *reinterpret_cast<const uint32_t *>(
             reinterpret_cast<const char *>(prof_lane) + rec.z);
+        const uint32_t X0h = *reinterpret_cast<const uint32_t *>(
+            reinterpret_cast<const char *>(prof_lane + kProfRows * 32) + rec.z);
         const V2 S{static_cast<int32_t>(X0 << 16) >> 16, static_cast<int32_t>(s.X1) >> 16};
         const V2 M = add(s.L3, S);
         const V2 Iopen = sub(s.L0, c.qe), Iext = sub(s.IL, c.e);
@@ -509,7 +529,7 @@ struct Ops32 {
         s.A1 = A0; s.B1 = B0; s.C1 = C0;
         s.VD2 = s.VD1; s.VD1 = VD0;
         s.VA2 = s.VA1; s.VA1 = VA0;
-        s.X1 = X0;
+        s.X1 = X0h;
 
         if (vlo && H0.lo > s.bslo) { s.bslo = H0.lo; s.btlo = s.t; }
         if (vhi && H0.hi > s.bshi) { s.bshi = H0.hi; s.bthi = s.t; }
@@ -937,8 +957,9 @@ __device__ void run_strip(const DPArgs &a, typename Ops::Smem &sm, const PairDes
         Ops::set_row0(c, row0(jcol), row0(jcol + 1));
         if (pf) {
             const int jl = jcol <= m ? jcol : 0, jh = jcol + 1 <= m ? jcol + 1 : 0;
+            const int jn = jcol + 2 <= m ? jcol + 2 : 0;
             Ops::set_gaps(c, jl ? pf[jl].q : a.sp.q, jl ? pf[jl].e : a.sp.e, jh ? pf[jh].q : a.sp.q,
-                          jh ? pf[jh].e : a.sp.e);
+                          jh ? pf[jh].e : a.sp.e, jn ? pf[jn].e : a.sp.e);
         }
     }
     const int nsteps = n + W - 1;
@@ -977,14 +998,18 @@ __device__ void run_strip(const DPArgs &a, typename Ops::Smem &sm, const PairDes
         if (pf) {
             // a profile query: position-specific scores (no codon: -512 as subst_score)
 #pragma unroll 2
-            for (int aa = 0; aa < kProfRows; ++aa)
+            for (int aa = 0; aa < kProfRows; ++aa) {
                 sm.prof[aa * 32 + lane] =
-                    Ops::prof_entry(aa == 21 ? -512 : jlo < m ? pf[jlo + 1].s[aa] : subst_score(a.sp, aa, 21),
-                                    aa == 21 ? -512 : jhi < m ? pf[jhi + 1].s[aa] : subst_score(a.sp, aa, 21));
+                    Ops::prof_entry(aa == 21 ? -512 : jlo < m ? pf[jlo + 1].s[aa] : subst_score(a.sp, aa, 21), 0);
+                sm.prof[(kProfRows + aa) * 32 + lane] =
+                    Ops::prof_entry(0, aa == 21 ? -512 : jhi < m ? pf[jhi + 1].s[aa] : subst_score(a.sp, aa, 21));
+            }
         } else {
 #pragma unroll 2
-            for (int aa = 0; aa < kProfRows; ++aa)
-                sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), subst_score(a.sp, aa, phi));
+            for (int aa = 0; aa < kProfRows; ++aa) {
+                sm.prof[aa * 32 + lane] = Ops::prof_entry(subst_score(a.sp, aa, plo), 0);
+                sm.prof[(kProfRows + aa) * 32 + lane] = Ops::prof_entry(0, subst_score(a.sp, aa, phi));
+            }
         }
         // records for ii in [-kChunk, kChunk)
         fetch_records(sm, recs, -kChunk, lane);
@@ -1006,7 +1031,7 @@ __device__ void run_strip(const DPArgs &a, typename Ops::Smem &sm, const PairDes
             const int ii0 = -2 * lane;
             const uint4 rm1 = get_record(sm, ii0 - 1);
             const uint4 rm2 = get_record(sm, ii0 - 2);
-            const uint32_t xm1 = sm.prof[(rm1.z >> 7) * 32 + lane];
+            const uint32_t xm1 = sm.prof[(kProfRows + (rm1.z >> 7)) * 32 + lane];   // the hi table
             Ops::init(st, lane, w0, rm1, rm2, xm1, row0(jcol), row0(jcol - 1));
         }
     }
