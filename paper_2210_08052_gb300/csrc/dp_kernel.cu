@@ -307,13 +307,13 @@ struct Ops16 {
         uint32_t B0 = vaddmax(s.L1, s.VD1, s.B1);         // max(H[i-1][j-1] - r - d(i), B[i-1][j])
         uint32_t C0 = vaddmax(s.L1, VD0, s.C1);           // max(H[i-1][j-1] - r - d(i+1), C[i-1][j])
         // H: the intron exits and the frameshift terms in one chain, the terms
-        // known a step early (H two rows up, the B and C exits) first and
-        // those of the previous step's H last; the match and D in another;
-        // I, which depends on this step's neighbour, joins in the last max
-        uint32_t Y = vaddmax(s.H2, c.NF, c.FLOOR);        // H[i-2][j] - f
-        Y = vaddmax(C0, s.VA1, Y);                        // C - a(i-1)
+        // known a step early (the B and C exits) first and those of the
+        // previous step's H last; the match and D in another; I, which
+        // depends on this step's neighbour, joins in the last max
+        uint32_t Y = vaddmax(C0, s.VA1, c.FLOOR);         // C - a(i-1)
         Y = vaddmax(B0, s.VA2, Y);                        // B - a(i-2)
-        Y = vaddmax(vmax3(s.L1, s.L2, s.H1), c.NF, Y);    // H[i-1][j-1], H[i-2][j-1], H[i-1][j] - f
+        // the four frameshift terms H[i-1][j-1], H[i-2][j-1], H[i-2][j], H[i-1][j], less f
+        Y = vaddmax(vmax(vmax3(s.L1, s.L2, s.H2), s.H1), c.NF, Y);
         Y = vaddmax(A0, VA0, Y);                          // A - a(i)
         uint32_t H0 = vmax3(vaddmax(s.L3, S, D0), I0, Y); // H[i-3][j-1] + s(i, j), D, I
 
