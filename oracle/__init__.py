@@ -340,7 +340,14 @@ class Chain(ctypes.Structure):
                 ("y_first", ctypes.c_int64), ("y_last", ctypes.c_int64)]
 
 
+class Chain2(ctypes.Structure):
+    _fields_ = [("n_anchors", ctypes.c_int32), ("reserved", ctypes.c_int32), ("score", ctypes.c_int64),
+                ("x_first", ctypes.c_int64), ("x_last", ctypes.c_int64),
+                ("y_first", ctypes.c_int64), ("y_last", ctypes.c_int64)]
+
+
 CHAIN_K = 6
+REFINE_K = 5                   # k-mer length of the second chaining round
 CHAIN_SCALE = 65536
 
 
@@ -363,6 +370,12 @@ def _chain_lib():
         L.orc_chain_anchors.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(Chain), ctypes.c_void_p]
         L.orc_chain_anchors.restype = ctypes.c_int
+        L.orc_refine_anchors.argtypes = [ctypes.c_char_p, ctypes.c_int64, ctypes.c_char_p, ctypes.c_int64,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]
+        L.orc_refine_anchors.restype = ctypes.c_int64
+        L.orc_refine_chain.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(Chain2),
+                                       ctypes.c_void_p]
+        L.orc_refine_chain.restype = ctypes.c_int
         L._chain_ready = True
     return L
 
@@ -426,3 +439,37 @@ def gap(dx: int, dy: int) -> int:
 def gap_penalty(g: int) -> int:
     """Eq. 3 in units of 2^-16, -1 for an infinite penalty."""
     return _chain_lib().orc_gap_penalty(g)
+
+
+def refine_anchors(prot: str, nt: str, strand: int, k: int = REFINE_K) -> np.ndarray:
+    """Second chaining round ("Chaining", last paragraph): every k-mer of the
+    protein against every k-mer of the region's three frames on its aligned
+    strand, as sorted (x, y) rows (x: base of the first codon, y: residue)."""
+    L = _chain_lib()
+    pb = prot.encode() if isinstance(prot, str) else bytes(prot)
+    nb = nt.encode() if isinstance(nt, str) else bytes(nt)
+    n = L.orc_refine_anchors(pb, len(pb), nb, len(nb), strand, k, None, 0)
+    if n < 0:
+        raise MemoryError("oracle anchors")
+    out = np.zeros((max(n, 1), 2), dtype=np.int64)
+    L.orc_refine_anchors(pb, len(pb), nb, len(nb), strand, k, out.ctypes.data, n)
+    return out[:n]
+
+
+def refine_chain(anc, k: int = REFINE_K):
+    """The best chain of sorted (x, y) anchors with g' = 3 dy - dx and Eq. 3:
+    (chain dict with n_anchors 0 if none, f of every anchor)."""
+    L = _chain_lib()
+    anc = np.ascontiguousarray(anc, dtype=np.int64).reshape(-1, 2)
+    n = len(anc)
+    f = np.zeros(max(n, 1), dtype=np.int64)
+    c = Chain2()
+    if L.orc_refine_chain(anc.ctypes.data, n, k, ctypes.byref(c), f.ctypes.data) < 0:
+        raise MemoryError("oracle chaining")
+    keys = ("n_anchors", "score", "x_first", "x_last", "y_first", "y_last")
+    return {x: getattr(c, x) for x in keys}, f[:n]
+
+
+def refine(prot: str, nt: str, strand: int, k: int = REFINE_K):
+    """The pair's best second-round chain."""
+    return refine_chain(refine_anchors(prot, nt, strand, k), k)[0]

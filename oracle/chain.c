@@ -337,3 +337,104 @@ int orc_chain_anchors(const int64_t *anc, int64_t n, int k, int top, orc_chain_t
     free(a);
     return nc;
 }
+
+/* ------------------------------------------------- second chaining round */
+
+/*
+ * "Chaining", last paragraph: around each of a protein's top chains,
+ * every 5-mer of the protein is matched against every 5-mer of the local
+ * genome region (no sampling, no binning), and the anchors are chained
+ * with the gap g' = 3 dy - dx (dx in bases) and the same penalty, Eq. 3.
+ *
+ * Readings:
+ *   - The local region is given by the caller as a (protein, region,
+ *     strand) pair, the same pairs the DP aligns: the region's aligned
+ *     strand (its reverse complement for strand -1) is read in all three
+ *     frames, a 5-mer starting at every base position x with a full five
+ *     codons.  k-mers use the reduced alphabet of the first round (phi),
+ *     stop codons and codons with a base outside ACGT included (phi 14 and
+ *     15), as are X residues of the protein.
+ *   - Anchors (x, y): x the base of the 5-mer's first codon on the aligned
+ *     strand, y the residue of its first residue.  Sorted by (x, y); f and
+ *     the predecessor rule as in the first round (x_i <= x_j, y_i < y_j,
+ *     alpha = min(dy, k), the first best predecessor, f >= k).
+ *   - The pair's result is its best chain: the anchor with the largest f
+ *     (the earliest on ties) and its predecessors; none if it has a single
+ *     anchor.  Its score is that f.
+ */
+typedef struct {
+    int32_t n_anchors, reserved;
+    int64_t score;
+    int64_t x_first, x_last, y_first, y_last;
+} orc_chain2_t;
+
+static int ch_cmp_xy(const void *a, const void *b)
+{
+    const int64_t *p = (const int64_t *)a, *q = (const int64_t *)b;
+    if (p[0] != q[0]) return p[0] < q[0] ? -1 : 1;
+    return p[1] < q[1] ? -1 : p[1] > q[1];
+}
+
+/* Anchors of the pair as (x, y) pairs in out[2 * cap], sorted; returns the
+ * count (which may exceed cap), or -1. */
+int64_t orc_refine_anchors(const char *prot, int64_t m, const char *nt, int64_t n, int strand, int k,
+                           int64_t *out, int64_t cap)
+{
+    char *seq = (char *)malloc((size_t)n + 1);
+    if (!seq) return -1;
+    for (int64_t t = 0; t < n; ++t) seq[t] = strand >= 0 ? nt[t] : ch_complement(nt[n - 1 - t]);
+    int64_t cnt = 0;
+    for (int64_t x = 0; x + 3 * k <= n; ++x) {
+        uint64_t gk = 0;
+        for (int u = 0; u < k; ++u) gk = gk * 16 + (uint64_t)orc_phi(ch_translate(seq + x + 3 * u));
+        for (int64_t y = 0; y + k <= m; ++y) {
+            uint64_t pk = 0;
+            for (int u = 0; u < k; ++u) pk = pk * 16 + (uint64_t)orc_phi((unsigned char)prot[y + u]);
+            if (pk != gk) continue;
+            if (cnt < cap) { out[2 * cnt] = x; out[2 * cnt + 1] = y; }
+            ++cnt;
+        }
+    }
+    free(seq);
+    if (cnt <= cap) qsort(out, (size_t)cnt, 2 * sizeof(int64_t), ch_cmp_xy);
+    return cnt;
+}
+
+/* Chain n sorted (x, y) anchors with g' = 3 dy - dx: f of every anchor in
+ * f_out (may be NULL) and the best chain in *c.  Returns 0, or -1. */
+int orc_refine_chain(const int64_t *anc, int64_t n, int k, orc_chain2_t *c, int64_t *f_out)
+{
+    int64_t *f = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *pred = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!f || !pred) { free(f); free(pred); return -1; }
+    const int64_t S = CH_SCALE;
+    int64_t best = -1;
+    for (int64_t j = 0; j < n; ++j) {
+        f[j] = (int64_t)k * S;
+        pred[j] = -1;
+        for (int64_t i = 0; i < j; ++i) {
+            const int64_t dx = anc[2 * j] - anc[2 * i], dy = anc[2 * j + 1] - anc[2 * i + 1];
+            if (dx < 0 || dy <= 0) continue;
+            const int64_t pen = orc_gap_penalty(3 * dy - dx);
+            if (pen < 0) continue;
+            const int64_t cand = f[i] + (dy < k ? dy : k) * S - pen;
+            if (cand > f[j]) { f[j] = cand; pred[j] = i; }
+        }
+        if (f_out) f_out[j] = f[j];
+        if (best < 0 || f[j] > f[best]) best = j;
+    }
+    memset(c, 0, sizeof(*c));
+    if (best >= 0 && pred[best] >= 0) {
+        int64_t cnt = 0, cur = best, first = best;
+        while (cur >= 0) { first = cur; ++cnt; cur = pred[cur]; }
+        c->n_anchors = (int32_t)cnt;
+        c->score = f[best];
+        c->x_first = anc[2 * first];
+        c->x_last = anc[2 * best];
+        c->y_first = anc[2 * first + 1];
+        c->y_last = anc[2 * best + 1];
+    }
+    free(f);
+    free(pred);
+    return 0;
+}

@@ -228,3 +228,128 @@ def test_protein_anchors_and_chains_find_a_planted_gene(orc):
     assert c["strand"] == 0
     assert len(left) // 256 - 1 <= c["x_first"] <= c["x_last"] <= (len(left) + len(gene)) // 256 + 1
     assert c["n_anchors"] >= 20
+
+
+# ------------------------------------------------------- second chaining round
+
+def _brute_refine_anchors(prot, nt, strand, k=5):
+    """Every (x, y) whose k codons on the aligned strand translate to a
+    k-mer with the protein's reduced-alphabet codes at y..y+k-1."""
+    g = _groups()
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A"}
+    seq = nt if strand > 0 else "".join(comp[c] for c in reversed(nt))
+    code = lambda c: g.get(c, g["X"])
+    pk = [tuple(code(c) for c in prot[y:y + k]) for y in range(len(prot) - k + 1)]
+    out = []
+    for x in range(len(seq) - 3 * k + 1):
+        gk = tuple(code(c) for c in _translate(seq[x:x + 3 * k]))
+        out += [(x, y) for y in range(len(pk)) if pk[y] == gk]
+    return sorted(out)
+
+
+def test_refine_anchors_against_brute_force(orc):
+    """All 5-mers of both sequences, no sampling or binning, all three frames
+    of the aligned strand (stop codons included), both strands."""
+    rng = np.random.default_rng(21)
+    for trial in range(6):
+        prot = synth.random_protein(rng, int(rng.integers(12, 60)))
+        cds = synth.reverse_translate(rng, prot)
+        region = synth.random_dna(rng, int(rng.integers(0, 90)), 0.4) + cds + synth.random_dna(rng, 40, 0.4)
+        strand = 1 if trial % 2 == 0 else -1
+        if strand < 0:
+            region = synth.revcomp(region)
+        got = [tuple(r) for r in orc.refine_anchors(prot, region, strand)]
+        assert got == _brute_refine_anchors(prot, region, strand)
+        assert len(got) >= len(prot) - 4          # the planted diagonal is there
+
+
+def test_refine_gap_hand_values(orc):
+    """g' = 3 dy - dx with Eq. 3: on the diagonal (dx = 3 dy) no penalty; one
+    base more (dx = 3 dy + 1, g' = -1) costs min(1/3, 0.75 log2 2) = 1/3;
+    one base less (g' = +1) costs 1/3 + 0.75."""
+    S = orc.CHAIN_SCALE
+    c, f = orc.refine_chain([(0, 0), (3, 1)])
+    assert list(f) == [5 * S, 6 * S] and c["n_anchors"] == 2 and c["score"] == 6 * S
+    _, f = orc.refine_chain([(0, 0), (4, 1)])
+    assert f[1] == 6 * S - S // 3
+    _, f = orc.refine_chain([(0, 0), (2, 1)])      # 6 - 1/3 - 0.75 < k: a new chain
+    assert f[1] == 5 * S
+    _, f = orc.refine_chain([(0, 0), (14, 5)])
+    assert f[1] == 10 * S - (S // 3 + 3 * S // 4)
+    # a gap of 60 bases inserted in the genome (dx = 3 dy + 60): min(20, 0.75 log2 61)
+    _, f = orc.refine_chain([(0, 0), (75, 5)])
+    assert f[1] == 10 * S - math.floor(0.75 * S * math.log2(61))
+    # y must increase, x may repeat: (0, 5) after (0, 3) has g' = 6 (2 + 0.75
+    # log2 7 > 2: a new chain); (9, 5) follows (0, 3) with g' = -3 (cost 1)
+    _, f = orc.refine_chain([(0, 3), (0, 5), (9, 5)])
+    assert list(f) == [5 * S, 5 * S, 6 * S]
+    c, _ = orc.refine_chain([(7, 2)])
+    assert c["n_anchors"] == 0 and c["score"] == 0
+
+
+def test_refine_chain_against_enumeration(orc):
+    """f of every anchor is the best k + sum(alpha - gamma(g')) over every
+    chain ending there (x non-decreasing, y increasing), enumerated."""
+    rng = random.Random(13)
+    S, k = orc.CHAIN_SCALE, orc.REFINE_K
+    for _ in range(60):
+        n = rng.randint(1, 8)
+        anc = sorted((rng.randint(0, 60), rng.randint(0, 25)) for _ in range(n))
+        c, f = orc.refine_chain(anc)
+        best = []
+        for j, b in enumerate(anc):
+            v = k * S
+            for r in range(1, j + 1):
+                for sub in itertools.combinations(range(j), r):
+                    seq = [anc[t] for t in sub] + [b]
+                    tot, ok = k * S, True
+                    for a1, a2 in zip(seq, seq[1:]):
+                        dx, dy = a2[0] - a1[0], a2[1] - a1[1]
+                        if dx < 0 or dy <= 0:
+                            ok = False
+                            break
+                        p = orc.gap_penalty(3 * dy - dx)
+                        if p < 0:
+                            ok = False
+                            break
+                        tot += min(dy, k) * S - p
+                    if ok:
+                        v = max(v, tot)
+            best.append(v)
+        assert list(f) == best, (anc, list(f), best)
+        top = max(best) if best else None
+        if c["n_anchors"]:
+            assert c["score"] == top and c["n_anchors"] >= 2
+        else:
+            assert top is None or top == k * S
+
+
+def test_refine_finds_the_planted_gene_at_base_resolution(orc):
+    """A protein and its coding sequence (inside flanks, either strand): the
+    best chain scores the protein's length (k for the first 5-mer, one per
+    further residue on the diagonal) and spans it; with a 1-nt insertion in
+    the middle the chain crosses the frameshift at the cost of Eq. 3."""
+    rng = np.random.default_rng(5)
+    S = orc.CHAIN_SCALE
+    for strand in (1, -1):
+        prot = synth.random_protein(rng, 150)
+        cds = synth.reverse_translate(rng, prot)
+        flank = synth.random_dna(rng, 300, 0.4)
+        region = flank + cds + synth.random_dna(rng, 300, 0.4)
+        if strand < 0:
+            region = synth.revcomp(region)
+        c = orc.refine(prot, region, strand)
+        assert c["score"] == len(prot) * S
+        assert c["y_first"] == 0 and c["y_last"] == len(prot) - 5
+        assert c["x_last"] - c["x_first"] == 3 * (c["y_last"] - c["y_first"])
+        assert c["x_first"] == 300
+    prot = synth.random_protein(rng, 120)
+    cds = synth.reverse_translate(rng, prot)
+    shifted = cds[:180] + "A" + cds[180:]             # one extra base after residue 60
+    c = orc.refine(prot, synth.random_dna(rng, 200, 0.4) + shifted + synth.random_dna(rng, 200, 0.4), 1)
+    # the best chain crosses the shift: one link with dx = 3 dy + 1 (g' = -1,
+    # penalty 1/3), every other link on a diagonal; residues 56..60 are lost
+    # to the 5-mers that straddle the extra base at most
+    assert c["y_first"] == 0 and c["y_last"] == len(prot) - 5
+    assert c["x_last"] - c["x_first"] == 3 * (c["y_last"] - c["y_first"]) + 1
+    assert len(prot) * S - 5 * S - S // 3 <= c["score"] <= len(prot) * S - S // 3
