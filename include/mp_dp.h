@@ -337,6 +337,35 @@ int mp_index_download(mp_dp_ctx *ctx, const mp_index *idx, uint64_t *offsets, ui
 
 void mp_index_free(mp_index *idx);
 
+/* Second round of chaining ("Chaining", last paragraph): around a chain of
+ * the first round, every 5-mer of the protein is matched against every
+ * 5-mer of the local genome region, without sampling or binning, and the
+ * anchors are chained with the gap g' = 3 dy - dx (dx in bases) and the
+ * penalty of Eq. 3, giving a chain at base resolution.
+ *
+ * Each pair is a (protein, region, strand) as for mp_dp_align_batch (flags
+ * ignored): the region's aligned strand (its reverse complement for strand
+ * -1) is read in all three frames, a 5-mer of the reduced alphabet starting
+ * at every base with five full codons (stop codons and codons with a base
+ * outside ACGT included, as codes 14 and 15); anchors (x, y) are the base x
+ * of a 5-mer's first codon and the residue y of the equal protein 5-mer's
+ * first residue.  Chaining as in mp_index_chain (x non-decreasing, y
+ * increasing, alpha = min(dy, 5), G = 200,000, beta = 0.75, scores in units
+ * of 2^-16, the first best predecessor, f >= 5).  out[k] receives pair k's
+ * best chain: the anchor with the largest score (the earliest in (x, y)
+ * order on ties) and its predecessors; n_anchors 0 if that is a single
+ * anchor.  MP_EINVAL: a null argument, a protein longer than 8,192
+ * residues or a strand other than +1 / -1.  Device memory: the sequences,
+ * plus 20 bytes per anchor in groups of at most about 200 M anchors. */
+typedef struct {
+    int32_t n_anchors;
+    int32_t reserved;
+    int64_t score;              /* f of the last anchor, units of 2^-16 */
+    int64_t x_first, x_last;    /* 0-based base on the aligned strand */
+    int64_t y_first, y_last;    /* 0-based residue */
+} mp_chain2;
+int mp_chain_refine(mp_dp_ctx *ctx, const mp_pair *pairs, size_t n, mp_chain2 *out);
+
 /* Static string for a return code. */
 const char *mp_dp_strerror(int code);
 

@@ -31,7 +31,8 @@ EXPORTED = ["mp_dp_default_params", "mp_dp_init", "mp_dp_align_batch", "mp_dp_ba
             "mp_dp_set_timing", "mp_dp_get_stats", "mp_dp_num_sms", "mp_dp_get_serve_stats",
             "mp_dp_score_pair_noalloc", "mp_dp_autotune", "mp_dp_set_tuning", "mp_dp_get_tuning",
             "mp_dp_tuning_save", "mp_dp_tuning_load", "mp_dp_exon_rescore", "mp_dp_debug_h",
-            "mp_index_build", "mp_index_chain", "mp_index_download", "mp_index_free", "mp_dp_op_rates"]
+            "mp_index_build", "mp_index_chain", "mp_index_download", "mp_index_free", "mp_dp_op_rates",
+            "mp_chain_refine"]
 
 
 class mp_dp_params(ctypes.Structure):
@@ -154,6 +155,7 @@ def lib():
             "mp_dp_debug_h": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
             "mp_index_build": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_uint64, P(vp)]),
             "mp_index_chain": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_int32, vp, vp]),
+            "mp_chain_refine": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
             "mp_index_download": (ctypes.c_int, [vp, vp, vp, vp, P(ctypes.c_uint64)]),
             "mp_index_free": (None, [vp]),
         }
@@ -517,6 +519,18 @@ class mp_chain(ctypes.Structure):
 
 CHAIN_DTYPE = np.dtype([("strand", "<i4"), ("n_anchors", "<i4"), ("score", "<i8"), ("x_first", "<i8"),
                         ("x_last", "<i8"), ("y_first", "<i8"), ("y_last", "<i8")])
+CHAIN2_DTYPE = np.dtype([("n_anchors", "<i4"), ("reserved", "<i4"), ("score", "<i8"), ("x_first", "<i8"),
+                         ("x_last", "<i8"), ("y_first", "<i8"), ("y_last", "<i8")])
+
+
+def mp_chain_refine(ctx, pairs):
+    """Second chaining round of each (protein, region, strand) pair (a list
+    of pairs, or a PairBatch): structured array of mp_chain2 records."""
+    pa = pairs if isinstance(pairs, _PairArray) else _PairArray(pairs)
+    out = np.zeros(max(pa.n, 1), dtype=CHAIN2_DTYPE)
+    _check(lib().mp_chain_refine(ctx, ctypes.cast(pa.arr, ctypes.c_void_p), pa.n, out.ctypes.data),
+           "mp_chain_refine")
+    return out[:pa.n]
 
 
 def mp_index_build(ctx, genome):

