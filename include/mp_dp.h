@@ -355,7 +355,8 @@ void mp_index_free(mp_index *idx);
  * best chain: the anchor with the largest score (the earliest in (x, y)
  * order on ties) and its predecessors; n_anchors 0 if that is a single
  * anchor.  MP_EINVAL: a null argument, a protein longer than 8,192
- * residues or a strand other than +1 / -1.  Device memory: the sequences,
+ * residues, a region longer than about 134 Mb (with such a protein) or a
+ * strand other than +1 / -1.  Device memory: the sequences,
  * plus 20 bytes per anchor in groups of at most about 200 M anchors. */
 typedef struct {
     int32_t n_anchors;

@@ -1122,8 +1122,11 @@ extern "C" int mp_chain_refine(mp_dp_ctx *ctx, const mp_pair *pairs, size_t n, m
     uint64_t tot = 0;
     for (size_t k = 0; k < n; ++k) {
         const mp_pair &q = pairs[k];
+        // (a thread's anchor count, at most its bases times the protein's
+        // k-mers, is 32-bit)
         if ((q.prot_len && !q.prot) || (q.nt_len && !q.nt) || q.prot_len > static_cast<uint32_t>(kRefineMaxProt) ||
-            (q.strand != 1 && q.strand != -1))
+            (q.strand != 1 && q.strand != -1) ||
+            (static_cast<uint64_t>(q.nt_len) / kRefineThreads + 1) * q.prot_len >= (1ull << 32))
             return MP_EINVAL;
         poff[k] = tot;
         tot += q.prot_len;
