@@ -645,6 +645,7 @@ constexpr int kK2 = 5;                      // k-mer length of the second round
 constexpr int kRefineMaxProt = 8192;        // protein k-mer table in shared memory (64 KB)
 constexpr int kRefineThreads = 256;
 constexpr size_t kRefineSmem = kRefineMaxProt * sizeof(uint64_t);
+constexpr int64_t kRefineBig = 512;          // pairs with more anchors are chained by a whole block
 
 struct RefineArgs {
     const char *seq;                        // every pair's protein and region (ASCII)
@@ -780,6 +781,7 @@ __global__ void refine_chain_kernel(RefineArgs a)
     for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n; p += (gridDim.x * blockDim.x) >> 5) {
         const uint64_t b0 = a.anc_off[p];
         const int64_t n = static_cast<int64_t>(a.anc_off[p + 1] - b0);
+        if (n > kRefineBig) continue;               // refine_chain_block_kernel's
         const uint64_t *A = a.anc + b0;
         int64_t *F = a.f + b0;
         int32_t *Pr = a.pred + b0;
@@ -848,6 +850,100 @@ __global__ void refine_chain_kernel(RefineArgs a)
             a.out[p] = c;
         }
         __syncwarp();
+    }
+}
+
+// The pair's best chain from f and the predecessors (one thread).
+__device__ __forceinline__ mp_chain2 best_chain(const uint64_t *A, const int64_t *F, const int32_t *Pr, int64_t bi)
+{
+    mp_chain2 c{};
+    if (bi >= 0 && Pr[bi] >= 0) {
+        int64_t cnt = 0, cur = bi, first = bi;
+        while (cur >= 0) {
+            first = cur;
+            ++cnt;
+            cur = Pr[cur];
+        }
+        c.n_anchors = static_cast<int32_t>(cnt);
+        c.score = F[bi];
+        c.x_first = static_cast<int64_t>(A[first] >> 20);
+        c.x_last = static_cast<int64_t>(A[bi] >> 20);
+        c.y_first = static_cast<int64_t>(A[first] & 0xfffffu);
+        c.y_last = static_cast<int64_t>(A[bi] & 0xfffffu);
+    }
+    return c;
+}
+
+// The same recurrence for the pairs with more than kRefineBig anchors, one
+// block per pair: each anchor's predecessors split over the block's
+// threads, the best (largest, then first) found by a block reduction.
+__global__ void __launch_bounds__(kRefineThreads) refine_chain_block_kernel(RefineArgs a)
+{
+    __shared__ int64_t rv[kRefineThreads / 32];
+    __shared__ int64_t ri[kRefineThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t S = kScale;
+    for (uint32_t p = blockIdx.x; p < a.n; p += gridDim.x) {
+        const uint64_t b0 = a.anc_off[p];
+        const int64_t n = static_cast<int64_t>(a.anc_off[p + 1] - b0);
+        if (n <= kRefineBig) continue;              // uniform across the block
+        const uint64_t *A = a.anc + b0;
+        int64_t *F = a.f + b0;
+        int32_t *Pr = a.pred + b0;
+        const int64_t wx = kG + 3 * static_cast<int64_t>(a.prot_len[p]);
+        int64_t lo = 0, bf = INT64_MIN, bi = -1;
+        for (int64_t j = 0; j < n; ++j) {
+            const int64_t xj = static_cast<int64_t>(A[j] >> 20), yj = static_cast<int64_t>(A[j] & 0xfffffu);
+            while (lo < j && static_cast<int64_t>(A[lo] >> 20) < xj - wx) ++lo;
+            int64_t cv = INT64_MIN, ci = INT64_MAX;
+            for (int64_t i = lo + threadIdx.x; i < j; i += blockDim.x) {
+                const uint64_t vi = A[i];
+                const int64_t dx = xj - static_cast<int64_t>(vi >> 20);
+                const int64_t dy = yj - static_cast<int64_t>(vi & 0xfffffu);
+                if (dx >= 0 && dy > 0) {
+                    const int64_t pen = penalty_eq3(3 * dy - dx, a.log_tab);
+                    if (pen >= 0) {
+                        const int64_t cand = F[i] + (dy < kK2 ? dy : kK2) * S - pen;
+                        if (cand > cv) {            // i ascends: the first of equals stays
+                            cv = cand;
+                            ci = i;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int64_t oc = __shfl_xor_sync(0xffffffffu, cv, o);
+                const int64_t oi = __shfl_xor_sync(0xffffffffu, ci, o);
+                if (oc > cv || (oc == cv && oi < ci)) {
+                    cv = oc;
+                    ci = oi;
+                }
+            }
+            if (lane == 0) {
+                rv[warp] = cv;
+                ri[warp] = ci;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int64_t best = static_cast<int64_t>(kK2) * S, arg = -1;
+                for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+                    if (rv[w] > best || (rv[w] == best && arg >= 0 && ri[w] < arg)) {
+                        best = rv[w];
+                        arg = ri[w];
+                    }
+                }
+                F[j] = best;
+                Pr[j] = static_cast<int32_t>(arg);
+                if (best > bf) {
+                    bf = best;
+                    bi = j;
+                }
+            }
+            __syncthreads();                        // F[j] is read by the next anchors
+        }
+        if (threadIdx.x == 0) a.out[p] = best_chain(A, F, Pr, bi);
+        __syncthreads();
     }
 }
 
@@ -1222,6 +1318,7 @@ extern "C" int mp_chain_refine(mp_dp_ctx *ctx, const mp_pair *pairs, size_t n, m
         refine_anchor_kernel<true><<<gb, kRefineThreads, kRefineSmem, st>>>(b, d_tcnt.p + p0 * kRefineThreads,
                                                                              nullptr);
         refine_chain_kernel<<<grid_for(np * 32ull, 128), 128, 0, st>>>(b);
+        refine_chain_block_kernel<<<gb, kRefineThreads, 0, st>>>(b);
         SCK(cudaGetLastError());
         SCK(cudaStreamSynchronize(st));
         p0 = p1;
