@@ -20,10 +20,13 @@
 // Arithmetic
 // ----------
 // The int16 path keeps each state as two biased 16-bit lanes in one 32-bit
-// register (value v stored as v + 32768).  Maxima use max.u16x2; additions
-// of packed penalties are plain 32-bit adds, exact because no half crosses
-// 0 or 65536.  A pair whose best score reaches 32000 is re-run in the int32
-// instantiation of the same kernel.
+// register (value v stored as v + 32768).  Every penalised term of Eq. 7 is
+// one fused per-halfword add-max (the penalty held negated per half, the
+// addition modulo 2^16, exact because no biased operand leaves 0..65535);
+// the remaining maxima use three- and two-way max.u16x2; the few plain
+// 32-bit adds (the gap extension, the two profile halves) never carry
+// across halves.  A pair whose best score reaches 32000 is re-run in the
+// int32 instantiation of the same kernel.
 //
 // Traceback stream
 // ----------------
