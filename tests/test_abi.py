@@ -99,4 +99,7 @@ def test_null_arguments(mp):
     assert L.mp_dp_tuning_save(None, b"x") == mp.MP_EINVAL
     assert L.mp_dp_tuning_load(None, b"x") == mp.MP_EINVAL
     assert L.mp_dp_debug_h(None, None, 0, None) == mp.MP_EINVAL
+    assert L.mp_chain_refine(None, None, 0, None) == mp.MP_EINVAL
+    assert L.mp_dp_op_rates(0, None) == mp.MP_EINVAL
+    assert L.mp_dp_op_rates(-1, ctypes.byref(mp.mp_op_rates())) == mp.MP_EINVAL
     L.mp_dp_destroy(None)
