@@ -113,17 +113,22 @@ REFINE_FIELDS = ("n_anchors", "score", "x_first", "x_last", "y_first", "y_last")
 
 
 def _refine_compare(mp, orc, pairs):
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
     ctx = mp.mp_dp_init(None, 0)
     try:
         got = mp.mp_chain_refine(ctx, pairs)
     finally:
         mp.mp_dp_destroy(ctx)
+    # the oracle on every host core (its C calls release the interpreter lock)
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        want = list(ex.map(lambda p: orc.refine(p.prot, p.nt, p.strand), pairs))
     bad = []
-    for k, p in enumerate(pairs):
-        want = orc.refine(p.prot, p.nt, p.strand)
+    for k, w in enumerate(want):
         g = {f: int(got[k][f]) for f in REFINE_FIELDS}
-        if g != want:
-            bad.append((k, g, want))
+        if g != w:
+            bad.append((k, g, w))
     assert not bad, (len(bad), bad[:3])
     return got
 
@@ -159,9 +164,8 @@ def test_refine_matches_oracle(mp, orc):
 
 def test_refine_genome_regions_match_oracle(mp, orc, genome_workload):
     """The candidate regions of the first round's chains (the genome-scale
-    workload shrunk 50 times), refined: every region equals the oracle; the
-    refined chains of the planted genes' sources run along their coding
-    sequence at base resolution."""
+    workload shrunk 50 times: about 12,000 regions), refined: every region
+    equals the oracle."""
     w = genome_workload
     ctx = mp.mp_dp_init(None, 0)
     try:
@@ -173,7 +177,7 @@ def test_refine_genome_regions_match_oracle(mp, orc, genome_workload):
     finally:
         mp.mp_dp_destroy(ctx)
     wr = synth.regions_from_chains(w, chains, nch)
-    sel = np.random.default_rng(3).choice(wr.n_regions, size=min(600, wr.n_regions), replace=False)
-    pairs = [wr.pair(int(r)) for r in sorted(sel)]
+    pairs = [wr.pair(r) for r in range(wr.n_regions)]
     got = _refine_compare(mp, orc, pairs)
+    assert len(pairs) > 10_000
     assert (got["n_anchors"] >= 2).mean() > 0.5
