@@ -9,6 +9,10 @@
 * The candidate regions of those chains, aligned by the batch DP, match the
   oracle (the DP parity of the genome-scale workload is covered in
   test_gpu_genome).
+* The second chaining round ("Chaining", last paragraph) gives every pair
+  the oracle's best chain: synthetic pairs (planted genes with introns and
+  frameshifts on either strand, unrelated regions, non-ACGT letters, pairs
+  shorter than a 5-mer) and every candidate region of the shrunk workload.
 """
 import numpy as np
 import pytest
